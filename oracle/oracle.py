@@ -1,0 +1,164 @@
+"""ctypes front end of the C oracle (``yee_oracle.c``).
+
+TEST INFRASTRUCTURE ONLY (see the package docstring). Each call follows the
+paper's Sec. 2.1 scheme; the C file documents every step and its citation.
+
+Arrays are numpy arrays of shape (nz+1, ny+1, nx+1) (x fastest) per component,
+in the component order ex, ey, ez, hx, hy, hz.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+C0 = 299792458.0
+EPS0 = 8.8541878128e-12
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "yee_oracle.c")
+_BODY = os.path.join(_HERE, "yee_oracle_body.h")
+_LIB = os.path.join(_HERE, "_build", "libyee_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (-O2 -fopenmp -ffp-contract=off)."""
+    os.makedirs(os.path.dirname(_LIB), exist_ok=True)
+    newest = max(os.path.getmtime(_SRC), os.path.getmtime(_BODY))
+    if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= newest:
+        return _LIB
+    tmp = _LIB + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp",
+           "-ffp-contract=off", "-fno-fast-math", "-o", tmp, _SRC, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB)
+    return _LIB
+
+
+def load() -> ctypes.CDLL:
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            lib = ctypes.CDLL(_LIB)
+            P = ctypes.c_void_p
+            I = ctypes.c_int
+            L = ctypes.c_long
+            D = ctypes.c_double
+            F = ctypes.c_float
+            for suf, R in (("f64", D), ("f32", F)):
+                getattr(lib, f"oracle_coefs_{suf}").argtypes = [I, I, I, D, D, P, P] + [P] * 6 + [P] * 3
+                getattr(lib, f"oracle_coefs_{suf}").restype = None
+                getattr(lib, f"oracle_step_{suf}").argtypes = (
+                    [I, I, I, R] + [P] * 6 + [P] * 6 + [I, P, P, L, I, P, P, L, I])
+                getattr(lib, f"oracle_step_{suf}").restype = None
+                getattr(lib, f"oracle_energy_{suf}").argtypes = [I, I, I, R, D] + [P] * 6 + [P] * 3
+                getattr(lib, f"oracle_energy_{suf}").restype = D
+            lib.oracle_waveform.argtypes = [I, D, D, D, D, D, L, L, P]
+            lib.oracle_waveform.restype = None
+            _lib = lib
+    return _lib
+
+
+def _ptr(a: np.ndarray) -> int:
+    assert a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data
+
+
+def cfl_dt(dx: float, frac: float = 0.99) -> float:
+    """dt = frac * dx / (c sqrt(3)): a fraction of the 3-D Courant limit."""
+    return frac * dx / (C0 * math.sqrt(3.0))
+
+
+def waveform(kind: int, amp: float, f0: float, bw: float, t0: float, dt: float,
+             n0: int, n: int) -> np.ndarray:
+    """amp * w((n0 + m + 1/2) dt) for m in [0, n), in float64."""
+    out = np.empty(n, np.float64)
+    load().oracle_waveform(int(kind), amp, f0, bw, t0, dt, int(n0), int(n), _ptr(out))
+    return out
+
+
+class OracleGrid:
+    """State of one cavity advanced by the oracle.
+
+    precision: "f64" or "f32". Materials are per-cell float32 arrays of shape
+    (nz, ny, nx); the oracle turns them into per-edge coefficients (Ca, Cb).
+    """
+
+    COMPS = ("ex", "ey", "ez", "hx", "hy", "hz")
+
+    def __init__(self, nx: int, ny: int, nz: int, dx: float, dt: float,
+                 precision: str = "f64"):
+        assert precision in ("f64", "f32")
+        self.nx, self.ny, self.nz = nx, ny, nz
+        self.dx, self.dt = float(dx), float(dt)
+        self.precision = precision
+        self.dtype = np.float64 if precision == "f64" else np.float32
+        self.S = self.dtype(C0 * dt / dx)
+        shp = (nz + 1, ny + 1, nx + 1)
+        self.f = [np.zeros(shp, self.dtype) for _ in range(6)]
+        self.n = 0
+        self.sources = []  # (comp, i, j, k, amp, f0, bw, t0, kind)
+        self.probes = []   # (comp, i, j, k)
+        self.probe_trace = []
+        self.set_materials(np.ones((nz, ny, nx), np.float32), np.zeros((nz, ny, nx), np.float32))
+
+    # -- inputs ---------------------------------------------------------------
+    def set_materials(self, eps_cell: np.ndarray, sig_cell: np.ndarray) -> None:
+        nx, ny, nz = self.nx, self.ny, self.nz
+        eps_cell = np.ascontiguousarray(eps_cell, np.float32).reshape(nz, ny, nx)
+        sig_cell = np.ascontiguousarray(sig_cell, np.float32).reshape(nz, ny, nx)
+        shp = (nz + 1, ny + 1, nx + 1)
+        self.coef = [np.zeros(shp, self.dtype) for _ in range(6)]  # cax cbx cay cby caz cbz
+        self.eps_edge = [np.zeros(shp, np.float64) for _ in range(3)]
+        fn = getattr(load(), f"oracle_coefs_{self.precision}")
+        fn(nx, ny, nz, self.dx, self.dt, _ptr(eps_cell), _ptr(sig_cell),
+           *[_ptr(c) for c in self.coef], *[_ptr(e) for e in self.eps_edge])
+
+    def set_field(self, comp: int, arr: np.ndarray) -> None:
+        self.f[comp][...] = arr
+
+    def add_source(self, comp: int, i: int, j: int, k: int, amp: float, f0: float,
+                   bw: float, t0: float, kind: int) -> None:
+        self.sources.append((comp, i, j, k, amp, f0, bw, t0, kind))
+
+    def add_probe(self, comp: int, i: int, j: int, k: int) -> int:
+        self.probes.append((comp, i, j, k))
+        self.probe_trace.append([])
+        return len(self.probes) - 1
+
+    # -- stepping -------------------------------------------------------------
+    def step(self, nsteps: int) -> None:
+        if nsteps <= 0:
+            return
+        nsrc = len(self.sources)
+        src = np.array([s[:4] for s in self.sources] or [[0, 0, 0, 0]], np.int32).reshape(-1)
+        sval = np.zeros((max(nsrc, 1), nsteps), self.dtype)
+        for q, s in enumerate(self.sources):
+            w = waveform(s[8], s[4], s[5], s[6], s[7], self.dt, self.n, nsteps)
+            sval[q] = w.astype(self.dtype)  # one rounding from the double value
+        nprb = len(self.probes)
+        prb = np.array(self.probes or [[0, 0, 0, 0]], np.int32).reshape(-1)
+        pout = np.zeros((max(nprb, 1), nsteps), self.dtype)
+        fn = getattr(load(), f"oracle_step_{self.precision}")
+        fn(self.nx, self.ny, self.nz, self.S, *[_ptr(a) for a in self.f],
+           *[_ptr(c) for c in self.coef], nsrc, _ptr(src), _ptr(sval), nsteps,
+           nprb, _ptr(prb), _ptr(pout), nsteps, nsteps)
+        for q in range(nprb):
+            self.probe_trace[q].extend(pout[q].astype(np.float64).tolist())
+        self.n += nsteps
+
+    def energy(self) -> float:
+        fn = getattr(load(), f"oracle_energy_{self.precision}")
+        return fn(self.nx, self.ny, self.nz, self.S, self.dx, *[_ptr(a) for a in self.f],
+                  *[_ptr(e) for e in self.eps_edge])
+
+    def probe(self, q: int) -> np.ndarray:
+        return np.asarray(self.probe_trace[q], np.float64)

@@ -1,0 +1,304 @@
+/*
+ * Body of the plain CPU oracle, instantiated twice by yee_oracle.c: once with
+ * REAL = double (suffix _f64) and once with REAL = float (suffix _f32).
+ *
+ * TEST INFRASTRUCTURE ONLY. Nothing in the library links, includes or calls
+ * this file; it shares no code with the CUDA path.
+ *
+ * Storage (one array per component, no padding, x fastest):
+ *   value(i,j,k) = a[(k*(ny+1) + j)*(nx+1) + i],  0<=i<=nx, 0<=j<=ny, 0<=k<=nz.
+ * Staggering (cell (i,j,k) occupies [i,i+1]x[j,j+1]x[k,k+1]):
+ *   ex(i,j,k) at (i+1/2, j, k)      ey at (i, j+1/2, k)      ez at (i, j, k+1/2)
+ *   hx(i,j,k) at (i, j+1/2, k+1/2)  hy at (i+1/2, j, k+1/2)  hz at (i+1/2, j+1/2, k)
+ * Variables are the paper's antisymmetric pair scaled to V/m: e = E and
+ * h = eta0*H, so that the leapfrog of Sec. 2.1 (Eqs. ma2, mf2) reads
+ *   h += S * (discrete -curl e),   e = Ca*e + Cb*(discrete curl h),   S = c dt / dx.
+ */
+
+#ifndef REAL
+#error "define REAL before including yee_oracle_body.h"
+#endif
+
+#define CAT_(a, b) a##_##b
+#define CAT(a, b) CAT_(a, b)
+#define FN(name) CAT(name, SUF)
+
+/*
+ * Per-edge update coefficients from per-cell material values.
+ * eps_r(edge), sigma(edge) = arithmetic mean of the four cells sharing the
+ * edge (summed in the fixed order (-,-), (+,-), (-,+), (+,+) of the two
+ * transverse offsets, in double). Loss: semi-implicit average of sigma*E
+ * (Taflove's standard lossy Yee update, cited by the paper in Sec. 2.1):
+ *   beta = sigma*dt / (2*eps0*eps_r),  Ca = (1-beta)/(1+beta),
+ *   Cb = (S/eps_r)/(1+beta),           S  = c*dt/dx  (double).
+ * Only interior (non-PEC) edges get coefficients; wall edges keep Ca = Cb = 0.
+ * epsx/epsy/epsz (double, may be NULL) receive eps_r(edge), 0 on walls.
+ */
+void FN(oracle_coefs)(int nx, int ny, int nz, double dx, double dt,
+                      const float *eps_cell, const float *sig_cell,
+                      REAL *cax, REAL *cbx, REAL *cay, REAL *cby, REAL *caz, REAL *cbz,
+                      double *epsx, double *epsy, double *epsz)
+{
+    const long sx = 1, sy = nx + 1, sz = (long)(nx + 1) * (ny + 1);
+    const long ntot = sz * (nz + 1);
+    const double S = C0 * dt / dx;
+    for (long p = 0; p < ntot; ++p) {
+        cax[p] = cbx[p] = cay[p] = cby[p] = caz[p] = cbz[p] = 0;
+        if (epsx) epsx[p] = 0.0;
+        if (epsy) epsy[p] = 0.0;
+        if (epsz) epsz[p] = 0.0;
+    }
+    (void)sx;
+#define CELL(arr, i, j, k) ((double)(arr)[((long)(k) * ny + (j)) * nx + (i)])
+#define COEF(eps4, sig4, ca, cb)                                                  \
+    do {                                                                          \
+        const double e_ = (eps4) * 0.25, s_ = (sig4) * 0.25;                      \
+        const double beta_ = (s_ * dt) / (2.0 * EPS0 * e_);                       \
+        ca = (REAL)((1.0 - beta_) / (1.0 + beta_));                               \
+        cb = (REAL)((S / e_) / (1.0 + beta_));                                    \
+        epsv = e_;                                                                \
+    } while (0)
+    /* ex(i,j,k): cells (i, j-1..j, k-1..k) */
+    for (int k = 1; k < nz; ++k)
+        for (int j = 1; j < ny; ++j)
+            for (int i = 0; i < nx; ++i) {
+                const long p = k * sz + j * sy + i;
+                const double e4 = ((CELL(eps_cell, i, j - 1, k - 1) + CELL(eps_cell, i, j, k - 1)) +
+                                   CELL(eps_cell, i, j - 1, k)) + CELL(eps_cell, i, j, k);
+                const double s4 = ((CELL(sig_cell, i, j - 1, k - 1) + CELL(sig_cell, i, j, k - 1)) +
+                                   CELL(sig_cell, i, j - 1, k)) + CELL(sig_cell, i, j, k);
+                double epsv;
+                COEF(e4, s4, cax[p], cbx[p]);
+                if (epsx) epsx[p] = epsv;
+            }
+    /* ey(i,j,k): cells (i-1..i, j, k-1..k) */
+    for (int k = 1; k < nz; ++k)
+        for (int j = 0; j < ny; ++j)
+            for (int i = 1; i < nx; ++i) {
+                const long p = k * sz + j * sy + i;
+                const double e4 = ((CELL(eps_cell, i - 1, j, k - 1) + CELL(eps_cell, i, j, k - 1)) +
+                                   CELL(eps_cell, i - 1, j, k)) + CELL(eps_cell, i, j, k);
+                const double s4 = ((CELL(sig_cell, i - 1, j, k - 1) + CELL(sig_cell, i, j, k - 1)) +
+                                   CELL(sig_cell, i - 1, j, k)) + CELL(sig_cell, i, j, k);
+                double epsv;
+                COEF(e4, s4, cay[p], cby[p]);
+                if (epsy) epsy[p] = epsv;
+            }
+    /* ez(i,j,k): cells (i-1..i, j-1..j, k) */
+    for (int k = 0; k < nz; ++k)
+        for (int j = 1; j < ny; ++j)
+            for (int i = 1; i < nx; ++i) {
+                const long p = k * sz + j * sy + i;
+                const double e4 = ((CELL(eps_cell, i - 1, j - 1, k) + CELL(eps_cell, i, j - 1, k)) +
+                                   CELL(eps_cell, i - 1, j, k)) + CELL(eps_cell, i, j, k);
+                const double s4 = ((CELL(sig_cell, i - 1, j - 1, k) + CELL(sig_cell, i, j - 1, k)) +
+                                   CELL(sig_cell, i - 1, j, k)) + CELL(sig_cell, i, j, k);
+                double epsv;
+                COEF(e4, s4, caz[p], cbz[p]);
+                if (epsz) epsz[p] = epsv;
+            }
+#undef COEF
+#undef CELL
+}
+
+/*
+ * H update (Maxwell-Faraday, Sec. 2.1 displayed Hx formula and its analogues):
+ *   hx += S*((ey(k+1)-ey(k)) - (ez(j+1)-ez(j)))     i in [0,nx], j in [0,ny), k in [0,nz)
+ *   hy += S*((ez(i+1)-ez(i)) - (ex(k+1)-ex(k)))     i in [0,nx), j in [0,ny], k in [0,nz)
+ *   hz += S*((ex(j+1)-ex(j)) - (ey(i+1)-ey(i)))     i in [0,nx), j in [0,ny), k in [0,nz]
+ * Faces normal to a wall see only zero (PEC) tangential E and keep their value.
+ */
+static void FN(update_h)(int nx, int ny, int nz, REAL S,
+                         const REAL *ex, const REAL *ey, const REAL *ez,
+                         REAL *hx, REAL *hy, REAL *hz)
+{
+    const long sy = nx + 1, sz = (long)(nx + 1) * (ny + 1);
+#pragma omp parallel for schedule(static)
+    for (int k = 0; k < nz; ++k)
+        for (int j = 0; j < ny; ++j)
+            for (int i = 0; i <= nx; ++i) {
+                const long p = k * sz + j * sy + i;
+                hx[p] = hx[p] + S * ((ey[p + sz] - ey[p]) - (ez[p + sy] - ez[p]));
+            }
+#pragma omp parallel for schedule(static)
+    for (int k = 0; k < nz; ++k)
+        for (int j = 0; j <= ny; ++j)
+            for (int i = 0; i < nx; ++i) {
+                const long p = k * sz + j * sy + i;
+                hy[p] = hy[p] + S * ((ez[p + 1] - ez[p]) - (ex[p + sz] - ex[p]));
+            }
+#pragma omp parallel for schedule(static)
+    for (int k = 0; k <= nz; ++k)
+        for (int j = 0; j < ny; ++j)
+            for (int i = 0; i < nx; ++i) {
+                const long p = k * sz + j * sy + i;
+                hz[p] = hz[p] + S * ((ex[p + sy] - ex[p]) - (ey[p + 1] - ey[p]));
+            }
+}
+
+/* Curl-h brackets of the E update (Maxwell-Ampere), at storage offset p. */
+#define BR_X(p) ((hz[p] - hz[(p) - sy]) - (hy[p] - hy[(p) - sz]))
+#define BR_Y(p) ((hx[p] - hx[(p) - sz]) - (hz[p] - hz[(p) - 1]))
+#define BR_Z(p) ((hy[p] - hy[(p) - 1]) - (hx[p] - hx[(p) - sy]))
+
+/*
+ * E update on interior (non-PEC) edges, Sec. 2.1 leapfrog with loss:
+ *   e = Ca*e + Cb*bracket.
+ * Tangential E on the six walls is never written (PEC, Sec. 3.3).
+ * A soft source is a current on the Ampere right-hand side (Sec. 3.3): at
+ * its edge the bracket becomes (bracket + s), s = amp*w(t^{n+1/2}).
+ * Source edges are evaluated after the sweep from their saved old value; the
+ * sweep itself does not read E, so the result equals the in-loop form.
+ */
+static void FN(update_e)(int nx, int ny, int nz,
+                         REAL *ex, REAL *ey, REAL *ez,
+                         const REAL *hx, const REAL *hy, const REAL *hz,
+                         const REAL *cax, const REAL *cbx, const REAL *cay,
+                         const REAL *cby, const REAL *caz, const REAL *cbz,
+                         int nsrc, const int *src, const REAL *sval, REAL *eold)
+{
+    const long sy = nx + 1, sz = (long)(nx + 1) * (ny + 1);
+    for (int s = 0; s < nsrc; ++s) {
+        const int c = src[4 * s];
+        const long p = (long)src[4 * s + 3] * sz + (long)src[4 * s + 2] * sy + src[4 * s + 1];
+        eold[s] = (c == 0 ? ex : c == 1 ? ey : ez)[p];
+    }
+#pragma omp parallel for schedule(static)
+    for (int k = 1; k < nz; ++k)
+        for (int j = 1; j < ny; ++j)
+            for (int i = 0; i < nx; ++i) {
+                const long p = k * sz + j * sy + i;
+                ex[p] = cax[p] * ex[p] + cbx[p] * BR_X(p);
+            }
+#pragma omp parallel for schedule(static)
+    for (int k = 1; k < nz; ++k)
+        for (int j = 0; j < ny; ++j)
+            for (int i = 1; i < nx; ++i) {
+                const long p = k * sz + j * sy + i;
+                ey[p] = cay[p] * ey[p] + cby[p] * BR_Y(p);
+            }
+#pragma omp parallel for schedule(static)
+    for (int k = 0; k < nz; ++k)
+        for (int j = 1; j < ny; ++j)
+            for (int i = 1; i < nx; ++i) {
+                const long p = k * sz + j * sy + i;
+                ez[p] = caz[p] * ez[p] + cbz[p] * BR_Z(p);
+            }
+    /* Several sources on one edge add their currents in list order. */
+    for (int s = 0; s < nsrc; ++s) {
+        const int c = src[4 * s];
+        const long p = (long)src[4 * s + 3] * sz + (long)src[4 * s + 2] * sy + src[4 * s + 1];
+        int first = 1;
+        for (int q = 0; q < s; ++q)
+            if (src[4 * q] == c && src[4 * q + 1] == src[4 * s + 1] &&
+                src[4 * q + 2] == src[4 * s + 2] && src[4 * q + 3] == src[4 * s + 3])
+                first = 0;
+        if (!first) continue;
+        REAL br = (c == 0 ? BR_X(p) : c == 1 ? BR_Y(p) : BR_Z(p));
+        for (int q = s; q < nsrc; ++q)
+            if (src[4 * q] == c && src[4 * q + 1] == src[4 * s + 1] &&
+                src[4 * q + 2] == src[4 * s + 2] && src[4 * q + 3] == src[4 * s + 3])
+                br = br + sval[q];
+        const REAL *ca = c == 0 ? cax : c == 1 ? cay : caz;
+        const REAL *cb = c == 0 ? cbx : c == 1 ? cby : cbz;
+        REAL *e = c == 0 ? ex : c == 1 ? ey : ez;
+        e[p] = ca[p] * eold[s] + cb[p] * br;
+    }
+}
+
+/*
+ * Advance nsteps leapfrog steps: for each step, all H (a1), then all E with
+ * PEC and sources (a2-a4), then the probes (a5). Taflove-standard order, one
+ * separate sweep per component.
+ *   src:   nsrc x {comp(0..2), i, j, k}; edge must be interior.
+ *   sval:  nsrc x sstride values; step m (0-based within this call) uses
+ *          sval[s*sstride + m] = amp*w((n0+m+1/2)*dt) (computed by the caller).
+ *   prb:   nprb x {comp(0..5), i, j, k}; after step m, E probes record e^{n+1},
+ *          H probes record h^{n+1/2}, into pout[q*pstride + m].
+ */
+void FN(oracle_step)(int nx, int ny, int nz, REAL S,
+                     REAL *ex, REAL *ey, REAL *ez, REAL *hx, REAL *hy, REAL *hz,
+                     const REAL *cax, const REAL *cbx, const REAL *cay,
+                     const REAL *cby, const REAL *caz, const REAL *cbz,
+                     int nsrc, const int *src, const REAL *sval, long sstride,
+                     int nprb, const int *prb, REAL *pout, long pstride, int nsteps)
+{
+    const long sy = nx + 1, sz = (long)(nx + 1) * (ny + 1);
+    REAL eold[64];
+    REAL sv[64];
+    if (nsrc > 64) nsrc = 64;
+    for (int m = 0; m < nsteps; ++m) {
+        FN(update_h)(nx, ny, nz, S, ex, ey, ez, hx, hy, hz);
+        for (int s = 0; s < nsrc; ++s) sv[s] = sval[s * sstride + m];
+        FN(update_e)(nx, ny, nz, ex, ey, ez, hx, hy, hz, cax, cbx, cay, cby, caz, cbz,
+                     nsrc, src, sv, eold);
+        for (int q = 0; q < nprb; ++q) {
+            const int c = prb[4 * q];
+            const long p = (long)prb[4 * q + 3] * sz + (long)prb[4 * q + 2] * sy + prb[4 * q + 1];
+            const REAL *f = c == 0 ? ex : c == 1 ? ey : c == 2 ? ez : c == 3 ? hx : c == 4 ? hy : hz;
+            pout[q * pstride + m] = f[p];
+        }
+    }
+}
+
+/*
+ * Discrete Yee energy at time level n (fields hold e^n and h^{n-1/2}):
+ *   W^n = 1/2 eps0 dx^3 [ sum_edges eps_r(edge) (e^n)^2 + sum_faces h^{n-1/2} h^{n+1/2} ]
+ * h^{n+1/2} is formed with the same H-update expression in REAL precision and
+ * never stored; products and sums are in double, summed in storage order.
+ */
+double FN(oracle_energy)(int nx, int ny, int nz, REAL S, double dx,
+                         const REAL *ex, const REAL *ey, const REAL *ez,
+                         const REAL *hx, const REAL *hy, const REAL *hz,
+                         const double *epsx, const double *epsy, const double *epsz)
+{
+    const long sy = nx + 1, sz = (long)(nx + 1) * (ny + 1);
+    double we = 0.0, wh = 0.0;
+    for (int k = 1; k < nz; ++k)
+        for (int j = 1; j < ny; ++j)
+            for (int i = 0; i < nx; ++i) {
+                const long p = k * sz + j * sy + i;
+                we += epsx[p] * ((double)ex[p] * (double)ex[p]);
+            }
+    for (int k = 1; k < nz; ++k)
+        for (int j = 0; j < ny; ++j)
+            for (int i = 1; i < nx; ++i) {
+                const long p = k * sz + j * sy + i;
+                we += epsy[p] * ((double)ey[p] * (double)ey[p]);
+            }
+    for (int k = 0; k < nz; ++k)
+        for (int j = 1; j < ny; ++j)
+            for (int i = 1; i < nx; ++i) {
+                const long p = k * sz + j * sy + i;
+                we += epsz[p] * ((double)ez[p] * (double)ez[p]);
+            }
+    for (int k = 0; k < nz; ++k)
+        for (int j = 0; j < ny; ++j)
+            for (int i = 0; i <= nx; ++i) {
+                const long p = k * sz + j * sy + i;
+                const REAL hn = hx[p] + S * ((ey[p + sz] - ey[p]) - (ez[p + sy] - ez[p]));
+                wh += (double)hx[p] * (double)hn;
+            }
+    for (int k = 0; k < nz; ++k)
+        for (int j = 0; j <= ny; ++j)
+            for (int i = 0; i < nx; ++i) {
+                const long p = k * sz + j * sy + i;
+                const REAL hn = hy[p] + S * ((ez[p + 1] - ez[p]) - (ex[p + sz] - ex[p]));
+                wh += (double)hy[p] * (double)hn;
+            }
+    for (int k = 0; k <= nz; ++k)
+        for (int j = 0; j < ny; ++j)
+            for (int i = 0; i < nx; ++i) {
+                const long p = k * sz + j * sy + i;
+                const REAL hn = hz[p] + S * ((ex[p + sy] - ex[p]) - (ey[p + 1] - ey[p]));
+                wh += (double)hz[p] * (double)hn;
+            }
+    return 0.5 * EPS0 * dx * dx * dx * (we + wh);
+}
+
+#undef BR_X
+#undef BR_Y
+#undef BR_Z
+#undef FN
+#undef CAT
+#undef CAT_
