@@ -1,0 +1,337 @@
+#!/usr/bin/env python3
+"""Throughput of the 3-D Yee leapfrog sweep on GB300 (Gcell-updates/s).
+
+Workload: the 256^3 PEC sphere cavity (64 seeded lossy dielectric spheres,
+a centre Ez Gaussian-modulated-sine source, 16 seeded Ez probes), 1000 time
+steps. One bench step = one whole run of that workload through the library:
+reset fields, 1000 leapfrog steps (H, E with loss, PEC, source, probes), one
+energy evaluation. Inputs (fields, material words) are resident in HBM and
+larger than L2 (~0.9 GB of fields per step), so no extra L2 flush is needed.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Multi-GPU: the sweep is run as independent replicas (one cavity per rank, no
+collective); `value` sums the cell-updates of all ranks over the slowest rank's
+time (weak scaling).
+
+The reference arm (--impl reference) times the plain CPU oracle, unmodified, on
+the host cores on a bounded sample of the same workload (same grid and
+materials, fewer time steps per bench step).
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import threading
+import time
+
+import numpy as np
+
+N_CELLS_SIDE = 256
+T_STEPS = 1000
+FIELD_BYTES = 48   # read + write six float32 components per cell-update
+MAT_BYTES = 4      # one 32-bit material word read per cell per launch
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--n", type=int, default=N_CELLS_SIDE)
+    p.add_argument("--tsteps", type=int, default=T_STEPS)
+    p.add_argument("--k", type=int, default=0, help="steps fused per launch (0 = library default)")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    return p.parse_args()
+
+
+def peaks():
+    here = os.path.dirname(os.path.abspath(__file__))
+    try:
+        with open(os.path.join(here, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples every 200 ms while the timed region runs."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.rows = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([c.strip() for c in line.split(",")])
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            if len(r) < 9:
+                continue
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, r[5:9]):
+                if v.strip().lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def workload(n: int):
+    from paper_1301_4539_gb300 import workloads as wl
+    return wl.sphere_cavity(n)
+
+
+def cpu_baseline(w, budget_s: float = 15.0):
+    """Time the float32 oracle on the host cores on a bounded sample of the workload."""
+    import oracle
+    oracle.build()
+    nthreads = os.cpu_count() or 1
+    os.environ.setdefault("OMP_NUM_THREADS", str(nthreads))
+    n = w["nx"]
+    g = oracle.OracleGrid(n, n, n, w["dx"], w["dt"], "f32")
+    g.set_materials(w["eps"], w["sigma"])
+    for s in w["sources"]:
+        g.add_source(*s)
+    for p in w["probes"]:
+        g.add_probe(*p)
+    t0 = time.perf_counter()
+    g.step(1)
+    t1 = time.perf_counter()
+    per = max(t1 - t0, 1e-3)
+    m = max(1, min(200, int(budget_s / per)))
+    t0 = time.perf_counter()
+    g.step(m)
+    dt = time.perf_counter() - t0
+    g.energy()
+    cells = n ** 3
+    return {"value": cells * m / dt / 1e9, "unit": "Gcell-updates/s", "cores": nthreads,
+            "kind": "oracle",
+            "sample": f"{n}^3 sphere cavity, float32 oracle, {m} time steps (of the {T_STEPS}-step run), "
+                      f"OMP over z-planes, {dt:.1f} s"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    w = workload(args.n)
+    import oracle
+    oracle.build()
+    nthreads = os.cpu_count() or 1
+    n = w["nx"]
+    g = oracle.OracleGrid(n, n, n, w["dx"], w["dt"], "f32")
+    g.set_materials(w["eps"], w["sigma"])
+    for s in w["sources"]:
+        g.add_source(*s)
+    for p in w["probes"]:
+        g.add_probe(*p)
+    t0 = time.perf_counter()
+    g.step(1)
+    per = max(time.perf_counter() - t0, 1e-3)
+    # each bench step: a bounded sample of the run, ~10 s of CPU work
+    m = max(1, min(100, int(10.0 / per)))
+    for _ in range(args.warmup):
+        g.step(1)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        g.step(m)
+        g.energy()
+        times.append(time.perf_counter() - t0)
+    tot = sum(times)
+    val = n ** 3 * m * args.steps / tot / 1e9
+    line = {"metric": "Gcell-updates/s 3D Yee FDTD", "value": val, "unit": "Gcell-updates/s",
+            "impl": "reference", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": tot / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"{n}^3 PEC sphere cavity (64 lossy dielectric spheres, centre Ez "
+                                   f"source, 16 probes); {m} time steps per bench step",
+                       "grid": [n, n, n], "time_steps_per_bench_step": m},
+            "cpu_baseline": {"value": val, "unit": "Gcell-updates/s", "cores": nthreads, "kind": "oracle",
+                             "sample": f"{m} time steps of the {n}^3 sphere cavity per bench step"},
+            "e2e": {"value": val, "unit": "Gcell-updates/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    rank, world, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    from paper_1301_4539_gb300 import sophie as so
+
+    w = workload(args.n)
+    n = w["nx"]
+    cells = n ** 3
+    g = so.Grid(n, n, n, w["dx"], w["dt"])
+    stream = torch.cuda.current_stream()
+    g.set_stream(stream.cuda_stream)
+    if args.k:
+        g.configure(temporal_k=args.k)
+    g.set_materials(w["eps"], w["sigma"])
+    for s in w["sources"]:
+        g.add_source(*s)
+    pids = [g.add_probe(*p) for p in w["probes"]]
+
+    def one_run():
+        g.reset()
+        g.step(args.tsteps)
+        return g.energy()
+
+    for _ in range(args.warmup):
+        one_run()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    sampler = ClockSampler(local)
+    sampler.start()
+    l0 = g.launch_count()
+    g.profile(True)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    energies = []
+    for _ in range(args.steps):
+        g.reset()
+        g.step(args.tsteps)
+        energies.append(g.energy())
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    launches = g.launch_count() - l0
+    prof = {k: g.profile_read(k) for k in (so.KERNEL_PLAIN, so.KERNEL_BLOCKED, so.KERNEL_ENERGY)}
+    g.profile(False)
+    clocks = sampler.stop()
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    total_updates = cells * args.tsteps * args.steps * world
+    value = total_updates / (ms / 1e3) / 1e9
+
+    # dominant kernel and its roofline
+    kid = max(prof, key=lambda k: prof[k][1])
+    kl, kms = prof[kid]
+    k_fused = args.k if (kid == so.KERNEL_BLOCKED and args.k) else 1
+    bytes_per_launch = cells * (FIELD_BYTES + MAT_BYTES)
+    peak, peak_kind = peaks()
+    avg_ms = kms / max(kl, 1)
+    achieved = bytes_per_launch / (avg_ms / 1e3) / 1e9
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": None, "kernel": {0: "yee_plain", 1: "yee_blocked", 2: "energy"}[kid],
+            "steps_per_launch": k_fused, "avg_launch_ms": avg_ms, "peak_source": peak_kind,
+            "algorithmic_bytes_per_launch": bytes_per_launch}
+
+    e2e = None
+    if not args.no_e2e and rank == 0:
+        e2e = run_e2e(args, g, w, pids, stream)
+
+    cpu = None
+    if not args.no_cpu_baseline and rank == 0 and world == 1:
+        cpu = cpu_baseline(w)
+
+    if rank == 0:
+        line = {"metric": "Gcell-updates/s 3D Yee FDTD", "value": value, "unit": "Gcell-updates/s",
+                "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": f"{n}^3 PEC sphere cavity (64 lossy dielectric spheres, centre Ez "
+                                       f"source, 16 probes), {args.tsteps} time steps per bench step",
+                           "grid": [n, n, n], "time_steps_per_bench_step": args.tsteps,
+                           "temporal_k": args.k or "default", "parallelism": f"replicas x{world}",
+                           "l2": "inputs larger than L2 (no flush)"},
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+                "clocks": clocks, "energy_J": energies[-1]}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def run_e2e(args, g, w, pids, stream):
+    """Same metric through the public API with host buffers: upload the
+    materials from pinned host memory, run, read the probes and the energy."""
+    import torch
+    n = w["nx"]
+    eps = torch.from_numpy(np.ascontiguousarray(w["eps"])).pin_memory().numpy()
+    sig = torch.from_numpy(np.ascontiguousarray(w["sigma"])).pin_memory().numpy()
+    reps = max(1, min(args.steps, 3))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        g.set_materials(eps, sig)
+        g.reset()
+        g.step(args.tsteps)
+        for p in pids:
+            g.read_probe(p, args.tsteps)
+        g.energy()
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    npts = (n + 1) * (n + 1) * (((n + 1) + 7) // 8 * 8)
+    return {"value": n ** 3 * args.tsteps * reps / dt / 1e9, "unit": "Gcell-updates/s",
+            "h2d_bytes_per_step": npts * 4, "d2h_bytes_per_step": len(pids) * args.tsteps * 4 + 8,
+            "note": "material words built on the host from eps/sigma and uploaded each step"}
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

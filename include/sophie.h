@@ -1,0 +1,208 @@
+/*
+ * libsophie - GB300 (sm_103a) 3-D Yee FDTD leapfrog sweep behind a C ABI.
+ *
+ * The method is the one of O. Cessenat, "Sophie, an FDTD code on the way to
+ * multicore" (arXiv:1301.4539): Sec. 2.1 gives the scheme (Maxwell-Ampere and
+ * Maxwell-Faraday in antisymmetric scaled form, Yee staggering, leapfrog in
+ * time, displayed Hx update); Sec. 3.3 gives PEC walls (tangential E held at 0)
+ * and sources (a current added to Ampere's equation); Sec. 3.4 gives pin-point
+ * outputs and multi-step cache reuse; Sec. 3.1 states that any such
+ * restructuring leaves every output value unchanged.
+ *
+ * Units and variables. e = E (V/m) and h = eta0*H (V/m), i.e. the paper's
+ * (E~, H~) = eps0*(e, h). With S = c*dt/dx one step n -> n+1 is
+ *   h^{n+1/2} = h^{n-1/2} + S * (discrete -curl e^n)              (Faraday)
+ *   e^{n+1}   = Ca*e^n + Cb*(discrete curl h^{n+1/2} + s^{n+1/2}) (Ampere)
+ * with, per edge, eps_r and sigma the mean of the four cells sharing the edge,
+ *   beta = sigma*dt/(2*eps0*eps_r), Ca = (1-beta)/(1+beta),
+ *   Cb = (S/eps_r)/(1+beta)   (computed in double, rounded once to float),
+ * and s the source term (only on source edges). Fields are float32; every
+ * update is evaluated without fused multiply-add, in the operand order
+ *   h + S*((a1-a0) - (b1-b0))   and   Ca*e + Cb*((a1-a0) - (b1-b0)).
+ *
+ * Storage indices (the "field layout" below). For a grid of nx*ny*nz cells,
+ * every component is addressed on the (nx+1)*(ny+1)*(nz+1) index box, x
+ * fastest; cell (i,j,k) occupies [i,i+1]x[j,j+1]x[k,k+1] (units of dx):
+ *   comp 0 ex(i,j,k) at (i+1/2, j, k)      valid i<nx
+ *   comp 1 ey(i,j,k) at (i, j+1/2, k)      valid j<ny
+ *   comp 2 ez(i,j,k) at (i, j, k+1/2)      valid k<nz
+ *   comp 3 hx(i,j,k) at (i, j+1/2, k+1/2)  valid j<ny, k<nz
+ *   comp 4 hy(i,j,k) at (i+1/2, j, k+1/2)  valid i<nx, k<nz
+ *   comp 5 hz(i,j,k) at (i+1/2, j+1/2, k)  valid i<nx, j<ny
+ * Tangential E on the six walls (PEC) is always 0. Entries outside a
+ * component's valid range are always 0.
+ *
+ * Threading: a grid handle is used by one host thread at a time. Errors are
+ * reported by a negative return code and a thread-local message
+ * (sophie_last_error). Device memory is owned by the library.
+ */
+#ifndef SOPHIE_H
+#define SOPHIE_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Return codes. */
+#define SOPHIE_OK           0
+#define SOPHIE_EINVAL      -1  /* bad argument (NULL, range, state)            */
+#define SOPHIE_EUNSTABLE   -2  /* dt above the 3-D Courant limit dx/(c*sqrt 3) */
+#define SOPHIE_ENOMEM      -3  /* device or host allocation failed / too big   */
+#define SOPHIE_ECUDA       -4  /* a CUDA runtime call failed                   */
+#define SOPHIE_ENONFINITE  -5  /* a non-finite value was found (energy)        */
+#define SOPHIE_ETIMEOUT    -6  /* a kernel's bounded wait ran out              */
+#define SOPHIE_ETOOMANYMAT -7  /* more distinct edge materials than supported  */
+#define SOPHIE_ENOTSUP     -8  /* option not supported by this build           */
+
+/* Component ids (storage indices above). */
+#define SOPHIE_EX 0
+#define SOPHIE_EY 1
+#define SOPHIE_EZ 2
+#define SOPHIE_HX 3
+#define SOPHIE_HY 4
+#define SOPHIE_HZ 5
+
+/* Source waveform kinds for sophie_add_source. */
+#define SOPHIE_GAUSS_SINE 0
+#define SOPHIE_GAUSS      1
+
+/* Storage precision for sophie_configure. */
+#define SOPHIE_FP32 0
+
+/* Kernel ids for sophie_profile_read. */
+#define SOPHIE_KERNEL_PLAIN   0  /* one fused H+E step per launch           */
+#define SOPHIE_KERNEL_BLOCKED 1  /* k fused H+E steps per launch (k >= 2)   */
+#define SOPHIE_KERNEL_ENERGY  2  /* discrete energy reduction               */
+
+typedef struct sophie_grid sophie_grid;
+
+/* Library version, e.g. 10000 for 1.0.0. */
+int sophie_version(void);
+
+/*
+ * Create a PEC cavity of nx*ny*nz cells of edge dx (m), time step dt (s).
+ * Sec. 2.1: uniform Cartesian Yee grid. Requires nx,ny,nz >= 1, dx > 0,
+ * 0 < dt <= dx/(c*sqrt(3)) (else SOPHIE_EUNSTABLE). All fields start at 0, the
+ * medium is vacuum (eps_r = 1, sigma = 0), no sources, no probes, step 0.
+ * Allocates two device copies of the six fields (ping-pong), one 32-bit
+ * material word per index point and small tables. On success *out owns them.
+ * Errors: EINVAL (bad argument, out == NULL), EUNSTABLE, ENOMEM, ECUDA.
+ */
+int sophie_create_grid(int nx, int ny, int nz, double dx, double dt, sophie_grid **out);
+
+/* Free a grid and all its device memory; NULL is accepted. Waits for pending work. */
+int sophie_destroy_grid(sophie_grid *g);
+
+/*
+ * Per-cell relative permittivity and conductivity (S/m), host arrays of
+ * nx*ny*nz floats each (x fastest, then y, then z), copied. eps_r >= 1 and
+ * finite; sigma >= 0 and finite (else EINVAL). Edge values are the mean of the
+ * four cells sharing the edge (Sec. 2.1 coefficients, see top of file); at
+ * most 1023 distinct (eps_r, sigma) edge pairs (else ETOOMANYMAT, grid left
+ * unchanged). Enqueued on the grid's stream; the host arrays may be reused on
+ * return.
+ */
+int sophie_set_materials(sophie_grid *g, const float *eps_r, const float *sigma);
+
+/*
+ * Add a soft current source on the E edge (comp in {0,1,2}, storage indices
+ * i,j,k; the edge must be interior, i.e. not PEC). Sec. 3.3: a current added
+ * to Ampere's equation. At step n -> n+1 the term s = amp*w((n+1/2)*dt),
+ * computed in double and rounded once to float, is added inside the curl
+ * bracket of that edge: e = Ca*e + Cb*(bracket + s). Waveforms:
+ *   kind 0: w(t) = sin(2 pi f0 (t-t0)) * exp(-(t-t0)^2/(2 st^2))
+ *   kind 1: w(t) = exp(-(t-t0)^2/(2 st^2))
+ * with st = 1/(2 pi sf), sf = bw/(2 sqrt(2 ln 2)) (bw = FWHM of the amplitude
+ * spectrum of the envelope). Up to 16 sources; several on one edge add in the
+ * order they were added. Errors: EINVAL.
+ */
+int sophie_add_source(sophie_grid *g, int comp, int i, int j, int k,
+                      double amp, double f0, double bw, double t0, int kind);
+
+/*
+ * Add a pin-point output (Sec. 3.4) on component comp (0..5) at storage
+ * indices (i,j,k) within the component's valid range. Sample m (m >= 0) is the
+ * value after step m -> m+1: e^{m+1} for E, h^{m+1/2} for H. Samples of steps
+ * taken before the probe existed read 0. Up to 64 probes; *probe_id gets the
+ * probe's index. Errors: EINVAL.
+ */
+int sophie_add_probe(sophie_grid *g, int comp, int i, int j, int k, int *probe_id);
+
+/*
+ * Advance n >= 0 leapfrog steps (H then E, PEC, sources, probes). Steps are
+ * fused: one launch advances k steps when temporal blocking is configured
+ * (Sec. 3.4 multi-step cache reuse); results are bitwise identical for every
+ * k. Asynchronous: returns once the work is enqueued on the grid's stream.
+ * Errors: EINVAL, ECUDA, ENOMEM.
+ */
+int sophie_step(sophie_grid *g, int n);
+
+/* Steps taken since creation or the last sophie_reset. */
+int sophie_get_step(sophie_grid *g, long long *n);
+
+/*
+ * Copy up to cap samples of probe probe_id, widened to double, into out
+ * (host); *n_written gets min(cap, steps taken). Synchronises the stream.
+ * Errors: EINVAL, ECUDA, ETIMEOUT.
+ */
+int sophie_read_probe(sophie_grid *g, int probe_id, double *out, int cap, int *n_written);
+
+/*
+ * Discrete Yee energy at the current step n (Sec. 2.1 antisymmetric form):
+ *   W = 1/2 eps0 dx^3 [ sum_edges eps_r(edge) (e^n)^2 + sum_faces h^{n-1/2} h^{n+1/2} ]
+ * with h^{n+1/2} formed from the same float update and never stored,
+ * accumulated in double. Synchronises the stream.
+ * Errors: EINVAL, ECUDA, ETIMEOUT, ENONFINITE (W not finite; *W still set).
+ */
+int sophie_energy(sophie_grid *g, double *W);
+
+/*
+ * Copy one component from / to a host array of (nx+1)*(ny+1)*(nz+1) floats in
+ * the storage layout above (x fastest). sophie_set_fields zeroes PEC edges
+ * and out-of-range entries after the copy. Both synchronise.
+ * Errors: EINVAL, ECUDA.
+ */
+int sophie_set_fields(sophie_grid *g, int comp, const float *host);
+int sophie_get_fields(sophie_grid *g, int comp, float *host);
+
+/* Zero all fields and probe samples and set the step counter to 0
+ * (materials, sources and probes are kept). Enqueued on the stream. */
+int sophie_reset(sophie_grid *g);
+
+/*
+ * Use cuda_stream (a cudaStream_t, e.g. torch.cuda.current_stream().cuda_stream;
+ * NULL = legacy default stream) for all later work of this grid. The caller
+ * keeps the stream alive while the grid uses it. Synchronises the old stream.
+ */
+int sophie_set_stream(sophie_grid *g, void *cuda_stream);
+
+/* Wait for all work of the grid; reports ETIMEOUT if a kernel gave up a wait. */
+int sophie_sync(sophie_grid *g);
+
+/*
+ * temporal_k: steps fused per launch (1 = plain kernel, 2..8 = temporally
+ * blocked), 0 = library default. tile_x, tile_y: 0 = default (reserved).
+ * precision: SOPHIE_FP32 (others: ENOTSUP). Errors: EINVAL, ENOTSUP.
+ */
+int sophie_configure(sophie_grid *g, int temporal_k, int tile_x, int tile_y, int precision);
+
+/* Number of kernels this grid has launched since creation. */
+int sophie_launch_count(sophie_grid *g, long long *launches);
+
+/*
+ * Per-kernel timing with CUDA events recorded on the grid's stream around each
+ * launch while enabled (enable != 0 also clears the totals). sophie_profile_read
+ * synchronises and returns the launch count and the summed device milliseconds
+ * of kernel id (SOPHIE_KERNEL_*).
+ */
+int sophie_profile(sophie_grid *g, int enable);
+int sophie_profile_read(sophie_grid *g, int kernel, long long *launches, double *ms);
+
+/* Message of the last error on this thread ("" if none). */
+const char *sophie_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SOPHIE_H */

@@ -1,0 +1,751 @@
+// Host runtime of libsophie: the C ABI declared in include/sophie.h.
+//
+// Owns the grid handle, device memory (two ping-pong copies of the six fields,
+// the per-point material words and class tables), source waveform tables,
+// probe buffers, the energy reduction and error reporting. Every step of the
+// method runs in the CUDA kernels; this file validates arguments, builds
+// tables and enqueues launches.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <mutex>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "../../include/sophie.h"
+#include "sophie_internal.h"
+
+using namespace sophie;
+
+namespace {
+
+constexpr double kC0 = 299792458.0;
+constexpr double kEps0 = 8.8541878128e-12;
+
+thread_local std::string g_err;
+
+int fail(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return code;
+}
+
+#define CUDA_TRY(call)                                                              \
+  do {                                                                              \
+    cudaError_t e_ = (call);                                                        \
+    if (e_ != cudaSuccess)                                                          \
+      return fail(SOPHIE_ECUDA, "%s failed: %s", #call, cudaGetErrorString(e_));    \
+  } while (0)
+
+struct Source {
+  int comp, i, j, k, kind;
+  double amp, f0, bw, t0;
+  long long pos;
+};
+
+struct Probe {
+  int comp, i, j, k;
+  long long pos;
+};
+
+struct ProfEntry {
+  int kernel;
+  cudaEvent_t a, b;
+};
+
+}  // namespace
+
+struct sophie_grid {
+  Dims d{};
+  double dx = 0, dt = 0, S64 = 0;
+  float S32 = 0;
+  float* F[2] = {nullptr, nullptr};
+  int cur = 0;
+  uint32_t* mat = nullptr;     // device material words
+  uint32_t* mat_host = nullptr;  // pinned staging for uploads
+  float2* coef = nullptr;      // device class table (Ca, Cb)
+  double* eps_tab = nullptr;   // device class table eps_r(edge)
+  std::vector<float2> coef_h;
+  std::vector<double> eps_h;
+  cudaEvent_t mat_upload_done = nullptr;
+  std::vector<Source> src;
+  std::vector<Probe> prb;
+  float* sval = nullptr;  // device [kMaxSources][scap]
+  int scap = 0;
+  float* pbuf = nullptr;  // device [kMaxProbes][pcap]
+  int pcap = 0;
+  long long n = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  int temporal_k = 1;
+  int precision = SOPHIE_FP32;
+  double* e_partials = nullptr;
+  double* e_out = nullptr;
+  int e_blocks = 0;
+  int* err = nullptr;
+  long long launches = 0;
+  bool prof = false;
+  std::vector<ProfEntry> prof_live;
+  std::vector<cudaEvent_t> ev_pool;
+  long long prof_count[3] = {0, 0, 0};
+  double prof_ms[3] = {0, 0, 0};
+};
+
+namespace {
+
+long long point_index(const Dims& d, int i, int j, int k) {
+  return ((long long)k * d.ny1 + j) * d.nxp + i;
+}
+
+bool e_edge_interior(const Dims& d, int c, int i, int j, int k) {
+  switch (c) {
+    case 0: return i >= 0 && i < d.nx && j >= 1 && j < d.ny && k >= 1 && k < d.nz;
+    case 1: return i >= 1 && i < d.nx && j >= 0 && j < d.ny && k >= 1 && k < d.nz;
+    default: return i >= 1 && i < d.nx && j >= 1 && j < d.ny && k >= 0 && k < d.nz;
+  }
+}
+
+bool comp_valid(const Dims& d, int c, int i, int j, int k) {
+  if (i < 0 || j < 0 || k < 0 || i > d.nx || j > d.ny || k > d.nz) return false;
+  switch (c) {
+    case 0: return i < d.nx;
+    case 1: return j < d.ny;
+    case 2: return k < d.nz;
+    case 3: return j < d.ny && k < d.nz;
+    case 4: return i < d.nx && k < d.nz;
+    default: return i < d.nx && j < d.ny;
+  }
+}
+
+// Coefficients of one edge from the four (eps_r, sigma) cell values, in the
+// fixed order (-,-), (+,-), (-,+), (+,+) of the two transverse offsets:
+// mean in double, beta = sigma dt/(2 eps0 eps_r), Ca = (1-beta)/(1+beta),
+// Cb = (S/eps_r)/(1+beta), both rounded once to float.
+struct EdgeKey {
+  uint64_t e, s;
+  bool operator==(const EdgeKey& o) const { return e == o.e && s == o.s; }
+};
+struct EdgeKeyHash {
+  size_t operator()(const EdgeKey& k) const {
+    return (size_t)(k.e * 0x9E3779B97F4A7C15ull ^ (k.s + 0x632BE59BD9B4E019ull + (k.e << 6)));
+  }
+};
+
+uint64_t dbits(double v) {
+  uint64_t u;
+  memcpy(&u, &v, 8);
+  return u;
+}
+
+struct ClassBuilder {
+  const sophie_grid* g;
+  std::unordered_map<EdgeKey, int, EdgeKeyHash> map;
+  std::vector<float2> coef;
+  std::vector<double> eps;
+  bool overflow = false;
+  explicit ClassBuilder(const sophie_grid* gg) : g(gg) {
+    coef.push_back(make_float2(0.f, 0.f));  // class 0: PEC / absent edge
+    eps.push_back(0.0);
+  }
+  int classify(double e4, double s4) {
+    const double e = e4 * 0.25, s = s4 * 0.25;
+    const EdgeKey key{dbits(e), dbits(s)};
+    auto it = map.find(key);
+    if (it != map.end()) return it->second;
+    const int id = (int)coef.size();
+    if (id >= kMaxClasses) {
+      overflow = true;
+      return 0;
+    }
+    const double beta = (s * g->dt) / (2.0 * kEps0 * e);
+    const double ca = (1.0 - beta) / (1.0 + beta);
+    const double cb = (g->S64 / e) / (1.0 + beta);
+    coef.push_back(make_float2((float)ca, (float)cb));
+    eps.push_back(e);
+    map.emplace(key, id);
+    return id;
+  }
+};
+
+// Fill g->mat_host with class words for per-cell eps/sigma (nullptr = vacuum).
+int build_material_words(sophie_grid* g, const float* eps, const float* sig) {
+  const Dims& d = g->d;
+  const int nx = d.nx, ny = d.ny, nz = d.nz;
+  auto E = [&](int i, int j, int k) -> double {
+    return eps ? (double)eps[((long long)k * ny + j) * nx + i] : 1.0;
+  };
+  auto Sg = [&](int i, int j, int k) -> double {
+    return sig ? (double)sig[((long long)k * ny + j) * nx + i] : 0.0;
+  };
+  ClassBuilder cb(g);
+  uint32_t* w = g->mat_host;
+  // One-entry cache: neighbouring edges usually share their material.
+  double le[3] = {-1, -1, -1}, ls[3] = {-1, -1, -1};
+  int lc[3] = {0, 0, 0};
+  auto cls = [&](int c, double e4, double s4) -> uint32_t {
+    if (e4 == le[c] && s4 == ls[c]) return (uint32_t)lc[c];
+    le[c] = e4;
+    ls[c] = s4;
+    lc[c] = cb.classify(e4, s4);
+    return (uint32_t)lc[c];
+  };
+  for (int k = 0; k <= nz; ++k)
+    for (int j = 0; j <= ny; ++j) {
+      uint32_t* row = w + ((long long)k * d.ny1 + j) * d.nxp;
+      for (int i = 0; i < d.nxp; ++i) {
+        uint32_t word = 0;
+        if (e_edge_interior(d, 0, i, j, k)) {
+          const double e4 = ((E(i, j - 1, k - 1) + E(i, j, k - 1)) + E(i, j - 1, k)) + E(i, j, k);
+          const double s4 = ((Sg(i, j - 1, k - 1) + Sg(i, j, k - 1)) + Sg(i, j - 1, k)) + Sg(i, j, k);
+          word |= cls(0, e4, s4);
+        }
+        if (e_edge_interior(d, 1, i, j, k)) {
+          const double e4 = ((E(i - 1, j, k - 1) + E(i, j, k - 1)) + E(i - 1, j, k)) + E(i, j, k);
+          const double s4 = ((Sg(i - 1, j, k - 1) + Sg(i, j, k - 1)) + Sg(i - 1, j, k)) + Sg(i, j, k);
+          word |= cls(1, e4, s4) << 10;
+        }
+        if (e_edge_interior(d, 2, i, j, k)) {
+          const double e4 = ((E(i - 1, j - 1, k) + E(i, j - 1, k)) + E(i - 1, j, k)) + E(i, j, k);
+          const double s4 = ((Sg(i - 1, j - 1, k) + Sg(i, j - 1, k)) + Sg(i - 1, j, k)) + Sg(i, j, k);
+          word |= cls(2, e4, s4) << 20;
+        }
+        row[i] = word;
+      }
+      if (cb.overflow) break;
+    }
+  if (cb.overflow)
+    return fail(SOPHIE_ETOOMANYMAT, "more than %d distinct (eps_r, sigma) edge pairs", kMaxClasses - 1);
+  for (const Source& s : g->src) w[s.pos] |= kSrcFlag;
+  for (const Probe& p : g->prb) w[p.pos] |= kPrbFlag;
+  g->coef_h = std::move(cb.coef);
+  g->eps_h = std::move(cb.eps);
+  return SOPHIE_OK;
+}
+
+int upload_materials(sophie_grid* g) {
+  const Dims& d = g->d;
+  const size_t npts = (size_t)d.nz1 * d.ny1 * d.nxp;
+  CUDA_TRY(cudaMemcpyAsync(g->mat, g->mat_host, npts * 4, cudaMemcpyHostToDevice, g->stream));
+  CUDA_TRY(cudaMemcpyAsync(g->coef, g->coef_h.data(), g->coef_h.size() * sizeof(float2),
+                           cudaMemcpyHostToDevice, g->stream));
+  CUDA_TRY(cudaMemcpyAsync(g->eps_tab, g->eps_h.data(), g->eps_h.size() * sizeof(double),
+                           cudaMemcpyHostToDevice, g->stream));
+  CUDA_TRY(cudaEventRecord(g->mat_upload_done, g->stream));
+  // coef_h / eps_h are pageable: the copies above complete before return.
+  return SOPHIE_OK;
+}
+
+double waveform(const Source& s, long long n, double dt) {
+  const double pi = 3.14159265358979323846;
+  const double sf = s.bw / (2.0 * std::sqrt(2.0 * std::log(2.0)));
+  const double st = 1.0 / (2.0 * pi * sf);
+  const double t = ((double)n + 0.5) * dt;
+  const double u = t - s.t0;
+  const double env = std::exp(-(u * u) / (2.0 * st * st));
+  return s.amp * (s.kind == 0 ? std::sin(2.0 * pi * s.f0 * u) * env : env);
+}
+
+// Make the source table cover steps [0, need) and the probe buffer [0, need).
+int ensure_capacity(sophie_grid* g, long long need) {
+  if (need > (1ll << 30)) return fail(SOPHIE_EINVAL, "step count too large");
+  if (need > g->scap) {
+    int cap = g->scap ? g->scap : 4096;
+    while (cap < need) cap *= 2;
+    std::vector<float> h((size_t)kMaxSources * cap, 0.f);
+    for (size_t s = 0; s < g->src.size(); ++s)
+      for (int m = 0; m < cap; ++m) h[s * cap + m] = (float)waveform(g->src[s], m, g->dt);
+    float* dnew = nullptr;
+    CUDA_TRY(cudaStreamSynchronize(g->stream));
+    if (cudaMalloc(&dnew, h.size() * 4) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(SOPHIE_ENOMEM, "source table allocation failed");
+    }
+    CUDA_TRY(cudaMemcpy(dnew, h.data(), h.size() * 4, cudaMemcpyHostToDevice));
+    if (g->sval) cudaFree(g->sval);
+    g->sval = dnew;
+    g->scap = cap;
+  }
+  if (need > g->pcap) {
+    int cap = g->pcap ? g->pcap : 4096;
+    while (cap < need) cap *= 2;
+    float* dnew = nullptr;
+    CUDA_TRY(cudaStreamSynchronize(g->stream));
+    if (cudaMalloc(&dnew, (size_t)kMaxProbes * cap * 4) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(SOPHIE_ENOMEM, "probe buffer allocation failed");
+    }
+    CUDA_TRY(cudaMemset(dnew, 0, (size_t)kMaxProbes * cap * 4));
+    if (g->pbuf) {
+      CUDA_TRY(cudaMemcpy2D(dnew, (size_t)cap * 4, g->pbuf, (size_t)g->pcap * 4, (size_t)g->pcap * 4,
+                            kMaxProbes, cudaMemcpyDeviceToDevice));
+      cudaFree(g->pbuf);
+    }
+    g->pbuf = dnew;
+    g->pcap = cap;
+  }
+  return SOPHIE_OK;
+}
+
+// Rebuild one source's waveform column after it was added.
+int refresh_source_table(sophie_grid* g, int s) {
+  if (!g->sval) return SOPHIE_OK;
+  std::vector<float> h(g->scap);
+  for (int m = 0; m < g->scap; ++m) h[m] = (float)waveform(g->src[s], m, g->dt);
+  CUDA_TRY(cudaStreamSynchronize(g->stream));
+  CUDA_TRY(cudaMemcpy(g->sval + (size_t)s * g->scap, h.data(), h.size() * 4, cudaMemcpyHostToDevice));
+  return SOPHIE_OK;
+}
+
+cudaEvent_t prof_event(sophie_grid* g) {
+  if (!g->ev_pool.empty()) {
+    cudaEvent_t e = g->ev_pool.back();
+    g->ev_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+int prof_drain(sophie_grid* g) {
+  if (g->prof_live.empty()) return SOPHIE_OK;
+  CUDA_TRY(cudaStreamSynchronize(g->stream));
+  for (ProfEntry& p : g->prof_live) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
+      g->prof_count[p.kernel] += 1;
+      g->prof_ms[p.kernel] += ms;
+    }
+    g->ev_pool.push_back(p.a);
+    g->ev_pool.push_back(p.b);
+  }
+  g->prof_live.clear();
+  return SOPHIE_OK;
+}
+
+StepArgs make_step_args(sophie_grid* g) {
+  StepArgs a{};
+  a.fin = g->F[g->cur];
+  a.fout = g->F[1 - g->cur];
+  a.mat = g->mat;
+  a.coef = g->coef;
+  a.d = g->d;
+  a.S = g->S32;
+  a.n0 = g->n;
+  a.src.n = (int)g->src.size();
+  for (size_t s = 0; s < g->src.size(); ++s) {
+    a.src.comp[s] = g->src[s].comp;
+    a.src.pos[s] = g->src[s].pos;
+  }
+  a.src.val = g->sval;
+  a.src.cap = g->scap;
+  a.prb.n = (int)g->prb.size();
+  for (size_t p = 0; p < g->prb.size(); ++p) {
+    a.prb.comp[p] = g->prb[p].comp;
+    a.prb.pos[p] = g->prb[p].pos;
+  }
+  a.prb.buf = g->pbuf;
+  a.prb.cap = g->pcap;
+  a.err = g->err;
+  return a;
+}
+
+int check_err_word(sophie_grid* g) {
+  int h = 0;
+  CUDA_TRY(cudaMemcpyAsync(&h, g->err, sizeof(int), cudaMemcpyDeviceToHost, g->stream));
+  CUDA_TRY(cudaStreamSynchronize(g->stream));
+  if (h != 0) {
+    cudaMemsetAsync(g->err, 0, sizeof(int), g->stream);
+    return fail(SOPHIE_ETIMEOUT, "a kernel ran out of its bounded wait (code %d)", h);
+  }
+  return SOPHIE_OK;
+}
+
+void free_grid(sophie_grid* g) {
+  if (!g) return;
+  if (g->stream) cudaStreamSynchronize(g->stream);
+  for (int b = 0; b < 2; ++b)
+    if (g->F[b]) cudaFree(g->F[b]);
+  if (g->mat) cudaFree(g->mat);
+  if (g->mat_host) cudaFreeHost(g->mat_host);
+  if (g->coef) cudaFree(g->coef);
+  if (g->eps_tab) cudaFree(g->eps_tab);
+  if (g->sval) cudaFree(g->sval);
+  if (g->pbuf) cudaFree(g->pbuf);
+  if (g->e_partials) cudaFree(g->e_partials);
+  if (g->e_out) cudaFree(g->e_out);
+  if (g->err) cudaFree(g->err);
+  if (g->mat_upload_done) cudaEventDestroy(g->mat_upload_done);
+  for (ProfEntry& p : g->prof_live) {
+    cudaEventDestroy(p.a);
+    cudaEventDestroy(p.b);
+  }
+  for (cudaEvent_t e : g->ev_pool) cudaEventDestroy(e);
+  if (g->own_stream && g->stream) cudaStreamDestroy(g->stream);
+  delete g;
+}
+
+int copy_component(sophie_grid* g, int comp, void* host, bool to_device, int buf) {
+  const Dims& d = g->d;
+  cudaMemcpy3DParms p{};
+  cudaPitchedPtr dev = make_cudaPitchedPtr(g->F[buf] + (size_t)comp * d.plane, (size_t)d.nxp * 4,
+                                           (size_t)d.nx + 1, (size_t)6 * d.ny1);
+  cudaPitchedPtr hst = make_cudaPitchedPtr(host, (size_t)(d.nx + 1) * 4, (size_t)d.nx + 1, (size_t)d.ny1);
+  p.extent = make_cudaExtent((size_t)(d.nx + 1) * 4, (size_t)d.ny1, (size_t)d.nz1);
+  if (to_device) {
+    p.srcPtr = hst;
+    p.dstPtr = dev;
+    p.kind = cudaMemcpyHostToDevice;
+  } else {
+    p.srcPtr = dev;
+    p.dstPtr = hst;
+    p.kind = cudaMemcpyDeviceToHost;
+  }
+  CUDA_TRY(cudaMemcpy3DAsync(&p, g->stream));
+  return SOPHIE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int sophie_version(void) { return 10000; }
+
+const char* sophie_last_error(void) { return g_err.c_str(); }
+
+int sophie_create_grid(int nx, int ny, int nz, double dx, double dt, sophie_grid** out) {
+  g_err.clear();
+  if (!out) return fail(SOPHIE_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (nx < 1 || ny < 1 || nz < 1) return fail(SOPHIE_EINVAL, "grid sizes must be >= 1");
+  if (!(dx > 0) || !std::isfinite(dx)) return fail(SOPHIE_EINVAL, "dx must be finite and > 0");
+  if (!(dt > 0) || !std::isfinite(dt)) return fail(SOPHIE_EINVAL, "dt must be finite and > 0");
+  if (kC0 * dt * std::sqrt(3.0) > dx * (1.0 + 1e-12))
+    return fail(SOPHIE_EUNSTABLE, "dt above the 3-D Courant limit dx/(c sqrt 3)");
+  if (nx > (1 << 20) || ny > (1 << 20) || nz > (1 << 20))
+    return fail(SOPHIE_EINVAL, "grid size above 2^20 per axis");
+  Dims d{};
+  d.nx = nx;
+  d.ny = ny;
+  d.nz = nz;
+  d.nxp = ((nx + 1) + 7) / 8 * 8;
+  d.ny1 = ny + 1;
+  d.nz1 = nz + 1;
+  d.plane = (long long)d.ny1 * d.nxp;
+  d.zstride = 6 * d.plane;
+  const double field_bytes = (double)d.zstride * d.nz1 * 4.0;
+  const double pts = (double)d.plane * d.nz1;
+  if (d.zstride > (1ll << 31) || field_bytes * 2 + pts * 4 > 2.5e11)
+    return fail(SOPHIE_ENOMEM, "grid too large (%.3g bytes of fields)", field_bytes * 2);
+  sophie_grid* g = new (std::nothrow) sophie_grid();
+  if (!g) return fail(SOPHIE_ENOMEM, "host allocation failed");
+  g->d = d;
+  g->dx = dx;
+  g->dt = dt;
+  g->S64 = kC0 * dt / dx;
+  g->S32 = (float)g->S64;
+  int rc = SOPHIE_OK;
+  auto alloc = [&](void** p, size_t bytes) -> bool {
+    if (cudaMalloc(p, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      rc = fail(SOPHIE_ENOMEM, "cudaMalloc of %zu bytes failed", bytes);
+      return false;
+    }
+    return true;
+  };
+  const size_t fbytes = (size_t)d.zstride * d.nz1 * 4;
+  const size_t npts = (size_t)d.plane * d.nz1;
+  do {
+    if (cudaStreamCreateWithFlags(&g->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      rc = fail(SOPHIE_ECUDA, "cudaStreamCreate failed: %s", cudaGetErrorString(cudaGetLastError()));
+      break;
+    }
+    g->own_stream = true;
+    if (!alloc((void**)&g->F[0], fbytes) || !alloc((void**)&g->F[1], fbytes)) break;
+    if (!alloc((void**)&g->mat, npts * 4)) break;
+    if (!alloc((void**)&g->coef, kMaxClasses * sizeof(float2))) break;
+    if (!alloc((void**)&g->eps_tab, kMaxClasses * sizeof(double))) break;
+    if (!alloc((void**)&g->err, sizeof(int))) break;
+    g->e_blocks = energy_blocks(d);
+    if (!alloc((void**)&g->e_partials, (size_t)g->e_blocks * 8)) break;
+    if (!alloc((void**)&g->e_out, 8)) break;
+    if (cudaMallocHost(&g->mat_host, npts * 4) != cudaSuccess) {
+      cudaGetLastError();
+      rc = fail(SOPHIE_ENOMEM, "pinned host allocation failed");
+      break;
+    }
+    if (cudaEventCreateWithFlags(&g->mat_upload_done, cudaEventDisableTiming) != cudaSuccess) {
+      rc = fail(SOPHIE_ECUDA, "cudaEventCreate failed");
+      break;
+    }
+    if (cudaMemsetAsync(g->F[0], 0, fbytes, g->stream) != cudaSuccess ||
+        cudaMemsetAsync(g->F[1], 0, fbytes, g->stream) != cudaSuccess ||
+        cudaMemsetAsync(g->err, 0, sizeof(int), g->stream) != cudaSuccess ||
+        cudaMemsetAsync(g->coef, 0, kMaxClasses * sizeof(float2), g->stream) != cudaSuccess ||
+        cudaMemsetAsync(g->eps_tab, 0, kMaxClasses * sizeof(double), g->stream) != cudaSuccess) {
+      rc = fail(SOPHIE_ECUDA, "cudaMemsetAsync failed");
+      break;
+    }
+    rc = build_material_words(g, nullptr, nullptr);
+    if (rc) break;
+    rc = upload_materials(g);
+    if (rc) break;
+    rc = ensure_capacity(g, 1);
+    if (rc) break;
+    if (cudaStreamSynchronize(g->stream) != cudaSuccess) {
+      rc = fail(SOPHIE_ECUDA, "initialisation failed: %s", cudaGetErrorString(cudaGetLastError()));
+      break;
+    }
+  } while (0);
+  if (rc != SOPHIE_OK) {
+    free_grid(g);
+    return rc;
+  }
+  *out = g;
+  return SOPHIE_OK;
+}
+
+int sophie_destroy_grid(sophie_grid* g) {
+  free_grid(g);
+  return SOPHIE_OK;
+}
+
+int sophie_set_materials(sophie_grid* g, const float* eps, const float* sig) {
+  if (!g || !eps || !sig) return fail(SOPHIE_EINVAL, "NULL argument");
+  const long long ncell = (long long)g->d.nx * g->d.ny * g->d.nz;
+  for (long long c = 0; c < ncell; ++c) {
+    if (!(eps[c] >= 1.0f) || !std::isfinite(eps[c]))
+      return fail(SOPHIE_EINVAL, "eps_r[%lld] = %g must be finite and >= 1", c, (double)eps[c]);
+    if (!(sig[c] >= 0.0f) || !std::isfinite(sig[c]))
+      return fail(SOPHIE_EINVAL, "sigma[%lld] = %g must be finite and >= 0", c, (double)sig[c]);
+  }
+  // The staging buffer may still feed an earlier upload.
+  CUDA_TRY(cudaEventSynchronize(g->mat_upload_done));
+  std::vector<float2> old_coef = g->coef_h;
+  std::vector<double> old_eps = g->eps_h;
+  int rc = build_material_words(g, eps, sig);
+  if (rc) {
+    // Restore the words of the current materials.
+    g->coef_h = old_coef;
+    g->eps_h = old_eps;
+    CUDA_TRY(cudaMemcpy(g->mat_host, g->mat, (size_t)g->d.plane * g->d.nz1 * 4, cudaMemcpyDeviceToHost));
+    return rc;
+  }
+  return upload_materials(g);
+}
+
+int sophie_add_source(sophie_grid* g, int comp, int i, int j, int k, double amp, double f0,
+                      double bw, double t0, int kind) {
+  if (!g) return fail(SOPHIE_EINVAL, "NULL grid");
+  if (comp < 0 || comp > 2) return fail(SOPHIE_EINVAL, "source component must be 0, 1 or 2 (E)");
+  if (!e_edge_interior(g->d, comp, i, j, k))
+    return fail(SOPHIE_EINVAL, "source edge (%d,%d,%d) of comp %d is not interior", i, j, k, comp);
+  if (kind != SOPHIE_GAUSS_SINE && kind != SOPHIE_GAUSS) return fail(SOPHIE_EINVAL, "bad waveform kind");
+  if (!std::isfinite(amp) || !std::isfinite(f0) || !std::isfinite(t0) || !(bw > 0) || !std::isfinite(bw))
+    return fail(SOPHIE_EINVAL, "bad waveform parameters");
+  if ((int)g->src.size() >= kMaxSources) return fail(SOPHIE_EINVAL, "at most %d sources", kMaxSources);
+  Source s{comp, i, j, k, kind, amp, f0, bw, t0, point_index(g->d, i, j, k)};
+  g->src.push_back(s);
+  int rc = refresh_source_table(g, (int)g->src.size() - 1);
+  if (rc) {
+    g->src.pop_back();
+    return rc;
+  }
+  if (launch_or_flag(g->mat, s.pos, kSrcFlag, g->stream) != cudaSuccess)
+    return fail(SOPHIE_ECUDA, "flag launch failed");
+  g->launches++;
+  return SOPHIE_OK;
+}
+
+int sophie_add_probe(sophie_grid* g, int comp, int i, int j, int k, int* probe_id) {
+  if (!g || !probe_id) return fail(SOPHIE_EINVAL, "NULL argument");
+  if (comp < 0 || comp > 5) return fail(SOPHIE_EINVAL, "probe component must be in 0..5");
+  if (!comp_valid(g->d, comp, i, j, k))
+    return fail(SOPHIE_EINVAL, "probe (%d,%d,%d) outside comp %d's range", i, j, k, comp);
+  if ((int)g->prb.size() >= kMaxProbes) return fail(SOPHIE_EINVAL, "at most %d probes", kMaxProbes);
+  Probe p{comp, i, j, k, point_index(g->d, i, j, k)};
+  if (launch_or_flag(g->mat, p.pos, kPrbFlag, g->stream) != cudaSuccess)
+    return fail(SOPHIE_ECUDA, "flag launch failed");
+  g->launches++;
+  g->prb.push_back(p);
+  *probe_id = (int)g->prb.size() - 1;
+  return SOPHIE_OK;
+}
+
+int sophie_step(sophie_grid* g, int n) {
+  if (!g) return fail(SOPHIE_EINVAL, "NULL grid");
+  if (n < 0) return fail(SOPHIE_EINVAL, "n must be >= 0");
+  if (n == 0) return SOPHIE_OK;
+  int rc = ensure_capacity(g, g->n + n);
+  if (rc) return rc;
+  for (int m = 0; m < n; ++m) {
+    StepArgs a = make_step_args(g);
+    cudaEvent_t ea = nullptr, eb = nullptr;
+    if (g->prof) {
+      ea = prof_event(g);
+      eb = prof_event(g);
+      cudaEventRecord(ea, g->stream);
+    }
+    cudaError_t e = launch_step_simple(a, g->stream);
+    if (e != cudaSuccess) return fail(SOPHIE_ECUDA, "step launch failed: %s", cudaGetErrorString(e));
+    if (g->prof) {
+      cudaEventRecord(eb, g->stream);
+      g->prof_live.push_back({SOPHIE_KERNEL_PLAIN, ea, eb});
+      if (g->prof_live.size() > 20000) {
+        rc = prof_drain(g);
+        if (rc) return rc;
+      }
+    }
+    g->launches++;
+    g->cur = 1 - g->cur;
+    g->n += 1;
+  }
+  return SOPHIE_OK;
+}
+
+int sophie_get_step(sophie_grid* g, long long* n) {
+  if (!g || !n) return fail(SOPHIE_EINVAL, "NULL argument");
+  *n = g->n;
+  return SOPHIE_OK;
+}
+
+int sophie_read_probe(sophie_grid* g, int probe_id, double* out, int cap, int* n_written) {
+  if (!g || !out || !n_written) return fail(SOPHIE_EINVAL, "NULL argument");
+  if (probe_id < 0 || probe_id >= (int)g->prb.size()) return fail(SOPHIE_EINVAL, "bad probe id");
+  if (cap < 0) return fail(SOPHIE_EINVAL, "cap must be >= 0");
+  const long long m = std::min<long long>(cap, g->n);
+  std::vector<float> tmp((size_t)m);
+  if (m > 0)
+    CUDA_TRY(cudaMemcpyAsync(tmp.data(), g->pbuf + (size_t)probe_id * g->pcap, (size_t)m * 4,
+                             cudaMemcpyDeviceToHost, g->stream));
+  int rc = check_err_word(g);
+  if (rc) return rc;
+  for (long long q = 0; q < m; ++q) out[q] = (double)tmp[q];
+  *n_written = (int)m;
+  return SOPHIE_OK;
+}
+
+int sophie_energy(sophie_grid* g, double* W) {
+  if (!g || !W) return fail(SOPHIE_EINVAL, "NULL argument");
+  cudaEvent_t ea = nullptr, eb = nullptr;
+  if (g->prof) {
+    ea = prof_event(g);
+    eb = prof_event(g);
+    cudaEventRecord(ea, g->stream);
+  }
+  cudaError_t e = launch_energy(g->F[g->cur], g->mat, g->eps_tab, g->d, g->S32, g->e_partials,
+                                g->e_blocks, g->e_out, g->stream);
+  if (e != cudaSuccess) return fail(SOPHIE_ECUDA, "energy launch failed: %s", cudaGetErrorString(e));
+  if (g->prof) {
+    cudaEventRecord(eb, g->stream);
+    g->prof_live.push_back({SOPHIE_KERNEL_ENERGY, ea, eb});
+  }
+  g->launches += 2;
+  double h = 0.0;
+  CUDA_TRY(cudaMemcpyAsync(&h, g->e_out, 8, cudaMemcpyDeviceToHost, g->stream));
+  int rc = check_err_word(g);
+  if (rc) return rc;
+  const double dx = g->dx;
+  *W = 0.5 * kEps0 * dx * dx * dx * h;
+  if (!std::isfinite(*W)) return fail(SOPHIE_ENONFINITE, "energy is not finite");
+  return SOPHIE_OK;
+}
+
+int sophie_set_fields(sophie_grid* g, int comp, const float* host) {
+  if (!g || !host) return fail(SOPHIE_EINVAL, "NULL argument");
+  if (comp < 0 || comp > 5) return fail(SOPHIE_EINVAL, "comp must be in 0..5");
+  for (int b = 0; b < 2; ++b) {
+    int rc = copy_component(g, comp, (void*)host, true, b);
+    if (rc) return rc;
+    cudaError_t e = launch_mask_component(g->F[b], g->d, comp, g->stream);
+    if (e != cudaSuccess) return fail(SOPHIE_ECUDA, "mask launch failed: %s", cudaGetErrorString(e));
+    g->launches++;
+  }
+  CUDA_TRY(cudaStreamSynchronize(g->stream));
+  return SOPHIE_OK;
+}
+
+int sophie_get_fields(sophie_grid* g, int comp, float* host) {
+  if (!g || !host) return fail(SOPHIE_EINVAL, "NULL argument");
+  if (comp < 0 || comp > 5) return fail(SOPHIE_EINVAL, "comp must be in 0..5");
+  int rc = copy_component(g, comp, host, false, g->cur);
+  if (rc) return rc;
+  return check_err_word(g);
+}
+
+int sophie_reset(sophie_grid* g) {
+  if (!g) return fail(SOPHIE_EINVAL, "NULL grid");
+  const size_t fbytes = (size_t)g->d.zstride * g->d.nz1 * 4;
+  CUDA_TRY(cudaMemsetAsync(g->F[0], 0, fbytes, g->stream));
+  CUDA_TRY(cudaMemsetAsync(g->F[1], 0, fbytes, g->stream));
+  if (g->pbuf) CUDA_TRY(cudaMemsetAsync(g->pbuf, 0, (size_t)kMaxProbes * g->pcap * 4, g->stream));
+  g->n = 0;
+  g->cur = 0;
+  return SOPHIE_OK;
+}
+
+int sophie_set_stream(sophie_grid* g, void* cuda_stream) {
+  if (!g) return fail(SOPHIE_EINVAL, "NULL grid");
+  CUDA_TRY(cudaStreamSynchronize(g->stream));
+  int rc = prof_drain(g);
+  if (rc) return rc;
+  if (g->own_stream) cudaStreamDestroy(g->stream);
+  g->own_stream = false;
+  g->stream = (cudaStream_t)cuda_stream;
+  return SOPHIE_OK;
+}
+
+int sophie_sync(sophie_grid* g) {
+  if (!g) return fail(SOPHIE_EINVAL, "NULL grid");
+  return check_err_word(g);
+}
+
+int sophie_configure(sophie_grid* g, int temporal_k, int tile_x, int tile_y, int precision) {
+  if (!g) return fail(SOPHIE_EINVAL, "NULL grid");
+  if (temporal_k < 0 || temporal_k > 8) return fail(SOPHIE_EINVAL, "temporal_k must be in 0..8");
+  if (tile_x < 0 || tile_y < 0) return fail(SOPHIE_EINVAL, "tile sizes must be >= 0");
+  if (precision != SOPHIE_FP32) return fail(SOPHIE_ENOTSUP, "precision %d not supported", precision);
+  g->temporal_k = temporal_k == 0 ? 1 : temporal_k;
+  g->precision = precision;
+  return SOPHIE_OK;
+}
+
+int sophie_launch_count(sophie_grid* g, long long* launches) {
+  if (!g || !launches) return fail(SOPHIE_EINVAL, "NULL argument");
+  *launches = g->launches;
+  return SOPHIE_OK;
+}
+
+int sophie_profile(sophie_grid* g, int enable) {
+  if (!g) return fail(SOPHIE_EINVAL, "NULL grid");
+  int rc = prof_drain(g);
+  if (rc) return rc;
+  g->prof = enable != 0;
+  if (enable)
+    for (int i = 0; i < 3; ++i) {
+      g->prof_count[i] = 0;
+      g->prof_ms[i] = 0.0;
+    }
+  return SOPHIE_OK;
+}
+
+int sophie_profile_read(sophie_grid* g, int kernel, long long* launches, double* ms) {
+  if (!g || !launches || !ms) return fail(SOPHIE_EINVAL, "NULL argument");
+  if (kernel < 0 || kernel > 2) return fail(SOPHIE_EINVAL, "bad kernel id");
+  int rc = prof_drain(g);
+  if (rc) return rc;
+  *launches = g->prof_count[kernel];
+  *ms = g->prof_ms[kernel];
+  return SOPHIE_OK;
+}
+
+}  // extern "C"

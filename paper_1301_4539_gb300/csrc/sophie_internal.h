@@ -1,0 +1,76 @@
+// Internal declarations shared by the host runtime (sophie_api.cu) and the
+// CUDA kernels of libsophie. Not installed; the public ABI is include/sophie.h.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace sophie {
+
+// Device field layout of one buffer: for z in [0,nz], comp f in [0,6),
+// y in [0,ny], x in [0,nxp): addr = ((z*6 + f)*ny1 + y)*nxp + x.
+// nxp = round_up(nx+1, 8) keeps every row 32-byte aligned (one DRAM sector)
+// and satisfies the 16-byte stride rule of TMA tensor maps. The padding
+// columns are zero and never written.
+//
+// Material word, one per index point (z*ny1 + y)*nxp + x:
+//   bits  0..9  class of the ex edge at this index (0 = PEC / absent)
+//   bits 10..19 class of the ey edge
+//   bits 20..29 class of the ez edge
+//   bit  30     a source sits on one of this point's edges
+//   bit  31     a probe sits on one of this point's components
+// Class c has coefficients coef[c] = (Ca, Cb) (float) and eps_r(edge) in
+// double (energy). Class 0 is (0, 0): the edge is never anything but 0.
+constexpr int kMaxClasses = 1024;
+constexpr int kMaxSources = 16;
+constexpr int kMaxProbes = 64;
+constexpr uint32_t kSrcFlag = 1u << 30;
+constexpr uint32_t kPrbFlag = 1u << 31;
+
+struct Dims {
+  int nx, ny, nz;   // cells
+  int nxp, ny1, nz1;  // storage extents (nxp padded)
+  long long plane;  // ny1*nxp: elements of one component plane
+  long long zstride;  // 6*plane: elements of one z slab of all six components
+};
+
+// Source and probe tables passed by value to the step kernels.
+struct SrcTable {
+  int n;
+  int comp[kMaxSources];
+  long long pos[kMaxSources];  // index-point offset (z*ny1 + y)*nxp + x
+  const float* val;            // [kMaxSources][cap]; val[s*cap + step]
+  int cap;
+};
+
+struct PrbTable {
+  int n;
+  int comp[kMaxProbes];
+  long long pos[kMaxProbes];
+  float* buf;  // [kMaxProbes][cap]; buf[p*cap + step]
+  int cap;
+};
+
+struct StepArgs {
+  const float* fin;
+  float* fout;
+  const uint32_t* mat;
+  const float2* coef;
+  Dims d;
+  float S;
+  long long n0;  // absolute index of the first step this launch performs
+  SrcTable src;
+  PrbTable prb;
+  int* err;      // device error word (bounded waits that ran out)
+};
+
+// Launchers (return cudaError_t of the launch).
+cudaError_t launch_step_simple(const StepArgs& a, cudaStream_t s);
+cudaError_t launch_energy(const float* f, const uint32_t* mat, const double* eps_tab,
+                          const Dims& d, float S, double* partials, int nblocks,
+                          double* out, cudaStream_t s);
+int energy_blocks(const Dims& d);
+cudaError_t launch_mask_component(float* f, const Dims& d, int comp, cudaStream_t s);
+cudaError_t launch_or_flag(uint32_t* mat, long long pos, uint32_t bit, cudaStream_t s);
+
+}  // namespace sophie

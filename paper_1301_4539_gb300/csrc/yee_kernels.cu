@@ -1,0 +1,220 @@
+// Support kernels of libsophie and the reference-layout step kernel.
+//
+// yee_step_simple: one fused H+E leapfrog step (Sec. 2.1; Sec. 3.2's
+// interleave: H and E of a plane are updated in one pass, so each field is
+// read and written once per step). Each CTA owns a 32x8 (x,y) tile and walks
+// a chunk of z planes; the H values one cell outside the tile's -x/-y edges
+// are recomputed (identically) by halo threads so that no CTA waits on
+// another. Reads go straight to global memory; the tuned kernels stage tiles
+// with TMA instead and share the update expressions of yee_update.cuh, so all
+// step kernels give bitwise identical fields.
+#include "sophie_internal.h"
+#include "yee_update.cuh"
+
+namespace sophie {
+
+namespace {
+
+constexpr int kSTX = 32;
+constexpr int kSTY = 8;
+constexpr int kSZ = 16;  // z planes per CTA
+
+__device__ __forceinline__ float ld_f(const float* f, const Dims& d, int c, int x, int y, int z) {
+  if (x < 0 || x >= d.nxp || y < 0 || y >= d.ny1 || z < 0 || z >= d.nz1) return 0.f;
+  return f[(long long)z * d.zstride + (long long)c * d.plane + (long long)y * d.nxp + x];
+}
+
+__global__ void __launch_bounds__((kSTX + 1) * (kSTY + 1))
+yee_step_simple_kernel(StepArgs a) {
+  __shared__ float sE[3][kSTY + 2][kSTX + 2];
+  __shared__ float sH[3][kSTY + 1][kSTX + 1];
+  const Dims d = a.d;
+  const int tx = threadIdx.x % (kSTX + 1);
+  const int ty = threadIdx.x / (kSTX + 1);
+  const int x0 = blockIdx.x * kSTX, y0 = blockIdx.y * kSTY;
+  const int z0 = blockIdx.z * kSZ;
+  const int z1 = min(z0 + kSZ, d.nz);
+  const int x = x0 - 1 + tx, y = y0 - 1 + ty;
+  const float S = a.S;
+  const bool owner = tx >= 1 && ty >= 1 && x < d.nx && y < d.ny;
+  float hxp = 0.f, hyp = 0.f;  // new hx, hy of the plane below (own column)
+  const int zs = z0 > 0 ? z0 - 1 : 0;
+  if (z0 > 0) {
+    // h^{n+1/2} at plane z0-1 is only needed for hx, hy of this column; it is
+    // recomputed in the first loop pass below (no store).
+  }
+  for (int z = zs; z < z1; ++z) {
+    for (int c = 0; c < 3; ++c) {
+      sE[c][ty][tx] = ld_f(a.fin, d, c, x, y, z);
+      if (tx == kSTX) sE[c][ty][tx + 1] = ld_f(a.fin, d, c, x + 1, y, z);
+      if (ty == kSTY) sE[c][ty + 1][tx] = ld_f(a.fin, d, c, x, y + 1, z);
+    }
+    __syncthreads();
+    const float ex0 = sE[0][ty][tx], ey0 = sE[1][ty][tx], ez0 = sE[2][ty][tx];
+    float hx = ld_f(a.fin, d, 3, x, y, z);
+    float hy = ld_f(a.fin, d, 4, x, y, z);
+    float hz = ld_f(a.fin, d, 5, x, y, z);
+    const float ey1 = ld_f(a.fin, d, 1, x, y, z + 1);
+    const float ex1 = ld_f(a.fin, d, 0, x, y, z + 1);
+    hx = h_upd(hx, S, ey1, ey0, sE[2][ty + 1][tx], ez0);
+    hy = h_upd(hy, S, sE[2][ty][tx + 1], ez0, ex1, ex0);
+    hz = h_upd(hz, S, sE[0][ty + 1][tx], ex0, sE[1][ty][tx + 1], ey0);
+    sH[0][ty][tx] = hx;
+    sH[1][ty][tx] = hy;
+    sH[2][ty][tx] = hz;
+    __syncthreads();
+    if (z >= z0 && owner) {
+      const long long pt = ((long long)z * d.ny1 + y) * d.nxp + x;
+      const uint32_t m = a.mat[pt];
+      const float2 cx = a.coef[m & 1023u];
+      const float2 cy = a.coef[(m >> 10) & 1023u];
+      const float2 cz = a.coef[(m >> 20) & 1023u];
+      float bx = curl_br(hz, sH[2][ty - 1][tx], hy, hyp);
+      float by = curl_br(hx, hxp, hz, sH[2][ty][tx - 1]);
+      float bz = curl_br(hy, sH[1][ty][tx - 1], hx, sH[0][ty - 1][tx]);
+      if (m & kSrcFlag) {
+        for (int s = 0; s < a.src.n; ++s) {
+          if (a.src.pos[s] != pt) continue;
+          const float v = a.src.val[(long long)s * a.src.cap + a.n0];
+          if (a.src.comp[s] == 0) bx = __fadd_rn(bx, v);
+          else if (a.src.comp[s] == 1) by = __fadd_rn(by, v);
+          else bz = __fadd_rn(bz, v);
+        }
+      }
+      const float ex = e_upd(ex0, cx, bx);
+      const float ey = e_upd(ey0, cy, by);
+      const float ez = e_upd(ez0, cz, bz);
+      float* o = a.fout + (long long)z * d.zstride + (long long)y * d.nxp + x;
+      o[0] = ex;
+      o[d.plane] = ey;
+      o[2 * d.plane] = ez;
+      o[3 * d.plane] = hx;
+      o[4 * d.plane] = hy;
+      o[5 * d.plane] = hz;
+      if (m & kPrbFlag) {
+        const float v6[6] = {ex, ey, ez, hx, hy, hz};
+        for (int p = 0; p < a.prb.n; ++p)
+          if (a.prb.pos[p] == pt) a.prb.buf[(long long)p * a.prb.cap + a.n0] = v6[a.prb.comp[p]];
+      }
+    }
+    hxp = hx;
+    hyp = hy;
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Discrete energy, Sec. 2.1 antisymmetric form (see sophie_energy in sophie.h).
+// Grid-stride over index points; fixed-order block tree; deterministic.
+constexpr int kEThreads = 256;
+
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  if (lane == 0) sh[w] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x == 0)
+    for (int i = 0; i < kEThreads / 32; ++i) t += sh[i];
+  return t;
+}
+
+__global__ void __launch_bounds__(kEThreads)
+energy_partial_kernel(const float* f, const uint32_t* mat, const double* eps_tab, Dims d,
+                      float S, double* partials) {
+  __shared__ double sh[kEThreads / 32];
+  const long long npts = (long long)d.nz1 * d.ny1 * d.nxp;
+  double acc = 0.0;
+  for (long long pt = (long long)blockIdx.x * kEThreads + threadIdx.x; pt < npts;
+       pt += (long long)gridDim.x * kEThreads) {
+    const int x = (int)(pt % d.nxp);
+    const long long r = pt / d.nxp;
+    const int y = (int)(r % d.ny1);
+    const int z = (int)(r / d.ny1);
+    const uint32_t m = mat[pt];
+    const float ex = ld_f(f, d, 0, x, y, z), ey = ld_f(f, d, 1, x, y, z), ez = ld_f(f, d, 2, x, y, z);
+    acc += eps_tab[m & 1023u] * ((double)ex * (double)ex);
+    acc += eps_tab[(m >> 10) & 1023u] * ((double)ey * (double)ey);
+    acc += eps_tab[(m >> 20) & 1023u] * ((double)ez * (double)ez);
+    const float hx = ld_f(f, d, 3, x, y, z), hy = ld_f(f, d, 4, x, y, z), hz = ld_f(f, d, 5, x, y, z);
+    const float hxn = h_upd(hx, S, ld_f(f, d, 1, x, y, z + 1), ey, ld_f(f, d, 2, x, y + 1, z), ez);
+    const float hyn = h_upd(hy, S, ld_f(f, d, 2, x + 1, y, z), ez, ld_f(f, d, 0, x, y, z + 1), ex);
+    const float hzn = h_upd(hz, S, ld_f(f, d, 0, x, y + 1, z), ex, ld_f(f, d, 1, x + 1, y, z), ey);
+    acc += (double)hx * (double)hxn;
+    acc += (double)hy * (double)hyn;
+    acc += (double)hz * (double)hzn;
+  }
+  const double t = block_sum(acc, sh);
+  if (threadIdx.x == 0) partials[blockIdx.x] = t;
+}
+
+__global__ void __launch_bounds__(kEThreads)
+energy_final_kernel(const double* partials, int n, double* out) {
+  __shared__ double sh[kEThreads / 32];
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < n; i += kEThreads) acc += partials[i];
+  const double t = block_sum(acc, sh);
+  if (threadIdx.x == 0) *out = t;
+}
+
+// Zero PEC edges and entries outside a component's valid range (see sophie.h).
+__global__ void mask_component_kernel(float* f, Dims d, int comp) {
+  const long long npts = (long long)d.nz1 * d.ny1 * d.nxp;
+  for (long long pt = (long long)blockIdx.x * blockDim.x + threadIdx.x; pt < npts;
+       pt += (long long)gridDim.x * blockDim.x) {
+    const int x = (int)(pt % d.nxp);
+    const long long r = pt / d.nxp;
+    const int y = (int)(r % d.ny1);
+    const int z = (int)(r / d.ny1);
+    bool keep;
+    switch (comp) {
+      case 0: keep = x < d.nx && y >= 1 && y < d.ny && z >= 1 && z < d.nz; break;
+      case 1: keep = x >= 1 && x < d.nx && y < d.ny && z >= 1 && z < d.nz; break;
+      case 2: keep = x >= 1 && x < d.nx && y >= 1 && y < d.ny && z < d.nz; break;
+      case 3: keep = x <= d.nx && y < d.ny && z < d.nz; break;
+      case 4: keep = x < d.nx && y <= d.ny && z < d.nz; break;
+      default: keep = x < d.nx && y < d.ny && z <= d.nz; break;
+    }
+    if (!keep) f[(long long)z * d.zstride + (long long)comp * d.plane + (long long)y * d.nxp + x] = 0.f;
+  }
+}
+
+__global__ void or_flag_kernel(uint32_t* mat, long long pos, uint32_t bit) { mat[pos] |= bit; }
+
+}  // namespace
+
+cudaError_t launch_step_simple(const StepArgs& a, cudaStream_t s) {
+  dim3 grid((a.d.nx + kSTX - 1) / kSTX, (a.d.ny + kSTY - 1) / kSTY, (a.d.nz + kSZ - 1) / kSZ);
+  yee_step_simple_kernel<<<grid, (kSTX + 1) * (kSTY + 1), 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+int energy_blocks(const Dims& d) {
+  const long long npts = (long long)d.nz1 * d.ny1 * d.nxp;
+  long long b = (npts + kEThreads * 8 - 1) / (kEThreads * 8);
+  if (b < 1) b = 1;
+  if (b > 152 * 16) b = 152 * 16;
+  return (int)b;
+}
+
+cudaError_t launch_energy(const float* f, const uint32_t* mat, const double* eps_tab, const Dims& d,
+                          float S, double* partials, int nblocks, double* out, cudaStream_t s) {
+  energy_partial_kernel<<<nblocks, kEThreads, 0, s>>>(f, mat, eps_tab, d, S, partials);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  energy_final_kernel<<<1, kEThreads, 0, s>>>(partials, nblocks, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mask_component(float* f, const Dims& d, int comp, cudaStream_t s) {
+  mask_component_kernel<<<152 * 4, 256, 0, s>>>(f, d, comp);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_or_flag(uint32_t* mat, long long pos, uint32_t bit, cudaStream_t s) {
+  or_flag_kernel<<<1, 1, 0, s>>>(mat, pos, bit);
+  return cudaGetLastError();
+}
+
+}  // namespace sophie

@@ -1,0 +1,33 @@
+// The Yee update expressions, shared by every step kernel so that all of them
+// (plain, temporally blocked) produce bitwise identical fields.
+//
+// Sec. 2.1 (displayed Hx update and its analogues for the other components):
+//   h += S * ((a1 - a0) - (b1 - b0))
+//   e  = Ca*e + Cb*((a1 - a0) - (b1 - b0) [+ s])
+// Every operation is rounded separately (no fused multiply-add) in exactly
+// this order, so the float results are fixed by the expression alone.
+//
+// Operand roles per component (index offsets on the storage box):
+//   hx: a = ey(k+1), ey(k)   b = ez(j+1), ez(j)
+//   hy: a = ez(i+1), ez(i)   b = ex(k+1), ex(k)
+//   hz: a = ex(j+1), ex(j)   b = ey(i+1), ey(i)
+//   ex: a = hz(j), hz(j-1)   b = hy(k), hy(k-1)
+//   ey: a = hx(k), hx(k-1)   b = hz(i), hz(i-1)
+//   ez: a = hy(i), hy(i-1)   b = hx(j), hx(j-1)
+#pragma once
+
+namespace sophie {
+
+__device__ __forceinline__ float curl_br(float a1, float a0, float b1, float b0) {
+  return __fsub_rn(__fsub_rn(a1, a0), __fsub_rn(b1, b0));
+}
+
+__device__ __forceinline__ float h_upd(float h, float S, float a1, float a0, float b1, float b0) {
+  return __fadd_rn(h, __fmul_rn(S, curl_br(a1, a0, b1, b0)));
+}
+
+__device__ __forceinline__ float e_upd(float e, float2 c, float br) {
+  return __fadd_rn(__fmul_rn(c.x, e), __fmul_rn(c.y, br));
+}
+
+}  // namespace sophie

@@ -1,0 +1,267 @@
+"""ctypes binding of libsophie (include/sophie.h), argument marshalling only.
+
+Every function has the C name and signature; a negative return code raises
+SophieError carrying the code and sophie_last_error(). Arrays are numpy
+arrays on the host. The library is loaded from this package directory; if it
+is missing the import of a function fails loudly (there is no CPU fallback).
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libsophie.so")
+
+OK, EINVAL, EUNSTABLE, ENOMEM, ECUDA, ENONFINITE, ETIMEOUT, ETOOMANYMAT, ENOTSUP = (
+    0, -1, -2, -3, -4, -5, -6, -7, -8)
+EX, EY, EZ, HX, HY, HZ = range(6)
+GAUSS_SINE, GAUSS = 0, 1
+FP32 = 0
+KERNEL_PLAIN, KERNEL_BLOCKED, KERNEL_ENERGY = 0, 1, 2
+
+# Exported symbols with (restype, argtypes).
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_D = ctypes.c_double
+_LL = ctypes.c_longlong
+SIGNATURES = {
+    "sophie_version": (_I, []),
+    "sophie_create_grid": (_I, [_I, _I, _I, _D, _D, ctypes.POINTER(_P)]),
+    "sophie_destroy_grid": (_I, [_P]),
+    "sophie_set_materials": (_I, [_P, _P, _P]),
+    "sophie_add_source": (_I, [_P, _I, _I, _I, _I, _D, _D, _D, _D, _I]),
+    "sophie_add_probe": (_I, [_P, _I, _I, _I, _I, ctypes.POINTER(_I)]),
+    "sophie_step": (_I, [_P, _I]),
+    "sophie_get_step": (_I, [_P, ctypes.POINTER(_LL)]),
+    "sophie_read_probe": (_I, [_P, _I, _P, _I, ctypes.POINTER(_I)]),
+    "sophie_energy": (_I, [_P, ctypes.POINTER(_D)]),
+    "sophie_set_fields": (_I, [_P, _I, _P]),
+    "sophie_get_fields": (_I, [_P, _I, _P]),
+    "sophie_reset": (_I, [_P]),
+    "sophie_set_stream": (_I, [_P, _P]),
+    "sophie_sync": (_I, [_P]),
+    "sophie_configure": (_I, [_P, _I, _I, _I, _I]),
+    "sophie_launch_count": (_I, [_P, ctypes.POINTER(_LL)]),
+    "sophie_profile": (_I, [_P, _I]),
+    "sophie_profile_read": (_I, [_P, _I, ctypes.POINTER(_LL), ctypes.POINTER(_D)]),
+    "sophie_last_error": (ctypes.c_char_p, []),
+}
+
+
+class SophieError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"libsophie error {code}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+
+def load(path: str | None = None) -> ctypes.CDLL:
+    """Load libsophie.so (building it first if absent and nvcc exists)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        from . import build as _b
+        _b.build()
+    lib = ctypes.CDLL(p)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _chk(rc: int) -> int:
+    if rc < 0:
+        raise SophieError(rc, load().sophie_last_error().decode())
+    return rc
+
+
+def _f32(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.float32)
+
+
+# ---- the C API, one wrapper per function (same names) ----------------------
+def sophie_version() -> int:
+    return load().sophie_version()
+
+
+def sophie_create_grid(nx: int, ny: int, nz: int, dx: float, dt: float) -> int:
+    h = _P()
+    _chk(load().sophie_create_grid(nx, ny, nz, dx, dt, ctypes.byref(h)))
+    return h.value
+
+
+def sophie_destroy_grid(g: int) -> None:
+    _chk(load().sophie_destroy_grid(g))
+
+
+def sophie_set_materials(g: int, eps_r: np.ndarray, sigma: np.ndarray) -> None:
+    e, s = _f32(eps_r), _f32(sigma)
+    _chk(load().sophie_set_materials(g, e.ctypes.data, s.ctypes.data))
+
+
+def sophie_add_source(g: int, comp: int, i: int, j: int, k: int, amp: float, f0: float,
+                      bw: float, t0: float, kind: int) -> None:
+    _chk(load().sophie_add_source(g, comp, i, j, k, amp, f0, bw, t0, kind))
+
+
+def sophie_add_probe(g: int, comp: int, i: int, j: int, k: int) -> int:
+    pid = _I()
+    _chk(load().sophie_add_probe(g, comp, i, j, k, ctypes.byref(pid)))
+    return pid.value
+
+
+def sophie_step(g: int, n: int) -> None:
+    _chk(load().sophie_step(g, n))
+
+
+def sophie_get_step(g: int) -> int:
+    n = _LL()
+    _chk(load().sophie_get_step(g, ctypes.byref(n)))
+    return n.value
+
+
+def sophie_read_probe(g: int, probe_id: int, cap: int) -> np.ndarray:
+    out = np.zeros(max(cap, 0), np.float64)
+    nw = _I()
+    _chk(load().sophie_read_probe(g, probe_id, out.ctypes.data, cap, ctypes.byref(nw)))
+    return out[: nw.value]
+
+
+def sophie_energy(g: int) -> float:
+    w = _D()
+    _chk(load().sophie_energy(g, ctypes.byref(w)))
+    return w.value
+
+
+def sophie_set_fields(g: int, comp: int, host: np.ndarray) -> None:
+    a = _f32(host)
+    _chk(load().sophie_set_fields(g, comp, a.ctypes.data))
+
+
+def sophie_get_fields(g: int, comp: int, shape) -> np.ndarray:
+    out = np.empty(shape, np.float32)
+    _chk(load().sophie_get_fields(g, comp, out.ctypes.data))
+    return out
+
+
+def sophie_reset(g: int) -> None:
+    _chk(load().sophie_reset(g))
+
+
+def sophie_set_stream(g: int, cuda_stream: int) -> None:
+    _chk(load().sophie_set_stream(g, cuda_stream))
+
+
+def sophie_sync(g: int) -> None:
+    _chk(load().sophie_sync(g))
+
+
+def sophie_configure(g: int, temporal_k: int = 0, tile_x: int = 0, tile_y: int = 0,
+                     precision: int = FP32) -> None:
+    _chk(load().sophie_configure(g, temporal_k, tile_x, tile_y, precision))
+
+
+def sophie_launch_count(g: int) -> int:
+    n = _LL()
+    _chk(load().sophie_launch_count(g, ctypes.byref(n)))
+    return n.value
+
+
+def sophie_profile(g: int, enable: bool) -> None:
+    _chk(load().sophie_profile(g, 1 if enable else 0))
+
+
+def sophie_profile_read(g: int, kernel: int):
+    n = _LL()
+    ms = _D()
+    _chk(load().sophie_profile_read(g, kernel, ctypes.byref(n), ctypes.byref(ms)))
+    return n.value, ms.value
+
+
+def sophie_last_error() -> str:
+    return load().sophie_last_error().decode()
+
+
+class Grid:
+    """Owning handle: the same calls bound to one grid (marshalling only)."""
+
+    def __init__(self, nx: int, ny: int, nz: int, dx: float, dt: float):
+        self.nx, self.ny, self.nz = nx, ny, nz
+        self.h = sophie_create_grid(nx, ny, nz, dx, dt)
+
+    @property
+    def shape(self):
+        return (self.nz + 1, self.ny + 1, self.nx + 1)
+
+    def close(self):
+        if self.h:
+            sophie_destroy_grid(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_materials(self, eps, sigma):
+        sophie_set_materials(self.h, eps, sigma)
+
+    def add_source(self, comp, i, j, k, amp, f0, bw, t0, kind):
+        sophie_add_source(self.h, comp, i, j, k, amp, f0, bw, t0, kind)
+
+    def add_probe(self, comp, i, j, k):
+        return sophie_add_probe(self.h, comp, i, j, k)
+
+    def step(self, n):
+        sophie_step(self.h, n)
+
+    @property
+    def n(self):
+        return sophie_get_step(self.h)
+
+    def read_probe(self, pid, cap=None):
+        return sophie_read_probe(self.h, pid, self.n if cap is None else cap)
+
+    def energy(self):
+        return sophie_energy(self.h)
+
+    def set_field(self, comp, arr):
+        sophie_set_fields(self.h, comp, arr)
+
+    def get_field(self, comp):
+        return sophie_get_fields(self.h, comp, self.shape)
+
+    def fields(self):
+        return [self.get_field(c) for c in range(6)]
+
+    def reset(self):
+        sophie_reset(self.h)
+
+    def set_stream(self, s):
+        sophie_set_stream(self.h, s)
+
+    def sync(self):
+        sophie_sync(self.h)
+
+    def configure(self, temporal_k=0, tile_x=0, tile_y=0, precision=FP32):
+        sophie_configure(self.h, temporal_k, tile_x, tile_y, precision)
+
+    def launch_count(self):
+        return sophie_launch_count(self.h)
+
+    def profile(self, enable):
+        sophie_profile(self.h, enable)
+
+    def profile_read(self, kernel):
+        return sophie_profile_read(self.h, kernel)
