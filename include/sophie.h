@@ -181,7 +181,9 @@ int sophie_sync(sophie_grid *g);
 
 /*
  * temporal_k: steps fused per launch (1 = plain kernel, 2..8 = temporally
- * blocked), 0 = library default. tile_x, tile_y: 0 = default (reserved).
+ * blocked), 0 = library default. tile_x: 0 or 64 = TMA-staged 64x16 tiles
+ * (default), 32 = 32x8 tiles with direct loads (a slower reference kernel;
+ * identical results); tile_y: reserved, 0.
  * precision: SOPHIE_FP32 (others: ENOTSUP). Errors: EINVAL, ENOTSUP.
  */
 int sophie_configure(sophie_grid *g, int temporal_k, int tile_x, int tile_y, int precision);

@@ -66,6 +66,11 @@ struct ProfEntry {
 
 struct sophie_grid {
   Dims d{};
+  CUtensorMap tmF[2];  // TMA maps of the two field buffers
+  CUtensorMap tmM;     // TMA map of the material words
+  PlainTiling ptile{};
+  int num_sms = 0;
+  bool use_simple = false;  // tile_x == 32: untiled-load reference kernel
   double dx = 0, dt = 0, S64 = 0;
   float S32 = 0;
   float* F[2] = {nullptr, nullptr};
@@ -495,6 +500,18 @@ int sophie_create_grid(int nx, int ny, int nz, double dx, double dt, sophie_grid
       rc = fail(SOPHIE_ECUDA, "cudaMemsetAsync failed");
       break;
     }
+    {
+      int dev = 0;
+      cudaGetDevice(&dev);
+      cudaDeviceGetAttribute(&g->num_sms, cudaDevAttrMultiProcessorCount, dev);
+      if (g->num_sms <= 0) g->num_sms = 1;
+    }
+    if (!encode_plain_maps(d, g->F[0], g->mat, &g->tmF[0], &g->tmM) ||
+        !encode_plain_maps(d, g->F[1], nullptr, &g->tmF[1], nullptr)) {
+      rc = fail(SOPHIE_ECUDA, "cuTensorMapEncodeTiled failed");
+      break;
+    }
+    g->ptile = plain_tiling(d, g->num_sms);
     rc = build_material_words(g, nullptr, nullptr);
     if (rc) break;
     rc = upload_materials(g);
@@ -595,7 +612,8 @@ int sophie_step(sophie_grid* g, int n) {
       eb = prof_event(g);
       cudaEventRecord(ea, g->stream);
     }
-    cudaError_t e = launch_step_simple(a, g->stream);
+    cudaError_t e = g->use_simple ? launch_step_simple(a, g->stream)
+                                  : launch_step_plain(a, g->tmF[g->cur], g->tmM, g->ptile, g->stream);
     if (e != cudaSuccess) return fail(SOPHIE_ECUDA, "step launch failed: %s", cudaGetErrorString(e));
     if (g->prof) {
       cudaEventRecord(eb, g->stream);
@@ -714,7 +732,9 @@ int sophie_configure(sophie_grid* g, int temporal_k, int tile_x, int tile_y, int
   if (temporal_k < 0 || temporal_k > 8) return fail(SOPHIE_EINVAL, "temporal_k must be in 0..8");
   if (tile_x < 0 || tile_y < 0) return fail(SOPHIE_EINVAL, "tile sizes must be >= 0");
   if (precision != SOPHIE_FP32) return fail(SOPHIE_ENOTSUP, "precision %d not supported", precision);
+  if (tile_x != 0 && tile_x != 32 && tile_x != 64) return fail(SOPHIE_EINVAL, "tile_x must be 0, 32 or 64");
   g->temporal_k = temporal_k == 0 ? 1 : temporal_k;
+  g->use_simple = tile_x == 32;
   g->precision = precision;
   return SOPHIE_OK;
 }

@@ -2,6 +2,7 @@
 // CUDA kernels of libsophie. Not installed; the public ABI is include/sophie.h.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -64,8 +65,19 @@ struct StepArgs {
   int* err;      // device error word (bounded waits that ran out)
 };
 
+// Work decomposition of the TMA step kernels: (x tile, y tile, z chunk) units
+// walked by `grid` persistent CTAs.
+struct PlainTiling {
+  int tiles_x, tiles_y, zchunk, grid;
+  long long units;
+};
+
 // Launchers (return cudaError_t of the launch).
 cudaError_t launch_step_simple(const StepArgs& a, cudaStream_t s);
+bool encode_plain_maps(const Dims& d, float* fields, uint32_t* mat, CUtensorMap* tmF, CUtensorMap* tmM);
+PlainTiling plain_tiling(const Dims& d, int num_sms);
+cudaError_t launch_step_plain(const StepArgs& a, const CUtensorMap& tmF, const CUtensorMap& tmM,
+                              const PlainTiling& t, cudaStream_t s);
 cudaError_t launch_energy(const float* f, const uint32_t* mat, const double* eps_tab,
                           const Dims& d, float S, double* partials, int nblocks,
                           double* out, cudaStream_t s);

@@ -1,0 +1,356 @@
+// yee_plain: one fused H+E leapfrog step per launch, TMA-staged (sm_103a).
+//
+// Method: Sec. 2.1 leapfrog, with Sec. 3.2's interleave and Sec. 3.3's plane
+// by plane order: within one (x,y) tile the H update of plane z is followed by
+// the E update of plane z, so each field is read once and written once per
+// step (48 B of fields per cell-update + a 4 B material word).
+//
+// GPU design:
+//  * Persistent CTAs walk a list of work units (64x16 output tile, chunk of z
+//    planes). One producer warp streams planes of all six fields plus the
+//    material words into a 3-stage shared-memory ring with 4-D/3-D TMA tile
+//    loads (72x18 box: the tile plus a 4-column / 1-row halo; out-of-range
+//    parts of the box arrive as zeros, which is exactly the PEC / outside
+//    value). Full/empty mbarriers pace the ring; every wait is bounded.
+//  * Eight consumer warps own two rows each; a lane owns two adjacent x.
+//    H of the plane is computed in place in the ring (plus the halo H at x0-1
+//    and y0-1, recomputed identically to the neighbouring tile's), one named
+//    barrier, then E from the updated H. H of the plane below stays in
+//    registers (z streaming), so only x-y neighbours go through shared memory.
+//  * Results go straight from registers to HBM (the other ping-pong buffer)
+//    with coalesced 8-byte stores.
+#include "sophie_internal.h"
+#include "tma_util.cuh"
+#include "yee_update.cuh"
+
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+
+namespace sophie {
+
+namespace {
+
+constexpr int kPX = 64, kPY = 16;
+constexpr int kBX = kPX + 8, kBY = kPY + 2;
+constexpr int kNS = 3;
+constexpr int kCW = kPY / 2;  // consumer warps
+constexpr int kConsumers = kCW * 32;
+constexpr int kThreads = kConsumers + 32;
+constexpr uint32_t kFieldBytes = kBX * kBY * 6 * 4;
+constexpr uint32_t kMatBytes = kBX * kBY * 4;
+constexpr uint32_t kLoadBytes = kFieldBytes + kMatBytes;
+constexpr uint32_t kStageBytes = (kLoadBytes + 127) / 128 * 128;
+constexpr uint32_t kBarOff = kNS * kStageBytes;
+constexpr uint32_t kSmemBytes = kBarOff + 2 * kNS * 8 + 128;
+
+static_assert(kFieldBytes % 128 == 0, "material box must start 128-byte aligned");
+
+__device__ __forceinline__ int FI(int f, int r, int c) { return (f * kBY + r) * kBX + c; }
+
+struct Unit {
+  int x0, y0, z0, z1;
+};
+
+__device__ __forceinline__ Unit unit_of(long long u, const PlainTiling& t, int nz) {
+  Unit w;
+  const int tx = (int)(u % t.tiles_x);
+  const long long q = u / t.tiles_x;
+  const int ty = (int)(q % t.tiles_y);
+  const int zc = (int)(q / t.tiles_y);
+  w.x0 = tx * kPX;
+  w.y0 = ty * kPY;
+  w.z0 = zc * t.zchunk;
+  w.z1 = min(w.z0 + t.zchunk, nz);
+  return w;
+}
+
+__device__ __forceinline__ void set_err(int* err, int code) { atomicOr(err, code); }
+
+__global__ void __launch_bounds__(kThreads, 2)
+yee_plain_kernel(const __grid_constant__ CUtensorMap tmF, const __grid_constant__ CUtensorMap tmM,
+                 StepArgs a, PlainTiling t) {
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* base = reinterpret_cast<unsigned char*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+  const uint32_t bar0 = smem_u32(base + kBarOff);
+  auto full = [&](int s) { return bar0 + 8u * s; };
+  auto empty = [&](int s) { return bar0 + 8u * (kNS + s); };
+  auto sF = [&](int s) { return reinterpret_cast<float*>(base + s * kStageBytes); };
+  auto sM = [&](int s) { return reinterpret_cast<const uint32_t*>(base + s * kStageBytes + kFieldBytes); };
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kNS; ++s) {
+      mbar_init(full(s), 1);
+      mbar_init(empty(s), kCW);
+    }
+    fence_mbar_init();
+  }
+  __syncthreads();
+  const Dims d = a.d;
+
+  if (warp == kCW) {
+    // ---------------- producer warp ----------------
+    if (lane != 0) return;
+    prefetch_tmap(&tmF);
+    prefetch_tmap(&tmM);
+    long long L = 0;
+    bool ok = true;
+    for (long long u = blockIdx.x; u < t.units && ok; u += gridDim.x) {
+      const Unit w = unit_of(u, t, d.nz);
+      const int ps = w.z0 > 0 ? w.z0 - 1 : 0;
+      for (int p = ps; p <= w.z1; ++p, ++L) {
+        const int s = (int)(L % kNS);
+        if (L >= kNS && !mbar_wait(empty(s), (uint32_t)(((L / kNS) - 1) & 1))) {
+          set_err(a.err, 1);
+          ok = false;
+          break;
+        }
+        mbar_arrive_expect_tx(full(s), kLoadBytes);
+        tma_load_4d(smem_u32(sF(s)), &tmF, w.x0 - 4, w.y0 - 1, 0, p, full(s));
+        tma_load_3d(smem_u32(sM(s)), &tmM, w.x0 - 4, w.y0 - 1, p, full(s));
+      }
+    }
+    if (!ok) {
+      // Give the copies already issued a bounded chance to land before exit.
+      for (long long e = L - 1; e >= 0 && e >= L - kNS; --e)
+        mbar_wait(full((int)(e % kNS)), (uint32_t)((e / kNS) & 1));
+    }
+    return;
+  }
+
+  // ---------------- consumer warps ----------------
+  const int c0 = 4 + 2 * lane;
+  const int r0 = 1 + 2 * warp;
+  int hr = -1, hc = -1;  // halo H position computed by this lane
+  if (lane < 2) {
+    hr = r0 + lane;
+    hc = 3;
+  } else if (lane < 10) {
+    hr = 0;
+    hc = 4 + 8 * warp + (lane - 2);
+  }
+  const float S = a.S;
+  long long C = 0;
+  bool abort = false;
+  for (long long u = blockIdx.x; u < t.units && !abort; u += gridDim.x) {
+    const Unit w = unit_of(u, t, d.nz);
+    const int ps = w.z0 > 0 ? w.z0 - 1 : 0;
+    float hxp[2][2] = {{0.f, 0.f}, {0.f, 0.f}}, hyp[2][2] = {{0.f, 0.f}, {0.f, 0.f}};
+    for (int z = ps; z < w.z1; ++z, ++C) {
+      const int sc = (int)(C % kNS), sn = (int)((C + 1) % kNS);
+      const bool ok = mbar_wait(full(sc), (uint32_t)((C / kNS) & 1)) &&
+                      mbar_wait(full(sn), (uint32_t)(((C + 1) / kNS) & 1));
+      if (!ok) set_err(a.err, 2);
+      float* F = sF(sc);
+      const float* Fn = sF(sn);
+      float ex[2][2], ey[2][2], ez[2][2], hx[2][2], hy[2][2], hz[2][2];
+      if (ok) {
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+          const int row = r0 + r;
+          const float2 vex = *reinterpret_cast<const float2*>(&F[FI(0, row, c0)]);
+          const float2 vey = *reinterpret_cast<const float2*>(&F[FI(1, row, c0)]);
+          const float2 vez = *reinterpret_cast<const float2*>(&F[FI(2, row, c0)]);
+          ex[r][0] = vex.x; ex[r][1] = vex.y;
+          ey[r][0] = vey.x; ey[r][1] = vey.y;
+          ez[r][0] = vez.x; ez[r][1] = vez.y;
+        }
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+          const int row = r0 + r;
+          const float2 vhx = *reinterpret_cast<const float2*>(&F[FI(3, row, c0)]);
+          const float2 vhy = *reinterpret_cast<const float2*>(&F[FI(4, row, c0)]);
+          const float2 vhz = *reinterpret_cast<const float2*>(&F[FI(5, row, c0)]);
+          const float2 nex = *reinterpret_cast<const float2*>(&Fn[FI(0, row, c0)]);
+          const float2 ney = *reinterpret_cast<const float2*>(&Fn[FI(1, row, c0)]);
+          float exj[2], ezj[2];
+          if (r == 0) {
+            exj[0] = ex[1][0]; exj[1] = ex[1][1];
+            ezj[0] = ez[1][0]; ezj[1] = ez[1][1];
+          } else {
+            const float2 a2 = *reinterpret_cast<const float2*>(&F[FI(0, row + 1, c0)]);
+            const float2 b2 = *reinterpret_cast<const float2*>(&F[FI(2, row + 1, c0)]);
+            exj[0] = a2.x; exj[1] = a2.y;
+            ezj[0] = b2.x; ezj[1] = b2.y;
+          }
+          const float ez_ip1 = F[FI(2, row, c0 + 2)];
+          const float ey_ip1 = F[FI(1, row, c0 + 2)];
+          hx[r][0] = h_upd(vhx.x, S, ney.x, ey[r][0], ezj[0], ez[r][0]);
+          hx[r][1] = h_upd(vhx.y, S, ney.y, ey[r][1], ezj[1], ez[r][1]);
+          hy[r][0] = h_upd(vhy.x, S, ez[r][1], ez[r][0], nex.x, ex[r][0]);
+          hy[r][1] = h_upd(vhy.y, S, ez_ip1, ez[r][1], nex.y, ex[r][1]);
+          hz[r][0] = h_upd(vhz.x, S, exj[0], ex[r][0], ey[r][1], ey[r][0]);
+          hz[r][1] = h_upd(vhz.y, S, exj[1], ex[r][1], ey_ip1, ey[r][1]);
+          *reinterpret_cast<float2*>(&F[FI(3, row, c0)]) = make_float2(hx[r][0], hx[r][1]);
+          *reinterpret_cast<float2*>(&F[FI(4, row, c0)]) = make_float2(hy[r][0], hy[r][1]);
+          *reinterpret_cast<float2*>(&F[FI(5, row, c0)]) = make_float2(hz[r][0], hz[r][1]);
+        }
+        if (hr >= 0) {
+          const float e0 = F[FI(0, hr, hc)], e1 = F[FI(1, hr, hc)], e2 = F[FI(2, hr, hc)];
+          const float nx_ = h_upd(F[FI(3, hr, hc)], S, Fn[FI(1, hr, hc)], e1, F[FI(2, hr + 1, hc)], e2);
+          const float ny_ = h_upd(F[FI(4, hr, hc)], S, F[FI(2, hr, hc + 1)], e2, Fn[FI(0, hr, hc)], e0);
+          const float nz_ = h_upd(F[FI(5, hr, hc)], S, F[FI(0, hr + 1, hc)], e0, F[FI(1, hr, hc + 1)], e1);
+          F[FI(3, hr, hc)] = nx_;
+          F[FI(4, hr, hc)] = ny_;
+          F[FI(5, hr, hc)] = nz_;
+        }
+      }
+      abort = named_bar_or(1, kConsumers, !ok);
+      if (abort) break;
+      const bool out_plane = z >= w.z0;
+      const uint32_t* M = sM(sc);
+#pragma unroll
+      for (int r = 0; r < 2; ++r) {
+        const int row = r0 + r;
+        float hzj[2], hxj[2];
+        if (r == 0) {
+          const float2 a2 = *reinterpret_cast<const float2*>(&F[FI(5, row - 1, c0)]);
+          const float2 b2 = *reinterpret_cast<const float2*>(&F[FI(3, row - 1, c0)]);
+          hzj[0] = a2.x; hzj[1] = a2.y;
+          hxj[0] = b2.x; hxj[1] = b2.y;
+        } else {
+          hzj[0] = hz[0][0]; hzj[1] = hz[0][1];
+          hxj[0] = hx[0][0]; hxj[1] = hx[0][1];
+        }
+        const float hz_im = F[FI(5, row, c0 - 1)];
+        const float hy_im = F[FI(4, row, c0 - 1)];
+        const uint2 m2 = *reinterpret_cast<const uint2*>(&M[row * kBX + c0]);
+        const int y = w.y0 + 2 * warp + r;
+        const int x = w.x0 + 2 * lane;
+        float eo[3][2];
+#pragma unroll
+        for (int cc = 0; cc < 2; ++cc) {
+          const uint32_t m = cc ? m2.y : m2.x;
+          float bx = curl_br(hz[r][cc], hzj[cc], hy[r][cc], hyp[r][cc]);
+          float by = curl_br(hx[r][cc], hxp[r][cc], hz[r][cc], cc ? hz[r][0] : hz_im);
+          float bz = curl_br(hy[r][cc], cc ? hy[r][0] : hy_im, hx[r][cc], hxj[cc]);
+          if ((m & kSrcFlag) && out_plane) {
+            const long long pt = ((long long)z * d.ny1 + y) * d.nxp + x + cc;
+            for (int s = 0; s < a.src.n; ++s) {
+              if (a.src.pos[s] != pt) continue;
+              const float v = a.src.val[(long long)s * a.src.cap + a.n0];
+              if (a.src.comp[s] == 0) bx = __fadd_rn(bx, v);
+              else if (a.src.comp[s] == 1) by = __fadd_rn(by, v);
+              else bz = __fadd_rn(bz, v);
+            }
+          }
+          eo[0][cc] = e_upd(ex[r][cc], __ldg(&a.coef[m & 1023u]), bx);
+          eo[1][cc] = e_upd(ey[r][cc], __ldg(&a.coef[(m >> 10) & 1023u]), by);
+          eo[2][cc] = e_upd(ez[r][cc], __ldg(&a.coef[(m >> 20) & 1023u]), bz);
+          if ((m & kPrbFlag) && out_plane && y < d.ny && x + cc < d.nx) {
+            const long long pt = ((long long)z * d.ny1 + y) * d.nxp + x + cc;
+            const float v6[6] = {eo[0][cc], eo[1][cc], eo[2][cc], hx[r][cc], hy[r][cc], hz[r][cc]};
+            for (int p = 0; p < a.prb.n; ++p)
+              if (a.prb.pos[p] == pt) a.prb.buf[(long long)p * a.prb.cap + a.n0] = v6[a.prb.comp[p]];
+          }
+        }
+        if (out_plane && y < d.ny && x < d.nx) {
+          float* o = a.fout + (long long)z * d.zstride + (long long)y * d.nxp + x;
+          const float vals[6][2] = {{eo[0][0], eo[0][1]}, {eo[1][0], eo[1][1]}, {eo[2][0], eo[2][1]},
+                                    {hx[r][0], hx[r][1]}, {hy[r][0], hy[r][1]}, {hz[r][0], hz[r][1]}};
+          if (x + 1 < d.nx) {
+#pragma unroll
+            for (int f = 0; f < 6; ++f)
+              *reinterpret_cast<float2*>(o + f * d.plane) = make_float2(vals[f][0], vals[f][1]);
+          } else {
+#pragma unroll
+            for (int f = 0; f < 6; ++f) o[f * d.plane] = vals[f][0];
+          }
+        }
+#pragma unroll
+        for (int cc = 0; cc < 2; ++cc) {
+          hxp[r][cc] = hx[r][cc];
+          hyp[r][cc] = hy[r][cc];
+        }
+      }
+      fence_proxy_async_smem();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(empty(sc));
+    }
+    if (abort) break;
+    // The unit's last plane was only read as the "next" plane: release it.
+    __syncwarp();
+    if (lane == 0) mbar_arrive(empty((int)(C % kNS)));
+    ++C;
+  }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
+
+}  // namespace
+
+bool encode_plain_maps(const Dims& d, float* fields, uint32_t* mat, CUtensorMap* tmF, CUtensorMap* tmM) {
+  auto fn = encode_fn();
+  if (!fn) return false;
+  cuuint64_t gdF[4] = {(cuuint64_t)d.nxp, (cuuint64_t)d.ny1, 6, (cuuint64_t)d.nz1};
+  cuuint64_t gsF[3] = {(cuuint64_t)d.nxp * 4, (cuuint64_t)d.plane * 4, (cuuint64_t)d.zstride * 4};
+  cuuint32_t boxF[4] = {kBX, kBY, 6, 1};
+  cuuint32_t es[4] = {1, 1, 1, 1};
+  if (fn(tmF, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, fields, gdF, gsF, boxF, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+         CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    return false;
+  if (tmM) {
+    cuuint64_t gdM[3] = {(cuuint64_t)d.nxp, (cuuint64_t)d.ny1, (cuuint64_t)d.nz1};
+    cuuint64_t gsM[2] = {(cuuint64_t)d.nxp * 4, (cuuint64_t)d.plane * 4};
+    cuuint32_t boxM[3] = {kBX, kBY, 1};
+    if (fn(tmM, CU_TENSOR_MAP_DATA_TYPE_UINT32, 3, mat, gdM, gsM, boxM, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+           CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      return false;
+  }
+  return true;
+}
+
+PlainTiling plain_tiling(const Dims& d, int num_sms) {
+  PlainTiling best{};
+  double best_cost = 1e300;
+  const int tiles_x = (d.nx + kPX - 1) / kPX, tiles_y = (d.ny + kPY - 1) / kPY;
+  const int slots = 2 * num_sms;
+  const int cands[] = {4, 6, 8, 12, 16, 24, 32, 48, 64, 96, 128, 256};
+  for (int zc : cands) {
+    if (zc > d.nz && zc != cands[0]) continue;
+    const long long nzc = (d.nz + zc - 1) / zc;
+    const long long units = (long long)tiles_x * tiles_y * nzc;
+    const long long per = (units + slots - 1) / slots;
+    // time ~ units per CTA x (planes per unit + ~0.7 plane of warm-up/pipeline refill)
+    const double cost = (double)per * (std::min(zc, d.nz) + 0.7);
+    if (cost < best_cost - 1e-9) {
+      best_cost = cost;
+      best.tiles_x = tiles_x;
+      best.tiles_y = tiles_y;
+      best.zchunk = zc;
+      best.units = units;
+      best.grid = (int)((units + per - 1) / per);
+    }
+  }
+  return best;
+}
+
+cudaError_t launch_step_plain(const StepArgs& a, const CUtensorMap& tmF, const CUtensorMap& tmM,
+                              const PlainTiling& t, cudaStream_t s) {
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(yee_plain_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)kSmemBytes);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  yee_plain_kernel<<<t.grid, kThreads, kSmemBytes, s>>>(tmF, tmM, a, t);
+  return cudaGetLastError();
+}
+
+}  // namespace sophie
