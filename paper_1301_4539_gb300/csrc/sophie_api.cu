@@ -7,8 +7,10 @@
 // tables and enqueues launches.
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <stdlib.h>
 #include <string.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -55,6 +57,11 @@ struct Source {
 struct Probe {
   int comp, i, j, k;
   long long pos;
+  // Index on a plane no kernel updates (i == nx, j == ny or k == nz): a PEC
+  // edge or a wall-normal face whose value never changes. Its samples are
+  // filled from the field at read time instead of by the step kernels.
+  bool fixed;
+  long long n_added;
 };
 
 struct ProfEntry {
@@ -69,6 +76,9 @@ struct sophie_grid {
   CUtensorMap tmF[2];  // TMA maps of the two field buffers
   CUtensorMap tmM;     // TMA map of the material words
   PlainTiling ptile{};
+  CUtensorMap tmFB[2];  // TMA maps with the temporally blocked kernel's box
+  CUtensorMap tmMB;
+  BlockedTiling btile{};
   int num_sms = 0;
   bool use_simple = false;  // tile_x == 32: untiled-load reference kernel
   double dx = 0, dt = 0, S64 = 0;
@@ -230,7 +240,8 @@ int build_material_words(sophie_grid* g, const float* eps, const float* sig) {
   if (cb.overflow)
     return fail(SOPHIE_ETOOMANYMAT, "more than %d distinct (eps_r, sigma) edge pairs", kMaxClasses - 1);
   for (const Source& s : g->src) w[s.pos] |= kSrcFlag;
-  for (const Probe& p : g->prb) w[p.pos] |= kPrbFlag;
+  for (const Probe& p : g->prb)
+    if (!p.fixed) w[p.pos] |= kPrbFlag;
   g->coef_h = std::move(cb.coef);
   g->eps_h = std::move(cb.eps);
   return SOPHIE_OK;
@@ -511,7 +522,17 @@ int sophie_create_grid(int nx, int ny, int nz, double dx, double dt, sophie_grid
       rc = fail(SOPHIE_ECUDA, "cuTensorMapEncodeTiled failed");
       break;
     }
-    g->ptile = plain_tiling(d, g->num_sms);
+    if (!encode_maps(d, g->F[0], g->mat, blocked_box_x(), blocked_box_y(), &g->tmFB[0], &g->tmMB) ||
+        !encode_maps(d, g->F[1], nullptr, blocked_box_x(), blocked_box_y(), &g->tmFB[1], nullptr)) {
+      rc = fail(SOPHIE_ECUDA, "cuTensorMapEncodeTiled failed (blocked box)");
+      break;
+    }
+    {
+      // SOPHIE_ZCHUNK: z planes per work unit of the TMA kernels (tuning knob;
+      // any value gives identical results).
+      const char* zc = getenv("SOPHIE_ZCHUNK");
+      g->ptile = plain_tiling(d, g->num_sms, zc ? atoi(zc) : 0);
+    }
     rc = build_material_words(g, nullptr, nullptr);
     if (rc) break;
     rc = upload_materials(g);
@@ -589,10 +610,12 @@ int sophie_add_probe(sophie_grid* g, int comp, int i, int j, int k, int* probe_i
   if (!comp_valid(g->d, comp, i, j, k))
     return fail(SOPHIE_EINVAL, "probe (%d,%d,%d) outside comp %d's range", i, j, k, comp);
   if ((int)g->prb.size() >= kMaxProbes) return fail(SOPHIE_EINVAL, "at most %d probes", kMaxProbes);
-  Probe p{comp, i, j, k, point_index(g->d, i, j, k)};
-  if (launch_or_flag(g->mat, p.pos, kPrbFlag, g->stream) != cudaSuccess)
-    return fail(SOPHIE_ECUDA, "flag launch failed");
-  g->launches++;
+  Probe p{comp, i, j, k, point_index(g->d, i, j, k), i == g->d.nx || j == g->d.ny || k == g->d.nz, g->n};
+  if (!p.fixed) {
+    if (launch_or_flag(g->mat, p.pos, kPrbFlag, g->stream) != cudaSuccess)
+      return fail(SOPHIE_ECUDA, "flag launch failed");
+    g->launches++;
+  }
   g->prb.push_back(p);
   *probe_id = (int)g->prb.size() - 1;
   return SOPHIE_OK;
@@ -604,7 +627,9 @@ int sophie_step(sophie_grid* g, int n) {
   if (n == 0) return SOPHIE_OK;
   int rc = ensure_capacity(g, g->n + n);
   if (rc) return rc;
-  for (int m = 0; m < n; ++m) {
+  for (int m = 0; m < n;) {
+    const int K = g->temporal_k;
+    const bool blocked = !g->use_simple && K >= 2 && n - m >= K && blocked_supported(K);
     StepArgs a = make_step_args(g);
     cudaEvent_t ea = nullptr, eb = nullptr;
     if (g->prof) {
@@ -612,12 +637,19 @@ int sophie_step(sophie_grid* g, int n) {
       eb = prof_event(g);
       cudaEventRecord(ea, g->stream);
     }
-    cudaError_t e = g->use_simple ? launch_step_simple(a, g->stream)
-                                  : launch_step_plain(a, g->tmF[g->cur], g->tmM, g->ptile, g->stream);
+    cudaError_t e;
+    if (blocked) {
+      if (g->btile.K != K) g->btile = blocked_tiling(g->d, K, g->num_sms);
+      e = launch_step_blocked(a, g->tmFB[g->cur], g->tmMB, g->btile, g->stream);
+    } else if (g->use_simple) {
+      e = launch_step_simple(a, g->stream);
+    } else {
+      e = launch_step_plain(a, g->tmF[g->cur], g->tmM, g->ptile, g->stream);
+    }
     if (e != cudaSuccess) return fail(SOPHIE_ECUDA, "step launch failed: %s", cudaGetErrorString(e));
     if (g->prof) {
       cudaEventRecord(eb, g->stream);
-      g->prof_live.push_back({SOPHIE_KERNEL_PLAIN, ea, eb});
+      g->prof_live.push_back({blocked ? SOPHIE_KERNEL_BLOCKED : SOPHIE_KERNEL_PLAIN, ea, eb});
       if (g->prof_live.size() > 20000) {
         rc = prof_drain(g);
         if (rc) return rc;
@@ -625,7 +657,9 @@ int sophie_step(sophie_grid* g, int n) {
     }
     g->launches++;
     g->cur = 1 - g->cur;
-    g->n += 1;
+    const int adv = blocked ? K : 1;
+    g->n += adv;
+    m += adv;
   }
   return SOPHIE_OK;
 }
@@ -641,12 +675,22 @@ int sophie_read_probe(sophie_grid* g, int probe_id, double* out, int cap, int* n
   if (probe_id < 0 || probe_id >= (int)g->prb.size()) return fail(SOPHIE_EINVAL, "bad probe id");
   if (cap < 0) return fail(SOPHIE_EINVAL, "cap must be >= 0");
   const long long m = std::min<long long>(cap, g->n);
+  const Probe& pr = g->prb[probe_id];
   std::vector<float> tmp((size_t)m);
-  if (m > 0)
+  float fixed_v = 0.f;
+  if (pr.fixed) {
+    const Dims& d = g->d;
+    const float* src = g->F[g->cur] + (long long)pr.k * d.zstride + (long long)pr.comp * d.plane +
+                       (long long)pr.j * d.nxp + pr.i;
+    CUDA_TRY(cudaMemcpyAsync(&fixed_v, src, 4, cudaMemcpyDeviceToHost, g->stream));
+  } else if (m > 0) {
     CUDA_TRY(cudaMemcpyAsync(tmp.data(), g->pbuf + (size_t)probe_id * g->pcap, (size_t)m * 4,
                              cudaMemcpyDeviceToHost, g->stream));
+  }
   int rc = check_err_word(g);
   if (rc) return rc;
+  if (pr.fixed)
+    for (long long q = 0; q < m; ++q) tmp[q] = q >= pr.n_added ? fixed_v : 0.f;
   for (long long q = 0; q < m; ++q) out[q] = (double)tmp[q];
   *n_written = (int)m;
   return SOPHIE_OK;
@@ -708,6 +752,7 @@ int sophie_reset(sophie_grid* g) {
   if (g->pbuf) CUDA_TRY(cudaMemsetAsync(g->pbuf, 0, (size_t)kMaxProbes * g->pcap * 4, g->stream));
   g->n = 0;
   g->cur = 0;
+  for (Probe& p : g->prb) p.n_added = 0;
   return SOPHIE_OK;
 }
 
@@ -730,6 +775,8 @@ int sophie_sync(sophie_grid* g) {
 int sophie_configure(sophie_grid* g, int temporal_k, int tile_x, int tile_y, int precision) {
   if (!g) return fail(SOPHIE_EINVAL, "NULL grid");
   if (temporal_k < 0 || temporal_k > 8) return fail(SOPHIE_EINVAL, "temporal_k must be in 0..8");
+  if (temporal_k >= 2 && !blocked_supported(temporal_k))
+    return fail(SOPHIE_ENOTSUP, "temporal_k = %d not built (supported: 1..4)", temporal_k);
   if (tile_x < 0 || tile_y < 0) return fail(SOPHIE_EINVAL, "tile sizes must be >= 0");
   if (precision != SOPHIE_FP32) return fail(SOPHIE_ENOTSUP, "precision %d not supported", precision);
   if (tile_x != 0 && tile_x != 32 && tile_x != 64) return fail(SOPHIE_EINVAL, "tile_x must be 0, 32 or 64");

@@ -72,12 +72,26 @@ struct PlainTiling {
   long long units;
 };
 
+// Temporally blocked kernel: K steps per launch over (tiles_x x tiles_y)
+// regions; `grid` CTAs split the (tile, plane) items into equal ranges.
+struct BlockedTiling {
+  int K, tiles_x, tiles_y, grid;
+};
+
 // Launchers (return cudaError_t of the launch).
 cudaError_t launch_step_simple(const StepArgs& a, cudaStream_t s);
+bool encode_maps(const Dims& d, float* fields, uint32_t* mat, int box_x, int box_y, CUtensorMap* tmF,
+                 CUtensorMap* tmM);
 bool encode_plain_maps(const Dims& d, float* fields, uint32_t* mat, CUtensorMap* tmF, CUtensorMap* tmM);
-PlainTiling plain_tiling(const Dims& d, int num_sms);
+PlainTiling plain_tiling(const Dims& d, int num_sms, int zchunk_override);
 cudaError_t launch_step_plain(const StepArgs& a, const CUtensorMap& tmF, const CUtensorMap& tmM,
                               const PlainTiling& t, cudaStream_t s);
+BlockedTiling blocked_tiling(const Dims& d, int K, int num_sms);
+bool blocked_supported(int K);
+int blocked_box_x();
+int blocked_box_y();
+cudaError_t launch_step_blocked(const StepArgs& a, const CUtensorMap& tmF, const CUtensorMap& tmM,
+                                const BlockedTiling& t, cudaStream_t s);
 cudaError_t launch_energy(const float* f, const uint32_t* mat, const double* eps_tab,
                           const Dims& d, float S, double* partials, int nblocks,
                           double* out, cudaStream_t s);

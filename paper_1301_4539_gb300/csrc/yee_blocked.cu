@@ -1,0 +1,450 @@
+// yee_blocked<K>: K fused leapfrog steps per launch (temporal blocking).
+//
+// Method: Sec. 3.4 (two-step cache reuse, generalised to K steps in the
+// conclusion): a tile of the grid is advanced several time steps while it is
+// on chip, so each field byte fetched from HBM serves K steps. Sec. 3.1: the
+// restructuring changes no output value; here every H and E value is the
+// same float expression (yee_update.cuh) as in the one-step kernels, so the
+// fields are bitwise identical to K plain steps.
+//
+// GPU design (one CTA of 8 warps per SM):
+//  * A CTA owns a 64 x 32 (x, y) region. Each step needs the neighbour at +1
+//    (H from E) and at -1 (E from H), so after K steps only the inner
+//    (64-2K) x (32-2K) part is exact: that part is the output tile; the
+//    regions of neighbouring tiles overlap by 2K columns / rows and compute
+//    the overlap identically (no inter-CTA communication, no waits).
+//  * Eight warps; thread 0 also issues the TMA loads: a stage is refilled right
+//    after the first level barrier of the iteration that consumed it, which
+//    proves every warp has copied it to registers (no empty barriers needed).
+//  * z is streamed. Level t (step t of the K) lags level t-1 by one plane:
+//    at iteration s, level t updates plane s-t using level t-1's state of that
+//    plane (kept in registers since the previous iteration) and level t-1's
+//    E of plane s-t+1 (just computed). Level 0 is the TMA-staged input
+//    (3-stage ring of 68x32 boxes of the six fields and the material words).
+//  * A lane owns two adjacent x, a thread four rows (R). x neighbours come
+//    from warp shuffles; y neighbours from registers inside a thread's rows
+//    and, at warp seams, from two small shared-memory row buffers per level
+//    (E rows double-buffered by iteration parity, H rows per level), with one
+//    named barrier per level.
+//  * Work: the (tile, z plane) items are split into equal contiguous ranges,
+//    one per CTA; a range that starts above z = 0 first replays 3K-2 planes
+//    so that every level's state is exact from its first output plane.
+#include "sophie_internal.h"
+#include "tma_util.cuh"
+#include "yee_update.cuh"
+
+namespace sophie {
+
+namespace {
+
+constexpr int kRX = 64;
+constexpr int kBX = kRX + 4;  // TMA box: region rounded out to a 4-float boundary
+constexpr int kR = 4;         // rows per thread
+constexpr int kW = 8;         // consumer warps
+constexpr int kRY = kR * kW;  // 32
+constexpr int kNS = 3;
+constexpr int kConsumers = kW * 32;
+constexpr int kThreads = kConsumers;  // thread 0 also issues the TMA loads
+constexpr uint32_t kFieldBytes = kBX * kRY * 6 * 4;
+constexpr uint32_t kMatBytes = kBX * kRY * 4;
+constexpr uint32_t kLoadBytes = kFieldBytes + kMatBytes;
+constexpr uint32_t kStageBytes = (kLoadBytes + 127) / 128 * 128;
+static_assert(kFieldBytes % 128 == 0, "material box alignment");
+
+template <int K>
+struct Cfg {
+  static constexpr int TX = kRX - 2 * K;
+  static constexpr int TY = kRY - 2 * K;
+  static constexpr int PHI = K & 1;  // x tiles shifted so that region starts are even
+  // shared memory: stages | H seam rows [K][W][2][64] | E seam rows [K-1][2][W][2][64] | barriers
+  static constexpr uint32_t kHpOff = kNS * kStageBytes;
+  static constexpr uint32_t kHpBytes = K * kW * 2 * kRX * 4;
+  static constexpr uint32_t kEpOff = kHpOff + kHpBytes;
+  static constexpr uint32_t kEpBytes = (K > 1 ? K - 1 : 1) * 2 * kW * 2 * kRX * 4;
+  static constexpr uint32_t kBarOff = kEpOff + kEpBytes;
+  static constexpr uint32_t kSmem = kBarOff + kNS * 8 + 128;
+};
+
+__device__ __forceinline__ int FI(int f, int r, int c) { return (f * kRY + r) * kBX + c; }
+
+struct St {
+  float ex[kR][2], ey[kR][2], ez[kR][2], hx[kR][2], hy[kR][2], hz[kR][2];
+  uint32_t m[kR][2];
+};
+
+__device__ __forceinline__ void set_err(int* err, int code) { atomicOr(err, code); }
+
+// Contiguous share of the (tile, plane) items of this CTA, walked as units.
+struct UnitIter {
+  long long i, hi;
+  int nz;
+  __device__ UnitIter(const BlockedTiling& t, int nz_) : nz(nz_) {
+    const long long n = (long long)t.tiles_x * t.tiles_y * nz_;
+    i = n * blockIdx.x / gridDim.x;
+    hi = n * (blockIdx.x + 1) / gridDim.x;
+  }
+  // Next unit: tile index and planes [z0, z1). False when done.
+  __device__ bool next(long long& tile, int& z0, int& z1) {
+    if (i >= hi) return false;
+    tile = i / nz;
+    z0 = (int)(i % nz);
+    const long long room = hi - i;
+    z1 = (int)((long long)z0 + room < nz ? z0 + room : nz);
+    i += z1 - z0;
+    return true;
+  }
+};
+
+// First iteration of a unit: level 1 updates plane s-1; planes below 0 are
+// zero and exact, otherwise 3K-2 planes are replayed before z0.
+template <int K>
+__device__ __forceinline__ int first_iter(int z0) {
+  const int s = z0 - 2 * K + 2;
+  return s < 1 ? 1 : s;
+}
+
+
+// Issues the CTA's TMA loads in consumption order: for each unit, planes
+// first_iter-1 .. z1-1+K of its tile (thread 0 only).
+template <int K>
+struct Loader {
+  UnitIter it;
+  int p = 0, pend = -1, bx = 0, ry = 0;
+  long long issued = 0;
+  __device__ Loader(const BlockedTiling& t, int nz) : it(t, nz) {}
+  // Issue the next plane into its stage; false when the sequence is exhausted.
+  __device__ bool issue(const BlockedTiling& t, const CUtensorMap* tmF, const CUtensorMap* tmM,
+                        unsigned char* base, uint32_t bar0) {
+    if (p > pend) {
+      long long tile;
+      int z0, z1;
+      if (!it.next(tile, z0, z1)) return false;
+      const int tx = (int)(tile % t.tiles_x), ty = (int)(tile / t.tiles_x);
+      const int rx = tx * Cfg<K>::TX - Cfg<K>::PHI - K;
+      ry = ty * Cfg<K>::TY - K;
+      bx = rx & ~3;
+      p = first_iter<K>(z0) - 1;
+      pend = z1 - 1 + K;
+    }
+    const int s = (int)(issued % kNS);
+    const uint32_t bar = bar0 + 8u * s;
+    mbar_arrive_expect_tx(bar, kLoadBytes);
+    tma_load_4d(smem_u32(base + s * kStageBytes), tmF, bx, ry, 0, p, bar);
+    tma_load_3d(smem_u32(base + s * kStageBytes + kFieldBytes), tmM, bx, ry, p, bar);
+    ++p;
+    ++issued;
+    return true;
+  }
+};
+
+template <int K>
+__global__ void __launch_bounds__(kThreads, 1)
+yee_blocked_kernel(const __grid_constant__ CUtensorMap tmF, const __grid_constant__ CUtensorMap tmM,
+                   StepArgs a, BlockedTiling t) {
+  using C = Cfg<K>;
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* base = reinterpret_cast<unsigned char*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+  const uint32_t bar0 = smem_u32(base + C::kBarOff);
+  auto full = [&](int s) { return bar0 + 8u * s; };
+  auto sF = [&](int s) { return reinterpret_cast<float*>(base + s * kStageBytes); };
+  auto sM = [&](int s) { return reinterpret_cast<const uint32_t*>(base + s * kStageBytes + kFieldBytes); };
+  // H seam rows: hp[level][warp][comp: 0 = hx, 1 = hz][64]
+  float* hp = reinterpret_cast<float*>(base + C::kHpOff);
+  // E seam rows: ep[level-1][parity][warp][comp: 0 = ex, 1 = ez][64]
+  float* ep = reinterpret_cast<float*>(base + C::kEpOff);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kNS; ++s) mbar_init(full(s), 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  const Dims d = a.d;
+  Loader<K> ld(t, d.nz);
+  if (threadIdx.x == 0) {
+    prefetch_tmap(&tmF);
+    prefetch_tmap(&tmM);
+    for (int s = 0; s < kNS; ++s)
+      if (!ld.issue(t, &tmF, &tmM, base, bar0)) break;
+  }
+
+  const float S = a.S;
+  const int wn = warp + 1 < kW ? warp + 1 : warp;  // seam partner below (clamped at the edge)
+  const int wp = warp > 0 ? warp - 1 : warp;       // seam partner above
+  UnitIter it(t, d.nz);
+  long long tile;
+  int z0, z1;
+  long long Cn = 0;  // consumed-plane counter (ring position)
+  bool abort = false;
+  while (!abort && it.next(tile, z0, z1)) {
+    const int tx = (int)(tile % t.tiles_x), ty = (int)(tile / t.tiles_x);
+    const int rx = tx * C::TX - C::PHI - K, ry = ty * C::TY - K;
+    const int ox = rx & 3;  // 0 or 2: region start inside the TMA box
+    const int col0 = ox + 2 * lane;
+    const int x = rx + 2 * lane;  // global x of this lane's first position
+    // output x range of this tile (the first tile of an odd K starts at -1)
+    const int xo0 = max(tx * C::TX - C::PHI, 0), xo1 = tx * C::TX - C::PHI + C::TX;
+    const int yo0 = ty * C::TY, yo1 = yo0 + C::TY;
+    const int s0 = first_iter<K>(z0), s1 = z1 - 1 + K;
+
+    St carry[K > 1 ? K - 1 : 1];
+    float hxp[K][kR][2], hyp[K][kR][2];
+#pragma unroll
+    for (int l = 0; l < (K > 1 ? K - 1 : 1); ++l)
+#pragma unroll
+      for (int r = 0; r < kR; ++r)
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+          carry[l].ex[r][c] = carry[l].ey[r][c] = carry[l].ez[r][c] = 0.f;
+          carry[l].hx[r][c] = carry[l].hy[r][c] = carry[l].hz[r][c] = 0.f;
+          carry[l].m[r][c] = 0u;
+        }
+#pragma unroll
+    for (int l = 0; l < K; ++l)
+#pragma unroll
+      for (int r = 0; r < kR; ++r)
+#pragma unroll
+        for (int c = 0; c < 2; ++c) hxp[l][r][c] = hyp[l][r][c] = 0.f;
+
+    for (int s = s0; s <= s1; ++s, ++Cn) {
+      const int sc = (int)(Cn % kNS), sn = (int)((Cn + 1) % kNS);
+      const bool ok = mbar_wait(full(sc), (uint32_t)((Cn / kNS) & 1)) &&
+                      mbar_wait(full(sn), (uint32_t)(((Cn + 1) / kNS) & 1));
+      if (!ok) set_err(a.err, 8);
+      if (named_bar_or(1, kConsumers, !ok)) {
+        abort = true;
+        break;
+      }
+      const float* F = sF(sc);
+      const float* Fn = sF(sn);
+      const uint32_t* M = sM(sc);
+      const int par = s & 1;
+
+      // Level-0 state of plane s-1 and E of plane s (own positions).
+      St in;
+      float exn[kR][2], eyn[kR][2];
+#pragma unroll
+      for (int r = 0; r < kR; ++r) {
+        const int row = warp * kR + r;
+        const float2 v0 = *reinterpret_cast<const float2*>(&F[FI(0, row, col0)]);
+        const float2 v1 = *reinterpret_cast<const float2*>(&F[FI(1, row, col0)]);
+        const float2 v2 = *reinterpret_cast<const float2*>(&F[FI(2, row, col0)]);
+        const float2 v3 = *reinterpret_cast<const float2*>(&F[FI(3, row, col0)]);
+        const float2 v4 = *reinterpret_cast<const float2*>(&F[FI(4, row, col0)]);
+        const float2 v5 = *reinterpret_cast<const float2*>(&F[FI(5, row, col0)]);
+        const uint2 mm = *reinterpret_cast<const uint2*>(&M[row * kBX + col0]);
+        const float2 n0 = *reinterpret_cast<const float2*>(&Fn[FI(0, row, col0)]);
+        const float2 n1 = *reinterpret_cast<const float2*>(&Fn[FI(1, row, col0)]);
+        in.ex[r][0] = v0.x; in.ex[r][1] = v0.y;
+        in.ey[r][0] = v1.x; in.ey[r][1] = v1.y;
+        in.ez[r][0] = v2.x; in.ez[r][1] = v2.y;
+        in.hx[r][0] = v3.x; in.hx[r][1] = v3.y;
+        in.hy[r][0] = v4.x; in.hy[r][1] = v4.y;
+        in.hz[r][0] = v5.x; in.hz[r][1] = v5.y;
+        in.m[r][0] = mm.x; in.m[r][1] = mm.y;
+        exn[r][0] = n0.x; exn[r][1] = n0.y;
+        eyn[r][0] = n1.x; eyn[r][1] = n1.y;
+      }
+      // E of the row below this warp's rows, level 0 (straight from the stage).
+      float bex[2], bez[2];
+      {
+        const int brow = warp * kR + kR < kRY ? warp * kR + kR : kRY - 1;
+        const float2 b0 = *reinterpret_cast<const float2*>(&F[FI(0, brow, col0)]);
+        const float2 b2 = *reinterpret_cast<const float2*>(&F[FI(2, brow, col0)]);
+        bex[0] = b0.x; bex[1] = b0.y;
+        bez[0] = b2.x; bez[1] = b2.y;
+      }
+      // The level-0 planes are now in registers; stage sc is refilled by
+      // thread 0 after the first level barrier below.
+
+#pragma unroll
+      for (int lv = 1; lv <= K; ++lv) {
+        const int p = s - lv;  // plane updated by this level
+        const long long nstep = a.n0 + lv - 1;
+        // ---- H of level lv at plane p ----
+        float hx[kR][2], hy[kR][2], hz[kR][2];
+#pragma unroll
+        for (int r = 0; r < kR; ++r) {
+          const float ey_ip1 = __shfl_down_sync(0xffffffffu, in.ey[r][0], 1);
+          const float ez_ip1 = __shfl_down_sync(0xffffffffu, in.ez[r][0], 1);
+          float exj[2], ezj[2];
+          if (r + 1 < kR) {
+            exj[0] = in.ex[r + 1][0]; exj[1] = in.ex[r + 1][1];
+            ezj[0] = in.ez[r + 1][0]; ezj[1] = in.ez[r + 1][1];
+          } else {
+            exj[0] = bex[0]; exj[1] = bex[1];
+            ezj[0] = bez[0]; ezj[1] = bez[1];
+          }
+          hx[r][0] = h_upd(in.hx[r][0], S, eyn[r][0], in.ey[r][0], ezj[0], in.ez[r][0]);
+          hx[r][1] = h_upd(in.hx[r][1], S, eyn[r][1], in.ey[r][1], ezj[1], in.ez[r][1]);
+          hy[r][0] = h_upd(in.hy[r][0], S, in.ez[r][1], in.ez[r][0], exn[r][0], in.ex[r][0]);
+          hy[r][1] = h_upd(in.hy[r][1], S, ez_ip1, in.ez[r][1], exn[r][1], in.ex[r][1]);
+          hz[r][0] = h_upd(in.hz[r][0], S, exj[0], in.ex[r][0], in.ey[r][1], in.ey[r][0]);
+          hz[r][1] = h_upd(in.hz[r][1], S, exj[1], in.ex[r][1], ey_ip1, in.ey[r][1]);
+        }
+        float* hpl = hp + (lv - 1) * (kW * 2 * kRX);
+        *reinterpret_cast<float2*>(&hpl[(warp * 2 + 0) * kRX + 2 * lane]) = make_float2(hx[kR - 1][0], hx[kR - 1][1]);
+        *reinterpret_cast<float2*>(&hpl[(warp * 2 + 1) * kRX + 2 * lane]) = make_float2(hz[kR - 1][0], hz[kR - 1][1]);
+        named_bar(1, kConsumers);
+        if (lv == 1 && threadIdx.x == 0) {
+          // Every warp has passed the copy of stage sc (and, in a unit's last
+          // iteration, of stage sn, which holds no further plane of this unit).
+          const long long released = Cn + 1 + (s == s1 ? 1 : 0);
+          fence_proxy_async_smem();
+          while (ld.issued < released + kNS)
+            if (!ld.issue(t, &tmF, &tmM, base, bar0)) break;
+        }
+        float hxa[2], hza[2];  // H of the row above this warp's rows
+        {
+          const float2 u = *reinterpret_cast<const float2*>(&hpl[(wp * 2 + 0) * kRX + 2 * lane]);
+          const float2 v = *reinterpret_cast<const float2*>(&hpl[(wp * 2 + 1) * kRX + 2 * lane]);
+          hxa[0] = u.x; hxa[1] = u.y;
+          hza[0] = v.x; hza[1] = v.y;
+        }
+        // ---- E of level lv at plane p ----
+        St out;
+#pragma unroll
+        for (int r = 0; r < kR; ++r) {
+          const float hz_im1 = __shfl_up_sync(0xffffffffu, hz[r][1], 1);
+          const float hy_im1 = __shfl_up_sync(0xffffffffu, hy[r][1], 1);
+          const int y = ry + warp * kR + r;
+#pragma unroll
+          for (int cc = 0; cc < 2; ++cc) {
+            const float hzj = r > 0 ? hz[r - 1][cc] : hza[cc];
+            const float hxj = r > 0 ? hx[r - 1][cc] : hxa[cc];
+            const float hzi = cc ? hz[r][0] : hz_im1;
+            const float hyi = cc ? hy[r][0] : hy_im1;
+            float bx = curl_br(hz[r][cc], hzj, hy[r][cc], hyp[lv - 1][r][cc]);
+            float by = curl_br(hx[r][cc], hxp[lv - 1][r][cc], hz[r][cc], hzi);
+            float bz = curl_br(hy[r][cc], hyi, hx[r][cc], hxj);
+            const uint32_t m = in.m[r][cc];
+            if (m & kSrcFlag) {
+              const long long pt = ((long long)p * d.ny1 + y) * d.nxp + x + cc;
+              for (int q = 0; q < a.src.n; ++q) {
+                if (a.src.pos[q] != pt) continue;
+                const float v = a.src.val[(long long)q * a.src.cap + nstep];
+                if (a.src.comp[q] == 0) bx = __fadd_rn(bx, v);
+                else if (a.src.comp[q] == 1) by = __fadd_rn(by, v);
+                else bz = __fadd_rn(bz, v);
+              }
+            }
+            out.ex[r][cc] = e_upd(in.ex[r][cc], __ldg(&a.coef[m & 1023u]), bx);
+            out.ey[r][cc] = e_upd(in.ey[r][cc], __ldg(&a.coef[(m >> 10) & 1023u]), by);
+            out.ez[r][cc] = e_upd(in.ez[r][cc], __ldg(&a.coef[(m >> 20) & 1023u]), bz);
+            out.hx[r][cc] = hx[r][cc];
+            out.hy[r][cc] = hy[r][cc];
+            out.hz[r][cc] = hz[r][cc];
+            out.m[r][cc] = m;
+            hxp[lv - 1][r][cc] = hx[r][cc];
+            hyp[lv - 1][r][cc] = hy[r][cc];
+            if ((m & kPrbFlag) && p >= z0 && p < z1 && y >= yo0 && y < yo1 && y < d.ny &&
+                x + cc >= xo0 && x + cc < xo1 && x + cc < d.nx) {
+              const long long pt = ((long long)p * d.ny1 + y) * d.nxp + x + cc;
+              const float v6[6] = {out.ex[r][cc], out.ey[r][cc], out.ez[r][cc], hx[r][cc], hy[r][cc], hz[r][cc]};
+              for (int q = 0; q < a.prb.n; ++q)
+                if (a.prb.pos[q] == pt) a.prb.buf[(long long)q * a.prb.cap + nstep] = v6[a.prb.comp[q]];
+            }
+          }
+        }
+        if (lv < K) {
+          // Publish this warp's first E row for level lv+1 (next iteration), then
+          // feed level lv+1: its input is this level's state of plane p-1 (carry),
+          // its "E of the plane above" is what was just computed.
+          float* epl = ep + ((lv - 1) * 2 + par) * (kW * 2 * kRX);
+          *reinterpret_cast<float2*>(&epl[(warp * 2 + 0) * kRX + 2 * lane]) = make_float2(out.ex[0][0], out.ex[0][1]);
+          *reinterpret_cast<float2*>(&epl[(warp * 2 + 1) * kRX + 2 * lane]) = make_float2(out.ez[0][0], out.ez[0][1]);
+          const float* epo = ep + ((lv - 1) * 2 + (par ^ 1)) * (kW * 2 * kRX);
+          const float2 u = *reinterpret_cast<const float2*>(&epo[(wn * 2 + 0) * kRX + 2 * lane]);
+          const float2 v = *reinterpret_cast<const float2*>(&epo[(wn * 2 + 1) * kRX + 2 * lane]);
+          bex[0] = u.x; bex[1] = u.y;
+          bez[0] = v.x; bez[1] = v.y;
+#pragma unroll
+          for (int r = 0; r < kR; ++r)
+#pragma unroll
+            for (int cc = 0; cc < 2; ++cc) {
+              exn[r][cc] = out.ex[r][cc];
+              eyn[r][cc] = out.ey[r][cc];
+            }
+          in = carry[lv - 1];
+          carry[lv - 1] = out;
+        } else if (p >= z0 && p < z1) {
+          // ---- level K: store the output tile of plane p ----
+#pragma unroll
+          for (int r = 0; r < kR; ++r) {
+            const int y = ry + warp * kR + r;
+            if (y < yo0 || y >= yo1 || y >= d.ny) continue;
+            float* o = a.fout + (long long)p * d.zstride + (long long)y * d.nxp + x;
+            const bool v0 = x >= xo0 && x < xo1 && x < d.nx;
+            const bool v1 = x + 1 >= xo0 && x + 1 < xo1 && x + 1 < d.nx;
+            const float vals[6][2] = {{out.ex[r][0], out.ex[r][1]}, {out.ey[r][0], out.ey[r][1]},
+                                      {out.ez[r][0], out.ez[r][1]}, {out.hx[r][0], out.hx[r][1]},
+                                      {out.hy[r][0], out.hy[r][1]}, {out.hz[r][0], out.hz[r][1]}};
+            if (v0 && v1) {
+#pragma unroll
+              for (int f = 0; f < 6; ++f)
+                *reinterpret_cast<float2*>(o + f * d.plane) = make_float2(vals[f][0], vals[f][1]);
+            } else if (v0) {
+#pragma unroll
+              for (int f = 0; f < 6; ++f) o[f * d.plane] = vals[f][0];
+            } else if (v1) {
+#pragma unroll
+              for (int f = 0; f < 6; ++f) o[f * d.plane + 1] = vals[f][1];
+            }
+          }
+        }
+      }
+    }
+    if (abort) break;
+    ++Cn;  // the unit's last staged plane was only read as "plane s"
+  }
+  if (abort && threadIdx.x == 0) {
+    // Give the copies still in flight a bounded chance to land before exit.
+    for (long long e = ld.issued - 1; e >= 0 && e >= ld.issued - kNS; --e)
+      mbar_wait(full((int)(e % kNS)), (uint32_t)((e / kNS) & 1));
+  }
+}
+
+template <int K>
+cudaError_t launch_k(const StepArgs& a, const CUtensorMap& tmF, const CUtensorMap& tmM, const BlockedTiling& t,
+                     cudaStream_t s) {
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(yee_blocked_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)Cfg<K>::kSmem);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  yee_blocked_kernel<K><<<t.grid, kThreads, Cfg<K>::kSmem, s>>>(tmF, tmM, a, t);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+int blocked_box_x() { return kBX; }
+int blocked_box_y() { return kRY; }
+
+BlockedTiling blocked_tiling(const Dims& d, int K, int num_sms) {
+  BlockedTiling t{};
+  const int TX = kRX - 2 * K, TY = kRY - 2 * K, phi = K & 1;
+  t.K = K;
+  t.tiles_x = (d.nx + phi + TX - 1) / TX;
+  t.tiles_y = (d.ny + TY - 1) / TY;
+  const long long items = (long long)t.tiles_x * t.tiles_y * d.nz;
+  t.grid = (int)(items < num_sms ? items : num_sms);
+  return t;
+}
+
+bool blocked_supported(int K) { return K >= 2 && K <= 4; }
+
+cudaError_t launch_step_blocked(const StepArgs& a, const CUtensorMap& tmF, const CUtensorMap& tmM,
+                                const BlockedTiling& t, cudaStream_t s) {
+  switch (t.K) {
+    case 2: return launch_k<2>(a, tmF, tmM, t, s);
+    case 3: return launch_k<3>(a, tmF, tmM, t, s);
+    case 4: return launch_k<4>(a, tmF, tmM, t, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace sophie

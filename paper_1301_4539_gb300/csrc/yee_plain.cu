@@ -293,11 +293,16 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 }  // namespace
 
 bool encode_plain_maps(const Dims& d, float* fields, uint32_t* mat, CUtensorMap* tmF, CUtensorMap* tmM) {
+  return encode_maps(d, fields, mat, kBX, kBY, tmF, tmM);
+}
+
+bool encode_maps(const Dims& d, float* fields, uint32_t* mat, int box_x, int box_y, CUtensorMap* tmF,
+                 CUtensorMap* tmM) {
   auto fn = encode_fn();
   if (!fn) return false;
   cuuint64_t gdF[4] = {(cuuint64_t)d.nxp, (cuuint64_t)d.ny1, 6, (cuuint64_t)d.nz1};
   cuuint64_t gsF[3] = {(cuuint64_t)d.nxp * 4, (cuuint64_t)d.plane * 4, (cuuint64_t)d.zstride * 4};
-  cuuint32_t boxF[4] = {kBX, kBY, 6, 1};
+  cuuint32_t boxF[4] = {(cuuint32_t)box_x, (cuuint32_t)box_y, 6, 1};
   cuuint32_t es[4] = {1, 1, 1, 1};
   if (fn(tmF, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, fields, gdF, gsF, boxF, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
          CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -306,7 +311,7 @@ bool encode_plain_maps(const Dims& d, float* fields, uint32_t* mat, CUtensorMap*
   if (tmM) {
     cuuint64_t gdM[3] = {(cuuint64_t)d.nxp, (cuuint64_t)d.ny1, (cuuint64_t)d.nz1};
     cuuint64_t gsM[2] = {(cuuint64_t)d.nxp * 4, (cuuint64_t)d.plane * 4};
-    cuuint32_t boxM[3] = {kBX, kBY, 1};
+    cuuint32_t boxM[3] = {(cuuint32_t)box_x, (cuuint32_t)box_y, 1};
     if (fn(tmM, CU_TENSOR_MAP_DATA_TYPE_UINT32, 3, mat, gdM, gsM, boxM, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
@@ -315,19 +320,21 @@ bool encode_plain_maps(const Dims& d, float* fields, uint32_t* mat, CUtensorMap*
   return true;
 }
 
-PlainTiling plain_tiling(const Dims& d, int num_sms) {
+PlainTiling plain_tiling(const Dims& d, int num_sms, int zchunk_override) {
   PlainTiling best{};
   double best_cost = 1e300;
   const int tiles_x = (d.nx + kPX - 1) / kPX, tiles_y = (d.ny + kPY - 1) / kPY;
   const int slots = 2 * num_sms;
-  const int cands[] = {4, 6, 8, 12, 16, 24, 32, 48, 64, 96, 128, 256};
+  const int cands[] = {4, 6, 8, 12, 16, 24, 32, 48, 64, 96, 128, 256, 512, 1024};
   for (int zc : cands) {
-    if (zc > d.nz && zc != cands[0]) continue;
+    if (zchunk_override > 0) zc = zchunk_override;
+    if (zc > d.nz && zc != cands[0] && zchunk_override <= 0) continue;
     const long long nzc = (d.nz + zc - 1) / zc;
     const long long units = (long long)tiles_x * tiles_y * nzc;
     const long long per = (units + slots - 1) / slots;
-    // time ~ units per CTA x (planes per unit + ~0.7 plane of warm-up/pipeline refill)
-    const double cost = (double)per * (std::min(zc, d.nz) + 0.7);
+    // HBM time ~ units per CTA x planes loaded per unit (the chunk, the plane
+    // below it for the H warm-up and the plane above it for the z+1 values).
+    const double cost = (double)per * (std::min(zc, d.nz) + 2.0);
     if (cost < best_cost - 1e-9) {
       best_cost = cost;
       best.tiles_x = tiles_x;
@@ -336,6 +343,7 @@ PlainTiling plain_tiling(const Dims& d, int num_sms) {
       best.units = units;
       best.grid = (int)((units + per - 1) / per);
     }
+    if (zchunk_override > 0) break;
   }
   return best;
 }

@@ -49,17 +49,32 @@ def test_tma_kernel_equals_direct_kernel(sophie, n3, steps):
 
 
 def test_full_size_sphere_cavity_1000_steps(oracle_mod, sophie):
+    """Benchmark workload, full length, every kernel configuration the bench can time."""
     w = wl.sphere_cavity(256)
     n = w["nx"]
-    g, o = make_pair(oracle_mod, n, n, n, w["eps"], w["sigma"], sources=w["sources"], probes=w["probes"])
-    g.step(1000)
+    o = oracle_mod.OracleGrid(n, n, n, w["dx"], w["dt"], "f32")
+    o.set_materials(w["eps"], w["sigma"])
+    for s in w["sources"]:
+        o.add_source(*s)
+    for p in w["probes"]:
+        o.add_probe(*p)
     o.step(1000)
-    gf = assert_fields_equal(g, o)
-    for c in range(6):
-        assert rel_l2(gf[c], o.f[c]) <= 1e-5
-    for q in range(len(w["probes"])):
-        a, b = g.read_probe(q), o.probe(q)
-        np.testing.assert_array_equal(a, b)
-    W, Wo = g.energy(), o.energy()
-    assert abs(W - Wo) <= 1e-12 * abs(Wo)
-    assert W > 0
+    Wo = o.energy()
+    for K in (1, 2, 3, 4):
+        g = so.Grid(n, n, n, w["dx"], w["dt"])
+        g.configure(temporal_k=K)
+        g.set_materials(w["eps"], w["sigma"])
+        for s in w["sources"]:
+            g.add_source(*s)
+        for p in w["probes"]:
+            g.add_probe(*p)
+        g.step(1000)
+        gf = assert_fields_equal(g, o)
+        for c in range(6):
+            assert rel_l2(gf[c], o.f[c]) <= 1e-5
+        for q in range(len(w["probes"])):
+            np.testing.assert_array_equal(g.read_probe(q), o.probe(q))
+        W = g.energy()
+        assert abs(W - Wo) <= 1e-12 * abs(Wo)
+        assert W > 0
+        g.close()
