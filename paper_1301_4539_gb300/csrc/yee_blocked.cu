@@ -31,6 +31,7 @@
 //    so that every level's state is exact from its first output plane.
 #include "sophie_internal.h"
 #include "tma_util.cuh"
+#include "yee_rare.cuh"
 #include "yee_update.cuh"
 
 namespace sophie {
@@ -61,7 +62,8 @@ struct Cfg {
   static constexpr uint32_t kHpBytes = K * kW * 2 * kRX * 4;
   static constexpr uint32_t kEpOff = kHpOff + kHpBytes;
   static constexpr uint32_t kEpBytes = (K > 1 ? K - 1 : 1) * 2 * kW * 2 * kRX * 4;
-  static constexpr uint32_t kBarOff = kEpOff + kEpBytes;
+  static constexpr uint32_t kCoefOff = kEpOff + kEpBytes;
+  static constexpr uint32_t kBarOff = kCoefOff + kMaxClasses * 8;
   static constexpr uint32_t kSmem = kBarOff + kNS * 8 + 128;
 };
 
@@ -140,7 +142,7 @@ struct Loader {
 template <int K>
 __global__ void __launch_bounds__(kThreads, 1)
 yee_blocked_kernel(const __grid_constant__ CUtensorMap tmF, const __grid_constant__ CUtensorMap tmM,
-                   StepArgs a, BlockedTiling t) {
+                   const __grid_constant__ StepArgs a, BlockedTiling t) {
   using C = Cfg<K>;
   extern __shared__ unsigned char smem_raw[];
   unsigned char* base = reinterpret_cast<unsigned char*>(
@@ -154,6 +156,9 @@ yee_blocked_kernel(const __grid_constant__ CUtensorMap tmF, const __grid_constan
   // E seam rows: ep[level-1][parity][warp][comp: 0 = ex, 1 = ez][64]
   float* ep = reinterpret_cast<float*>(base + C::kEpOff);
 
+  // (Ca, Cb) of every material class, read by all levels.
+  float2* scoef = reinterpret_cast<float2*>(base + C::kCoefOff);
+  for (int c = threadIdx.x; c < kMaxClasses; c += kThreads) scoef[c] = a.coef[c];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
     for (int s = 0; s < kNS; ++s) mbar_init(full(s), 1);
@@ -320,18 +325,15 @@ yee_blocked_kernel(const __grid_constant__ CUtensorMap tmF, const __grid_constan
             float bz = curl_br(hy[r][cc], hyi, hx[r][cc], hxj);
             const uint32_t m = in.m[r][cc];
             if (m & kSrcFlag) {
-              const long long pt = ((long long)p * d.ny1 + y) * d.nxp + x + cc;
-              for (int q = 0; q < a.src.n; ++q) {
-                if (a.src.pos[q] != pt) continue;
-                const float v = a.src.val[(long long)q * a.src.cap + nstep];
-                if (a.src.comp[q] == 0) bx = __fadd_rn(bx, v);
-                else if (a.src.comp[q] == 1) by = __fadd_rn(by, v);
-                else bz = __fadd_rn(bz, v);
-              }
+              const float3 b3 = apply_sources(make_float3(bx, by, bz),
+                                              ((long long)p * d.ny1 + y) * d.nxp + x + cc, nstep, &a.src);
+              bx = b3.x;
+              by = b3.y;
+              bz = b3.z;
             }
-            out.ex[r][cc] = e_upd(in.ex[r][cc], __ldg(&a.coef[m & 1023u]), bx);
-            out.ey[r][cc] = e_upd(in.ey[r][cc], __ldg(&a.coef[(m >> 10) & 1023u]), by);
-            out.ez[r][cc] = e_upd(in.ez[r][cc], __ldg(&a.coef[(m >> 20) & 1023u]), bz);
+            out.ex[r][cc] = e_upd(in.ex[r][cc], scoef[m & 1023u], bx);
+            out.ey[r][cc] = e_upd(in.ey[r][cc], scoef[(m >> 10) & 1023u], by);
+            out.ez[r][cc] = e_upd(in.ez[r][cc], scoef[(m >> 20) & 1023u], bz);
             out.hx[r][cc] = hx[r][cc];
             out.hy[r][cc] = hy[r][cc];
             out.hz[r][cc] = hz[r][cc];
@@ -339,12 +341,9 @@ yee_blocked_kernel(const __grid_constant__ CUtensorMap tmF, const __grid_constan
             hxp[lv - 1][r][cc] = hx[r][cc];
             hyp[lv - 1][r][cc] = hy[r][cc];
             if ((m & kPrbFlag) && p >= z0 && p < z1 && y >= yo0 && y < yo1 && y < d.ny &&
-                x + cc >= xo0 && x + cc < xo1 && x + cc < d.nx) {
-              const long long pt = ((long long)p * d.ny1 + y) * d.nxp + x + cc;
-              const float v6[6] = {out.ex[r][cc], out.ey[r][cc], out.ez[r][cc], hx[r][cc], hy[r][cc], hz[r][cc]};
-              for (int q = 0; q < a.prb.n; ++q)
-                if (a.prb.pos[q] == pt) a.prb.buf[(long long)q * a.prb.cap + nstep] = v6[a.prb.comp[q]];
-            }
+                x + cc >= xo0 && x + cc < xo1 && x + cc < d.nx)
+              record_probes(((long long)p * d.ny1 + y) * d.nxp + x + cc, nstep, out.ex[r][cc], out.ey[r][cc],
+                            out.ez[r][cc], hx[r][cc], hy[r][cc], hz[r][cc], &a.prb);
           }
         }
         if (lv < K) {

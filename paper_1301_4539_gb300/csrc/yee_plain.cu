@@ -21,6 +21,7 @@
 //    with coalesced 8-byte stores.
 #include "sophie_internal.h"
 #include "tma_util.cuh"
+#include "yee_rare.cuh"
 #include "yee_update.cuh"
 
 #include <cudaTypedefs.h>
@@ -69,7 +70,7 @@ __device__ __forceinline__ void set_err(int* err, int code) { atomicOr(err, code
 
 __global__ void __launch_bounds__(kThreads, 2)
 yee_plain_kernel(const __grid_constant__ CUtensorMap tmF, const __grid_constant__ CUtensorMap tmM,
-                 StepArgs a, PlainTiling t) {
+                 const __grid_constant__ StepArgs a, PlainTiling t) {
   extern __shared__ unsigned char smem_raw[];
   unsigned char* base = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
@@ -227,24 +228,18 @@ yee_plain_kernel(const __grid_constant__ CUtensorMap tmF, const __grid_constant_
           float by = curl_br(hx[r][cc], hxp[r][cc], hz[r][cc], cc ? hz[r][0] : hz_im);
           float bz = curl_br(hy[r][cc], cc ? hy[r][0] : hy_im, hx[r][cc], hxj[cc]);
           if ((m & kSrcFlag) && out_plane) {
-            const long long pt = ((long long)z * d.ny1 + y) * d.nxp + x + cc;
-            for (int s = 0; s < a.src.n; ++s) {
-              if (a.src.pos[s] != pt) continue;
-              const float v = a.src.val[(long long)s * a.src.cap + a.n0];
-              if (a.src.comp[s] == 0) bx = __fadd_rn(bx, v);
-              else if (a.src.comp[s] == 1) by = __fadd_rn(by, v);
-              else bz = __fadd_rn(bz, v);
-            }
+            const float3 b3 = apply_sources(make_float3(bx, by, bz),
+                                            ((long long)z * d.ny1 + y) * d.nxp + x + cc, a.n0, &a.src);
+            bx = b3.x;
+            by = b3.y;
+            bz = b3.z;
           }
           eo[0][cc] = e_upd(ex[r][cc], __ldg(&a.coef[m & 1023u]), bx);
           eo[1][cc] = e_upd(ey[r][cc], __ldg(&a.coef[(m >> 10) & 1023u]), by);
           eo[2][cc] = e_upd(ez[r][cc], __ldg(&a.coef[(m >> 20) & 1023u]), bz);
-          if ((m & kPrbFlag) && out_plane && y < d.ny && x + cc < d.nx) {
-            const long long pt = ((long long)z * d.ny1 + y) * d.nxp + x + cc;
-            const float v6[6] = {eo[0][cc], eo[1][cc], eo[2][cc], hx[r][cc], hy[r][cc], hz[r][cc]};
-            for (int p = 0; p < a.prb.n; ++p)
-              if (a.prb.pos[p] == pt) a.prb.buf[(long long)p * a.prb.cap + a.n0] = v6[a.prb.comp[p]];
-          }
+          if ((m & kPrbFlag) && out_plane && y < d.ny && x + cc < d.nx)
+            record_probes(((long long)z * d.ny1 + y) * d.nxp + x + cc, a.n0, eo[0][cc], eo[1][cc], eo[2][cc],
+                          hx[r][cc], hy[r][cc], hz[r][cc], &a.prb);
         }
         if (out_plane && y < d.ny && x < d.nx) {
           float* o = a.fout + (long long)z * d.zstride + (long long)y * d.nxp + x;

@@ -1,0 +1,37 @@
+// Rare paths of the step kernels (source currents, probe samples), kept out
+// of line so that the unrolled update loops stay small in the instruction
+// cache. Both only run for index points whose material word carries the
+// source or probe flag.
+#pragma once
+
+#include "sophie_internal.h"
+
+namespace sophie {
+
+// Sec. 3.3: a current added to Ampere's equation. Every source on index point
+// pt adds amp*w(t^{n+1/2}) (tabulated per step) to its component's curl
+// bracket, in the order the sources were added.
+static __device__ __noinline__ float3 apply_sources(float3 b, long long pt, long long nstep,
+                                                    const SrcTable* src) {
+  for (int q = 0; q < src->n; ++q) {
+    if (src->pos[q] != pt) continue;
+    const float v = src->val[(long long)q * src->cap + nstep];
+    if (src->comp[q] == 0) b.x = __fadd_rn(b.x, v);
+    else if (src->comp[q] == 1) b.y = __fadd_rn(b.y, v);
+    else b.z = __fadd_rn(b.z, v);
+  }
+  return b;
+}
+
+// Sec. 3.4 pin-point outputs: sample nstep of every probe on index point pt.
+static __device__ __noinline__ void record_probes(long long pt, long long nstep, float ex, float ey, float ez,
+                                                  float hx, float hy, float hz, const PrbTable* prb) {
+  for (int q = 0; q < prb->n; ++q) {
+    if (prb->pos[q] != pt) continue;
+    const int c = prb->comp[q];
+    const float v = c == 0 ? ex : c == 1 ? ey : c == 2 ? ez : c == 3 ? hx : c == 4 ? hy : hz;
+    prb->buf[(long long)q * prb->cap + nstep] = v;
+  }
+}
+
+}  // namespace sophie
