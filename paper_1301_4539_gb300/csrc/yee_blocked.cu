@@ -192,6 +192,17 @@ yee_blocked_kernel(const __grid_constant__ CUtensorMap tmF, const __grid_constan
     const int xo0 = max(tx * C::TX - C::PHI, 0), xo1 = tx * C::TX - C::PHI + C::TX;
     const int yo0 = ty * C::TY, yo1 = yo0 + C::TY;
     const int s0 = first_iter<K>(z0), s1 = z1 - 1 + K;
+    // Output masks of this unit: rows of this thread inside the tile, and
+    // which of its two x positions are inside it.
+    const bool v0 = x >= xo0 && x < xo1 && x < d.nx;
+    const bool v1 = x + 1 >= xo0 && x + 1 < xo1 && x + 1 < d.nx;
+    uint32_t rowmask = 0;
+    const long long rowbase = (long long)(ry + warp * kR) * d.nxp + x;
+#pragma unroll
+    for (int r = 0; r < kR; ++r) {
+      const int y = ry + warp * kR + r;
+      if (y >= yo0 && y < yo1 && y < d.ny) rowmask |= 1u << r;
+    }
 
     St carry[K > 1 ? K - 1 : 1];
     float hxp[K][kR][2], hyp[K][kR][2];
@@ -308,44 +319,75 @@ yee_blocked_kernel(const __grid_constant__ CUtensorMap tmF, const __grid_constan
           hza[0] = v.x; hza[1] = v.y;
         }
         // ---- E of level lv at plane p ----
-        St out;
+        // Source and probe points are rare: one warp-uniform test per level
+        // picks the check-free loop or the one that handles them.
+        uint32_t fl = 0;
 #pragma unroll
-        for (int r = 0; r < kR; ++r) {
-          const float hz_im1 = __shfl_up_sync(0xffffffffu, hz[r][1], 1);
-          const float hy_im1 = __shfl_up_sync(0xffffffffu, hy[r][1], 1);
-          const int y = ry + warp * kR + r;
+        for (int r = 0; r < kR; ++r) fl |= in.m[r][0] | in.m[r][1];
+        const bool rare = __any_sync(0xffffffffu, fl & (kSrcFlag | kPrbFlag));
+        St out;
+        if (!rare) {
+#pragma unroll
+          for (int r = 0; r < kR; ++r) {
+            const float hz_im1 = __shfl_up_sync(0xffffffffu, hz[r][1], 1);
+            const float hy_im1 = __shfl_up_sync(0xffffffffu, hy[r][1], 1);
+#pragma unroll
+            for (int cc = 0; cc < 2; ++cc) {
+              const float hzj = r > 0 ? hz[r > 0 ? r - 1 : 0][cc] : hza[cc];
+              const float hxj = r > 0 ? hx[r > 0 ? r - 1 : 0][cc] : hxa[cc];
+              const float hzi = cc ? hz[r][0] : hz_im1;
+              const float hyi = cc ? hy[r][0] : hy_im1;
+              const uint32_t m = in.m[r][cc];
+              out.ex[r][cc] = e_upd(in.ex[r][cc], scoef[m & 1023u], curl_br(hz[r][cc], hzj, hy[r][cc], hyp[lv - 1][r][cc]));
+              out.ey[r][cc] = e_upd(in.ey[r][cc], scoef[(m >> 10) & 1023u], curl_br(hx[r][cc], hxp[lv - 1][r][cc], hz[r][cc], hzi));
+              out.ez[r][cc] = e_upd(in.ez[r][cc], scoef[(m >> 20) & 1023u], curl_br(hy[r][cc], hyi, hx[r][cc], hxj));
+              out.m[r][cc] = m;
+            }
+          }
+        } else {
+#pragma unroll
+          for (int r = 0; r < kR; ++r) {
+            const float hz_im1 = __shfl_up_sync(0xffffffffu, hz[r][1], 1);
+            const float hy_im1 = __shfl_up_sync(0xffffffffu, hy[r][1], 1);
+            const int y = ry + warp * kR + r;
+#pragma unroll
+            for (int cc = 0; cc < 2; ++cc) {
+              const float hzj = r > 0 ? hz[r > 0 ? r - 1 : 0][cc] : hza[cc];
+              const float hxj = r > 0 ? hx[r > 0 ? r - 1 : 0][cc] : hxa[cc];
+              const float hzi = cc ? hz[r][0] : hz_im1;
+              const float hyi = cc ? hy[r][0] : hy_im1;
+              float bx = curl_br(hz[r][cc], hzj, hy[r][cc], hyp[lv - 1][r][cc]);
+              float by = curl_br(hx[r][cc], hxp[lv - 1][r][cc], hz[r][cc], hzi);
+              float bz = curl_br(hy[r][cc], hyi, hx[r][cc], hxj);
+              const uint32_t m = in.m[r][cc];
+              if (m & kSrcFlag) {
+                const float3 b3 = apply_sources(make_float3(bx, by, bz),
+                                                ((long long)p * d.ny1 + y) * d.nxp + x + cc, nstep, &a.src);
+                bx = b3.x;
+                by = b3.y;
+                bz = b3.z;
+              }
+              out.ex[r][cc] = e_upd(in.ex[r][cc], scoef[m & 1023u], bx);
+              out.ey[r][cc] = e_upd(in.ey[r][cc], scoef[(m >> 10) & 1023u], by);
+              out.ez[r][cc] = e_upd(in.ez[r][cc], scoef[(m >> 20) & 1023u], bz);
+              out.m[r][cc] = m;
+              if ((m & kPrbFlag) && p >= z0 && p < z1 && y >= yo0 && y < yo1 && y < d.ny &&
+                  x + cc >= xo0 && x + cc < xo1 && x + cc < d.nx)
+                record_probes(((long long)p * d.ny1 + y) * d.nxp + x + cc, nstep, out.ex[r][cc], out.ey[r][cc],
+                              out.ez[r][cc], hx[r][cc], hy[r][cc], hz[r][cc], &a.prb);
+            }
+          }
+        }
+#pragma unroll
+        for (int r = 0; r < kR; ++r)
 #pragma unroll
           for (int cc = 0; cc < 2; ++cc) {
-            const float hzj = r > 0 ? hz[r - 1][cc] : hza[cc];
-            const float hxj = r > 0 ? hx[r - 1][cc] : hxa[cc];
-            const float hzi = cc ? hz[r][0] : hz_im1;
-            const float hyi = cc ? hy[r][0] : hy_im1;
-            float bx = curl_br(hz[r][cc], hzj, hy[r][cc], hyp[lv - 1][r][cc]);
-            float by = curl_br(hx[r][cc], hxp[lv - 1][r][cc], hz[r][cc], hzi);
-            float bz = curl_br(hy[r][cc], hyi, hx[r][cc], hxj);
-            const uint32_t m = in.m[r][cc];
-            if (m & kSrcFlag) {
-              const float3 b3 = apply_sources(make_float3(bx, by, bz),
-                                              ((long long)p * d.ny1 + y) * d.nxp + x + cc, nstep, &a.src);
-              bx = b3.x;
-              by = b3.y;
-              bz = b3.z;
-            }
-            out.ex[r][cc] = e_upd(in.ex[r][cc], scoef[m & 1023u], bx);
-            out.ey[r][cc] = e_upd(in.ey[r][cc], scoef[(m >> 10) & 1023u], by);
-            out.ez[r][cc] = e_upd(in.ez[r][cc], scoef[(m >> 20) & 1023u], bz);
             out.hx[r][cc] = hx[r][cc];
             out.hy[r][cc] = hy[r][cc];
             out.hz[r][cc] = hz[r][cc];
-            out.m[r][cc] = m;
             hxp[lv - 1][r][cc] = hx[r][cc];
             hyp[lv - 1][r][cc] = hy[r][cc];
-            if ((m & kPrbFlag) && p >= z0 && p < z1 && y >= yo0 && y < yo1 && y < d.ny &&
-                x + cc >= xo0 && x + cc < xo1 && x + cc < d.nx)
-              record_probes(((long long)p * d.ny1 + y) * d.nxp + x + cc, nstep, out.ex[r][cc], out.ey[r][cc],
-                            out.ez[r][cc], hx[r][cc], hy[r][cc], hz[r][cc], &a.prb);
           }
-        }
         if (lv < K) {
           // Publish this warp's first E row for level lv+1 (next iteration), then
           // feed level lv+1: its input is this level's state of plane p-1 (carry),
@@ -371,11 +413,8 @@ yee_blocked_kernel(const __grid_constant__ CUtensorMap tmF, const __grid_constan
           // ---- level K: store the output tile of plane p ----
 #pragma unroll
           for (int r = 0; r < kR; ++r) {
-            const int y = ry + warp * kR + r;
-            if (y < yo0 || y >= yo1 || y >= d.ny) continue;
-            float* o = a.fout + (long long)p * d.zstride + (long long)y * d.nxp + x;
-            const bool v0 = x >= xo0 && x < xo1 && x < d.nx;
-            const bool v1 = x + 1 >= xo0 && x + 1 < xo1 && x + 1 < d.nx;
+            if (!((rowmask >> r) & 1)) continue;
+            float* o = a.fout + (long long)p * d.zstride + rowbase + (long long)r * d.nxp;
             const float vals[6][2] = {{out.ex[r][0], out.ex[r][1]}, {out.ey[r][0], out.ey[r][1]},
                                       {out.ez[r][0], out.ez[r][1]}, {out.hx[r][0], out.hx[r][1]},
                                       {out.hy[r][0], out.hy[r][1]}, {out.hz[r][0], out.hz[r][1]}};
