@@ -98,7 +98,7 @@ int sophie_destroy_grid(sophie_grid *g);
  * nx*ny*nz floats each (x fastest, then y, then z), copied. eps_r >= 1 and
  * finite; sigma >= 0 and finite (else EINVAL). Edge values are the mean of the
  * four cells sharing the edge (Sec. 2.1 coefficients, see top of file); at
- * most 1023 distinct (eps_r, sigma) edge pairs (else ETOOMANYMAT, grid left
+ * most 511 distinct (eps_r, sigma) edge pairs (else ETOOMANYMAT, grid left
  * unchanged). Enqueued on the grid's stream; the host arrays may be reused on
  * return.
  */

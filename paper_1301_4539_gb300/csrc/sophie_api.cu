@@ -221,17 +221,17 @@ int build_material_words(sophie_grid* g, const float* eps, const float* sig) {
         if (e_edge_interior(d, 0, i, j, k)) {
           const double e4 = ((E(i, j - 1, k - 1) + E(i, j, k - 1)) + E(i, j - 1, k)) + E(i, j, k);
           const double s4 = ((Sg(i, j - 1, k - 1) + Sg(i, j, k - 1)) + Sg(i, j - 1, k)) + Sg(i, j, k);
-          word |= cls(0, e4, s4);
+          word |= cls(0, e4, s4) << kClsShift[0];
         }
         if (e_edge_interior(d, 1, i, j, k)) {
           const double e4 = ((E(i - 1, j, k - 1) + E(i, j, k - 1)) + E(i - 1, j, k)) + E(i, j, k);
           const double s4 = ((Sg(i - 1, j, k - 1) + Sg(i, j, k - 1)) + Sg(i - 1, j, k)) + Sg(i, j, k);
-          word |= cls(1, e4, s4) << 10;
+          word |= cls(1, e4, s4) << kClsShift[1];
         }
         if (e_edge_interior(d, 2, i, j, k)) {
           const double e4 = ((E(i - 1, j - 1, k) + E(i, j - 1, k)) + E(i - 1, j, k)) + E(i, j, k);
           const double s4 = ((Sg(i - 1, j - 1, k) + Sg(i, j - 1, k)) + Sg(i - 1, j, k)) + Sg(i, j, k);
-          word |= cls(2, e4, s4) << 20;
+          word |= cls(2, e4, s4) << kClsShift[2];
         }
         row[i] = word;
       }
@@ -639,7 +639,12 @@ int sophie_step(sophie_grid* g, int n) {
     }
     cudaError_t e;
     if (blocked) {
-      if (g->btile.K != K) g->btile = blocked_tiling(g->d, K, g->num_sms);
+      if (g->btile.K != K) {
+        // SOPHIE_BLOCKED_ALIGNED=0 cuts the work into equal contiguous ranges
+        // instead of equal z ranges per tile (tuning knob; same results).
+        const char* al = getenv("SOPHIE_BLOCKED_ALIGNED");
+        g->btile = blocked_tiling(g->d, K, g->num_sms, al ? atoi(al) : 1);
+      }
       e = launch_step_blocked(a, g->tmFB[g->cur], g->tmMB, g->btile, g->stream);
     } else if (g->use_simple) {
       e = launch_step_simple(a, g->stream);

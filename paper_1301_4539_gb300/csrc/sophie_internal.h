@@ -15,18 +15,34 @@ namespace sophie {
 // columns are zero and never written.
 //
 // Material word, one per index point (z*ny1 + y)*nxp + x:
-//   bits  0..9  class of the ex edge at this index (0 = PEC / absent)
-//   bits 10..19 class of the ey edge
-//   bits 20..29 class of the ez edge
-//   bit  30     a source sits on one of this point's edges
-//   bit  31     a probe sits on one of this point's components
+//   bit  0      a source sits on one of this point's edges
+//   bit  1      a probe sits on one of this point's components
+//   bits  3..11 class of the ex edge at this index (0 = PEC / absent)
+//   bits 12..20 class of the ey edge
+//   bits 21..29 class of the ez edge
+// Each class index sits 3 bits above a field boundary, so (word >> s) & 0xFF8
+// is directly the byte offset of the class's 8-byte (Ca, Cb) entry.
 // Class c has coefficients coef[c] = (Ca, Cb) (float) and eps_r(edge) in
 // double (energy). Class 0 is (0, 0): the edge is never anything but 0.
-constexpr int kMaxClasses = 1024;
+constexpr int kMaxClasses = 512;
 constexpr int kMaxSources = 16;
 constexpr int kMaxProbes = 64;
-constexpr uint32_t kSrcFlag = 1u << 30;
-constexpr uint32_t kPrbFlag = 1u << 31;
+constexpr uint32_t kSrcFlag = 1u;
+constexpr uint32_t kPrbFlag = 2u;
+constexpr int kClsShift[3] = {3, 12, 21};
+constexpr uint32_t kClsOffMask = 0xFF8u;  // 9-bit class index times 8
+
+__host__ __device__ constexpr uint32_t cls_word(uint32_t cx, uint32_t cy, uint32_t cz) {
+  return (cx << 3) | (cy << 12) | (cz << 21);
+}
+// Class index of edge component c (0..2) of a material word.
+__host__ __device__ __forceinline__ uint32_t cls_of(uint32_t m, int c) {
+  return (m >> (c == 0 ? 3 : c == 1 ? 12 : 21)) & 511u;
+}
+// Byte offset of that class's (Ca, Cb) pair in a float2 table.
+__device__ __forceinline__ uint32_t cls_off_x(uint32_t m) { return m & kClsOffMask; }
+__device__ __forceinline__ uint32_t cls_off_y(uint32_t m) { return (m >> 9) & kClsOffMask; }
+__device__ __forceinline__ uint32_t cls_off_z(uint32_t m) { return (m >> 18) & kClsOffMask; }
 
 struct Dims {
   int nx, ny, nz;   // cells
@@ -76,6 +92,7 @@ struct PlainTiling {
 // regions; `grid` CTAs split the (tile, plane) items into equal ranges.
 struct BlockedTiling {
   int K, tiles_x, tiles_y, grid;
+  int zsplit;  // > 0: CTA b works on tile b / zsplit, z range b % zsplit of zsplit
 };
 
 // Launchers (return cudaError_t of the launch).
@@ -86,7 +103,7 @@ bool encode_plain_maps(const Dims& d, float* fields, uint32_t* mat, CUtensorMap*
 PlainTiling plain_tiling(const Dims& d, int num_sms, int zchunk_override);
 cudaError_t launch_step_plain(const StepArgs& a, const CUtensorMap& tmF, const CUtensorMap& tmM,
                               const PlainTiling& t, cudaStream_t s);
-BlockedTiling blocked_tiling(const Dims& d, int K, int num_sms);
+BlockedTiling blocked_tiling(const Dims& d, int K, int num_sms, int aligned);
 bool blocked_supported(int K);
 int blocked_box_x();
 int blocked_box_y();

@@ -64,7 +64,7 @@ struct Cfg {
   static constexpr uint32_t kEpBytes = (K > 1 ? K - 1 : 1) * 2 * kW * 2 * kRX * 4;
   static constexpr uint32_t kCoefOff = kEpOff + kEpBytes;
   static constexpr uint32_t kBarOff = kCoefOff + kMaxClasses * 8;
-  static constexpr uint32_t kSmem = kBarOff + kNS * 8 + 128;
+  static constexpr uint32_t kSmem = kBarOff + kNS * 8;
 };
 
 __device__ __forceinline__ int FI(int f, int r, int c) { return (f * kRY + r) * kBX + c; }
@@ -76,14 +76,25 @@ struct St {
 
 __device__ __forceinline__ void set_err(int* err, int code) { atomicOr(err, code); }
 
-// Contiguous share of the (tile, plane) items of this CTA, walked as units.
+// The (tile, plane) items of this CTA, walked as units. With zsplit > 0
+// every tile's z column is cut into the same zsplit ranges, so regions of
+// neighbouring tiles stream the same planes at the same time (their
+// overlapping halos then come from L2). Otherwise the items are cut into
+// equal contiguous ranges, tile after tile.
 struct UnitIter {
   long long i, hi;
   int nz;
   __device__ UnitIter(const BlockedTiling& t, int nz_) : nz(nz_) {
-    const long long n = (long long)t.tiles_x * t.tiles_y * nz_;
-    i = n * blockIdx.x / gridDim.x;
-    hi = n * (blockIdx.x + 1) / gridDim.x;
+    if (t.zsplit > 0) {
+      const long long tile = blockIdx.x / t.zsplit;
+      const int part = blockIdx.x % t.zsplit;
+      i = tile * nz_ + (long long)nz_ * part / t.zsplit;
+      hi = tile * nz_ + (long long)nz_ * (part + 1) / t.zsplit;
+    } else {
+      const long long n = (long long)t.tiles_x * t.tiles_y * nz_;
+      i = n * blockIdx.x / gridDim.x;
+      hi = n * (blockIdx.x + 1) / gridDim.x;
+    }
   }
   // Next unit: tile index and planes [z0, z1). False when done.
   __device__ bool next(long long& tile, int& z0, int& z1) {
@@ -144,9 +155,15 @@ __global__ void __launch_bounds__(kThreads, 1)
 yee_blocked_kernel(const __grid_constant__ CUtensorMap tmF, const __grid_constant__ CUtensorMap tmM,
                    const __grid_constant__ StepArgs a, BlockedTiling t) {
   using C = Cfg<K>;
-  extern __shared__ unsigned char smem_raw[];
-  unsigned char* base = reinterpret_cast<unsigned char*>(
-      (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+  // Dynamic shared memory starts the CTA's shared window (no static shared
+  // variables here), so it is 1024-byte aligned and its offsets are
+  // compile-time constants.
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* const base = smem_raw;
+  if (smem_u32(smem_raw) & 1023u) {  // never expected; refuse rather than misalign TMA
+    if (threadIdx.x == 0) set_err(a.err, 16);
+    return;
+  }
   const uint32_t bar0 = smem_u32(base + C::kBarOff);
   auto full = [&](int s) { return bar0 + 8u * s; };
   auto sF = [&](int s) { return reinterpret_cast<float*>(base + s * kStageBytes); };
@@ -158,6 +175,7 @@ yee_blocked_kernel(const __grid_constant__ CUtensorMap tmF, const __grid_constan
 
   // (Ca, Cb) of every material class, read by all levels.
   float2* scoef = reinterpret_cast<float2*>(base + C::kCoefOff);
+  const unsigned char* scoefb = base + C::kCoefOff;
   for (int c = threadIdx.x; c < kMaxClasses; c += kThreads) scoef[c] = a.coef[c];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
@@ -228,10 +246,8 @@ yee_blocked_kernel(const __grid_constant__ CUtensorMap tmF, const __grid_constan
       const bool ok = mbar_wait(full(sc), (uint32_t)((Cn / kNS) & 1)) &&
                       mbar_wait(full(sn), (uint32_t)(((Cn + 1) / kNS) & 1));
       if (!ok) set_err(a.err, 8);
-      if (named_bar_or(1, kConsumers, !ok)) {
-        abort = true;
-        break;
-      }
+      // (a failed wait is acted on at the first level barrier below; until then
+      // the stage is only read, never written)
       const float* F = sF(sc);
       const float* Fn = sF(sn);
       const uint32_t* M = sM(sc);
@@ -302,7 +318,14 @@ yee_blocked_kernel(const __grid_constant__ CUtensorMap tmF, const __grid_constan
         float* hpl = hp + (lv - 1) * (kW * 2 * kRX);
         *reinterpret_cast<float2*>(&hpl[(warp * 2 + 0) * kRX + 2 * lane]) = make_float2(hx[kR - 1][0], hx[kR - 1][1]);
         *reinterpret_cast<float2*>(&hpl[(warp * 2 + 1) * kRX + 2 * lane]) = make_float2(hz[kR - 1][0], hz[kR - 1][1]);
-        named_bar(1, kConsumers);
+        if (lv == 1) {
+          if (named_bar_or(1, kConsumers, !ok)) {
+            abort = true;
+            break;
+          }
+        } else {
+          named_bar(1, kConsumers);
+        }
         if (lv == 1 && threadIdx.x == 0) {
           // Every warp has passed the copy of stage sc (and, in a unit's last
           // iteration, of stage sn, which holds no further plane of this unit).
@@ -338,9 +361,9 @@ yee_blocked_kernel(const __grid_constant__ CUtensorMap tmF, const __grid_constan
               const float hzi = cc ? hz[r][0] : hz_im1;
               const float hyi = cc ? hy[r][0] : hy_im1;
               const uint32_t m = in.m[r][cc];
-              out.ex[r][cc] = e_upd(in.ex[r][cc], scoef[m & 1023u], curl_br(hz[r][cc], hzj, hy[r][cc], hyp[lv - 1][r][cc]));
-              out.ey[r][cc] = e_upd(in.ey[r][cc], scoef[(m >> 10) & 1023u], curl_br(hx[r][cc], hxp[lv - 1][r][cc], hz[r][cc], hzi));
-              out.ez[r][cc] = e_upd(in.ez[r][cc], scoef[(m >> 20) & 1023u], curl_br(hy[r][cc], hyi, hx[r][cc], hxj));
+              out.ex[r][cc] = e_upd(in.ex[r][cc], *reinterpret_cast<const float2*>(scoefb + cls_off_x(m)), curl_br(hz[r][cc], hzj, hy[r][cc], hyp[lv - 1][r][cc]));
+              out.ey[r][cc] = e_upd(in.ey[r][cc], *reinterpret_cast<const float2*>(scoefb + cls_off_y(m)), curl_br(hx[r][cc], hxp[lv - 1][r][cc], hz[r][cc], hzi));
+              out.ez[r][cc] = e_upd(in.ez[r][cc], *reinterpret_cast<const float2*>(scoefb + cls_off_z(m)), curl_br(hy[r][cc], hyi, hx[r][cc], hxj));
               out.m[r][cc] = m;
             }
           }
@@ -367,9 +390,9 @@ yee_blocked_kernel(const __grid_constant__ CUtensorMap tmF, const __grid_constan
                 by = b3.y;
                 bz = b3.z;
               }
-              out.ex[r][cc] = e_upd(in.ex[r][cc], scoef[m & 1023u], bx);
-              out.ey[r][cc] = e_upd(in.ey[r][cc], scoef[(m >> 10) & 1023u], by);
-              out.ez[r][cc] = e_upd(in.ez[r][cc], scoef[(m >> 20) & 1023u], bz);
+              out.ex[r][cc] = e_upd(in.ex[r][cc], *reinterpret_cast<const float2*>(scoefb + cls_off_x(m)), bx);
+              out.ey[r][cc] = e_upd(in.ey[r][cc], *reinterpret_cast<const float2*>(scoefb + cls_off_y(m)), by);
+              out.ez[r][cc] = e_upd(in.ez[r][cc], *reinterpret_cast<const float2*>(scoefb + cls_off_z(m)), bz);
               out.m[r][cc] = m;
               if ((m & kPrbFlag) && p >= z0 && p < z1 && y >= yo0 && y < yo1 && y < d.ny &&
                   x + cc >= xo0 && x + cc < xo1 && x + cc < d.nx)
@@ -432,6 +455,7 @@ yee_blocked_kernel(const __grid_constant__ CUtensorMap tmF, const __grid_constan
           }
         }
       }
+      if (abort) break;
     }
     if (abort) break;
     ++Cn;  // the unit's last staged plane was only read as "plane s"
@@ -462,14 +486,21 @@ cudaError_t launch_k(const StepArgs& a, const CUtensorMap& tmF, const CUtensorMa
 int blocked_box_x() { return kBX; }
 int blocked_box_y() { return kRY; }
 
-BlockedTiling blocked_tiling(const Dims& d, int K, int num_sms) {
+BlockedTiling blocked_tiling(const Dims& d, int K, int num_sms, int aligned) {
   BlockedTiling t{};
   const int TX = kRX - 2 * K, TY = kRY - 2 * K, phi = K & 1;
   t.K = K;
   t.tiles_x = (d.nx + phi + TX - 1) / TX;
   t.tiles_y = (d.ny + TY - 1) / TY;
-  const long long items = (long long)t.tiles_x * t.tiles_y * d.nz;
-  t.grid = (int)(items < num_sms ? items : num_sms);
+  const long long tiles = (long long)t.tiles_x * t.tiles_y;
+  if (aligned && tiles <= num_sms) {
+    t.zsplit = (int)(num_sms / tiles < d.nz ? num_sms / tiles : d.nz);
+    t.grid = (int)(tiles * t.zsplit);
+  } else {
+    const long long items = tiles * d.nz;
+    t.zsplit = 0;
+    t.grid = (int)(items < num_sms ? items : num_sms);
+  }
   return t;
 }
 

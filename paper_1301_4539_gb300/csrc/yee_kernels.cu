@@ -66,9 +66,9 @@ yee_step_simple_kernel(StepArgs a) {
     if (z >= z0 && owner) {
       const long long pt = ((long long)z * d.ny1 + y) * d.nxp + x;
       const uint32_t m = a.mat[pt];
-      const float2 cx = a.coef[m & 1023u];
-      const float2 cy = a.coef[(m >> 10) & 1023u];
-      const float2 cz = a.coef[(m >> 20) & 1023u];
+      const float2 cx = a.coef[cls_of(m, 0)];
+      const float2 cy = a.coef[cls_of(m, 1)];
+      const float2 cz = a.coef[cls_of(m, 2)];
       float bx = curl_br(hz, sH[2][ty - 1][tx], hy, hyp);
       float by = curl_br(hx, hxp, hz, sH[2][ty][tx - 1]);
       float bz = curl_br(hy, sH[1][ty][tx - 1], hx, sH[0][ty - 1][tx]);
@@ -134,9 +134,9 @@ energy_partial_kernel(const float* f, const uint32_t* mat, const double* eps_tab
     const int z = (int)(r / d.ny1);
     const uint32_t m = mat[pt];
     const float ex = ld_f(f, d, 0, x, y, z), ey = ld_f(f, d, 1, x, y, z), ez = ld_f(f, d, 2, x, y, z);
-    acc += eps_tab[m & 1023u] * ((double)ex * (double)ex);
-    acc += eps_tab[(m >> 10) & 1023u] * ((double)ey * (double)ey);
-    acc += eps_tab[(m >> 20) & 1023u] * ((double)ez * (double)ez);
+    acc += eps_tab[cls_of(m, 0)] * ((double)ex * (double)ex);
+    acc += eps_tab[cls_of(m, 1)] * ((double)ey * (double)ey);
+    acc += eps_tab[cls_of(m, 2)] * ((double)ez * (double)ez);
     const float hx = ld_f(f, d, 3, x, y, z), hy = ld_f(f, d, 4, x, y, z), hz = ld_f(f, d, 5, x, y, z);
     const float hxn = h_upd(hx, S, ld_f(f, d, 1, x, y, z + 1), ey, ld_f(f, d, 2, x, y + 1, z), ez);
     const float hyn = h_upd(hy, S, ld_f(f, d, 2, x + 1, y, z), ez, ld_f(f, d, 0, x, y, z + 1), ex);

@@ -142,7 +142,7 @@ def test_argument_errors_on_gpu(sophie):
     bad[0, 0, 0] = np.nan
     with pytest.raises(so.SophieError):
         g.set_materials(bad, zeros)
-    # every cell distinct -> far more than 1023 distinct edge means
+    # every cell distinct -> far more than 511 distinct edge means
     g12 = so.Grid(12, 12, 12, DX, wl.cfl_dt(DX))
     many = (1.0 + np.arange(12 ** 3, dtype=np.float32).reshape(12, 12, 12) * 1e-3)
     with pytest.raises(so.SophieError) as e:
