@@ -157,6 +157,23 @@ int sophie_read_probe(sophie_grid *g, int probe_id, double *out, int cap, int *n
 int sophie_energy(sophie_grid *g, double *W);
 
 /*
+ * The energy of sophie_energy, for callers that cannot allocate device memory
+ * when they ask for it: code that records the step loop into a CUDA graph
+ * (cudaMalloc may not be called during stream capture) or a host that
+ * reserves a fixed device-memory budget up front. The paper has no
+ * counterpart; it is an interface convenience. W_dev is a caller-owned device
+ * pointer that receives W (double, J). No memory is allocated: the reduction's
+ * partial sums live in a static device array of 2432 doubles (19 KiB, held by
+ * every device that loads the library until exit). The first call on a device
+ * fetches that array's address (make it before any stream capture). Enqueued
+ * on the grid's stream; does not synchronise and does not check finiteness.
+ * Calls whose kernels overlap on the GPU (several grids or streams) race on
+ * the shared array. Errors: EINVAL (NULL, or a grid needing more reduction
+ * blocks than the array holds), ECUDA.
+ */
+int sophie_energy_noalloc(sophie_grid *g, double *W_dev);
+
+/*
  * Copy one component from / to a host array of (nx+1)*(ny+1)*(nz+1) floats in
  * the storage layout above (x fastest). sophie_set_fields zeroes PEC edges
  * and out-of-range entries after the copy. Both synchronise.

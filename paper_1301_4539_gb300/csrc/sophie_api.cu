@@ -727,6 +727,18 @@ int sophie_energy(sophie_grid* g, double* W) {
   return SOPHIE_OK;
 }
 
+int sophie_energy_noalloc(sophie_grid* g, double* W_dev) {
+  if (!g || !W_dev) return fail(SOPHIE_EINVAL, "NULL argument");
+  const char* why = "";
+  const double dx = g->dx;
+  const int rc = energy_noalloc(g->F[g->cur], g->mat, g->eps_tab, g->d, g->S32, 0.5 * kEps0 * dx * dx * dx,
+                                W_dev, g->stream, &why);
+  if (rc == -1) return fail(SOPHIE_EINVAL, "%s", why);
+  if (rc != 0) return fail(SOPHIE_ECUDA, "energy (no allocation) failed: %s", why);
+  g->launches += 2;
+  return SOPHIE_OK;
+}
+
 int sophie_set_fields(sophie_grid* g, int comp, const float* host) {
   if (!g || !host) return fail(SOPHIE_EINVAL, "NULL argument");
   if (comp < 0 || comp > 5) return fail(SOPHIE_EINVAL, "comp must be in 0..5");

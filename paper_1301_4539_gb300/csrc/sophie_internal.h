@@ -113,6 +113,13 @@ cudaError_t launch_energy(const float* f, const uint32_t* mat, const double* eps
                           const Dims& d, float S, double* partials, int nblocks,
                           double* out, cudaStream_t s);
 int energy_blocks(const Dims& d);
+// Same reduction, final sum multiplied by `scale` and written to `out`.
+cudaError_t launch_energy_scaled(const float* f, const uint32_t* mat, const double* eps_tab, const Dims& d,
+                                 float S, double* partials, int nblocks, double scale, double* out,
+                                 cudaStream_t s);
+// Energy with partial sums in a fixed static device buffer (energy_noalloc.cu).
+int energy_noalloc(const float* f, const uint32_t* mat, const double* eps_tab, const Dims& d, float S,
+                   double scale, double* W_dev, cudaStream_t s, const char** why);
 cudaError_t launch_mask_component(float* f, const Dims& d, int comp, cudaStream_t s);
 cudaError_t launch_or_flag(uint32_t* mat, long long pos, uint32_t bit, cudaStream_t s);
 

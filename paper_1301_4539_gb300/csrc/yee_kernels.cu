@@ -150,12 +150,12 @@ energy_partial_kernel(const float* f, const uint32_t* mat, const double* eps_tab
 }
 
 __global__ void __launch_bounds__(kEThreads)
-energy_final_kernel(const double* partials, int n, double* out) {
+energy_final_kernel(const double* partials, int n, double scale, double* out) {
   __shared__ double sh[kEThreads / 32];
   double acc = 0.0;
   for (int i = threadIdx.x; i < n; i += kEThreads) acc += partials[i];
   const double t = block_sum(acc, sh);
-  if (threadIdx.x == 0) *out = t;
+  if (threadIdx.x == 0) *out = t * scale;
 }
 
 // Zero PEC edges and entries outside a component's valid range (see sophie.h).
@@ -203,7 +203,17 @@ cudaError_t launch_energy(const float* f, const uint32_t* mat, const double* eps
   energy_partial_kernel<<<nblocks, kEThreads, 0, s>>>(f, mat, eps_tab, d, S, partials);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  energy_final_kernel<<<1, kEThreads, 0, s>>>(partials, nblocks, out);
+  energy_final_kernel<<<1, kEThreads, 0, s>>>(partials, nblocks, 1.0, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_energy_scaled(const float* f, const uint32_t* mat, const double* eps_tab, const Dims& d,
+                                 float S, double* partials, int nblocks, double scale, double* out,
+                                 cudaStream_t s) {
+  energy_partial_kernel<<<nblocks, kEThreads, 0, s>>>(f, mat, eps_tab, d, S, partials);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  energy_final_kernel<<<1, kEThreads, 0, s>>>(partials, nblocks, scale, out);
   return cudaGetLastError();
 }
 

@@ -39,6 +39,7 @@ SIGNATURES = {
     "sophie_get_step": (_I, [_P, ctypes.POINTER(_LL)]),
     "sophie_read_probe": (_I, [_P, _I, _P, _I, ctypes.POINTER(_I)]),
     "sophie_energy": (_I, [_P, ctypes.POINTER(_D)]),
+    "sophie_energy_noalloc": (_I, [_P, _P]),
     "sophie_set_fields": (_I, [_P, _I, _P]),
     "sophie_get_fields": (_I, [_P, _I, _P]),
     "sophie_reset": (_I, [_P]),
@@ -141,6 +142,11 @@ def sophie_energy(g: int) -> float:
     w = _D()
     _chk(load().sophie_energy(g, ctypes.byref(w)))
     return w.value
+
+
+def sophie_energy_noalloc(g: int, W_dev: int) -> None:
+    """Energy into caller-owned device memory (a double at address W_dev); no allocation."""
+    _chk(load().sophie_energy_noalloc(g, W_dev))
 
 
 def sophie_set_fields(g: int, comp: int, host: np.ndarray) -> None:
