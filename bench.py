@@ -35,6 +35,10 @@ N_CELLS_SIDE = 256
 T_STEPS = 1000
 FIELD_BYTES = 48   # read + write six float32 components per cell-update
 MAT_BYTES = 4      # one 32-bit material word read per cell per launch
+# DRAM bytes (read + write) per launch from one ncu capture of each kernel on
+# this workload (profiles/*.md); None where the kernel changed since.
+NCU_TRAFFIC = {("yee_blocked", 2): 522.851584e6 + 358.680064e6,
+               ("yee_blocked", 3): 546.369280e6 + 368.397312e6}
 
 
 def parse():
@@ -142,11 +146,11 @@ def cpu_baseline(w, budget_s: float = 15.0):
         g.add_source(*s)
     for p in w["probes"]:
         g.add_probe(*p)
+    g.step(2)  # warm the pages and caches
     t0 = time.perf_counter()
-    g.step(1)
-    t1 = time.perf_counter()
-    per = max(t1 - t0, 1e-3)
-    m = max(1, min(200, int(budget_s / per)))
+    g.step(3)
+    per = max((time.perf_counter() - t0) / 3, 1e-4)
+    m = max(1, min(1000, int(budget_s / per)))
     t0 = time.perf_counter()
     g.step(m)
     dt = time.perf_counter() - t0
@@ -173,11 +177,12 @@ def run_reference(args):
         g.add_source(*s)
     for p in w["probes"]:
         g.add_probe(*p)
+    g.step(2)  # warm the pages and caches
     t0 = time.perf_counter()
-    g.step(1)
-    per = max(time.perf_counter() - t0, 1e-3)
+    g.step(3)
+    per = max((time.perf_counter() - t0) / 3, 1e-4)
     # each bench step: a bounded sample of the run, ~10 s of CPU work
-    m = max(1, min(100, int(10.0 / per)))
+    m = max(1, min(1000, int(10.0 / per)))
     for _ in range(args.warmup):
         g.step(1)
     times = []
@@ -218,62 +223,78 @@ def run_ours(args):
     g = so.Grid(n, n, n, w["dx"], w["dt"])
     stream = torch.cuda.current_stream()
     g.set_stream(stream.cuda_stream)
-    if args.k:
-        g.configure(temporal_k=args.k)
     g.set_materials(w["eps"], w["sigma"])
     for s in w["sources"]:
         g.add_source(*s)
     pids = [g.add_probe(*p) for p in w["probes"]]
 
-    def one_run():
-        g.reset()
-        g.step(args.tsteps)
-        return g.energy()
+    def timed(k, steps, warmup, profile):
+        """Device time of `steps` whole runs (reset, tsteps steps, energy) at k steps per launch."""
+        g.configure(temporal_k=k)
+        for _ in range(warmup):
+            g.reset()
+            g.step(args.tsteps)
+            g.energy()
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        l0 = g.launch_count()
+        if profile:
+            g.profile(True)
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        energy = None
+        for _ in range(steps):
+            g.reset()
+            g.step(args.tsteps)
+            energy = g.energy()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        ms = ev0.elapsed_time(ev1)
+        launches = g.launch_count() - l0
+        prof = None
+        if profile:
+            prof = {kk: g.profile_read(kk) for kk in (so.KERNEL_PLAIN, so.KERNEL_BLOCKED, so.KERNEL_ENERGY)}
+            g.profile(False)
+        if world > 1:
+            t = torch.tensor([ms], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms, launches, prof, energy
 
-    for _ in range(args.warmup):
-        one_run()
-    torch.cuda.synchronize()
-    if world > 1:
-        dist.barrier()
+    K = args.k or 2
     sampler = ClockSampler(local)
     sampler.start()
-    l0 = g.launch_count()
-    g.profile(True)
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize()
-    ev0.record(stream)
-    energies = []
-    for _ in range(args.steps):
-        g.reset()
-        g.step(args.tsteps)
-        energies.append(g.energy())
-    ev1.record(stream)
-    torch.cuda.synchronize()
-    ms = ev0.elapsed_time(ev1)
-    launches = g.launch_count() - l0
-    prof = {k: g.profile_read(k) for k in (so.KERNEL_PLAIN, so.KERNEL_BLOCKED, so.KERNEL_ENERGY)}
-    g.profile(False)
+    ms, launches, prof, energy = timed(K, args.steps, args.warmup, True)
     clocks = sampler.stop()
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
     total_updates = cells * args.tsteps * args.steps * world
     value = total_updates / (ms / 1e3) / 1e9
 
-    # dominant kernel and its roofline
+    # dominant kernel of the timed region and its roofline
     kid = max(prof, key=lambda k: prof[k][1])
     kl, kms = prof[kid]
-    k_fused = args.k if (kid == so.KERNEL_BLOCKED and args.k) else 1
     bytes_per_launch = cells * (FIELD_BYTES + MAT_BYTES)
     peak, peak_kind = peaks()
     avg_ms = kms / max(kl, 1)
     achieved = bytes_per_launch / (avg_ms / 1e3) / 1e9
+    kname = {0: "yee_plain", 1: "yee_blocked", 2: "energy"}[kid]
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": None, "kernel": {0: "yee_plain", 1: "yee_blocked", 2: "energy"}[kid],
-            "steps_per_launch": k_fused, "avg_launch_ms": avg_ms, "peak_source": peak_kind,
-            "algorithmic_bytes_per_launch": bytes_per_launch}
+            "traffic": NCU_TRAFFIC.get((kname, K if kid == so.KERNEL_BLOCKED else 1)), "kernel": kname,
+            "steps_per_launch": K if kid == so.KERNEL_BLOCKED else 1, "avg_launch_ms": avg_ms,
+            "peak_source": peak_kind, "algorithmic_bytes_per_launch": bytes_per_launch,
+            "kernel_share_of_timed_region": kms / ms}
+
+    # the other step kernels on the same workload (fewer runs), for comparison
+    variants = {f"k{K}": value}
+    for kk in (1, 2, 3):
+        if kk == K:
+            continue
+        vms, _, _, _ = timed(kk, max(2, min(args.steps, 3)), 1, False)
+        variants[f"k{kk}"] = cells * args.tsteps * max(2, min(args.steps, 3)) * world / (vms / 1e3) / 1e9
+    variants["speedup_vs_plain"] = {k: v / variants["k1"] for k, v in variants.items() if k.startswith("k")}
+    g.configure(temporal_k=K)
 
     e2e = None
     if not args.no_e2e and rank == 0:
@@ -291,10 +312,10 @@ def run_ours(args):
                 "config": {"workload": f"{n}^3 PEC sphere cavity (64 lossy dielectric spheres, centre Ez "
                                        f"source, 16 probes), {args.tsteps} time steps per bench step",
                            "grid": [n, n, n], "time_steps_per_bench_step": args.tsteps,
-                           "temporal_k": args.k or "default", "parallelism": f"replicas x{world}",
+                           "temporal_k": K, "parallelism": f"replicas x{world}",
                            "l2": "inputs larger than L2 (no flush)"},
-                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-                "clocks": clocks, "energy_J": energies[-1]}
+                "roofline": roof, "variants_gcells": variants, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": launches, "clocks": clocks, "energy_J": energy}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

@@ -197,8 +197,8 @@ int sophie_set_stream(sophie_grid *g, void *cuda_stream);
 int sophie_sync(sophie_grid *g);
 
 /*
- * temporal_k: steps fused per launch (1 = plain kernel, 2..8 = temporally
- * blocked), 0 = library default. tile_x: 0 or 64 = TMA-staged 64x16 tiles
+ * temporal_k: steps fused per launch (1 = plain kernel, 2..4 = temporally
+ * blocked; 5..8 reserved, ENOTSUP), 0 = library default (2). tile_x: 0 or 64 = TMA-staged 64x16 tiles
  * (default), 32 = 32x8 tiles with direct loads (a slower reference kernel;
  * identical results); tile_y: reserved, 0.
  * precision: SOPHIE_FP32 (others: ENOTSUP). Errors: EINVAL, ENOTSUP.
