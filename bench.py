@@ -227,10 +227,11 @@ def run_ours(args):
     for s in w["sources"]:
         g.add_source(*s)
     pids = [g.add_probe(*p) for p in w["probes"]]
+    g_prec = [so.FP32]
 
     def timed(k, steps, warmup, profile):
         """Device time of `steps` whole runs (reset, tsteps steps, energy) at k steps per launch."""
-        g.configure(temporal_k=k)
+        g.configure(temporal_k=k, precision=g_prec[0])
         for _ in range(warmup):
             g.reset()
             g.step(args.tsteps)
@@ -288,13 +289,25 @@ def run_ours(args):
 
     # the other step kernels on the same workload (fewer runs), for comparison
     variants = {f"k{K}": value}
+    nv = max(2, min(args.steps, 3))
     for kk in (1, 2, 3):
         if kk == K:
             continue
-        vms, _, _, _ = timed(kk, max(2, min(args.steps, 3)), 1, False)
-        variants[f"k{kk}"] = cells * args.tsteps * max(2, min(args.steps, 3)) * world / (vms / 1e3) / 1e9
-    variants["speedup_vs_plain"] = {k: v / variants["k1"] for k, v in variants.items() if k.startswith("k")}
-    g.configure(temporal_k=K)
+        vms, _, _, _ = timed(kk, nv, 1, False)
+        variants[f"k{kk}"] = cells * args.tsteps * nv * world / (vms / 1e3) / 1e9
+    # storage-precision forms (float arithmetic, 2-byte fields in HBM)
+    for pname, prec in (("fp16", so.FP16), ("bf16", so.BF16)):
+        g.configure(temporal_k=1, precision=prec)
+        g_prec[0] = prec
+        if prec == so.FP16:
+            g.set_storage_scale([2.0 ** 10] * 6)
+        for kk in (1, 2):
+            vms, _, _, _ = timed(kk, nv, 1, False)
+            variants[f"{pname}_k{kk}"] = cells * args.tsteps * nv * world / (vms / 1e3) / 1e9
+        g_prec[0] = so.FP32
+        g.configure(temporal_k=1, precision=so.FP32)
+    variants["speedup_vs_plain"] = {k: v / variants["k1"] for k, v in variants.items() if k != "speedup_vs_plain"}
+    g.configure(temporal_k=K, precision=so.FP32)
 
     e2e = None
     if not args.no_e2e and rank == 0:

@@ -66,8 +66,12 @@ extern "C" {
 #define SOPHIE_GAUSS_SINE 0
 #define SOPHIE_GAUSS      1
 
-/* Storage precision for sophie_configure. */
+/* Storage precision of the six field arrays (sophie_configure). Arithmetic is
+ * float in every mode; the 2-byte modes store field * scale[comp] (see
+ * sophie_set_storage_scale) rounded to nearest even once per launch. */
 #define SOPHIE_FP32 0
+#define SOPHIE_FP16 1
+#define SOPHIE_BF16 2
 
 /* Kernel ids for sophie_profile_read. */
 #define SOPHIE_KERNEL_PLAIN   0  /* one fused H+E step per launch           */
@@ -201,9 +205,22 @@ int sophie_sync(sophie_grid *g);
  * blocked; 5..8 reserved, ENOTSUP), 0 = library default (2). tile_x: 0 or 64 = TMA-staged 64x16 tiles
  * (default), 32 = 32x8 tiles with direct loads (a slower reference kernel;
  * identical results); tile_y: reserved, 0.
- * precision: SOPHIE_FP32 (others: ENOTSUP). Errors: EINVAL, ENOTSUP.
+ * precision: SOPHIE_FP32, SOPHIE_FP16 or SOPHIE_BF16 storage of the fields
+ * (a change converts the current fields; synchronises). In the 2-byte modes
+ * one launch loads the stored fields, computes its k steps in float and
+ * rounds once when storing, so results depend on k (no longer bitwise equal
+ * across k). Errors: EINVAL, ENOTSUP, ENOMEM.
  */
 int sophie_configure(sophie_grid *g, int temporal_k, int tile_x, int tile_y, int precision);
+
+/*
+ * Per-component storage scales for the 2-byte modes (6 floats, powers of two
+ * in [2^-61, 2^60], default 1): component c is stored as field * scale[c], so
+ * a scale that brings the fields' working range near 1 keeps them clear of the
+ * half format's subnormals and overflow. The current fields are converted.
+ * No effect on float storage. Errors: EINVAL.
+ */
+int sophie_set_storage_scale(sophie_grid *g, const float *scale);
 
 /* Number of kernels this grid has launched since creation. */
 int sophie_launch_count(sophie_grid *g, long long *launches);

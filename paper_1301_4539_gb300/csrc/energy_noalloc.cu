@@ -33,9 +33,9 @@ double* g_addr[kMaxDevices] = {nullptr};
 
 }  // namespace
 
-int energy_noalloc(const float* f, const uint32_t* mat, const double* eps_tab, const Dims& d, float S,
-                   double scale, double* W_dev, cudaStream_t s, const char** why) {
-  const int nblocks = energy_blocks(d);
+int energy_noalloc(const StepArgs& a, const double* eps_tab, double scale, double* W_dev, cudaStream_t s,
+                   const char** why) {
+  const int nblocks = energy_blocks(a.d);
   if (nblocks > kMaxBlocks) {
     *why = "grid needs more reduction blocks than the static scratch holds";
     return -1;
@@ -59,7 +59,7 @@ int energy_noalloc(const float* f, const uint32_t* mat, const double* eps_tab, c
     }
     scratch = g_addr[dev];
   }
-  const cudaError_t e = launch_energy_scaled(f, mat, eps_tab, d, S, scratch, nblocks, scale, W_dev, s);
+  const cudaError_t e = launch_energy_scaled(a, eps_tab, scratch, nblocks, scale, W_dev, s);
   if (e != cudaSuccess) {
     *why = cudaGetErrorString(e);
     return -4;

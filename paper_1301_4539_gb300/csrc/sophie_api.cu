@@ -21,6 +21,7 @@
 
 #include "../../include/sophie.h"
 #include "sophie_internal.h"
+#include "yee_store.cuh"
 
 using namespace sophie;
 
@@ -83,7 +84,10 @@ struct sophie_grid {
   bool use_simple = false;  // tile_x == 32: untiled-load reference kernel
   double dx = 0, dt = 0, S64 = 0;
   float S32 = 0;
-  float* F[2] = {nullptr, nullptr};
+  void* F[2] = {nullptr, nullptr};  // field buffers in storage format `fmt`
+  int fmt = kF32;                   // StoreFmt
+  int esz = 4;                      // bytes per stored value
+  float sc[6] = {1, 1, 1, 1, 1, 1};  // stored = field * sc (2-byte formats)
   int cur = 0;
   uint32_t* mat = nullptr;     // device material words
   uint32_t* mat_host = nullptr;  // pinned staging for uploads
@@ -352,6 +356,11 @@ StepArgs make_step_args(sophie_grid* g) {
   StepArgs a{};
   a.fin = g->F[g->cur];
   a.fout = g->F[1 - g->cur];
+  a.fmt = g->fmt;
+  for (int c = 0; c < 6; ++c) {
+    a.sc[c] = g->fmt == kF32 ? 1.f : g->sc[c];
+    a.isc[c] = 1.f / a.sc[c];
+  }
   a.mat = g->mat;
   a.coef = g->coef;
   a.d = g->d;
@@ -413,10 +422,11 @@ void free_grid(sophie_grid* g) {
 int copy_component(sophie_grid* g, int comp, void* host, bool to_device, int buf) {
   const Dims& d = g->d;
   cudaMemcpy3DParms p{};
-  cudaPitchedPtr dev = make_cudaPitchedPtr(g->F[buf] + (size_t)comp * d.plane, (size_t)d.nxp * 4,
-                                           (size_t)d.nx + 1, (size_t)6 * d.ny1);
-  cudaPitchedPtr hst = make_cudaPitchedPtr(host, (size_t)(d.nx + 1) * 4, (size_t)d.nx + 1, (size_t)d.ny1);
-  p.extent = make_cudaExtent((size_t)(d.nx + 1) * 4, (size_t)d.ny1, (size_t)d.nz1);
+  const size_t es = (size_t)g->esz;
+  cudaPitchedPtr dev = make_cudaPitchedPtr(static_cast<unsigned char*>(g->F[buf]) + (size_t)comp * d.plane * es,
+                                           (size_t)d.nxp * es, (size_t)d.nx + 1, (size_t)6 * d.ny1);
+  cudaPitchedPtr hst = make_cudaPitchedPtr(host, (size_t)(d.nx + 1) * es, (size_t)d.nx + 1, (size_t)d.ny1);
+  p.extent = make_cudaExtent((size_t)(d.nx + 1) * es, (size_t)d.ny1, (size_t)d.nz1);
   if (to_device) {
     p.srcPtr = hst;
     p.dstPtr = dev;
@@ -427,6 +437,114 @@ int copy_component(sophie_grid* g, int comp, void* host, bool to_device, int buf
     p.kind = cudaMemcpyDeviceToHost;
   }
   CUDA_TRY(cudaMemcpy3DAsync(&p, g->stream));
+  return SOPHIE_OK;
+}
+
+bool encode_all_maps(sophie_grid* g) {
+  const Dims& d = g->d;
+  const int bxp = plain_box_x(g->fmt), bxb = blocked_box_x(g->fmt);
+  return encode_maps(d, g->fmt, g->F[0], g->mat, bxp, plain_box_y(), &g->tmF[0], &g->tmM) &&
+         encode_maps(d, g->fmt, g->F[1], nullptr, bxp, plain_box_y(), &g->tmF[1], nullptr) &&
+         encode_maps(d, g->fmt, g->F[0], g->mat, bxb, blocked_box_y(), &g->tmFB[0], &g->tmMB) &&
+         encode_maps(d, g->fmt, g->F[1], nullptr, bxb, blocked_box_y(), &g->tmFB[1], nullptr);
+}
+
+// float <-> stored value (host side), stored = field * scale, round to nearest even.
+void to_store(int fmt, float scale, const float* in, void* out, size_t n) {
+  if (fmt == kF16) {
+    __half* o = static_cast<__half*>(out);
+    for (size_t i = 0; i < n; ++i) o[i] = __float2half_rn(in[i] * scale);
+  } else if (fmt == kBF16) {
+    __nv_bfloat16* o = static_cast<__nv_bfloat16*>(out);
+    for (size_t i = 0; i < n; ++i) o[i] = __float2bfloat16_rn(in[i] * scale);
+  } else {
+    memcpy(out, in, n * 4);
+  }
+}
+
+void from_store(int fmt, float scale, const void* in, float* out, size_t n) {
+  const float inv = 1.f / scale;
+  if (fmt == kF16) {
+    const __half* p = static_cast<const __half*>(in);
+    for (size_t i = 0; i < n; ++i) out[i] = __half2float(p[i]) * inv;
+  } else if (fmt == kBF16) {
+    const __nv_bfloat16* p = static_cast<const __nv_bfloat16*>(in);
+    for (size_t i = 0; i < n; ++i) out[i] = __bfloat162float(p[i]) * inv;
+  } else {
+    memcpy(out, in, n * 4);
+  }
+}
+
+int set_component(sophie_grid* g, int comp, const float* host) {
+  const Dims& d = g->d;
+  const size_t n = (size_t)(d.nx + 1) * d.ny1 * d.nz1;
+  std::vector<unsigned char> tmp;
+  const void* src = host;
+  if (g->fmt != kF32) {
+    tmp.resize(n * g->esz);
+    to_store(g->fmt, g->sc[comp], host, tmp.data(), n);
+    src = tmp.data();
+  }
+  for (int b = 0; b < 2; ++b) {
+    int rc = copy_component(g, comp, const_cast<void*>(src), true, b);
+    if (rc) return rc;
+    cudaError_t e = launch_mask_component(g->F[b], g->esz, g->d, comp, g->stream);
+    if (e != cudaSuccess) return fail(SOPHIE_ECUDA, "mask launch failed: %s", cudaGetErrorString(e));
+    g->launches++;
+  }
+  CUDA_TRY(cudaStreamSynchronize(g->stream));
+  return SOPHIE_OK;
+}
+
+int get_component(sophie_grid* g, int comp, float* host) {
+  const Dims& d = g->d;
+  const size_t n = (size_t)(d.nx + 1) * d.ny1 * d.nz1;
+  if (g->fmt == kF32) return copy_component(g, comp, host, false, g->cur);
+  std::vector<unsigned char> tmp(n * g->esz);
+  int rc = copy_component(g, comp, tmp.data(), false, g->cur);
+  if (rc) return rc;
+  CUDA_TRY(cudaStreamSynchronize(g->stream));
+  from_store(g->fmt, g->sc[comp], tmp.data(), host, n);
+  return SOPHIE_OK;
+}
+
+// Re-store the current fields in format `fmt` with scales `sc` (host round trip).
+int restore_fields(sophie_grid* g, int fmt, const float* sc) {
+  const Dims& d = g->d;
+  const size_t n = (size_t)(d.nx + 1) * d.ny1 * d.nz1;
+  std::vector<float> all(6 * n);
+  for (int c = 0; c < 6; ++c) {
+    int rc = get_component(g, c, all.data() + c * n);
+    if (rc) return rc;
+  }
+  CUDA_TRY(cudaStreamSynchronize(g->stream));
+  const int esz = fmt == kF32 ? 4 : 2;
+  if (esz != g->esz) {
+    const size_t bytes = (size_t)d.zstride * d.nz1 * esz;
+    void* nb[2] = {nullptr, nullptr};
+    for (int b = 0; b < 2; ++b) {
+      if (cudaMalloc(&nb[b], bytes) != cudaSuccess) {
+        cudaGetLastError();
+        if (nb[0]) cudaFree(nb[0]);
+        return fail(SOPHIE_ENOMEM, "field buffer allocation failed");
+      }
+      CUDA_TRY(cudaMemsetAsync(nb[b], 0, bytes, g->stream));
+    }
+    CUDA_TRY(cudaStreamSynchronize(g->stream));
+    cudaFree(g->F[0]);
+    cudaFree(g->F[1]);
+    g->F[0] = nb[0];
+    g->F[1] = nb[1];
+    g->esz = esz;
+  }
+  g->fmt = fmt;
+  for (int c = 0; c < 6; ++c) g->sc[c] = sc[c];
+  if (!encode_all_maps(g)) return fail(SOPHIE_ECUDA, "cuTensorMapEncodeTiled failed");
+  g->cur = 0;
+  for (int c = 0; c < 6; ++c) {
+    int rc = set_component(g, c, all.data() + c * n);
+    if (rc) return rc;
+  }
   return SOPHIE_OK;
 }
 
@@ -517,14 +635,8 @@ int sophie_create_grid(int nx, int ny, int nz, double dx, double dt, sophie_grid
       cudaDeviceGetAttribute(&g->num_sms, cudaDevAttrMultiProcessorCount, dev);
       if (g->num_sms <= 0) g->num_sms = 1;
     }
-    if (!encode_plain_maps(d, g->F[0], g->mat, &g->tmF[0], &g->tmM) ||
-        !encode_plain_maps(d, g->F[1], nullptr, &g->tmF[1], nullptr)) {
+    if (!encode_all_maps(g)) {
       rc = fail(SOPHIE_ECUDA, "cuTensorMapEncodeTiled failed");
-      break;
-    }
-    if (!encode_maps(d, g->F[0], g->mat, blocked_box_x(), blocked_box_y(), &g->tmFB[0], &g->tmMB) ||
-        !encode_maps(d, g->F[1], nullptr, blocked_box_x(), blocked_box_y(), &g->tmFB[1], nullptr)) {
-      rc = fail(SOPHIE_ECUDA, "cuTensorMapEncodeTiled failed (blocked box)");
       break;
     }
     {
@@ -685,9 +797,12 @@ int sophie_read_probe(sophie_grid* g, int probe_id, double* out, int cap, int* n
   float fixed_v = 0.f;
   if (pr.fixed) {
     const Dims& d = g->d;
-    const float* src = g->F[g->cur] + (long long)pr.k * d.zstride + (long long)pr.comp * d.plane +
-                       (long long)pr.j * d.nxp + pr.i;
-    CUDA_TRY(cudaMemcpyAsync(&fixed_v, src, 4, cudaMemcpyDeviceToHost, g->stream));
+    const long long off = (long long)pr.k * d.zstride + (long long)pr.comp * d.plane + (long long)pr.j * d.nxp + pr.i;
+    unsigned char raw[4] = {0, 0, 0, 0};
+    CUDA_TRY(cudaMemcpyAsync(raw, static_cast<unsigned char*>(g->F[g->cur]) + off * g->esz, g->esz,
+                             cudaMemcpyDeviceToHost, g->stream));
+    CUDA_TRY(cudaStreamSynchronize(g->stream));
+    from_store(g->fmt, g->sc[pr.comp], raw, &fixed_v, 1);
   } else if (m > 0) {
     CUDA_TRY(cudaMemcpyAsync(tmp.data(), g->pbuf + (size_t)probe_id * g->pcap, (size_t)m * 4,
                              cudaMemcpyDeviceToHost, g->stream));
@@ -709,8 +824,8 @@ int sophie_energy(sophie_grid* g, double* W) {
     eb = prof_event(g);
     cudaEventRecord(ea, g->stream);
   }
-  cudaError_t e = launch_energy(g->F[g->cur], g->mat, g->eps_tab, g->d, g->S32, g->e_partials,
-                                g->e_blocks, g->e_out, g->stream);
+  const StepArgs sa = make_step_args(g);
+  cudaError_t e = launch_energy(sa, g->eps_tab, g->e_partials, g->e_blocks, g->e_out, g->stream);
   if (e != cudaSuccess) return fail(SOPHIE_ECUDA, "energy launch failed: %s", cudaGetErrorString(e));
   if (g->prof) {
     cudaEventRecord(eb, g->stream);
@@ -731,8 +846,8 @@ int sophie_energy_noalloc(sophie_grid* g, double* W_dev) {
   if (!g || !W_dev) return fail(SOPHIE_EINVAL, "NULL argument");
   const char* why = "";
   const double dx = g->dx;
-  const int rc = energy_noalloc(g->F[g->cur], g->mat, g->eps_tab, g->d, g->S32, 0.5 * kEps0 * dx * dx * dx,
-                                W_dev, g->stream, &why);
+  const StepArgs sa = make_step_args(g);
+  const int rc = energy_noalloc(sa, g->eps_tab, 0.5 * kEps0 * dx * dx * dx, W_dev, g->stream, &why);
   if (rc == -1) return fail(SOPHIE_EINVAL, "%s", why);
   if (rc != 0) return fail(SOPHIE_ECUDA, "energy (no allocation) failed: %s", why);
   g->launches += 2;
@@ -742,28 +857,31 @@ int sophie_energy_noalloc(sophie_grid* g, double* W_dev) {
 int sophie_set_fields(sophie_grid* g, int comp, const float* host) {
   if (!g || !host) return fail(SOPHIE_EINVAL, "NULL argument");
   if (comp < 0 || comp > 5) return fail(SOPHIE_EINVAL, "comp must be in 0..5");
-  for (int b = 0; b < 2; ++b) {
-    int rc = copy_component(g, comp, (void*)host, true, b);
-    if (rc) return rc;
-    cudaError_t e = launch_mask_component(g->F[b], g->d, comp, g->stream);
-    if (e != cudaSuccess) return fail(SOPHIE_ECUDA, "mask launch failed: %s", cudaGetErrorString(e));
-    g->launches++;
-  }
-  CUDA_TRY(cudaStreamSynchronize(g->stream));
-  return SOPHIE_OK;
+  return set_component(g, comp, host);
 }
 
 int sophie_get_fields(sophie_grid* g, int comp, float* host) {
   if (!g || !host) return fail(SOPHIE_EINVAL, "NULL argument");
   if (comp < 0 || comp > 5) return fail(SOPHIE_EINVAL, "comp must be in 0..5");
-  int rc = copy_component(g, comp, host, false, g->cur);
+  int rc = get_component(g, comp, host);
   if (rc) return rc;
   return check_err_word(g);
 }
 
+int sophie_set_storage_scale(sophie_grid* g, const float* scale) {
+  if (!g || !scale) return fail(SOPHIE_EINVAL, "NULL argument");
+  for (int c = 0; c < 6; ++c) {
+    int ex = 0;
+    const float m = std::frexp(scale[c], &ex);
+    if (!(scale[c] > 0) || !std::isfinite(scale[c]) || m != 0.5f || ex < -60 || ex > 61)
+      return fail(SOPHIE_EINVAL, "scale[%d] = %g must be a power of two in [2^-61, 2^60]", c, (double)scale[c]);
+  }
+  return restore_fields(g, g->fmt, scale);
+}
+
 int sophie_reset(sophie_grid* g) {
   if (!g) return fail(SOPHIE_EINVAL, "NULL grid");
-  const size_t fbytes = (size_t)g->d.zstride * g->d.nz1 * 4;
+  const size_t fbytes = (size_t)g->d.zstride * g->d.nz1 * g->esz;
   CUDA_TRY(cudaMemsetAsync(g->F[0], 0, fbytes, g->stream));
   CUDA_TRY(cudaMemsetAsync(g->F[1], 0, fbytes, g->stream));
   if (g->pbuf) CUDA_TRY(cudaMemsetAsync(g->pbuf, 0, (size_t)kMaxProbes * g->pcap * 4, g->stream));
@@ -795,11 +913,18 @@ int sophie_configure(sophie_grid* g, int temporal_k, int tile_x, int tile_y, int
   if (temporal_k >= 2 && !blocked_supported(temporal_k))
     return fail(SOPHIE_ENOTSUP, "temporal_k = %d not built (supported: 1..4)", temporal_k);
   if (tile_x < 0 || tile_y < 0) return fail(SOPHIE_EINVAL, "tile sizes must be >= 0");
-  if (precision != SOPHIE_FP32) return fail(SOPHIE_ENOTSUP, "precision %d not supported", precision);
   if (tile_x != 0 && tile_x != 32 && tile_x != 64) return fail(SOPHIE_EINVAL, "tile_x must be 0, 32 or 64");
+  if (precision < SOPHIE_FP32 || precision > SOPHIE_BF16)
+    return fail(SOPHIE_ENOTSUP, "precision %d not supported", precision);
+  if (tile_x == 32 && precision != SOPHIE_FP32)
+    return fail(SOPHIE_ENOTSUP, "the 32x8 reference kernel stores float only");
+  if (precision != g->fmt) {
+    int rc = restore_fields(g, precision, g->sc);
+    if (rc) return rc;
+  }
   g->temporal_k = temporal_k == 0 ? 2 : temporal_k;
-  g->use_simple = tile_x == 32;
   g->precision = precision;
+  g->use_simple = tile_x == 32;
   return SOPHIE_OK;
 }
 

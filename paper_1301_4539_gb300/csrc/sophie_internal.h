@@ -69,8 +69,11 @@ struct PrbTable {
 };
 
 struct StepArgs {
-  const float* fin;
-  float* fout;
+  const void* fin;  // field buffers in the storage format `fmt`
+  void* fout;
+  int fmt;          // StoreFmt (yee_store.cuh): 0 float, 1 half, 2 bfloat16
+  float sc[6];      // stored value = field * sc[comp] (2-byte formats)
+  float isc[6];     // 1 / sc
   const uint32_t* mat;
   const float2* coef;
   Dims d;
@@ -97,30 +100,29 @@ struct BlockedTiling {
 
 // Launchers (return cudaError_t of the launch).
 cudaError_t launch_step_simple(const StepArgs& a, cudaStream_t s);
-bool encode_maps(const Dims& d, float* fields, uint32_t* mat, int box_x, int box_y, CUtensorMap* tmF,
+bool encode_maps(const Dims& d, int fmt, void* fields, uint32_t* mat, int box_x, int box_y, CUtensorMap* tmF,
                  CUtensorMap* tmM);
-bool encode_plain_maps(const Dims& d, float* fields, uint32_t* mat, CUtensorMap* tmF, CUtensorMap* tmM);
+int plain_box_x(int fmt);
+int plain_box_y();
 PlainTiling plain_tiling(const Dims& d, int num_sms, int zchunk_override);
 cudaError_t launch_step_plain(const StepArgs& a, const CUtensorMap& tmF, const CUtensorMap& tmM,
                               const PlainTiling& t, cudaStream_t s);
 BlockedTiling blocked_tiling(const Dims& d, int K, int num_sms, int aligned);
 bool blocked_supported(int K);
-int blocked_box_x();
+int blocked_box_x(int fmt);
 int blocked_box_y();
 cudaError_t launch_step_blocked(const StepArgs& a, const CUtensorMap& tmF, const CUtensorMap& tmM,
                                 const BlockedTiling& t, cudaStream_t s);
-cudaError_t launch_energy(const float* f, const uint32_t* mat, const double* eps_tab,
-                          const Dims& d, float S, double* partials, int nblocks,
+cudaError_t launch_energy(const StepArgs& a, const double* eps_tab, double* partials, int nblocks,
                           double* out, cudaStream_t s);
 int energy_blocks(const Dims& d);
 // Same reduction, final sum multiplied by `scale` and written to `out`.
-cudaError_t launch_energy_scaled(const float* f, const uint32_t* mat, const double* eps_tab, const Dims& d,
-                                 float S, double* partials, int nblocks, double scale, double* out,
-                                 cudaStream_t s);
+cudaError_t launch_energy_scaled(const StepArgs& a, const double* eps_tab, double* partials, int nblocks,
+                                 double scale, double* out, cudaStream_t s);
 // Energy with partial sums in a fixed static device buffer (energy_noalloc.cu).
-int energy_noalloc(const float* f, const uint32_t* mat, const double* eps_tab, const Dims& d, float S,
-                   double scale, double* W_dev, cudaStream_t s, const char** why);
-cudaError_t launch_mask_component(float* f, const Dims& d, int comp, cudaStream_t s);
+int energy_noalloc(const StepArgs& a, const double* eps_tab, double scale, double* W_dev, cudaStream_t s,
+                   const char** why);
+cudaError_t launch_mask_component(void* f, int esz, const Dims& d, int comp, cudaStream_t s);
 cudaError_t launch_or_flag(uint32_t* mat, long long pos, uint32_t bit, cudaStream_t s);
 
 }  // namespace sophie

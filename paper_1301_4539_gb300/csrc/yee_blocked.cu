@@ -32,6 +32,7 @@
 #include "sophie_internal.h"
 #include "tma_util.cuh"
 #include "yee_rare.cuh"
+#include "yee_store.cuh"
 #include "yee_update.cuh"
 
 namespace sophie {
@@ -39,21 +40,29 @@ namespace sophie {
 namespace {
 
 constexpr int kRX = 64;
-constexpr int kBX = kRX + 4;  // TMA box: region rounded out to a 4-float boundary
 constexpr int kR = 4;         // rows per thread
 constexpr int kW = 8;         // consumer warps
 constexpr int kRY = kR * kW;  // 32
 constexpr int kNS = 3;
 constexpr int kConsumers = kW * 32;
 constexpr int kThreads = kConsumers;  // thread 0 also issues the TMA loads
-constexpr uint32_t kFieldBytes = kBX * kRY * 6 * 4;
-constexpr uint32_t kMatBytes = kBX * kRY * 4;
-constexpr uint32_t kLoadBytes = kFieldBytes + kMatBytes;
-constexpr uint32_t kStageBytes = (kLoadBytes + 127) / 128 * 128;
-static_assert(kFieldBytes % 128 == 0, "material box alignment");
 
-template <int K>
+// TMA box of a storage format: the region rounded out to the 16-byte x granule.
+template <int F>
+struct BoxCfg {
+  using T = typename Store<F>::T;
+  static constexpr int GX = Store<F>::kAlign;
+  static constexpr int BX = kRX + GX;
+  static constexpr uint32_t kFieldBytes = BX * kRY * 6 * sizeof(T);
+  static constexpr uint32_t kMatBytes = BX * kRY * 4;
+  static constexpr uint32_t kLoadBytes = kFieldBytes + kMatBytes;
+  static constexpr uint32_t kStageBytes = (kLoadBytes + 127) / 128 * 128;
+  static_assert(kFieldBytes % 128 == 0, "material box alignment");
+};
+
+template <int K, int F>
 struct Cfg {
+  static constexpr uint32_t kStageBytes = BoxCfg<F>::kStageBytes;
   static constexpr int TX = kRX - 2 * K;
   static constexpr int TY = kRY - 2 * K;
   static constexpr int PHI = K & 1;  // x tiles shifted so that region starts are even
@@ -67,7 +76,8 @@ struct Cfg {
   static constexpr uint32_t kSmem = kBarOff + kNS * 8;
 };
 
-__device__ __forceinline__ int FI(int f, int r, int c) { return (f * kRY + r) * kBX + c; }
+template <int F>
+__device__ __forceinline__ int FI(int f, int r, int c) { return (f * kRY + r) * BoxCfg<F>::BX + c; }
 
 struct St {
   float ex[kR][2], ey[kR][2], ez[kR][2], hx[kR][2], hy[kR][2], hz[kR][2];
@@ -119,7 +129,7 @@ __device__ __forceinline__ int first_iter(int z0) {
 
 // Issues the CTA's TMA loads in consumption order: for each unit, planes
 // first_iter-1 .. z1-1+K of its tile (thread 0 only).
-template <int K>
+template <int K, int F>
 struct Loader {
   UnitIter it;
   int p = 0, pend = -1, bx = 0, ry = 0;
@@ -133,28 +143,32 @@ struct Loader {
       int z0, z1;
       if (!it.next(tile, z0, z1)) return false;
       const int tx = (int)(tile % t.tiles_x), ty = (int)(tile / t.tiles_x);
-      const int rx = tx * Cfg<K>::TX - Cfg<K>::PHI - K;
-      ry = ty * Cfg<K>::TY - K;
-      bx = rx & ~3;
+      const int rx = tx * Cfg<K, F>::TX - Cfg<K, F>::PHI - K;
+      ry = ty * Cfg<K, F>::TY - K;
+      bx = rx & ~(BoxCfg<F>::GX - 1);
       p = first_iter<K>(z0) - 1;
       pend = z1 - 1 + K;
     }
     const int s = (int)(issued % kNS);
     const uint32_t bar = bar0 + 8u * s;
-    mbar_arrive_expect_tx(bar, kLoadBytes);
-    tma_load_4d(smem_u32(base + s * kStageBytes), tmF, bx, ry, 0, p, bar);
-    tma_load_3d(smem_u32(base + s * kStageBytes + kFieldBytes), tmM, bx, ry, p, bar);
+    using B = BoxCfg<F>;
+    mbar_arrive_expect_tx(bar, B::kLoadBytes);
+    tma_load_4d(smem_u32(base + s * B::kStageBytes), tmF, bx, ry, 0, p, bar);
+    tma_load_3d(smem_u32(base + s * B::kStageBytes + B::kFieldBytes), tmM, bx, ry, p, bar);
     ++p;
     ++issued;
     return true;
   }
 };
 
-template <int K>
+template <int K, int FMT>
 __global__ void __launch_bounds__(kThreads, 1)
 yee_blocked_kernel(const __grid_constant__ CUtensorMap tmF, const __grid_constant__ CUtensorMap tmM,
                    const __grid_constant__ StepArgs a, BlockedTiling t) {
-  using C = Cfg<K>;
+  using C = Cfg<K, FMT>;
+  using B = BoxCfg<FMT>;
+  using SF = Store<FMT>;
+  using T = typename B::T;
   // Dynamic shared memory starts the CTA's shared window (no static shared
   // variables here), so it is 1024-byte aligned and its offsets are
   // compile-time constants.
@@ -166,8 +180,8 @@ yee_blocked_kernel(const __grid_constant__ CUtensorMap tmF, const __grid_constan
   }
   const uint32_t bar0 = smem_u32(base + C::kBarOff);
   auto full = [&](int s) { return bar0 + 8u * s; };
-  auto sF = [&](int s) { return reinterpret_cast<float*>(base + s * kStageBytes); };
-  auto sM = [&](int s) { return reinterpret_cast<const uint32_t*>(base + s * kStageBytes + kFieldBytes); };
+  auto sF = [&](int s) { return reinterpret_cast<const T*>(base + s * B::kStageBytes); };
+  auto sM = [&](int s) { return reinterpret_cast<const uint32_t*>(base + s * B::kStageBytes + B::kFieldBytes); };
   // H seam rows: hp[level][warp][comp: 0 = hx, 1 = hz][64]
   float* hp = reinterpret_cast<float*>(base + C::kHpOff);
   // E seam rows: ep[level-1][parity][warp][comp: 0 = ex, 1 = ez][64]
@@ -184,7 +198,7 @@ yee_blocked_kernel(const __grid_constant__ CUtensorMap tmF, const __grid_constan
   }
   __syncthreads();
   const Dims d = a.d;
-  Loader<K> ld(t, d.nz);
+  Loader<K, FMT> ld(t, d.nz);
   if (threadIdx.x == 0) {
     prefetch_tmap(&tmF);
     prefetch_tmap(&tmM);
@@ -203,7 +217,7 @@ yee_blocked_kernel(const __grid_constant__ CUtensorMap tmF, const __grid_constan
   while (!abort && it.next(tile, z0, z1)) {
     const int tx = (int)(tile % t.tiles_x), ty = (int)(tile / t.tiles_x);
     const int rx = tx * C::TX - C::PHI - K, ry = ty * C::TY - K;
-    const int ox = rx & 3;  // 0 or 2: region start inside the TMA box
+    const int ox = rx & (B::GX - 1);  // even: region start inside the TMA box
     const int col0 = ox + 2 * lane;
     const int x = rx + 2 * lane;  // global x of this lane's first position
     // output x range of this tile (the first tile of an odd K starts at -1)
@@ -248,8 +262,8 @@ yee_blocked_kernel(const __grid_constant__ CUtensorMap tmF, const __grid_constan
       if (!ok) set_err(a.err, 8);
       // (a failed wait is acted on at the first level barrier below; until then
       // the stage is only read, never written)
-      const float* F = sF(sc);
-      const float* Fn = sF(sn);
+      const T* F = sF(sc);
+      const T* Fn = sF(sn);
       const uint32_t* M = sM(sc);
       const int par = s & 1;
 
@@ -259,15 +273,15 @@ yee_blocked_kernel(const __grid_constant__ CUtensorMap tmF, const __grid_constan
 #pragma unroll
       for (int r = 0; r < kR; ++r) {
         const int row = warp * kR + r;
-        const float2 v0 = *reinterpret_cast<const float2*>(&F[FI(0, row, col0)]);
-        const float2 v1 = *reinterpret_cast<const float2*>(&F[FI(1, row, col0)]);
-        const float2 v2 = *reinterpret_cast<const float2*>(&F[FI(2, row, col0)]);
-        const float2 v3 = *reinterpret_cast<const float2*>(&F[FI(3, row, col0)]);
-        const float2 v4 = *reinterpret_cast<const float2*>(&F[FI(4, row, col0)]);
-        const float2 v5 = *reinterpret_cast<const float2*>(&F[FI(5, row, col0)]);
-        const uint2 mm = *reinterpret_cast<const uint2*>(&M[row * kBX + col0]);
-        const float2 n0 = *reinterpret_cast<const float2*>(&Fn[FI(0, row, col0)]);
-        const float2 n1 = *reinterpret_cast<const float2*>(&Fn[FI(1, row, col0)]);
+        const float2 v0 = SF::ld2(&F[FI<FMT>(0, row, col0)], a.isc[0]);
+        const float2 v1 = SF::ld2(&F[FI<FMT>(1, row, col0)], a.isc[1]);
+        const float2 v2 = SF::ld2(&F[FI<FMT>(2, row, col0)], a.isc[2]);
+        const float2 v3 = SF::ld2(&F[FI<FMT>(3, row, col0)], a.isc[3]);
+        const float2 v4 = SF::ld2(&F[FI<FMT>(4, row, col0)], a.isc[4]);
+        const float2 v5 = SF::ld2(&F[FI<FMT>(5, row, col0)], a.isc[5]);
+        const uint2 mm = *reinterpret_cast<const uint2*>(&M[row * B::BX + col0]);
+        const float2 n0 = SF::ld2(&Fn[FI<FMT>(0, row, col0)], a.isc[0]);
+        const float2 n1 = SF::ld2(&Fn[FI<FMT>(1, row, col0)], a.isc[1]);
         in.ex[r][0] = v0.x; in.ex[r][1] = v0.y;
         in.ey[r][0] = v1.x; in.ey[r][1] = v1.y;
         in.ez[r][0] = v2.x; in.ez[r][1] = v2.y;
@@ -282,8 +296,8 @@ yee_blocked_kernel(const __grid_constant__ CUtensorMap tmF, const __grid_constan
       float bex[2], bez[2];
       {
         const int brow = warp * kR + kR < kRY ? warp * kR + kR : kRY - 1;
-        const float2 b0 = *reinterpret_cast<const float2*>(&F[FI(0, brow, col0)]);
-        const float2 b2 = *reinterpret_cast<const float2*>(&F[FI(2, brow, col0)]);
+        const float2 b0 = SF::ld2(&F[FI<FMT>(0, brow, col0)], a.isc[0]);
+        const float2 b2 = SF::ld2(&F[FI<FMT>(2, brow, col0)], a.isc[2]);
         bex[0] = b0.x; bex[1] = b0.y;
         bez[0] = b2.x; bez[1] = b2.y;
       }
@@ -437,20 +451,20 @@ yee_blocked_kernel(const __grid_constant__ CUtensorMap tmF, const __grid_constan
 #pragma unroll
           for (int r = 0; r < kR; ++r) {
             if (!((rowmask >> r) & 1)) continue;
-            float* o = a.fout + (long long)p * d.zstride + rowbase + (long long)r * d.nxp;
+            T* o = static_cast<T*>(a.fout) + (long long)p * d.zstride + rowbase + (long long)r * d.nxp;
             const float vals[6][2] = {{out.ex[r][0], out.ex[r][1]}, {out.ey[r][0], out.ey[r][1]},
                                       {out.ez[r][0], out.ez[r][1]}, {out.hx[r][0], out.hx[r][1]},
                                       {out.hy[r][0], out.hy[r][1]}, {out.hz[r][0], out.hz[r][1]}};
             if (v0 && v1) {
 #pragma unroll
               for (int f = 0; f < 6; ++f)
-                *reinterpret_cast<float2*>(o + f * d.plane) = make_float2(vals[f][0], vals[f][1]);
+                SF::st2(o + f * d.plane, vals[f][0], vals[f][1], a.sc[f]);
             } else if (v0) {
 #pragma unroll
-              for (int f = 0; f < 6; ++f) o[f * d.plane] = vals[f][0];
+              for (int f = 0; f < 6; ++f) SF::st(o + f * d.plane, vals[f][0], a.sc[f]);
             } else if (v1) {
 #pragma unroll
-              for (int f = 0; f < 6; ++f) o[f * d.plane + 1] = vals[f][1];
+              for (int f = 0; f < 6; ++f) SF::st(o + f * d.plane + 1, vals[f][1], a.sc[f]);
             }
           }
         }
@@ -467,23 +481,34 @@ yee_blocked_kernel(const __grid_constant__ CUtensorMap tmF, const __grid_constan
   }
 }
 
-template <int K>
+template <int K, int F>
 cudaError_t launch_k(const StepArgs& a, const CUtensorMap& tmF, const CUtensorMap& tmM, const BlockedTiling& t,
                      cudaStream_t s) {
   static bool attr = false;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(yee_blocked_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)Cfg<K>::kSmem);
+    cudaError_t e = cudaFuncSetAttribute(yee_blocked_kernel<K, F>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)Cfg<K, F>::kSmem);
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  yee_blocked_kernel<K><<<t.grid, kThreads, Cfg<K>::kSmem, s>>>(tmF, tmM, a, t);
+  yee_blocked_kernel<K, F><<<t.grid, kThreads, Cfg<K, F>::kSmem, s>>>(tmF, tmM, a, t);
   return cudaGetLastError();
+}
+
+template <int F>
+cudaError_t launch_fmt(const StepArgs& a, const CUtensorMap& tmF, const CUtensorMap& tmM, const BlockedTiling& t,
+                       cudaStream_t s) {
+  switch (t.K) {
+    case 2: return launch_k<2, F>(a, tmF, tmM, t, s);
+    case 3: return launch_k<3, F>(a, tmF, tmM, t, s);
+    case 4: return launch_k<4, F>(a, tmF, tmM, t, s);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 }  // namespace
 
-int blocked_box_x() { return kBX; }
+int blocked_box_x(int fmt) { return fmt == kF32 ? BoxCfg<kF32>::BX : BoxCfg<kF16>::BX; }
 int blocked_box_y() { return kRY; }
 
 BlockedTiling blocked_tiling(const Dims& d, int K, int num_sms, int aligned) {
@@ -508,10 +533,10 @@ bool blocked_supported(int K) { return K >= 2 && K <= 4; }
 
 cudaError_t launch_step_blocked(const StepArgs& a, const CUtensorMap& tmF, const CUtensorMap& tmM,
                                 const BlockedTiling& t, cudaStream_t s) {
-  switch (t.K) {
-    case 2: return launch_k<2>(a, tmF, tmM, t, s);
-    case 3: return launch_k<3>(a, tmF, tmM, t, s);
-    case 4: return launch_k<4>(a, tmF, tmM, t, s);
+  switch (a.fmt) {
+    case kF32: return launch_fmt<kF32>(a, tmF, tmM, t, s);
+    case kF16: return launch_fmt<kF16>(a, tmF, tmM, t, s);
+    case kBF16: return launch_fmt<kBF16>(a, tmF, tmM, t, s);
     default: return cudaErrorInvalidValue;
   }
 }

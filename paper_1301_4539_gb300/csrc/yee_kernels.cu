@@ -9,6 +9,7 @@
 // with TMA instead and share the update expressions of yee_update.cuh, so all
 // step kernels give bitwise identical fields.
 #include "sophie_internal.h"
+#include "yee_store.cuh"
 #include "yee_update.cuh"
 
 namespace sophie {
@@ -29,6 +30,7 @@ yee_step_simple_kernel(StepArgs a) {
   __shared__ float sE[3][kSTY + 2][kSTX + 2];
   __shared__ float sH[3][kSTY + 1][kSTX + 1];
   const Dims d = a.d;
+  const float* fin = static_cast<const float*>(a.fin);  // float storage only
   const int tx = threadIdx.x % (kSTX + 1);
   const int ty = threadIdx.x / (kSTX + 1);
   const int x0 = blockIdx.x * kSTX, y0 = blockIdx.y * kSTY;
@@ -45,17 +47,17 @@ yee_step_simple_kernel(StepArgs a) {
   }
   for (int z = zs; z < z1; ++z) {
     for (int c = 0; c < 3; ++c) {
-      sE[c][ty][tx] = ld_f(a.fin, d, c, x, y, z);
-      if (tx == kSTX) sE[c][ty][tx + 1] = ld_f(a.fin, d, c, x + 1, y, z);
-      if (ty == kSTY) sE[c][ty + 1][tx] = ld_f(a.fin, d, c, x, y + 1, z);
+      sE[c][ty][tx] = ld_f(fin, d, c, x, y, z);
+      if (tx == kSTX) sE[c][ty][tx + 1] = ld_f(fin, d, c, x + 1, y, z);
+      if (ty == kSTY) sE[c][ty + 1][tx] = ld_f(fin, d, c, x, y + 1, z);
     }
     __syncthreads();
     const float ex0 = sE[0][ty][tx], ey0 = sE[1][ty][tx], ez0 = sE[2][ty][tx];
-    float hx = ld_f(a.fin, d, 3, x, y, z);
-    float hy = ld_f(a.fin, d, 4, x, y, z);
-    float hz = ld_f(a.fin, d, 5, x, y, z);
-    const float ey1 = ld_f(a.fin, d, 1, x, y, z + 1);
-    const float ex1 = ld_f(a.fin, d, 0, x, y, z + 1);
+    float hx = ld_f(fin, d, 3, x, y, z);
+    float hy = ld_f(fin, d, 4, x, y, z);
+    float hz = ld_f(fin, d, 5, x, y, z);
+    const float ey1 = ld_f(fin, d, 1, x, y, z + 1);
+    const float ex1 = ld_f(fin, d, 0, x, y, z + 1);
     hx = h_upd(hx, S, ey1, ey0, sE[2][ty + 1][tx], ez0);
     hy = h_upd(hy, S, sE[2][ty][tx + 1], ez0, ex1, ex0);
     hz = h_upd(hz, S, sE[0][ty + 1][tx], ex0, sE[1][ty][tx + 1], ey0);
@@ -84,7 +86,7 @@ yee_step_simple_kernel(StepArgs a) {
       const float ex = e_upd(ex0, cx, bx);
       const float ey = e_upd(ey0, cy, by);
       const float ez = e_upd(ez0, cz, bz);
-      float* o = a.fout + (long long)z * d.zstride + (long long)y * d.nxp + x;
+      float* o = static_cast<float*>(a.fout) + (long long)z * d.zstride + (long long)y * d.nxp + x;
       o[0] = ex;
       o[d.plane] = ey;
       o[2 * d.plane] = ez;
@@ -120,10 +122,22 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
   return t;
 }
 
+template <int F>
+__device__ __forceinline__ float ld_s(const typename Store<F>::T* f, const Dims& d, const float* isc, int c, int x,
+                                      int y, int z) {
+  if (x < 0 || x >= d.nxp || y < 0 || y >= d.ny1 || z < 0 || z >= d.nz1) return 0.f;
+  return Store<F>::ld(f + (long long)z * d.zstride + (long long)c * d.plane + (long long)y * d.nxp + x, isc[c]);
+}
+
+template <int F>
 __global__ void __launch_bounds__(kEThreads)
-energy_partial_kernel(const float* f, const uint32_t* mat, const double* eps_tab, Dims d,
-                      float S, double* partials) {
+energy_partial_kernel(const __grid_constant__ StepArgs a, const double* eps_tab, double* partials) {
   __shared__ double sh[kEThreads / 32];
+  const Dims d = a.d;
+  const float S = a.S;
+  const float* isc = a.isc;
+  const auto* f = static_cast<const typename Store<F>::T*>(a.fin);
+  const uint32_t* mat = a.mat;
   const long long npts = (long long)d.nz1 * d.ny1 * d.nxp;
   double acc = 0.0;
   for (long long pt = (long long)blockIdx.x * kEThreads + threadIdx.x; pt < npts;
@@ -133,14 +147,16 @@ energy_partial_kernel(const float* f, const uint32_t* mat, const double* eps_tab
     const int y = (int)(r % d.ny1);
     const int z = (int)(r / d.ny1);
     const uint32_t m = mat[pt];
-    const float ex = ld_f(f, d, 0, x, y, z), ey = ld_f(f, d, 1, x, y, z), ez = ld_f(f, d, 2, x, y, z);
+    const float ex = ld_s<F>(f, d, isc, 0, x, y, z), ey = ld_s<F>(f, d, isc, 1, x, y, z);
+    const float ez = ld_s<F>(f, d, isc, 2, x, y, z);
     acc += eps_tab[cls_of(m, 0)] * ((double)ex * (double)ex);
     acc += eps_tab[cls_of(m, 1)] * ((double)ey * (double)ey);
     acc += eps_tab[cls_of(m, 2)] * ((double)ez * (double)ez);
-    const float hx = ld_f(f, d, 3, x, y, z), hy = ld_f(f, d, 4, x, y, z), hz = ld_f(f, d, 5, x, y, z);
-    const float hxn = h_upd(hx, S, ld_f(f, d, 1, x, y, z + 1), ey, ld_f(f, d, 2, x, y + 1, z), ez);
-    const float hyn = h_upd(hy, S, ld_f(f, d, 2, x + 1, y, z), ez, ld_f(f, d, 0, x, y, z + 1), ex);
-    const float hzn = h_upd(hz, S, ld_f(f, d, 0, x, y + 1, z), ex, ld_f(f, d, 1, x + 1, y, z), ey);
+    const float hx = ld_s<F>(f, d, isc, 3, x, y, z), hy = ld_s<F>(f, d, isc, 4, x, y, z);
+    const float hz = ld_s<F>(f, d, isc, 5, x, y, z);
+    const float hxn = h_upd(hx, S, ld_s<F>(f, d, isc, 1, x, y, z + 1), ey, ld_s<F>(f, d, isc, 2, x, y + 1, z), ez);
+    const float hyn = h_upd(hy, S, ld_s<F>(f, d, isc, 2, x + 1, y, z), ez, ld_s<F>(f, d, isc, 0, x, y, z + 1), ex);
+    const float hzn = h_upd(hz, S, ld_s<F>(f, d, isc, 0, x, y + 1, z), ex, ld_s<F>(f, d, isc, 1, x + 1, y, z), ey);
     acc += (double)hx * (double)hxn;
     acc += (double)hy * (double)hyn;
     acc += (double)hz * (double)hzn;
@@ -159,7 +175,7 @@ energy_final_kernel(const double* partials, int n, double scale, double* out) {
 }
 
 // Zero PEC edges and entries outside a component's valid range (see sophie.h).
-__global__ void mask_component_kernel(float* f, Dims d, int comp) {
+__global__ void mask_component_kernel(unsigned char* f, int esz, Dims d, int comp) {
   const long long npts = (long long)d.nz1 * d.ny1 * d.nxp;
   for (long long pt = (long long)blockIdx.x * blockDim.x + threadIdx.x; pt < npts;
        pt += (long long)gridDim.x * blockDim.x) {
@@ -176,7 +192,10 @@ __global__ void mask_component_kernel(float* f, Dims d, int comp) {
       case 4: keep = x < d.nx && y <= d.ny && z < d.nz; break;
       default: keep = x < d.nx && y < d.ny && z <= d.nz; break;
     }
-    if (!keep) f[(long long)z * d.zstride + (long long)comp * d.plane + (long long)y * d.nxp + x] = 0.f;
+    if (!keep) {
+      unsigned char* p = f + ((long long)z * d.zstride + (long long)comp * d.plane + (long long)y * d.nxp + x) * esz;
+      for (int b = 0; b < esz; ++b) p[b] = 0;
+    }
   }
 }
 
@@ -198,27 +217,33 @@ int energy_blocks(const Dims& d) {
   return (int)b;
 }
 
-cudaError_t launch_energy(const float* f, const uint32_t* mat, const double* eps_tab, const Dims& d,
-                          float S, double* partials, int nblocks, double* out, cudaStream_t s) {
-  energy_partial_kernel<<<nblocks, kEThreads, 0, s>>>(f, mat, eps_tab, d, S, partials);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  energy_final_kernel<<<1, kEThreads, 0, s>>>(partials, nblocks, 1.0, out);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_energy_scaled(const float* f, const uint32_t* mat, const double* eps_tab, const Dims& d,
-                                 float S, double* partials, int nblocks, double scale, double* out,
-                                 cudaStream_t s) {
-  energy_partial_kernel<<<nblocks, kEThreads, 0, s>>>(f, mat, eps_tab, d, S, partials);
+template <int F>
+cudaError_t launch_energy_f(const StepArgs& a, const double* eps_tab, double* partials, int nblocks, double scale,
+                            double* out, cudaStream_t s) {
+  energy_partial_kernel<F><<<nblocks, kEThreads, 0, s>>>(a, eps_tab, partials);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   energy_final_kernel<<<1, kEThreads, 0, s>>>(partials, nblocks, scale, out);
   return cudaGetLastError();
 }
 
-cudaError_t launch_mask_component(float* f, const Dims& d, int comp, cudaStream_t s) {
-  mask_component_kernel<<<152 * 4, 256, 0, s>>>(f, d, comp);
+cudaError_t launch_energy_scaled(const StepArgs& a, const double* eps_tab, double* partials, int nblocks,
+                                 double scale, double* out, cudaStream_t s) {
+  switch (a.fmt) {
+    case kF32: return launch_energy_f<kF32>(a, eps_tab, partials, nblocks, scale, out, s);
+    case kF16: return launch_energy_f<kF16>(a, eps_tab, partials, nblocks, scale, out, s);
+    case kBF16: return launch_energy_f<kBF16>(a, eps_tab, partials, nblocks, scale, out, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_energy(const StepArgs& a, const double* eps_tab, double* partials, int nblocks, double* out,
+                          cudaStream_t s) {
+  return launch_energy_scaled(a, eps_tab, partials, nblocks, 1.0, out, s);
+}
+
+cudaError_t launch_mask_component(void* f, int esz, const Dims& d, int comp, cudaStream_t s) {
+  mask_component_kernel<<<152 * 4, 256, 0, s>>>(static_cast<unsigned char*>(f), esz, d, comp);
   return cudaGetLastError();
 }
 

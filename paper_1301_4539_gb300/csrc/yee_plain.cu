@@ -22,6 +22,7 @@
 #include "sophie_internal.h"
 #include "tma_util.cuh"
 #include "yee_rare.cuh"
+#include "yee_store.cuh"
 #include "yee_update.cuh"
 
 #include <cudaTypedefs.h>
@@ -33,21 +34,32 @@ namespace sophie {
 namespace {
 
 constexpr int kPX = 64, kPY = 16;
-constexpr int kBX = kPX + 8, kBY = kPY + 2;
+constexpr int kBY = kPY + 2;
 constexpr int kNS = 3;
 constexpr int kCW = kPY / 2;  // consumer warps
 constexpr int kConsumers = kCW * 32;
 constexpr int kThreads = kConsumers + 32;
-constexpr uint32_t kFieldBytes = kBX * kBY * 6 * 4;
-constexpr uint32_t kMatBytes = kBX * kBY * 4;
-constexpr uint32_t kLoadBytes = kFieldBytes + kMatBytes;
-constexpr uint32_t kStageBytes = (kLoadBytes + 127) / 128 * 128;
-constexpr uint32_t kBarOff = kNS * kStageBytes;
-constexpr uint32_t kSmemBytes = kBarOff + 2 * kNS * 8 + 128;
 
-static_assert(kFieldBytes % 128 == 0, "material box must start 128-byte aligned");
-
-__device__ __forceinline__ int FI(int f, int r, int c) { return (f * kBY + r) * kBX + c; }
+// Per storage format: the box starts OX columns left of the tile (OX = the
+// TMA 16-byte granule in elements), so it is (64 + 2 OX) wide. With float
+// storage the updated H is written back into the ring in place; with 2-byte
+// storage it goes to a float buffer (two planes, by parity) instead.
+template <int F>
+struct PCfg {
+  using T = typename Store<F>::T;
+  static constexpr int OX = Store<F>::kAlign;
+  static constexpr int BX = kPX + 2 * OX;
+  static constexpr bool kInPlace = F == kF32;
+  static constexpr uint32_t kFieldBytes = BX * kBY * 6 * sizeof(T);
+  static constexpr uint32_t kMatBytes = BX * kBY * 4;
+  static constexpr uint32_t kLoadBytes = kFieldBytes + kMatBytes;
+  static constexpr uint32_t kStageBytes = (kLoadBytes + 127) / 128 * 128;
+  static constexpr uint32_t kHbOff = kNS * kStageBytes;
+  static constexpr uint32_t kHbBytes = kInPlace ? 0 : 2 * 3 * kBY * BX * 4;
+  static constexpr uint32_t kBarOff = kHbOff + kHbBytes;
+  static constexpr uint32_t kSmemBytes = kBarOff + 2 * kNS * 8 + 128;
+  static_assert(kFieldBytes % 128 == 0, "material box must start 128-byte aligned");
+};
 
 struct Unit {
   int x0, y0, z0, z1;
@@ -68,17 +80,25 @@ __device__ __forceinline__ Unit unit_of(long long u, const PlainTiling& t, int n
 
 __device__ __forceinline__ void set_err(int* err, int code) { atomicOr(err, code); }
 
+template <int FMT>
 __global__ void __launch_bounds__(kThreads, 2)
 yee_plain_kernel(const __grid_constant__ CUtensorMap tmF, const __grid_constant__ CUtensorMap tmM,
                  const __grid_constant__ StepArgs a, PlainTiling t) {
+  using C = PCfg<FMT>;
+  using St = Store<FMT>;
+  using T = typename C::T;
+  constexpr int BX = C::BX;
+  constexpr int OX = C::OX;
+  auto FI = [](int f, int r, int c) { return (f * kBY + r) * BX + c; };
   extern __shared__ unsigned char smem_raw[];
   unsigned char* base = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
-  const uint32_t bar0 = smem_u32(base + kBarOff);
+  const uint32_t bar0 = smem_u32(base + C::kBarOff);
   auto full = [&](int s) { return bar0 + 8u * s; };
   auto empty = [&](int s) { return bar0 + 8u * (kNS + s); };
-  auto sF = [&](int s) { return reinterpret_cast<float*>(base + s * kStageBytes); };
-  auto sM = [&](int s) { return reinterpret_cast<const uint32_t*>(base + s * kStageBytes + kFieldBytes); };
+  auto sF = [&](int s) { return reinterpret_cast<T*>(base + s * C::kStageBytes); };
+  auto sM = [&](int s) { return reinterpret_cast<const uint32_t*>(base + s * C::kStageBytes + C::kFieldBytes); };
+  float* const hbuf = reinterpret_cast<float*>(base + C::kHbOff);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
@@ -108,9 +128,9 @@ yee_plain_kernel(const __grid_constant__ CUtensorMap tmF, const __grid_constant_
           ok = false;
           break;
         }
-        mbar_arrive_expect_tx(full(s), kLoadBytes);
-        tma_load_4d(smem_u32(sF(s)), &tmF, w.x0 - 4, w.y0 - 1, 0, p, full(s));
-        tma_load_3d(smem_u32(sM(s)), &tmM, w.x0 - 4, w.y0 - 1, p, full(s));
+        mbar_arrive_expect_tx(full(s), C::kLoadBytes);
+        tma_load_4d(smem_u32(sF(s)), &tmF, w.x0 - OX, w.y0 - 1, 0, p, full(s));
+        tma_load_3d(smem_u32(sM(s)), &tmM, w.x0 - OX, w.y0 - 1, p, full(s));
       }
     }
     if (!ok) {
@@ -122,38 +142,47 @@ yee_plain_kernel(const __grid_constant__ CUtensorMap tmF, const __grid_constant_
   }
 
   // ---------------- consumer warps ----------------
-  const int c0 = 4 + 2 * lane;
+  const int c0 = OX + 2 * lane;
   const int r0 = 1 + 2 * warp;
   int hr = -1, hc = -1;  // halo H position computed by this lane
   if (lane < 2) {
     hr = r0 + lane;
-    hc = 3;
+    hc = OX - 1;
   } else if (lane < 10) {
     hr = 0;
-    hc = 4 + 8 * warp + (lane - 2);
+    hc = OX + 8 * warp + (lane - 2);
   }
   const float S = a.S;
-  long long C = 0;
+  T* const fout = static_cast<T*>(a.fout);
+  long long C_ = 0;
   bool abort = false;
   for (long long u = blockIdx.x; u < t.units && !abort; u += gridDim.x) {
     const Unit w = unit_of(u, t, d.nz);
     const int ps = w.z0 > 0 ? w.z0 - 1 : 0;
     float hxp[2][2] = {{0.f, 0.f}, {0.f, 0.f}}, hyp[2][2] = {{0.f, 0.f}, {0.f, 0.f}};
-    for (int z = ps; z < w.z1; ++z, ++C) {
-      const int sc = (int)(C % kNS), sn = (int)((C + 1) % kNS);
-      const bool ok = mbar_wait(full(sc), (uint32_t)((C / kNS) & 1)) &&
-                      mbar_wait(full(sn), (uint32_t)(((C + 1) / kNS) & 1));
+    for (int z = ps; z < w.z1; ++z, ++C_) {
+      const int sc = (int)(C_ % kNS), sn = (int)((C_ + 1) % kNS);
+      const bool ok = mbar_wait(full(sc), (uint32_t)((C_ / kNS) & 1)) &&
+                      mbar_wait(full(sn), (uint32_t)(((C_ + 1) / kNS) & 1));
       if (!ok) set_err(a.err, 2);
-      float* F = sF(sc);
-      const float* Fn = sF(sn);
+      T* F = sF(sc);
+      const T* Fn = sF(sn);
+      // Updated H of this plane: in the ring (float storage) or the float buffer.
+      float* const Hb = hbuf + (z & 1) * (3 * kBY * BX);
+      auto hp = [&](int comp, int r, int c) -> float* {
+        if constexpr (C::kInPlace)
+          return reinterpret_cast<float*>(&F[FI(3 + comp, r, c)]);
+        else
+          return &Hb[(comp * kBY + r) * BX + c];
+      };
       float ex[2][2], ey[2][2], ez[2][2], hx[2][2], hy[2][2], hz[2][2];
       if (ok) {
 #pragma unroll
         for (int r = 0; r < 2; ++r) {
           const int row = r0 + r;
-          const float2 vex = *reinterpret_cast<const float2*>(&F[FI(0, row, c0)]);
-          const float2 vey = *reinterpret_cast<const float2*>(&F[FI(1, row, c0)]);
-          const float2 vez = *reinterpret_cast<const float2*>(&F[FI(2, row, c0)]);
+          const float2 vex = St::ld2(&F[FI(0, row, c0)], a.isc[0]);
+          const float2 vey = St::ld2(&F[FI(1, row, c0)], a.isc[1]);
+          const float2 vez = St::ld2(&F[FI(2, row, c0)], a.isc[2]);
           ex[r][0] = vex.x; ex[r][1] = vex.y;
           ey[r][0] = vey.x; ey[r][1] = vey.y;
           ez[r][0] = vez.x; ez[r][1] = vez.y;
@@ -161,41 +190,46 @@ yee_plain_kernel(const __grid_constant__ CUtensorMap tmF, const __grid_constant_
 #pragma unroll
         for (int r = 0; r < 2; ++r) {
           const int row = r0 + r;
-          const float2 vhx = *reinterpret_cast<const float2*>(&F[FI(3, row, c0)]);
-          const float2 vhy = *reinterpret_cast<const float2*>(&F[FI(4, row, c0)]);
-          const float2 vhz = *reinterpret_cast<const float2*>(&F[FI(5, row, c0)]);
-          const float2 nex = *reinterpret_cast<const float2*>(&Fn[FI(0, row, c0)]);
-          const float2 ney = *reinterpret_cast<const float2*>(&Fn[FI(1, row, c0)]);
+          const float2 vhx = St::ld2(&F[FI(3, row, c0)], a.isc[3]);
+          const float2 vhy = St::ld2(&F[FI(4, row, c0)], a.isc[4]);
+          const float2 vhz = St::ld2(&F[FI(5, row, c0)], a.isc[5]);
+          const float2 nex = St::ld2(&Fn[FI(0, row, c0)], a.isc[0]);
+          const float2 ney = St::ld2(&Fn[FI(1, row, c0)], a.isc[1]);
           float exj[2], ezj[2];
           if (r == 0) {
             exj[0] = ex[1][0]; exj[1] = ex[1][1];
             ezj[0] = ez[1][0]; ezj[1] = ez[1][1];
           } else {
-            const float2 a2 = *reinterpret_cast<const float2*>(&F[FI(0, row + 1, c0)]);
-            const float2 b2 = *reinterpret_cast<const float2*>(&F[FI(2, row + 1, c0)]);
+            const float2 a2 = St::ld2(&F[FI(0, row + 1, c0)], a.isc[0]);
+            const float2 b2 = St::ld2(&F[FI(2, row + 1, c0)], a.isc[2]);
             exj[0] = a2.x; exj[1] = a2.y;
             ezj[0] = b2.x; ezj[1] = b2.y;
           }
-          const float ez_ip1 = F[FI(2, row, c0 + 2)];
-          const float ey_ip1 = F[FI(1, row, c0 + 2)];
+          const float ez_ip1 = St::ld(&F[FI(2, row, c0 + 2)], a.isc[2]);
+          const float ey_ip1 = St::ld(&F[FI(1, row, c0 + 2)], a.isc[1]);
           hx[r][0] = h_upd(vhx.x, S, ney.x, ey[r][0], ezj[0], ez[r][0]);
           hx[r][1] = h_upd(vhx.y, S, ney.y, ey[r][1], ezj[1], ez[r][1]);
           hy[r][0] = h_upd(vhy.x, S, ez[r][1], ez[r][0], nex.x, ex[r][0]);
           hy[r][1] = h_upd(vhy.y, S, ez_ip1, ez[r][1], nex.y, ex[r][1]);
           hz[r][0] = h_upd(vhz.x, S, exj[0], ex[r][0], ey[r][1], ey[r][0]);
           hz[r][1] = h_upd(vhz.y, S, exj[1], ex[r][1], ey_ip1, ey[r][1]);
-          *reinterpret_cast<float2*>(&F[FI(3, row, c0)]) = make_float2(hx[r][0], hx[r][1]);
-          *reinterpret_cast<float2*>(&F[FI(4, row, c0)]) = make_float2(hy[r][0], hy[r][1]);
-          *reinterpret_cast<float2*>(&F[FI(5, row, c0)]) = make_float2(hz[r][0], hz[r][1]);
+          *reinterpret_cast<float2*>(hp(0, row, c0)) = make_float2(hx[r][0], hx[r][1]);
+          *reinterpret_cast<float2*>(hp(1, row, c0)) = make_float2(hy[r][0], hy[r][1]);
+          *reinterpret_cast<float2*>(hp(2, row, c0)) = make_float2(hz[r][0], hz[r][1]);
         }
         if (hr >= 0) {
-          const float e0 = F[FI(0, hr, hc)], e1 = F[FI(1, hr, hc)], e2 = F[FI(2, hr, hc)];
-          const float nx_ = h_upd(F[FI(3, hr, hc)], S, Fn[FI(1, hr, hc)], e1, F[FI(2, hr + 1, hc)], e2);
-          const float ny_ = h_upd(F[FI(4, hr, hc)], S, F[FI(2, hr, hc + 1)], e2, Fn[FI(0, hr, hc)], e0);
-          const float nz_ = h_upd(F[FI(5, hr, hc)], S, F[FI(0, hr + 1, hc)], e0, F[FI(1, hr, hc + 1)], e1);
-          F[FI(3, hr, hc)] = nx_;
-          F[FI(4, hr, hc)] = ny_;
-          F[FI(5, hr, hc)] = nz_;
+          const float e0 = St::ld(&F[FI(0, hr, hc)], a.isc[0]);
+          const float e1 = St::ld(&F[FI(1, hr, hc)], a.isc[1]);
+          const float e2 = St::ld(&F[FI(2, hr, hc)], a.isc[2]);
+          const float nx_ = h_upd(St::ld(&F[FI(3, hr, hc)], a.isc[3]), S, St::ld(&Fn[FI(1, hr, hc)], a.isc[1]), e1,
+                                  St::ld(&F[FI(2, hr + 1, hc)], a.isc[2]), e2);
+          const float ny_ = h_upd(St::ld(&F[FI(4, hr, hc)], a.isc[4]), S, St::ld(&F[FI(2, hr, hc + 1)], a.isc[2]),
+                                  e2, St::ld(&Fn[FI(0, hr, hc)], a.isc[0]), e0);
+          const float nz_ = h_upd(St::ld(&F[FI(5, hr, hc)], a.isc[5]), S, St::ld(&F[FI(0, hr + 1, hc)], a.isc[0]),
+                                  e0, St::ld(&F[FI(1, hr, hc + 1)], a.isc[1]), e1);
+          *hp(0, hr, hc) = nx_;
+          *hp(1, hr, hc) = ny_;
+          *hp(2, hr, hc) = nz_;
         }
       }
       abort = named_bar_or(1, kConsumers, !ok);
@@ -207,17 +241,17 @@ yee_plain_kernel(const __grid_constant__ CUtensorMap tmF, const __grid_constant_
         const int row = r0 + r;
         float hzj[2], hxj[2];
         if (r == 0) {
-          const float2 a2 = *reinterpret_cast<const float2*>(&F[FI(5, row - 1, c0)]);
-          const float2 b2 = *reinterpret_cast<const float2*>(&F[FI(3, row - 1, c0)]);
+          const float2 a2 = *reinterpret_cast<const float2*>(hp(2, row - 1, c0));
+          const float2 b2 = *reinterpret_cast<const float2*>(hp(0, row - 1, c0));
           hzj[0] = a2.x; hzj[1] = a2.y;
           hxj[0] = b2.x; hxj[1] = b2.y;
         } else {
           hzj[0] = hz[0][0]; hzj[1] = hz[0][1];
           hxj[0] = hx[0][0]; hxj[1] = hx[0][1];
         }
-        const float hz_im = F[FI(5, row, c0 - 1)];
-        const float hy_im = F[FI(4, row, c0 - 1)];
-        const uint2 m2 = *reinterpret_cast<const uint2*>(&M[row * kBX + c0]);
+        const float hz_im = *hp(2, row, c0 - 1);
+        const float hy_im = *hp(1, row, c0 - 1);
+        const uint2 m2 = *reinterpret_cast<const uint2*>(&M[row * BX + c0]);
         const int y = w.y0 + 2 * warp + r;
         const int x = w.x0 + 2 * lane;
         float eo[3][2];
@@ -242,16 +276,15 @@ yee_plain_kernel(const __grid_constant__ CUtensorMap tmF, const __grid_constant_
                           hx[r][cc], hy[r][cc], hz[r][cc], &a.prb);
         }
         if (out_plane && y < d.ny && x < d.nx) {
-          float* o = a.fout + (long long)z * d.zstride + (long long)y * d.nxp + x;
+          T* o = fout + (long long)z * d.zstride + (long long)y * d.nxp + x;
           const float vals[6][2] = {{eo[0][0], eo[0][1]}, {eo[1][0], eo[1][1]}, {eo[2][0], eo[2][1]},
                                     {hx[r][0], hx[r][1]}, {hy[r][0], hy[r][1]}, {hz[r][0], hz[r][1]}};
           if (x + 1 < d.nx) {
 #pragma unroll
-            for (int f = 0; f < 6; ++f)
-              *reinterpret_cast<float2*>(o + f * d.plane) = make_float2(vals[f][0], vals[f][1]);
+            for (int f = 0; f < 6; ++f) St::st2(o + f * d.plane, vals[f][0], vals[f][1], a.sc[f]);
           } else {
 #pragma unroll
-            for (int f = 0; f < 6; ++f) o[f * d.plane] = vals[f][0];
+            for (int f = 0; f < 6; ++f) St::st(o + f * d.plane, vals[f][0], a.sc[f]);
           }
         }
 #pragma unroll
@@ -260,15 +293,15 @@ yee_plain_kernel(const __grid_constant__ CUtensorMap tmF, const __grid_constant_
           hyp[r][cc] = hy[r][cc];
         }
       }
-      fence_proxy_async_smem();
+      if constexpr (C::kInPlace) fence_proxy_async_smem();
       __syncwarp();
       if (lane == 0) mbar_arrive(empty(sc));
     }
     if (abort) break;
     // The unit's last plane was only read as the "next" plane: release it.
     __syncwarp();
-    if (lane == 0) mbar_arrive(empty((int)(C % kNS)));
-    ++C;
+    if (lane == 0) mbar_arrive(empty((int)(C_ % kNS)));
+    ++C_;
   }
 }
 
@@ -287,26 +320,31 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 
 }  // namespace
 
-bool encode_plain_maps(const Dims& d, float* fields, uint32_t* mat, CUtensorMap* tmF, CUtensorMap* tmM) {
-  return encode_maps(d, fields, mat, kBX, kBY, tmF, tmM);
-}
+int plain_box_x(int fmt) { return fmt == kF32 ? PCfg<kF32>::BX : PCfg<kF16>::BX; }
+int plain_box_y() { return kBY; }
 
-bool encode_maps(const Dims& d, float* fields, uint32_t* mat, int box_x, int box_y, CUtensorMap* tmF,
+bool encode_maps(const Dims& d, int fmt, void* fields, uint32_t* mat, int box_x, int box_y, CUtensorMap* tmF,
                  CUtensorMap* tmM) {
   auto fn = encode_fn();
   if (!fn) return false;
-  cuuint64_t gdF[4] = {(cuuint64_t)d.nxp, (cuuint64_t)d.ny1, 6, (cuuint64_t)d.nz1};
-  cuuint64_t gsF[3] = {(cuuint64_t)d.nxp * 4, (cuuint64_t)d.plane * 4, (cuuint64_t)d.zstride * 4};
-  cuuint32_t boxF[4] = {(cuuint32_t)box_x, (cuuint32_t)box_y, 6, 1};
-  cuuint32_t es[4] = {1, 1, 1, 1};
-  if (fn(tmF, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, fields, gdF, gsF, boxF, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
-         CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
-    return false;
+  const cuuint64_t esz = fmt == kF32 ? 4 : 2;
+  const CUtensorMapDataType dt = fmt == kF32   ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                 : fmt == kF16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
+                                               : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+  if (tmF) {
+    cuuint64_t gdF[4] = {(cuuint64_t)d.nxp, (cuuint64_t)d.ny1, 6, (cuuint64_t)d.nz1};
+    cuuint64_t gsF[3] = {(cuuint64_t)d.nxp * esz, (cuuint64_t)d.plane * esz, (cuuint64_t)d.zstride * esz};
+    cuuint32_t boxF[4] = {(cuuint32_t)box_x, (cuuint32_t)box_y, 6, 1};
+    cuuint32_t es[4] = {1, 1, 1, 1};
+    if (fn(tmF, dt, 4, fields, gdF, gsF, boxF, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      return false;
+  }
   if (tmM) {
     cuuint64_t gdM[3] = {(cuuint64_t)d.nxp, (cuuint64_t)d.ny1, (cuuint64_t)d.nz1};
     cuuint64_t gsM[2] = {(cuuint64_t)d.nxp * 4, (cuuint64_t)d.plane * 4};
     cuuint32_t boxM[3] = {(cuuint32_t)box_x, (cuuint32_t)box_y, 1};
+    cuuint32_t es[3] = {1, 1, 1};
     if (fn(tmM, CU_TENSOR_MAP_DATA_TYPE_UINT32, 3, mat, gdM, gsM, boxM, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
@@ -343,17 +381,28 @@ PlainTiling plain_tiling(const Dims& d, int num_sms, int zchunk_override) {
   return best;
 }
 
-cudaError_t launch_step_plain(const StepArgs& a, const CUtensorMap& tmF, const CUtensorMap& tmM,
-                              const PlainTiling& t, cudaStream_t s) {
+template <int F>
+cudaError_t launch_plain_f(const StepArgs& a, const CUtensorMap& tmF, const CUtensorMap& tmM, const PlainTiling& t,
+                           cudaStream_t s) {
   static bool attr = false;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(yee_plain_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)kSmemBytes);
+    cudaError_t e = cudaFuncSetAttribute(yee_plain_kernel<F>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)PCfg<F>::kSmemBytes);
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  yee_plain_kernel<<<t.grid, kThreads, kSmemBytes, s>>>(tmF, tmM, a, t);
+  yee_plain_kernel<F><<<t.grid, kThreads, PCfg<F>::kSmemBytes, s>>>(tmF, tmM, a, t);
   return cudaGetLastError();
+}
+
+cudaError_t launch_step_plain(const StepArgs& a, const CUtensorMap& tmF, const CUtensorMap& tmM,
+                              const PlainTiling& t, cudaStream_t s) {
+  switch (a.fmt) {
+    case kF32: return launch_plain_f<kF32>(a, tmF, tmM, t, s);
+    case kF16: return launch_plain_f<kF16>(a, tmF, tmM, t, s);
+    case kBF16: return launch_plain_f<kBF16>(a, tmF, tmM, t, s);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 }  // namespace sophie

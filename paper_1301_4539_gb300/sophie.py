@@ -20,7 +20,7 @@ OK, EINVAL, EUNSTABLE, ENOMEM, ECUDA, ENONFINITE, ETIMEOUT, ETOOMANYMAT, ENOTSUP
     0, -1, -2, -3, -4, -5, -6, -7, -8)
 EX, EY, EZ, HX, HY, HZ = range(6)
 GAUSS_SINE, GAUSS = 0, 1
-FP32 = 0
+FP32, FP16, BF16 = 0, 1, 2
 KERNEL_PLAIN, KERNEL_BLOCKED, KERNEL_ENERGY = 0, 1, 2
 
 # Exported symbols with (restype, argtypes).
@@ -46,6 +46,7 @@ SIGNATURES = {
     "sophie_set_stream": (_I, [_P, _P]),
     "sophie_sync": (_I, [_P]),
     "sophie_configure": (_I, [_P, _I, _I, _I, _I]),
+    "sophie_set_storage_scale": (_I, [_P, _P]),
     "sophie_launch_count": (_I, [_P, ctypes.POINTER(_LL)]),
     "sophie_profile": (_I, [_P, _I]),
     "sophie_profile_read": (_I, [_P, _I, ctypes.POINTER(_LL), ctypes.POINTER(_D)]),
@@ -177,6 +178,12 @@ def sophie_configure(g: int, temporal_k: int = 0, tile_x: int = 0, tile_y: int =
     _chk(load().sophie_configure(g, temporal_k, tile_x, tile_y, precision))
 
 
+def sophie_set_storage_scale(g: int, scale) -> None:
+    sc = np.ascontiguousarray(scale, dtype=np.float32)
+    assert sc.size == 6
+    _chk(load().sophie_set_storage_scale(g, sc.ctypes.data))
+
+
 def sophie_launch_count(g: int) -> int:
     n = _LL()
     _chk(load().sophie_launch_count(g, ctypes.byref(n)))
@@ -262,6 +269,9 @@ class Grid:
 
     def configure(self, temporal_k=0, tile_x=0, tile_y=0, precision=FP32):
         sophie_configure(self.h, temporal_k, tile_x, tile_y, precision)
+
+    def set_storage_scale(self, scale):
+        sophie_set_storage_scale(self.h, scale)
 
     def launch_count(self):
         return sophie_launch_count(self.h)

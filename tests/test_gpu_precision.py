@@ -1,0 +1,105 @@
+"""Storage-precision forms (float / half / bfloat16 fields, float arithmetic).
+
+* Round trips: values representable in the storage format come back exactly,
+  with per-component power-of-two scales; switching the format converts the
+  fields.
+* Accuracy: each form against the FP64 oracle on a seeded sphere cavity, as
+  relative L2 over all six fields and over the probe traces. Float storage must
+  stay within the 1e-5 bar; the 2-byte forms are held to loose bounds here
+  (to catch defects) and their measured errors are printed.
+"""
+
+import numpy as np
+import pytest
+
+from gpu_helpers import DX
+from modes import rel_l2
+from paper_1301_4539_gb300 import sophie as so
+from paper_1301_4539_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+
+def test_roundtrip_and_conversion(sophie):
+    nx, ny, nz = 20, 12, 9
+    g = so.Grid(nx, ny, nz, DX, wl.cfl_dt(DX))
+    rng = np.random.default_rng(5)
+    # k/32 with |k| < 128: at most 7 significant bits, exact in half and bfloat16
+    f = [rng.integers(-127, 128, size=(nz + 1, ny + 1, nx + 1)).astype(np.float32) / 32 for _ in range(6)]
+    ref = wl.random_fields(nx, ny, nz, 0)
+    masked = [np.where(ref[c] != 0, f[c], 0).astype(np.float32) for c in range(6)]
+    for c in range(6):
+        g.set_field(c, f[c])
+    for prec in (so.FP16, so.BF16, so.FP32, so.FP16):
+        g.configure(temporal_k=1, precision=prec)
+        for c in range(6):
+            np.testing.assert_array_equal(g.get_field(c), masked[c])
+    g.set_storage_scale([2.0 ** 4, 2.0 ** -3, 1.0, 2.0, 2.0 ** 10, 0.5])
+    for c in range(6):
+        np.testing.assert_array_equal(g.get_field(c), masked[c])
+    with pytest.raises(so.SophieError):
+        g.set_storage_scale([3.0, 1, 1, 1, 1, 1])
+    with pytest.raises(so.SophieError):
+        g.configure(tile_x=32, precision=so.FP16)
+
+
+def _run_modes(oracle_mod, n, steps, modes, full_generator=False):
+    nx = ny = nz = n
+    if full_generator:
+        w = wl.sphere_cavity(n)
+        eps, sig, src, prbs = w["eps"], w["sigma"], w["sources"][0], w["probes"]
+    else:
+        eps, sig = wl.sphere_materials(nx, ny, nz, nspheres=10, seed=1301, radius=(2, 8))
+        amp, f0, bw, t0, kind = wl.gaussian_sine_source()
+        src = (2, nx // 2, ny // 2, nz // 2, amp, f0, bw, t0, kind)
+        prbs = wl.probe_edges(nx, ny, nz, 8, seed=1302)
+    o = oracle_mod.OracleGrid(nx, ny, nz, DX, wl.cfl_dt(DX), "f64")
+    o.set_materials(eps, sig)
+    o.add_source(*src)
+    for p in prbs:
+        o.add_probe(*p)
+    o.step(steps)
+    ref = np.concatenate([a.ravel() for a in o.f])
+    pref = np.concatenate([o.probe(q) for q in range(len(prbs))])
+    out = {}
+    for name, prec, k, scale in modes:
+        g = so.Grid(nx, ny, nz, DX, wl.cfl_dt(DX))
+        g.configure(temporal_k=k, precision=prec)
+        if scale is not None:
+            g.set_storage_scale([scale] * 6)
+        g.set_materials(eps, sig)
+        g.add_source(*src)
+        for p in prbs:
+            g.add_probe(*p)
+        g.step(steps)
+        got = np.concatenate([g.get_field(c).astype(np.float64).ravel() for c in range(6)])
+        pgot = np.concatenate([g.read_probe(q) for q in range(len(prbs))])
+        out[name] = (rel_l2(got, ref), rel_l2(pgot, pref))
+        g.close()
+    return out
+
+
+def test_precision_forms_vs_fp64_oracle(oracle_mod, sophie):
+    modes = [("fp32_k1", so.FP32, 1, None), ("fp32_k2", so.FP32, 2, None),
+             ("fp16_k1", so.FP16, 1, 2.0 ** 10), ("fp16_k2", so.FP16, 2, 2.0 ** 10),
+             ("bf16_k1", so.BF16, 1, None), ("bf16_k2", so.BF16, 2, None)]
+    out = _run_modes(oracle_mod, 64, 400, modes)
+    for k, v in out.items():
+        print(f"precision 64^3 x 400 steps {k}: fields rel-L2 {v[0]:.3e}, probes rel-L2 {v[1]:.3e}")
+    assert out["fp32_k1"][0] < 1e-5 and out["fp32_k2"][0] < 1e-5
+    assert out["fp32_k1"] == out["fp32_k2"]
+    assert out["fp16_k1"][0] < 5e-2 and out["fp16_k2"][0] < 5e-2
+    assert out["bf16_k1"][0] < 5e-1 and out["bf16_k2"][0] < 5e-1
+    # two steps per rounding cannot be worse than one by much
+    assert out["fp16_k2"][0] < 1.5 * out["fp16_k1"][0] + 1e-6
+
+
+@pytest.mark.slow
+def test_precision_forms_256_2000_steps(oracle_mod, sophie):
+    """The precision protocol at 256^3: 2000 steps against the FP64 oracle."""
+    modes = [("fp32_k2", so.FP32, 2, None), ("fp16_k1", so.FP16, 1, 2.0 ** 10),
+             ("fp16_k2", so.FP16, 2, 2.0 ** 10), ("bf16_k2", so.BF16, 2, None)]
+    out = _run_modes(oracle_mod, 256, 2000, modes, full_generator=True)
+    for k, v in out.items():
+        print(f"precision 256^3 x 2000 steps {k}: fields rel-L2 {v[0]:.3e}, probes rel-L2 {v[1]:.3e}")
+    assert out["fp32_k2"][0] < 1e-5
