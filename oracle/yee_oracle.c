@@ -1,12 +1,14 @@
 /*
  * Plain CPU oracle of the 3-D Yee FDTD leapfrog sweep (Sec. 2.1 of Cessenat,
  * "Sophie, an FDTD code on the way to multicore"), in double (_f64) and
- * single (_f32) precision.
+ * single (_f32) precision. Each update uses one fused multiply-add (C's
+ * fma / fmaf, correctly rounded by definition), every other operation is
+ * rounded separately.
  *
  * TEST INFRASTRUCTURE ONLY: only tests/, the smoke check and the benchmark's
  * CPU-baseline leg may load this library. It shares no code, header or table
- * with the CUDA path. Build with -ffp-contract=off so that every a*b+c is two
- * rounded operations, exactly as written.
+ * with the CUDA path. Build with -ffp-contract=off so that no other a*b+c is
+ * fused: only the explicit fma/fmaf calls are.
  *
  * Pins (checked by tests/ with -m "not gpu"):
  *   - exact discrete cavity eigenmodes (closed form) in vacuum and in a uniform
@@ -25,15 +27,19 @@
 
 #define REAL double
 #define SUF f64
+#define FMA fma
 #include "yee_oracle_body.h"
 #undef REAL
 #undef SUF
+#undef FMA
 
 #define REAL float
 #define SUF f32
+#define FMA fmaf
 #include "yee_oracle_body.h"
 #undef REAL
 #undef SUF
+#undef FMA
 
 /*
  * Source waveform values s[m] = amp * w((n0 + m + 1/2) * dt), m in [0, n).

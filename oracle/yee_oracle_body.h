@@ -13,10 +13,16 @@
  * Variables are the paper's antisymmetric pair scaled to V/m: e = E and
  * h = eta0*H, so that the leapfrog of Sec. 2.1 (Eqs. ma2, mf2) reads
  *   h += S * (discrete -curl e),   e = Ca*e + Cb*(discrete curl h),   S = c dt / dx.
+ * Working-precision evaluation: with br the bracket (a1-a0)-(b1-b0),
+ *   h = FMA(S, br, h)   and   e = FMA(Cb, br, Ca*e)
+ * (one fused multiply-add each, every other operation rounded separately).
  */
 
 #ifndef REAL
 #error "define REAL before including yee_oracle_body.h"
+#endif
+#ifndef FMA
+#error "define FMA (fma or fmaf) before including yee_oracle_body.h"
 #endif
 
 #define CAT_(a, b) a##_##b
@@ -118,21 +124,21 @@ static void FN(update_h)(int nx, int ny, int nz, REAL S,
         for (int j = 0; j < ny; ++j)
             for (int i = 0; i <= nx; ++i) {
                 const long p = k * sz + j * sy + i;
-                hx[p] = hx[p] + S * ((ey[p + sz] - ey[p]) - (ez[p + sy] - ez[p]));
+                hx[p] = FMA(S, (ey[p + sz] - ey[p]) - (ez[p + sy] - ez[p]), hx[p]);
             }
 #pragma omp parallel for schedule(static)
     for (int k = 0; k < nz; ++k)
         for (int j = 0; j <= ny; ++j)
             for (int i = 0; i < nx; ++i) {
                 const long p = k * sz + j * sy + i;
-                hy[p] = hy[p] + S * ((ez[p + 1] - ez[p]) - (ex[p + sz] - ex[p]));
+                hy[p] = FMA(S, (ez[p + 1] - ez[p]) - (ex[p + sz] - ex[p]), hy[p]);
             }
 #pragma omp parallel for schedule(static)
     for (int k = 0; k <= nz; ++k)
         for (int j = 0; j < ny; ++j)
             for (int i = 0; i < nx; ++i) {
                 const long p = k * sz + j * sy + i;
-                hz[p] = hz[p] + S * ((ex[p + sy] - ex[p]) - (ey[p + 1] - ey[p]));
+                hz[p] = FMA(S, (ex[p + sy] - ex[p]) - (ey[p + 1] - ey[p]), hz[p]);
             }
 }
 
@@ -168,21 +174,21 @@ static void FN(update_e)(int nx, int ny, int nz,
         for (int j = 1; j < ny; ++j)
             for (int i = 0; i < nx; ++i) {
                 const long p = k * sz + j * sy + i;
-                ex[p] = cax[p] * ex[p] + cbx[p] * BR_X(p);
+                ex[p] = FMA(cbx[p], BR_X(p), cax[p] * ex[p]);
             }
 #pragma omp parallel for schedule(static)
     for (int k = 1; k < nz; ++k)
         for (int j = 0; j < ny; ++j)
             for (int i = 1; i < nx; ++i) {
                 const long p = k * sz + j * sy + i;
-                ey[p] = cay[p] * ey[p] + cby[p] * BR_Y(p);
+                ey[p] = FMA(cby[p], BR_Y(p), cay[p] * ey[p]);
             }
 #pragma omp parallel for schedule(static)
     for (int k = 0; k < nz; ++k)
         for (int j = 1; j < ny; ++j)
             for (int i = 1; i < nx; ++i) {
                 const long p = k * sz + j * sy + i;
-                ez[p] = caz[p] * ez[p] + cbz[p] * BR_Z(p);
+                ez[p] = FMA(cbz[p], BR_Z(p), caz[p] * ez[p]);
             }
     /* Several sources on one edge add their currents in list order. */
     for (int s = 0; s < nsrc; ++s) {
@@ -202,7 +208,7 @@ static void FN(update_e)(int nx, int ny, int nz,
         const REAL *ca = c == 0 ? cax : c == 1 ? cay : caz;
         const REAL *cb = c == 0 ? cbx : c == 1 ? cby : cbz;
         REAL *e = c == 0 ? ex : c == 1 ? ey : ez;
-        e[p] = ca[p] * eold[s] + cb[p] * br;
+        e[p] = FMA(cb[p], br, ca[p] * eold[s]);
     }
 }
 
@@ -276,21 +282,21 @@ double FN(oracle_energy)(int nx, int ny, int nz, REAL S, double dx,
         for (int j = 0; j < ny; ++j)
             for (int i = 0; i <= nx; ++i) {
                 const long p = k * sz + j * sy + i;
-                const REAL hn = hx[p] + S * ((ey[p + sz] - ey[p]) - (ez[p + sy] - ez[p]));
+                const REAL hn = FMA(S, (ey[p + sz] - ey[p]) - (ez[p + sy] - ez[p]), hx[p]);
                 wh += (double)hx[p] * (double)hn;
             }
     for (int k = 0; k < nz; ++k)
         for (int j = 0; j <= ny; ++j)
             for (int i = 0; i < nx; ++i) {
                 const long p = k * sz + j * sy + i;
-                const REAL hn = hy[p] + S * ((ez[p + 1] - ez[p]) - (ex[p + sz] - ex[p]));
+                const REAL hn = FMA(S, (ez[p + 1] - ez[p]) - (ex[p + sz] - ex[p]), hy[p]);
                 wh += (double)hy[p] * (double)hn;
             }
     for (int k = 0; k <= nz; ++k)
         for (int j = 0; j < ny; ++j)
             for (int i = 0; i < nx; ++i) {
                 const long p = k * sz + j * sy + i;
-                const REAL hn = hz[p] + S * ((ex[p + sy] - ex[p]) - (ey[p + 1] - ey[p]));
+                const REAL hn = FMA(S, (ex[p + sy] - ex[p]) - (ey[p + 1] - ey[p]), hz[p]);
                 wh += (double)hz[p] * (double)hn;
             }
     return 0.5 * EPS0 * dx * dx * dx * (we + wh);

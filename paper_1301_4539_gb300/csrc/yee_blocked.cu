@@ -236,8 +236,12 @@ yee_blocked_kernel(const __grid_constant__ CUtensorMap tmF, const __grid_constan
       if (y >= yo0 && y < yo1 && y < d.ny) rowmask |= 1u << r;
     }
 
-    St carry[K > 1 ? K - 1 : 1];
-    float hxp[K][kR][2], hyp[K][kR][2];
+    constexpr int NC = K > 1 ? K - 1 : 1;
+    St carry[NC];
+    // H of the plane below, per level: for levels 1..K-1 it is the level's own
+    // output of the previous iteration, which sits in carry[lv-1] until this
+    // iteration's output replaces it; only level K keeps a separate copy.
+    float hxK[kR][2], hyK[kR][2];
 #pragma unroll
     for (int l = 0; l < (K > 1 ? K - 1 : 1); ++l)
 #pragma unroll
@@ -249,11 +253,9 @@ yee_blocked_kernel(const __grid_constant__ CUtensorMap tmF, const __grid_constan
           carry[l].m[r][c] = 0u;
         }
 #pragma unroll
-    for (int l = 0; l < K; ++l)
+    for (int r = 0; r < kR; ++r)
 #pragma unroll
-      for (int r = 0; r < kR; ++r)
-#pragma unroll
-        for (int c = 0; c < 2; ++c) hxp[l][r][c] = hyp[l][r][c] = 0.f;
+      for (int c = 0; c < 2; ++c) hxK[r][c] = hyK[r][c] = 0.f;
 
     for (int s = s0; s <= s1; ++s, ++Cn) {
       const int sc = (int)(Cn % kNS), sn = (int)((Cn + 1) % kNS);
@@ -308,6 +310,13 @@ yee_blocked_kernel(const __grid_constant__ CUtensorMap tmF, const __grid_constan
       for (int lv = 1; lv <= K; ++lv) {
         const int p = s - lv;  // plane updated by this level
         const long long nstep = a.n0 + lv - 1;
+        // H of this level at plane p-1 (see hxK above)
+        auto hxprev = [&](int lvl, int r, int c) -> float {
+          return lvl < K ? carry[lvl - 1 < NC ? lvl - 1 : 0].hx[r][c] : hxK[r][c];
+        };
+        auto hyprev = [&](int lvl, int r, int c) -> float {
+          return lvl < K ? carry[lvl - 1 < NC ? lvl - 1 : 0].hy[r][c] : hyK[r][c];
+        };
         // ---- H of level lv at plane p ----
         float hx[kR][2], hy[kR][2], hz[kR][2];
 #pragma unroll
@@ -375,8 +384,8 @@ yee_blocked_kernel(const __grid_constant__ CUtensorMap tmF, const __grid_constan
               const float hzi = cc ? hz[r][0] : hz_im1;
               const float hyi = cc ? hy[r][0] : hy_im1;
               const uint32_t m = in.m[r][cc];
-              out.ex[r][cc] = e_upd(in.ex[r][cc], *reinterpret_cast<const float2*>(scoefb + cls_off_x(m)), curl_br(hz[r][cc], hzj, hy[r][cc], hyp[lv - 1][r][cc]));
-              out.ey[r][cc] = e_upd(in.ey[r][cc], *reinterpret_cast<const float2*>(scoefb + cls_off_y(m)), curl_br(hx[r][cc], hxp[lv - 1][r][cc], hz[r][cc], hzi));
+              out.ex[r][cc] = e_upd(in.ex[r][cc], *reinterpret_cast<const float2*>(scoefb + cls_off_x(m)), curl_br(hz[r][cc], hzj, hy[r][cc], hyprev(lv, r, cc)));
+              out.ey[r][cc] = e_upd(in.ey[r][cc], *reinterpret_cast<const float2*>(scoefb + cls_off_y(m)), curl_br(hx[r][cc], hxprev(lv, r, cc), hz[r][cc], hzi));
               out.ez[r][cc] = e_upd(in.ez[r][cc], *reinterpret_cast<const float2*>(scoefb + cls_off_z(m)), curl_br(hy[r][cc], hyi, hx[r][cc], hxj));
               out.m[r][cc] = m;
             }
@@ -393,8 +402,8 @@ yee_blocked_kernel(const __grid_constant__ CUtensorMap tmF, const __grid_constan
               const float hxj = r > 0 ? hx[r > 0 ? r - 1 : 0][cc] : hxa[cc];
               const float hzi = cc ? hz[r][0] : hz_im1;
               const float hyi = cc ? hy[r][0] : hy_im1;
-              float bx = curl_br(hz[r][cc], hzj, hy[r][cc], hyp[lv - 1][r][cc]);
-              float by = curl_br(hx[r][cc], hxp[lv - 1][r][cc], hz[r][cc], hzi);
+              float bx = curl_br(hz[r][cc], hzj, hy[r][cc], hyprev(lv, r, cc));
+              float by = curl_br(hx[r][cc], hxprev(lv, r, cc), hz[r][cc], hzi);
               float bz = curl_br(hy[r][cc], hyi, hx[r][cc], hxj);
               const uint32_t m = in.m[r][cc];
               if (m & kSrcFlag) {
@@ -422,8 +431,10 @@ yee_blocked_kernel(const __grid_constant__ CUtensorMap tmF, const __grid_constan
             out.hx[r][cc] = hx[r][cc];
             out.hy[r][cc] = hy[r][cc];
             out.hz[r][cc] = hz[r][cc];
-            hxp[lv - 1][r][cc] = hx[r][cc];
-            hyp[lv - 1][r][cc] = hy[r][cc];
+            if (lv == K) {
+              hxK[r][cc] = hx[r][cc];
+              hyK[r][cc] = hy[r][cc];
+            }
           }
         if (lv < K) {
           // Publish this warp's first E row for level lv+1 (next iteration), then

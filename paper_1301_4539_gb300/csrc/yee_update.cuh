@@ -2,10 +2,12 @@
 // (plain, temporally blocked) produce bitwise identical fields.
 //
 // Sec. 2.1 (displayed Hx update and its analogues for the other components):
-//   h += S * ((a1 - a0) - (b1 - b0))
-//   e  = Ca*e + Cb*((a1 - a0) - (b1 - b0) [+ s])
-// Every operation is rounded separately (no fused multiply-add) in exactly
-// this order, so the float results are fixed by the expression alone.
+//   br = (a1 - a0) - (b1 - b0) [+ s]
+//   h  = fma(S, br, h)
+//   e  = fma(Cb, br, Ca*e)
+// with every other operation rounded separately, in exactly this order, so
+// the float results are fixed by the expression alone (the CPU oracle
+// evaluates the same expression with C's fmaf).
 //
 // Operand roles per component (index offsets on the storage box):
 //   hx: a = ey(k+1), ey(k)   b = ez(j+1), ez(j)
@@ -23,11 +25,11 @@ __device__ __forceinline__ float curl_br(float a1, float a0, float b1, float b0)
 }
 
 __device__ __forceinline__ float h_upd(float h, float S, float a1, float a0, float b1, float b0) {
-  return __fadd_rn(h, __fmul_rn(S, curl_br(a1, a0, b1, b0)));
+  return __fmaf_rn(S, curl_br(a1, a0, b1, b0), h);
 }
 
 __device__ __forceinline__ float e_upd(float e, float2 c, float br) {
-  return __fadd_rn(__fmul_rn(c.x, e), __fmul_rn(c.y, br));
+  return __fmaf_rn(c.y, br, __fmul_rn(c.x, e));
 }
 
 }  // namespace sophie
