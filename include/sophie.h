@@ -101,10 +101,12 @@ int sophie_destroy_grid(sophie_grid *g);
  * Per-cell relative permittivity and conductivity (S/m), host arrays of
  * nx*ny*nz floats each (x fastest, then y, then z), copied. eps_r >= 1 and
  * finite; sigma >= 0 and finite (else EINVAL). Edge values are the mean of the
- * four cells sharing the edge (Sec. 2.1 coefficients, see top of file); at
- * most 511 distinct (eps_r, sigma) edge pairs (else ETOOMANYMAT, grid left
- * unchanged). Enqueued on the grid's stream; the host arrays may be reused on
- * return.
+ * four cells sharing the edge (Sec. 2.1 coefficients, see top of file). The
+ * 511 most frequent edge materials are held as classes in a table; index
+ * points with an edge outside them carry their own coefficients (any number
+ * of distinct materials; the explicit points cost 48 extra bytes each and are
+ * updated on a slower path). Enqueued on the grid's stream; the host arrays
+ * may be reused on return. Errors: EINVAL, ENOMEM, ECUDA.
  */
 int sophie_set_materials(sophie_grid *g, const float *eps_r, const float *sigma);
 

@@ -95,6 +95,11 @@ struct sophie_grid {
   double* eps_tab = nullptr;   // device class table eps_r(edge)
   std::vector<float2> coef_h;
   std::vector<double> eps_h;
+  std::vector<float2> ecoef_h;    // explicit points: (Ca, Cb) of ex, ey, ez
+  std::vector<double> eeps_h;     // explicit points: eps_r of ex, ey, ez
+  float2* ecoef = nullptr;        // device copies
+  double* eeps = nullptr;
+  size_t exp_cap = 0;
   cudaEvent_t mat_upload_done = nullptr;
   std::vector<Source> src;
   std::vector<Probe> prb;
@@ -165,37 +170,19 @@ uint64_t dbits(double v) {
   return u;
 }
 
-struct ClassBuilder {
-  const sophie_grid* g;
-  std::unordered_map<EdgeKey, int, EdgeKeyHash> map;
-  std::vector<float2> coef;
-  std::vector<double> eps;
-  bool overflow = false;
-  explicit ClassBuilder(const sophie_grid* gg) : g(gg) {
-    coef.push_back(make_float2(0.f, 0.f));  // class 0: PEC / absent edge
-    eps.push_back(0.0);
-  }
-  int classify(double e4, double s4) {
-    const double e = e4 * 0.25, s = s4 * 0.25;
-    const EdgeKey key{dbits(e), dbits(s)};
-    auto it = map.find(key);
-    if (it != map.end()) return it->second;
-    const int id = (int)coef.size();
-    if (id >= kMaxClasses) {
-      overflow = true;
-      return 0;
-    }
-    const double beta = (s * g->dt) / (2.0 * kEps0 * e);
-    const double ca = (1.0 - beta) / (1.0 + beta);
-    const double cb = (g->S64 / e) / (1.0 + beta);
-    coef.push_back(make_float2((float)ca, (float)cb));
-    eps.push_back(e);
-    map.emplace(key, id);
-    return id;
-  }
-};
+// Coefficients (Ca, Cb) of an edge whose mean material is (e, s).
+float2 edge_coef(const sophie_grid* g, double e, double s) {
+  const double beta = (s * g->dt) / (2.0 * kEps0 * e);
+  const double ca = (1.0 - beta) / (1.0 + beta);
+  const double cb = (g->S64 / e) / (1.0 + beta);
+  return make_float2((float)ca, (float)cb);
+}
 
-// Fill g->mat_host with class words for per-cell eps/sigma (nullptr = vacuum).
+// Fill g->mat_host with material words for per-cell eps/sigma (nullptr =
+// vacuum). Edge materials are means of four cells in double (summed in the
+// fixed order (-,-), (+,-), (-,+), (+,+)). The up to 511 most frequent edge
+// materials become classes; an index point with an edge outside them gets an
+// explicit entry (its three edges' (Ca, Cb) and eps_r).
 int build_material_words(sophie_grid* g, const float* eps, const float* sig) {
   const Dims& d = g->d;
   const int nx = d.nx, ny = d.ny, nz = d.nz;
@@ -205,49 +192,109 @@ int build_material_words(sophie_grid* g, const float* eps, const float* sig) {
   auto Sg = [&](int i, int j, int k) -> double {
     return sig ? (double)sig[((long long)k * ny + j) * nx + i] : 0.0;
   };
-  ClassBuilder cb(g);
-  uint32_t* w = g->mat_host;
-  // One-entry cache: neighbouring edges usually share their material.
-  double le[3] = {-1, -1, -1}, ls[3] = {-1, -1, -1};
-  int lc[3] = {0, 0, 0};
-  auto cls = [&](int c, double e4, double s4) -> uint32_t {
-    if (e4 == le[c] && s4 == ls[c]) return (uint32_t)lc[c];
-    le[c] = e4;
-    ls[c] = s4;
-    lc[c] = cb.classify(e4, s4);
-    return (uint32_t)lc[c];
+  // Mean (eps, sigma) of edge component c at index (i, j, k) (interior only).
+  auto edge_mat = [&](int c, int i, int j, int k, double& e, double& s) {
+    double e4, s4;
+    if (c == 0) {
+      e4 = ((E(i, j - 1, k - 1) + E(i, j, k - 1)) + E(i, j - 1, k)) + E(i, j, k);
+      s4 = ((Sg(i, j - 1, k - 1) + Sg(i, j, k - 1)) + Sg(i, j - 1, k)) + Sg(i, j, k);
+    } else if (c == 1) {
+      e4 = ((E(i - 1, j, k - 1) + E(i, j, k - 1)) + E(i - 1, j, k)) + E(i, j, k);
+      s4 = ((Sg(i - 1, j, k - 1) + Sg(i, j, k - 1)) + Sg(i - 1, j, k)) + Sg(i, j, k);
+    } else {
+      e4 = ((E(i - 1, j - 1, k) + E(i, j - 1, k)) + E(i - 1, j, k)) + E(i, j, k);
+      s4 = ((Sg(i - 1, j - 1, k) + Sg(i, j - 1, k)) + Sg(i - 1, j, k)) + Sg(i, j, k);
+    }
+    e = e4 * 0.25;
+    s = s4 * 0.25;
   };
+  // Pass 1: frequency of every edge material (runs along x are counted once).
+  std::unordered_map<EdgeKey, long long, EdgeKeyHash> freq;
+  for (int c = 0; c < 3; ++c) {
+    EdgeKey last{~0ull, ~0ull};
+    long long run = 0;
+    for (int k = 0; k <= nz; ++k)
+      for (int j = 0; j <= ny; ++j)
+        for (int i = 0; i <= nx; ++i) {
+          if (!e_edge_interior(d, c, i, j, k)) continue;
+          double e, s;
+          edge_mat(c, i, j, k, e, s);
+          const EdgeKey key{dbits(e), dbits(s)};
+          if (key == last) {
+            ++run;
+            continue;
+          }
+          if (run) freq[last] += run;
+          last = key;
+          run = 1;
+        }
+    if (run) freq[last] += run;
+  }
+  // Classes: the most frequent materials (class 0 is PEC / absent).
+  std::vector<std::pair<long long, EdgeKey>> order;
+  order.reserve(freq.size());
+  for (const auto& kv : freq) order.push_back({kv.second, kv.first});
+  std::sort(order.begin(), order.end(), [](const std::pair<long long, EdgeKey>& a, const std::pair<long long, EdgeKey>& b) {
+    if (a.first != b.first) return a.first > b.first;
+    return a.second.e != b.second.e ? a.second.e < b.second.e : a.second.s < b.second.s;
+  });
+  std::unordered_map<EdgeKey, int, EdgeKeyHash> cls;
+  std::vector<float2> coef(1, make_float2(0.f, 0.f));
+  std::vector<double> epsv(1, 0.0);
+  for (size_t q = 0; q < order.size() && (int)coef.size() < kMaxClasses; ++q) {
+    double e, s;
+    memcpy(&e, &order[q].second.e, 8);
+    memcpy(&s, &order[q].second.s, 8);
+    cls.emplace(order[q].second, (int)coef.size());
+    coef.push_back(edge_coef(g, e, s));
+    epsv.push_back(e);
+  }
+  // Pass 2: words.
+  std::vector<float2> ecoef;
+  std::vector<double> eeps;
+  uint32_t* w = g->mat_host;
+  EdgeKey lk[3] = {{~0ull, ~0ull}, {~0ull, ~0ull}, {~0ull, ~0ull}};
+  int lc[3] = {-1, -1, -1};
   for (int k = 0; k <= nz; ++k)
     for (int j = 0; j <= ny; ++j) {
       uint32_t* row = w + ((long long)k * d.ny1 + j) * d.nxp;
       for (int i = 0; i < d.nxp; ++i) {
-        uint32_t word = 0;
-        if (e_edge_interior(d, 0, i, j, k)) {
-          const double e4 = ((E(i, j - 1, k - 1) + E(i, j, k - 1)) + E(i, j - 1, k)) + E(i, j, k);
-          const double s4 = ((Sg(i, j - 1, k - 1) + Sg(i, j, k - 1)) + Sg(i, j - 1, k)) + Sg(i, j, k);
-          word |= cls(0, e4, s4) << kClsShift[0];
+        int ci[3] = {0, 0, 0};
+        double ce[3] = {0, 0, 0}, cs[3] = {0, 0, 0};
+        bool expl = false;
+        for (int c = 0; c < 3; ++c) {
+          if (!e_edge_interior(d, c, i, j, k)) continue;
+          edge_mat(c, i, j, k, ce[c], cs[c]);
+          const EdgeKey key{dbits(ce[c]), dbits(cs[c])};
+          if (!(key == lk[c])) {
+            auto it = cls.find(key);
+            lk[c] = key;
+            lc[c] = it == cls.end() ? -1 : it->second;
+          }
+          ci[c] = lc[c];
+          if (ci[c] < 0) expl = true;
         }
-        if (e_edge_interior(d, 1, i, j, k)) {
-          const double e4 = ((E(i - 1, j, k - 1) + E(i, j, k - 1)) + E(i - 1, j, k)) + E(i, j, k);
-          const double s4 = ((Sg(i - 1, j, k - 1) + Sg(i, j, k - 1)) + Sg(i - 1, j, k)) + Sg(i, j, k);
-          word |= cls(1, e4, s4) << kClsShift[1];
+        if (!expl) {
+          row[i] = cls_word((uint32_t)ci[0], (uint32_t)ci[1], (uint32_t)ci[2]);
+        } else {
+          const size_t q = eeps.size() / 3;
+          if (q >= (1u << 29)) return fail(SOPHIE_ETOOMANYMAT, "more than 2^29 explicit material points");
+          for (int c = 0; c < 3; ++c) {
+            const bool in = e_edge_interior(d, c, i, j, k);
+            ecoef.push_back(in ? edge_coef(g, ce[c], cs[c]) : make_float2(0.f, 0.f));
+            eeps.push_back(in ? ce[c] : 0.0);
+          }
+          row[i] = kExpFlag | ((uint32_t)q << 3);
         }
-        if (e_edge_interior(d, 2, i, j, k)) {
-          const double e4 = ((E(i - 1, j - 1, k) + E(i, j - 1, k)) + E(i - 1, j, k)) + E(i, j, k);
-          const double s4 = ((Sg(i - 1, j - 1, k) + Sg(i, j - 1, k)) + Sg(i - 1, j, k)) + Sg(i, j, k);
-          word |= cls(2, e4, s4) << kClsShift[2];
-        }
-        row[i] = word;
       }
-      if (cb.overflow) break;
     }
-  if (cb.overflow)
-    return fail(SOPHIE_ETOOMANYMAT, "more than %d distinct (eps_r, sigma) edge pairs", kMaxClasses - 1);
   for (const Source& s : g->src) w[s.pos] |= kSrcFlag;
   for (const Probe& p : g->prb)
     if (!p.fixed) w[p.pos] |= kPrbFlag;
-  g->coef_h = std::move(cb.coef);
-  g->eps_h = std::move(cb.eps);
+  g->coef_h = std::move(coef);
+  g->eps_h = std::move(epsv);
+  g->ecoef_h = std::move(ecoef);
+  g->eeps_h = std::move(eeps);
   return SOPHIE_OK;
 }
 
@@ -259,8 +306,29 @@ int upload_materials(sophie_grid* g) {
                            cudaMemcpyHostToDevice, g->stream));
   CUDA_TRY(cudaMemcpyAsync(g->eps_tab, g->eps_h.data(), g->eps_h.size() * sizeof(double),
                            cudaMemcpyHostToDevice, g->stream));
+  const size_t nexp = g->eeps_h.size() / 3;
+  if (nexp > g->exp_cap) {
+    CUDA_TRY(cudaStreamSynchronize(g->stream));
+    if (g->ecoef) cudaFree(g->ecoef);
+    if (g->eeps) cudaFree(g->eeps);
+    g->ecoef = nullptr;
+    g->eeps = nullptr;
+    g->exp_cap = 0;
+    if (cudaMalloc(&g->ecoef, nexp * 3 * sizeof(float2)) != cudaSuccess ||
+        cudaMalloc(&g->eeps, nexp * 3 * sizeof(double)) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(SOPHIE_ENOMEM, "explicit material table allocation failed");
+    }
+    g->exp_cap = nexp;
+  }
+  if (nexp) {
+    CUDA_TRY(cudaMemcpyAsync(g->ecoef, g->ecoef_h.data(), nexp * 3 * sizeof(float2), cudaMemcpyHostToDevice,
+                             g->stream));
+    CUDA_TRY(cudaMemcpyAsync(g->eeps, g->eeps_h.data(), nexp * 3 * sizeof(double), cudaMemcpyHostToDevice,
+                             g->stream));
+  }
   CUDA_TRY(cudaEventRecord(g->mat_upload_done, g->stream));
-  // coef_h / eps_h are pageable: the copies above complete before return.
+  // The tables are pageable host memory: the copies above complete before return.
   return SOPHIE_OK;
 }
 
@@ -363,6 +431,8 @@ StepArgs make_step_args(sophie_grid* g) {
   }
   a.mat = g->mat;
   a.coef = g->coef;
+  a.ecoef = g->ecoef;
+  a.eeps = g->eeps;
   a.d = g->d;
   a.S = g->S32;
   a.n0 = g->n;
@@ -403,6 +473,8 @@ void free_grid(sophie_grid* g) {
   if (g->mat) cudaFree(g->mat);
   if (g->mat_host) cudaFreeHost(g->mat_host);
   if (g->coef) cudaFree(g->coef);
+  if (g->ecoef) cudaFree(g->ecoef);
+  if (g->eeps) cudaFree(g->eeps);
   if (g->eps_tab) cudaFree(g->eps_tab);
   if (g->sval) cudaFree(g->sval);
   if (g->pbuf) cudaFree(g->pbuf);
@@ -680,13 +752,15 @@ int sophie_set_materials(sophie_grid* g, const float* eps, const float* sig) {
   }
   // The staging buffer may still feed an earlier upload.
   CUDA_TRY(cudaEventSynchronize(g->mat_upload_done));
-  std::vector<float2> old_coef = g->coef_h;
-  std::vector<double> old_eps = g->eps_h;
+  std::vector<float2> old_coef = g->coef_h, old_ecoef = g->ecoef_h;
+  std::vector<double> old_eps = g->eps_h, old_eeps = g->eeps_h;
   int rc = build_material_words(g, eps, sig);
   if (rc) {
     // Restore the words of the current materials.
     g->coef_h = old_coef;
     g->eps_h = old_eps;
+    g->ecoef_h = old_ecoef;
+    g->eeps_h = old_eeps;
     CUDA_TRY(cudaMemcpy(g->mat_host, g->mat, (size_t)g->d.plane * g->d.nz1 * 4, cudaMemcpyDeviceToHost));
     return rc;
   }

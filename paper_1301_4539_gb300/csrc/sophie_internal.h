@@ -17,6 +17,8 @@ namespace sophie {
 // Material word, one per index point (z*ny1 + y)*nxp + x:
 //   bit  0      a source sits on one of this point's edges
 //   bit  1      a probe sits on one of this point's components
+//   bit  2      explicit point: bits 3..31 index the explicit tables
+//               (3 x (Ca, Cb) and 3 x eps_r(edge) for ex, ey, ez); else:
 //   bits  3..11 class of the ex edge at this index (0 = PEC / absent)
 //   bits 12..20 class of the ey edge
 //   bits 21..29 class of the ez edge
@@ -29,6 +31,7 @@ constexpr int kMaxSources = 16;
 constexpr int kMaxProbes = 64;
 constexpr uint32_t kSrcFlag = 1u;
 constexpr uint32_t kPrbFlag = 2u;
+constexpr uint32_t kExpFlag = 4u;
 constexpr int kClsShift[3] = {3, 12, 21};
 constexpr uint32_t kClsOffMask = 0xFF8u;  // 9-bit class index times 8
 
@@ -75,7 +78,9 @@ struct StepArgs {
   float sc[6];      // stored value = field * sc[comp] (2-byte formats)
   float isc[6];     // 1 / sc
   const uint32_t* mat;
-  const float2* coef;
+  const float2* coef;   // class table (Ca, Cb)
+  const float2* ecoef;  // explicit points: 3 x (Ca, Cb) per entry
+  const double* eeps;   // explicit points: 3 x eps_r per entry (energy)
   Dims d;
   float S;
   long long n0;  // absolute index of the first step this launch performs

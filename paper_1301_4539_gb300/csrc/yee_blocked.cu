@@ -370,7 +370,7 @@ yee_blocked_kernel(const __grid_constant__ CUtensorMap tmF, const __grid_constan
         uint32_t fl = 0;
 #pragma unroll
         for (int r = 0; r < kR; ++r) fl |= in.m[r][0] | in.m[r][1];
-        const bool rare = __any_sync(0xffffffffu, fl & (kSrcFlag | kPrbFlag));
+        const bool rare = __any_sync(0xffffffffu, fl & (kSrcFlag | kPrbFlag | kExpFlag));
         St out;
         if (!rare) {
 #pragma unroll
@@ -413,9 +413,20 @@ yee_blocked_kernel(const __grid_constant__ CUtensorMap tmF, const __grid_constan
                 by = b3.y;
                 bz = b3.z;
               }
-              out.ex[r][cc] = e_upd(in.ex[r][cc], *reinterpret_cast<const float2*>(scoefb + cls_off_x(m)), bx);
-              out.ey[r][cc] = e_upd(in.ey[r][cc], *reinterpret_cast<const float2*>(scoefb + cls_off_y(m)), by);
-              out.ez[r][cc] = e_upd(in.ez[r][cc], *reinterpret_cast<const float2*>(scoefb + cls_off_z(m)), bz);
+              float2 k0, k1, k2;
+              if (m & kExpFlag) {
+                const float2* e3 = a.ecoef + 3ull * (m >> 3);
+                k0 = __ldg(e3);
+                k1 = __ldg(e3 + 1);
+                k2 = __ldg(e3 + 2);
+              } else {
+                k0 = *reinterpret_cast<const float2*>(scoefb + cls_off_x(m));
+                k1 = *reinterpret_cast<const float2*>(scoefb + cls_off_y(m));
+                k2 = *reinterpret_cast<const float2*>(scoefb + cls_off_z(m));
+              }
+              out.ex[r][cc] = e_upd(in.ex[r][cc], k0, bx);
+              out.ey[r][cc] = e_upd(in.ey[r][cc], k1, by);
+              out.ez[r][cc] = e_upd(in.ez[r][cc], k2, bz);
               out.m[r][cc] = m;
               if ((m & kPrbFlag) && p >= z0 && p < z1 && y >= yo0 && y < yo1 && y < d.ny &&
                   x + cc >= xo0 && x + cc < xo1 && x + cc < d.nx)

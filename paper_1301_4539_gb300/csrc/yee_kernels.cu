@@ -68,9 +68,11 @@ yee_step_simple_kernel(StepArgs a) {
     if (z >= z0 && owner) {
       const long long pt = ((long long)z * d.ny1 + y) * d.nxp + x;
       const uint32_t m = a.mat[pt];
-      const float2 cx = a.coef[cls_of(m, 0)];
-      const float2 cy = a.coef[cls_of(m, 1)];
-      const float2 cz = a.coef[cls_of(m, 2)];
+      const bool ex_pt = (m & kExpFlag) != 0;
+      const float2* e3 = a.ecoef + 3ull * (m >> 3);
+      const float2 cx = ex_pt ? e3[0] : a.coef[cls_of(m, 0)];
+      const float2 cy = ex_pt ? e3[1] : a.coef[cls_of(m, 1)];
+      const float2 cz = ex_pt ? e3[2] : a.coef[cls_of(m, 2)];
       float bx = curl_br(hz, sH[2][ty - 1][tx], hy, hyp);
       float by = curl_br(hx, hxp, hz, sH[2][ty][tx - 1]);
       float bz = curl_br(hy, sH[1][ty][tx - 1], hx, sH[0][ty - 1][tx]);
@@ -149,9 +151,20 @@ energy_partial_kernel(const __grid_constant__ StepArgs a, const double* eps_tab,
     const uint32_t m = mat[pt];
     const float ex = ld_s<F>(f, d, isc, 0, x, y, z), ey = ld_s<F>(f, d, isc, 1, x, y, z);
     const float ez = ld_s<F>(f, d, isc, 2, x, y, z);
-    acc += eps_tab[cls_of(m, 0)] * ((double)ex * (double)ex);
-    acc += eps_tab[cls_of(m, 1)] * ((double)ey * (double)ey);
-    acc += eps_tab[cls_of(m, 2)] * ((double)ez * (double)ez);
+    double e0, e1, e2;
+    if (m & kExpFlag) {
+      const double* p3 = a.eeps + 3ull * (m >> 3);
+      e0 = p3[0];
+      e1 = p3[1];
+      e2 = p3[2];
+    } else {
+      e0 = eps_tab[cls_of(m, 0)];
+      e1 = eps_tab[cls_of(m, 1)];
+      e2 = eps_tab[cls_of(m, 2)];
+    }
+    acc += e0 * ((double)ex * (double)ex);
+    acc += e1 * ((double)ey * (double)ey);
+    acc += e2 * ((double)ez * (double)ez);
     const float hx = ld_s<F>(f, d, isc, 3, x, y, z), hy = ld_s<F>(f, d, isc, 4, x, y, z);
     const float hz = ld_s<F>(f, d, isc, 5, x, y, z);
     const float hxn = h_upd(hx, S, ld_s<F>(f, d, isc, 1, x, y, z + 1), ey, ld_s<F>(f, d, isc, 2, x, y + 1, z), ez);

@@ -268,9 +268,20 @@ yee_plain_kernel(const __grid_constant__ CUtensorMap tmF, const __grid_constant_
             by = b3.y;
             bz = b3.z;
           }
-          eo[0][cc] = e_upd(ex[r][cc], __ldg(&a.coef[cls_of(m, 0)]), bx);
-          eo[1][cc] = e_upd(ey[r][cc], __ldg(&a.coef[cls_of(m, 1)]), by);
-          eo[2][cc] = e_upd(ez[r][cc], __ldg(&a.coef[cls_of(m, 2)]), bz);
+          float2 k0, k1, k2;
+          if (m & kExpFlag) {
+            const float2* e3 = a.ecoef + 3ull * (m >> 3);
+            k0 = __ldg(e3);
+            k1 = __ldg(e3 + 1);
+            k2 = __ldg(e3 + 2);
+          } else {
+            k0 = __ldg(&a.coef[cls_of(m, 0)]);
+            k1 = __ldg(&a.coef[cls_of(m, 1)]);
+            k2 = __ldg(&a.coef[cls_of(m, 2)]);
+          }
+          eo[0][cc] = e_upd(ex[r][cc], k0, bx);
+          eo[1][cc] = e_upd(ey[r][cc], k1, by);
+          eo[2][cc] = e_upd(ez[r][cc], k2, bz);
           if ((m & kPrbFlag) && out_plane && y < d.ny && x + cc < d.nx)
             record_probes(((long long)z * d.ny1 + y) * d.nxp + x + cc, a.n0, eo[0][cc], eo[1][cc], eo[2][cc],
                           hx[r][cc], hy[r][cc], hz[r][cc], &a.prb);
