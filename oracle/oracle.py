@@ -22,6 +22,7 @@ EPS0 = 8.8541878128e-12
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "yee_oracle.c")
+_GRAD = os.path.join(_HERE, "yee_oracle_grad.c")
 _BODY = os.path.join(_HERE, "yee_oracle_body.h")
 _LIB = os.path.join(_HERE, "_build", "libyee_oracle.so")
 _lock = threading.Lock()
@@ -31,12 +32,12 @@ _lib = None
 def build(force: bool = False) -> str:
     """Compile the oracle with gcc (-O2 -fopenmp -ffp-contract=off)."""
     os.makedirs(os.path.dirname(_LIB), exist_ok=True)
-    newest = max(os.path.getmtime(_SRC), os.path.getmtime(_BODY))
+    newest = max(os.path.getmtime(p) for p in (_SRC, _GRAD, _BODY, __file__))
     if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= newest:
         return _LIB
     tmp = _LIB + f".tmp{os.getpid()}"
     cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp",
-           "-ffp-contract=off", "-fno-fast-math", "-o", tmp, _SRC, "-lm"]
+           "-ffp-contract=off", "-fno-fast-math", "-o", tmp, _SRC, _GRAD, "-lm"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, _LIB)
     return _LIB
@@ -61,6 +62,8 @@ def load() -> ctypes.CDLL:
                 getattr(lib, f"oracle_step_{suf}").restype = None
                 getattr(lib, f"oracle_energy_{suf}").argtypes = [I, I, I, R, D] + [P] * 6 + [P] * 3
                 getattr(lib, f"oracle_energy_{suf}").restype = D
+            lib.oracle_grad_f64.argtypes = [I, I, I, D, D, P, P] + [P] * 6 + [I, P, P, I, I, I, I, I, I, P, P]
+            lib.oracle_grad_f64.restype = D
             lib.oracle_waveform.argtypes = [I, D, D, D, D, D, L, L, P]
             lib.oracle_waveform.restype = None
             _lib = lib
@@ -116,6 +119,7 @@ class OracleGrid:
         eps_cell = np.ascontiguousarray(eps_cell, np.float32).reshape(nz, ny, nx)
         sig_cell = np.ascontiguousarray(sig_cell, np.float32).reshape(nz, ny, nx)
         shp = (nz + 1, ny + 1, nx + 1)
+        self.eps_cell, self.sig_cell = eps_cell.copy(), sig_cell.copy()
         self.coef = [np.zeros(shp, self.dtype) for _ in range(6)]  # cax cbx cay cby caz cbz
         self.eps_edge = [np.zeros(shp, np.float64) for _ in range(3)]
         fn = getattr(load(), f"oracle_coefs_{self.precision}")
@@ -154,6 +158,34 @@ class OracleGrid:
         for q in range(nprb):
             self.probe_trace[q].extend(pout[q].astype(np.float64).tolist())
         self.n += nsteps
+
+    def _source_table(self, nsteps: int):
+        nsrc = len(self.sources)
+        src = np.array([s[:4] for s in self.sources] or [[0, 0, 0, 0]], np.int32).reshape(-1)
+        sval = np.zeros((max(nsrc, 1), nsteps), self.dtype)
+        for q, s in enumerate(self.sources):
+            sval[q] = waveform(s[8], s[4], s[5], s[6], s[7], self.dt, self.n, nsteps).astype(self.dtype)
+        return nsrc, src, sval
+
+    def grad_eps(self, pcomp: int, pi: int, pj: int, pk: int, nsteps: int, cells) -> tuple:
+        """Objective J = dt * sum over the next nsteps steps of (probe value)^2 and
+        dJ/d eps_r of each listed cell (reverse-mode sweep, yee_oracle_grad.c).
+
+        The probe is component pcomp at index (pi, pj, pk), sampled after every
+        step. Advances the state by nsteps steps (float64 grids only).
+        """
+        assert self.precision == "f64"
+        cells = np.ascontiguousarray(cells, np.int32).reshape(-1, 3)
+        grad = np.zeros(len(cells), np.float64)
+        nsrc, src, sval = self._source_table(nsteps)
+        J = load().oracle_grad_f64(self.nx, self.ny, self.nz, self.dx, self.dt,
+                                   _ptr(self.eps_cell), _ptr(self.sig_cell), *[_ptr(a) for a in self.f],
+                                   nsrc, _ptr(src), _ptr(sval), pcomp, pi, pj, pk, nsteps,
+                                   len(cells), _ptr(cells), _ptr(grad))
+        if not math.isfinite(J):
+            raise MemoryError("oracle gradient: allocation failed")
+        self.n += nsteps
+        return J, grad
 
     def energy(self) -> float:
         fn = getattr(load(), f"oracle_energy_{self.precision}")

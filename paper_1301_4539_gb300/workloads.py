@@ -156,3 +156,35 @@ def random_materials(nx: int, ny: int, nz: int, seed: int, nmat: int = 5,
     pal_s = rng.uniform(*sigma, size=nmat).astype(np.float32)
     idx = rng.integers(0, nmat, size=(nz, ny, nx))
     return pal_e[idx], pal_s[idx]
+
+
+def gaussian_pulse_source(bw: float = 10e9, amp: float = 1.0):
+    """Gaussian-pulse source parameters (amp, f0=0, bw, t0, kind=1); t0 = 5 widths."""
+    amp, _, bw, t0, _ = gaussian_sine_source(0.0, bw, amp)
+    return amp, 0.0, bw, t0, 1
+
+
+def design_cavity(n: int = 128, design: tuple = (48, 80), eps_range=(1.0, 4.0),
+                  seed_design: int = 1305, seed_cells: int = 1306, ncells: int = 16):
+    """The differentiation workload: an n^3 vacuum PEC cavity with a cubic design
+    region of cells [lo, hi)^3 whose eps_r is seeded uniform in eps_range, a
+    Gaussian-pulse Ez source 8 cells inside the x = 0 wall, the objective's Ez
+    probe 9 cells inside the x = n wall, and `ncells` seeded design cells at
+    which gradients are compared."""
+    lo, hi = design
+    eps = np.ones((n, n, n), np.float32)
+    rng = np.random.default_rng(seed_design)
+    m = hi - lo
+    eps[lo:hi, lo:hi, lo:hi] = rng.uniform(*eps_range, size=(m, m, m)).astype(np.float32)
+    sig = np.zeros((n, n, n), np.float32)
+    amp, f0, bw, t0, kind = gaussian_pulse_source()
+    src = (2, 8, n // 2, n // 2, amp, f0, bw, t0, kind)
+    probe = (2, n - 9, n // 2, n // 2)
+    g = SplitMix64(seed_cells)
+    cells = []
+    while len(cells) < ncells:
+        c = (g.randint(lo, hi), g.randint(lo, hi), g.randint(lo, hi))
+        if c not in cells:
+            cells.append(c)
+    return dict(nx=n, ny=n, nz=n, dx=DX_DEFAULT, dt=cfl_dt(DX_DEFAULT), eps=eps, sigma=sig,
+                sources=[src], probe=probe, design=(lo, lo, lo, m, m, m), cells=cells)
