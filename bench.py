@@ -52,6 +52,7 @@ def parse():
     p.add_argument("--k", type=int, default=0, help="steps fused per launch (0 = library default)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-adjoint", action="store_true")
     return p.parse_args()
 
 
@@ -317,6 +318,10 @@ def run_ours(args):
     if not args.no_cpu_baseline and rank == 0 and world == 1:
         cpu = cpu_baseline(w)
 
+    adjoint = None
+    if not args.no_adjoint and rank == 0:
+        adjoint = run_adjoint(stream)
+
     if rank == 0:
         line = {"metric": "Gcell-updates/s 3D Yee FDTD", "value": value, "unit": "Gcell-updates/s",
                 "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -328,7 +333,7 @@ def run_ours(args):
                            "temporal_k": K, "parallelism": f"replicas x{world}",
                            "l2": "inputs larger than L2 (no flush)"},
                 "roofline": roof, "variants_gcells": variants, "cpu_baseline": cpu, "e2e": e2e,
-                "gpu_launches": launches, "clocks": clocks, "energy_J": energy}
+                "gpu_launches": launches, "clocks": clocks, "energy_J": energy, "adjoint": adjoint}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
@@ -357,6 +362,55 @@ def run_e2e(args, g, w, pids, stream):
     return {"value": n ** 3 * args.tsteps * reps / dt / 1e9, "unit": "Gcell-updates/s",
             "h2d_bytes_per_step": npts * 4, "d2h_bytes_per_step": len(pids) * args.tsteps * 4 + 8,
             "note": "material words built on the host from eps/sigma and uploaded each step"}
+
+
+def run_adjoint(stream, reps: int = 3):
+    """The differentiation form on its workload (128^3 design cavity, 800 steps,
+    checkpoints every 50): wall time of one objective evaluation and of its
+    gradient over the whole 32^3 design region, and the adjoint step kernel's
+    HBM roofline (52 algorithmic bytes per cell: 6 float adjoint fields read and
+    written, one material word)."""
+    import torch
+    from paper_1301_4539_gb300 import sophie as so
+    from paper_1301_4539_gb300 import workloads as wl
+    w = wl.design_cavity()
+    n = w["nx"]
+    N = 800
+    g = so.Grid(n, n, n, w["dx"], w["dt"])
+    g.set_stream(stream.cuda_stream)
+    g.set_materials(w["eps"], w["sigma"])
+    g.add_source(*w["sources"][0])
+    fwd, rev = [], []
+    for r in range(reps + 1):
+        g.reset()
+        g.profile(r > 0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        g.objective_forward(N, *w["probe"], 50)
+        t1 = time.perf_counter()
+        g.objective_grad_eps(*w["design"])
+        t2 = time.perf_counter()
+        if r > 0:
+            fwd.append(t1 - t0)
+            rev.append(t2 - t1)
+    la, ams = g.profile_read(so.KERNEL_ADJOINT)
+    lp, pms = g.profile_read(so.KERNEL_PLAIN)
+    g.profile(False)
+    g.close()
+    peak, peak_kind = peaks()
+    cells = n ** 3
+    avg = ams / max(la, 1)
+    achieved = cells * (FIELD_BYTES + MAT_BYTES) / (avg / 1e3) / 1e9
+    t_f, t_r = float(np.median(fwd)), float(np.median(rev))
+    return {"workload": f"{n}^3 vacuum PEC cavity, 32^3 design region eps_r U(1,4), Gaussian-pulse Ez "
+                        f"source, {N} steps, checkpoints every 50, gradient over the 32^3 design cells",
+            "forward_ms": t_f * 1e3, "gradient_ms": t_r * 1e3, "total_ms": (t_f + t_r) * 1e3,
+            "cell_steps_per_s_total": 3 * cells * N / (t_f + t_r) / 1e9,
+            "unit_cell_steps": "G (forward + recompute + adjoint step) cell-updates/s",
+            "adjoint_kernel": {"bound": "hbm", "avg_launch_ms": avg, "achieved": achieved, "peak": peak,
+                               "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_kind,
+                               "launches": la // reps},
+            "recompute_kernel_avg_launch_ms": pms / max(lp, 1), "reps": reps}
 
 
 def main():

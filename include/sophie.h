@@ -77,6 +77,7 @@ extern "C" {
 #define SOPHIE_KERNEL_PLAIN   0  /* one fused H+E step per launch           */
 #define SOPHIE_KERNEL_BLOCKED 1  /* k fused H+E steps per launch (k >= 2)   */
 #define SOPHIE_KERNEL_ENERGY  2  /* discrete energy reduction               */
+#define SOPHIE_KERNEL_ADJOINT 3  /* one reverse (adjoint) step per launch    */
 
 typedef struct sophie_grid sophie_grid;
 
@@ -235,6 +236,45 @@ int sophie_launch_count(sophie_grid *g, long long *launches);
  */
 int sophie_profile(sophie_grid *g, int enable);
 int sophie_profile_read(sophie_grid *g, int kernel, long long *launches, double *ms);
+
+/*
+ * Gradients of a probe objective with respect to eps_r (the differentiation
+ * form; the paper has no adjoint, the steps it differentiates are Sec. 2.1's).
+ *
+ * sophie_objective_forward advances the grid by nsteps steps from its current
+ * state, exactly as sophie_step(g, nsteps) would (user probes record as
+ * usual), and returns in *J (host double)
+ *   J = dt * sum_{n=1..nsteps} (f^n)^2,
+ * f^n = component comp at index (i, j, k) after the n-th of these steps (an E
+ * component is e^{n0+n}, an H component h^{n0+n-1/2}), summed in double. It
+ * records the objective: the state every checkpoint_every steps (0 = 50), each
+ * a device copy of the float fields (6 (nz+1)(ny+1) nxp floats, where nxp is
+ * nx+1 rounded up to a multiple of 8), plus the nsteps samples. The record
+ * stays valid until the grid's fields, materials or sources change (any step,
+ * set_fields, reset, set_materials, add_source) and is freed by
+ * sophie_objective_release or sophie_destroy_grid.
+ * Errors: EINVAL (NULL, nsteps < 1, point outside comp's range or on a plane
+ * i == nx, j == ny or k == nz), ENOTSUP (half or bfloat16 storage; all probe
+ * slots in use, the objective needs one), ENOMEM (checkpoints), ECUDA,
+ * ETIMEOUT, ENONFINITE.
+ *
+ * sophie_objective_grad_eps returns dJ/d eps_r(cell) for the box of cells
+ * [i0, i0+ni) x [j0, j0+nj) x [k0, k0+nk), in grad (host, ni*nj*nk doubles,
+ * x fastest), sigma held fixed. It is the exact reverse mode of the recorded
+ * float steps (with the float coefficients): segments between checkpoints are
+ * recomputed, the adjoint fields are swept back in time by the transposed
+ * step, and the coefficient sensitivities on the box's edges accumulate in
+ * double; edge coefficients follow from the edge's mean material
+ * (Cb = (S/eps)/(1+beta), Ca = (1-beta)/(1+beta), beta = sigma dt/(2 eps0 eps),
+ * eps = mean of the 4 cells). The grid's state is not changed; the call may be
+ * repeated for other boxes. Synchronises the stream.
+ * Errors: EINVAL (NULL, box outside the cells, no valid record), ENOMEM,
+ * ECUDA, ETIMEOUT.
+ */
+int sophie_objective_forward(sophie_grid *g, int nsteps, int comp, int i, int j, int k, int checkpoint_every,
+                             double *J);
+int sophie_objective_grad_eps(sophie_grid *g, int i0, int j0, int k0, int ni, int nj, int nk, double *grad);
+int sophie_objective_release(sophie_grid *g);
 
 /* Message of the last error on this thread ("" if none). */
 const char *sophie_last_error(void);

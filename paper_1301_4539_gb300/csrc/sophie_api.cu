@@ -70,6 +70,31 @@ struct ProfEntry {
   cudaEvent_t a, b;
 };
 
+// Recorded forward pass of a probe objective (sophie_objective_forward) and
+// the workspace of its reverse sweep (sophie_objective_grad_eps).
+struct Tape {
+  bool valid = false;
+  long long gen = -1;  // grid generation the record belongs to
+  long long n0 = 0;    // first step of the recorded pass
+  int N = 0, K = 50;   // steps, checkpoint interval
+  int comp = 2;        // objective component and index point
+  long long pt = 0;
+  std::vector<void*> ck;     // states at n0 + s*K, s = 0 .. ceil(N/K)-1
+  float* samples = nullptr;  // objective samples f^{n0+1} .. f^{n0+N}
+  int samples_cap = 0;
+  void* R[2] = {nullptr, nullptr};  // segment recompute (float fields)
+  CUtensorMap tmR[2];
+  CUtensorMap tmRM;
+  void* L[2] = {nullptr, nullptr};  // adjoint fields
+  int* ecomp = nullptr;             // design edges: component, index point
+  long long* ept = nullptr;
+  float* etr = nullptr;  // [K][nedge] e^n on the design edges
+  float* ctr = nullptr;  // [K][nedge] B h^{n+1/2} + s on the design edges
+  double* gcb = nullptr;  // dJ/dCb, dJ/dCa per design edge
+  double* gca = nullptr;
+  int edge_cap = 0, tr_cap = 0;
+};
+
 }  // namespace
 
 struct sophie_grid {
@@ -97,6 +122,8 @@ struct sophie_grid {
   std::vector<double> eps_h;
   std::vector<float2> ecoef_h;    // explicit points: (Ca, Cb) of ex, ey, ez
   std::vector<double> eeps_h;     // explicit points: eps_r of ex, ey, ez
+  std::vector<double> sig_h;      // sigma(edge) of each class (host; gradients)
+  std::vector<double> esig_h;     // explicit points: sigma of ex, ey, ez
   float2* ecoef = nullptr;        // device copies
   double* eeps = nullptr;
   size_t exp_cap = 0;
@@ -120,8 +147,11 @@ struct sophie_grid {
   bool prof = false;
   std::vector<ProfEntry> prof_live;
   std::vector<cudaEvent_t> ev_pool;
-  long long prof_count[3] = {0, 0, 0};
-  double prof_ms[3] = {0, 0, 0};
+  long long prof_count[4] = {0, 0, 0, 0};
+  double prof_ms[4] = {0, 0, 0, 0};
+  long long gen = 0;       // bumped by every change of fields, materials or sources
+  bool obj_rec = false;    // the step kernels also sample the objective point
+  Tape tape;
 };
 
 namespace {
@@ -240,7 +270,7 @@ int build_material_words(sophie_grid* g, const float* eps, const float* sig) {
   });
   std::unordered_map<EdgeKey, int, EdgeKeyHash> cls;
   std::vector<float2> coef(1, make_float2(0.f, 0.f));
-  std::vector<double> epsv(1, 0.0);
+  std::vector<double> epsv(1, 0.0), sigv(1, 0.0);
   for (size_t q = 0; q < order.size() && (int)coef.size() < kMaxClasses; ++q) {
     double e, s;
     memcpy(&e, &order[q].second.e, 8);
@@ -248,10 +278,11 @@ int build_material_words(sophie_grid* g, const float* eps, const float* sig) {
     cls.emplace(order[q].second, (int)coef.size());
     coef.push_back(edge_coef(g, e, s));
     epsv.push_back(e);
+    sigv.push_back(s);
   }
   // Pass 2: words.
   std::vector<float2> ecoef;
-  std::vector<double> eeps;
+  std::vector<double> eeps, esig;
   uint32_t* w = g->mat_host;
   EdgeKey lk[3] = {{~0ull, ~0ull}, {~0ull, ~0ull}, {~0ull, ~0ull}};
   int lc[3] = {-1, -1, -1};
@@ -283,6 +314,7 @@ int build_material_words(sophie_grid* g, const float* eps, const float* sig) {
             const bool in = e_edge_interior(d, c, i, j, k);
             ecoef.push_back(in ? edge_coef(g, ce[c], cs[c]) : make_float2(0.f, 0.f));
             eeps.push_back(in ? ce[c] : 0.0);
+            esig.push_back(in ? cs[c] : 0.0);
           }
           row[i] = kExpFlag | ((uint32_t)q << 3);
         }
@@ -295,6 +327,8 @@ int build_material_words(sophie_grid* g, const float* eps, const float* sig) {
   g->eps_h = std::move(epsv);
   g->ecoef_h = std::move(ecoef);
   g->eeps_h = std::move(eeps);
+  g->sig_h = std::move(sigv);
+  g->esig_h = std::move(esig);
   return SOPHIE_OK;
 }
 
@@ -448,6 +482,12 @@ StepArgs make_step_args(sophie_grid* g) {
     a.prb.comp[p] = g->prb[p].comp;
     a.prb.pos[p] = g->prb[p].pos;
   }
+  if (g->obj_rec) {
+    // The objective's samples go to the first unused probe slot.
+    a.prb.comp[a.prb.n] = g->tape.comp;
+    a.prb.pos[a.prb.n] = g->tape.pt;
+    a.prb.n += 1;
+  }
   a.prb.buf = g->pbuf;
   a.prb.cap = g->pcap;
   a.err = g->err;
@@ -465,9 +505,19 @@ int check_err_word(sophie_grid* g) {
   return SOPHIE_OK;
 }
 
+void free_tape(Tape& t) {
+  for (void* p : t.ck) cudaFree(p);
+  t.ck.clear();
+  void* bufs[] = {t.samples, t.R[0], t.R[1], t.L[0], t.L[1], t.ecomp, t.ept, t.etr, t.ctr, t.gcb, t.gca};
+  for (void* p : bufs)
+    if (p) cudaFree(p);
+  t = Tape{};
+}
+
 void free_grid(sophie_grid* g) {
   if (!g) return;
   if (g->stream) cudaStreamSynchronize(g->stream);
+  free_tape(g->tape);
   for (int b = 0; b < 2; ++b)
     if (g->F[b]) cudaFree(g->F[b]);
   if (g->mat) cudaFree(g->mat);
@@ -548,6 +598,7 @@ void from_store(int fmt, float scale, const void* in, float* out, size_t n) {
 }
 
 int set_component(sophie_grid* g, int comp, const float* host) {
+  g->gen++;
   const Dims& d = g->d;
   const size_t n = (size_t)(d.nx + 1) * d.ny1 * d.nz1;
   std::vector<unsigned char> tmp;
@@ -753,7 +804,8 @@ int sophie_set_materials(sophie_grid* g, const float* eps, const float* sig) {
   // The staging buffer may still feed an earlier upload.
   CUDA_TRY(cudaEventSynchronize(g->mat_upload_done));
   std::vector<float2> old_coef = g->coef_h, old_ecoef = g->ecoef_h;
-  std::vector<double> old_eps = g->eps_h, old_eeps = g->eeps_h;
+  std::vector<double> old_eps = g->eps_h, old_eeps = g->eeps_h, old_sig = g->sig_h, old_esig = g->esig_h;
+  g->gen++;
   int rc = build_material_words(g, eps, sig);
   if (rc) {
     // Restore the words of the current materials.
@@ -761,6 +813,8 @@ int sophie_set_materials(sophie_grid* g, const float* eps, const float* sig) {
     g->eps_h = old_eps;
     g->ecoef_h = old_ecoef;
     g->eeps_h = old_eeps;
+    g->sig_h = old_sig;
+    g->esig_h = old_esig;
     CUDA_TRY(cudaMemcpy(g->mat_host, g->mat, (size_t)g->d.plane * g->d.nz1 * 4, cudaMemcpyDeviceToHost));
     return rc;
   }
@@ -778,6 +832,7 @@ int sophie_add_source(sophie_grid* g, int comp, int i, int j, int k, double amp,
     return fail(SOPHIE_EINVAL, "bad waveform parameters");
   if ((int)g->src.size() >= kMaxSources) return fail(SOPHIE_EINVAL, "at most %d sources", kMaxSources);
   Source s{comp, i, j, k, kind, amp, f0, bw, t0, point_index(g->d, i, j, k)};
+  g->gen++;
   g->src.push_back(s);
   int rc = refresh_source_table(g, (int)g->src.size() - 1);
   if (rc) {
@@ -813,6 +868,7 @@ int sophie_step(sophie_grid* g, int n) {
   if (n == 0) return SOPHIE_OK;
   int rc = ensure_capacity(g, g->n + n);
   if (rc) return rc;
+  g->gen++;
   for (int m = 0; m < n;) {
     const int K = g->temporal_k;
     const bool blocked = !g->use_simple && K >= 2 && n - m >= K && blocked_supported(K);
@@ -961,6 +1017,7 @@ int sophie_reset(sophie_grid* g) {
   if (g->pbuf) CUDA_TRY(cudaMemsetAsync(g->pbuf, 0, (size_t)kMaxProbes * g->pcap * 4, g->stream));
   g->n = 0;
   g->cur = 0;
+  g->gen++;
   for (Probe& p : g->prb) p.n_added = 0;
   return SOPHIE_OK;
 }
@@ -1014,7 +1071,7 @@ int sophie_profile(sophie_grid* g, int enable) {
   if (rc) return rc;
   g->prof = enable != 0;
   if (enable)
-    for (int i = 0; i < 3; ++i) {
+    for (int i = 0; i < 4; ++i) {
       g->prof_count[i] = 0;
       g->prof_ms[i] = 0.0;
     }
@@ -1023,11 +1080,267 @@ int sophie_profile(sophie_grid* g, int enable) {
 
 int sophie_profile_read(sophie_grid* g, int kernel, long long* launches, double* ms) {
   if (!g || !launches || !ms) return fail(SOPHIE_EINVAL, "NULL argument");
-  if (kernel < 0 || kernel > 2) return fail(SOPHIE_EINVAL, "bad kernel id");
+  if (kernel < 0 || kernel > 3) return fail(SOPHIE_EINVAL, "bad kernel id");
   int rc = prof_drain(g);
   if (rc) return rc;
   *launches = g->prof_count[kernel];
   *ms = g->prof_ms[kernel];
+  return SOPHIE_OK;
+}
+
+int sophie_objective_release(sophie_grid* g) {
+  if (!g) return fail(SOPHIE_EINVAL, "NULL grid");
+  CUDA_TRY(cudaStreamSynchronize(g->stream));
+  free_tape(g->tape);
+  return SOPHIE_OK;
+}
+
+int sophie_objective_forward(sophie_grid* g, int nsteps, int comp, int i, int j, int k, int checkpoint_every,
+                             double* J) {
+  if (!g || !J) return fail(SOPHIE_EINVAL, "NULL argument");
+  if (nsteps < 1) return fail(SOPHIE_EINVAL, "nsteps must be >= 1");
+  if (checkpoint_every < 0) return fail(SOPHIE_EINVAL, "checkpoint_every must be >= 0");
+  if (comp < 0 || comp > 5 || !comp_valid(g->d, comp, i, j, k))
+    return fail(SOPHIE_EINVAL, "objective point (%d,%d,%d) outside comp %d's range", i, j, k, comp);
+  if (i == g->d.nx || j == g->d.ny || k == g->d.nz)
+    return fail(SOPHIE_EINVAL, "objective point on a plane no step updates");
+  if (g->fmt != kF32) return fail(SOPHIE_ENOTSUP, "gradients need float field storage");
+  if ((int)g->prb.size() >= kMaxProbes) return fail(SOPHIE_ENOTSUP, "all %d probe slots are in use", kMaxProbes);
+  Tape& t = g->tape;
+  t.valid = false;
+  const int K = checkpoint_every == 0 ? 50 : checkpoint_every;
+  const int nseg = (nsteps + K - 1) / K;
+  const Dims& d = g->d;
+  const size_t fbytes = (size_t)d.zstride * d.nz1 * 4;
+  int rc = ensure_capacity(g, g->n + nsteps);
+  if (rc) return rc;
+  CUDA_TRY(cudaStreamSynchronize(g->stream));
+  while ((int)t.ck.size() < nseg) {
+    void* p = nullptr;
+    if (cudaMalloc(&p, fbytes) != cudaSuccess) {
+      cudaGetLastError();
+      free_tape(t);
+      return fail(SOPHIE_ENOMEM, "checkpoint allocation (%d x %zu bytes) failed", nseg, fbytes);
+    }
+    t.ck.push_back(p);
+  }
+  if (t.samples_cap < nsteps) {
+    if (t.samples) cudaFree(t.samples);
+    t.samples = nullptr;
+    t.samples_cap = 0;
+    if (cudaMalloc(&t.samples, (size_t)nsteps * 4) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(SOPHIE_ENOMEM, "objective sample buffer allocation failed");
+    }
+    t.samples_cap = nsteps;
+  }
+  t.comp = comp;
+  t.pt = point_index(d, i, j, k);
+  t.n0 = g->n;
+  t.N = nsteps;
+  t.K = K;
+  if (launch_or_flag(g->mat, t.pt, kPrbFlag, g->stream) != cudaSuccess)
+    return fail(SOPHIE_ECUDA, "flag launch failed");
+  g->launches++;
+  const int slot = (int)g->prb.size();
+  g->obj_rec = true;
+  for (int sg = 0; sg < nseg; ++sg) {
+    const cudaError_t e = cudaMemcpyAsync(t.ck[sg], g->F[g->cur], fbytes, cudaMemcpyDeviceToDevice, g->stream);
+    if (e != cudaSuccess) {
+      g->obj_rec = false;
+      return fail(SOPHIE_ECUDA, "checkpoint copy failed: %s", cudaGetErrorString(e));
+    }
+    rc = sophie_step(g, std::min(K, nsteps - sg * K));
+    if (rc) {
+      g->obj_rec = false;
+      return rc;
+    }
+  }
+  g->obj_rec = false;
+  float* slot_p = g->pbuf + (size_t)slot * g->pcap + t.n0;
+  CUDA_TRY(cudaMemcpyAsync(t.samples, slot_p, (size_t)nsteps * 4, cudaMemcpyDeviceToDevice, g->stream));
+  CUDA_TRY(cudaMemsetAsync(slot_p, 0, (size_t)nsteps * 4, g->stream));
+  std::vector<float> f((size_t)nsteps);
+  CUDA_TRY(cudaMemcpyAsync(f.data(), t.samples, (size_t)nsteps * 4, cudaMemcpyDeviceToHost, g->stream));
+  rc = check_err_word(g);
+  if (rc) return rc;
+  double acc = 0.0;
+  for (int n = 0; n < nsteps; ++n) acc += (double)f[n] * (double)f[n];
+  *J = g->dt * acc;
+  if (!std::isfinite(*J)) return fail(SOPHIE_ENONFINITE, "objective is not finite");
+  t.valid = true;
+  t.gen = g->gen;
+  return SOPHIE_OK;
+}
+
+int sophie_objective_grad_eps(sophie_grid* g, int i0, int j0, int k0, int ni, int nj, int nk, double* grad) {
+  if (!g || !grad) return fail(SOPHIE_EINVAL, "NULL argument");
+  Tape& t = g->tape;
+  if (!t.valid || t.gen != g->gen)
+    return fail(SOPHIE_EINVAL, "no objective recorded since the last change of the grid");
+  const Dims& d = g->d;
+  if (ni < 1 || nj < 1 || nk < 1 || i0 < 0 || j0 < 0 || k0 < 0 || i0 + ni > d.nx || j0 + nj > d.ny ||
+      k0 + nk > d.nz)
+    return fail(SOPHIE_EINVAL, "design box outside the grid's cells");
+  // Design edges: interior edges of the box's cells; box index -> edge index.
+  const int ext[3][3] = {{ni, nj + 1, nk + 1}, {ni + 1, nj, nk + 1}, {ni + 1, nj + 1, nk}};
+  std::vector<int> map[3];
+  std::vector<int> hcomp;
+  std::vector<long long> hpt;
+  std::vector<double> dcb, dca;
+  for (int c = 0; c < 3; ++c) {
+    map[c].assign((size_t)ext[c][0] * ext[c][1] * ext[c][2], -1);
+    for (int kk = 0; kk < ext[c][2]; ++kk)
+      for (int jj = 0; jj < ext[c][1]; ++jj)
+        for (int ii = 0; ii < ext[c][0]; ++ii) {
+          const int i = i0 + ii, j = j0 + jj, k = k0 + kk;
+          if (!e_edge_interior(d, c, i, j, k)) continue;
+          const long long pt = point_index(d, i, j, k);
+          const uint32_t w = g->mat_host[pt];
+          double e, sg;
+          if (w & kExpFlag) {
+            const size_t q = w >> 3;
+            e = g->eeps_h[3 * q + c];
+            sg = g->esig_h[3 * q + c];
+          } else {
+            e = g->eps_h[cls_of(w, c)];
+            sg = g->sig_h[cls_of(w, c)];
+          }
+          // Cb = (S/e)/(1+beta), Ca = (1-beta)/(1+beta), beta = sigma dt/(2 eps0 e)
+          const double beta = (sg * g->dt) / (2.0 * kEps0 * e);
+          const double cb = (g->S64 / e) / (1.0 + beta);
+          map[c][((size_t)kk * ext[c][1] + jj) * ext[c][0] + ii] = (int)hpt.size();
+          hcomp.push_back(c);
+          hpt.push_back(pt);
+          dcb.push_back(-cb / (e * (1.0 + beta)));
+          dca.push_back(2.0 * beta / (e * (1.0 + beta) * (1.0 + beta)));
+        }
+  }
+  const int nedge = (int)hpt.size();
+  const size_t fbytes = (size_t)d.zstride * d.nz1 * 4;
+  CUDA_TRY(cudaStreamSynchronize(g->stream));
+  auto grow = [&](void** p, size_t bytes) -> bool {
+    if (*p) cudaFree(*p);
+    *p = nullptr;
+    if (cudaMalloc(p, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      *p = nullptr;
+      return false;
+    }
+    return true;
+  };
+  if (!t.R[0]) {
+    for (int b = 0; b < 2; ++b)
+      if (!grow(&t.R[b], fbytes) || !grow(&t.L[b], fbytes))
+        return fail(SOPHIE_ENOMEM, "adjoint workspace allocation failed");
+    for (int b = 0; b < 2; ++b)
+      if (!encode_maps(d, kF32, t.R[b], g->mat, plain_box_x(kF32), plain_box_y(), &t.tmR[b], &t.tmRM))
+        return fail(SOPHIE_ECUDA, "cuTensorMapEncodeTiled failed");
+  }
+  if (nedge > t.edge_cap) {
+    if (!grow((void**)&t.ecomp, (size_t)nedge * 4) || !grow((void**)&t.ept, (size_t)nedge * 8) ||
+        !grow((void**)&t.gcb, (size_t)nedge * 8) || !grow((void**)&t.gca, (size_t)nedge * 8)) {
+      t.edge_cap = 0;
+      return fail(SOPHIE_ENOMEM, "design edge table allocation failed");
+    }
+    t.edge_cap = nedge;
+    t.tr_cap = 0;
+  }
+  if ((long long)nedge * t.K > t.tr_cap) {
+    if (!grow((void**)&t.etr, (size_t)nedge * t.K * 4) || !grow((void**)&t.ctr, (size_t)nedge * t.K * 4)) {
+      t.tr_cap = 0;
+      return fail(SOPHIE_ENOMEM, "design edge trace allocation failed");
+    }
+    t.tr_cap = nedge * t.K;
+  }
+  if (nedge) {
+    CUDA_TRY(cudaMemcpyAsync(t.ecomp, hcomp.data(), (size_t)nedge * 4, cudaMemcpyHostToDevice, g->stream));
+    CUDA_TRY(cudaMemcpyAsync(t.ept, hpt.data(), (size_t)nedge * 8, cudaMemcpyHostToDevice, g->stream));
+    CUDA_TRY(cudaMemsetAsync(t.gcb, 0, (size_t)nedge * 8, g->stream));
+    CUDA_TRY(cudaMemsetAsync(t.gca, 0, (size_t)nedge * 8, g->stream));
+  }
+  CUDA_TRY(cudaMemsetAsync(t.L[0], 0, fbytes, g->stream));
+  CUDA_TRY(cudaMemsetAsync(t.L[1], 0, fbytes, g->stream));
+  const double two_dt = 2.0 * g->dt;
+  int lc = 0;
+  const int nseg = (t.N + t.K - 1) / t.K;
+  for (int sg = nseg - 1; sg >= 0; --sg) {
+    const long long ns = t.n0 + (long long)sg * t.K;
+    const int len = std::min(t.K, t.N - sg * t.K);
+    // Recompute the segment from its checkpoint, keeping the design-edge values.
+    CUDA_TRY(cudaMemcpyAsync(t.R[0], t.ck[sg], fbytes, cudaMemcpyDeviceToDevice, g->stream));
+    for (int m = 0; m < len; ++m) {
+      StepArgs a = make_step_args(g);
+      a.fin = t.R[m & 1];
+      a.fout = t.R[(m + 1) & 1];
+      a.n0 = ns + m;
+      a.prb.n = 0;
+      cudaEvent_t ea = g->prof ? prof_event(g) : nullptr, eb = g->prof ? prof_event(g) : nullptr;
+      if (ea) cudaEventRecord(ea, g->stream);
+      cudaError_t e = launch_step_plain(a, t.tmR[m & 1], t.tmRM, g->ptile, g->stream);
+      if (eb) {
+        cudaEventRecord(eb, g->stream);
+        g->prof_live.push_back({SOPHIE_KERNEL_PLAIN, ea, eb});
+      }
+      if (e == cudaSuccess)
+        e = launch_gather(a, t.ecomp, t.ept, nedge, t.etr + (size_t)m * nedge, t.ctr + (size_t)m * nedge, g->stream);
+      if (e != cudaSuccess) return fail(SOPHIE_ECUDA, "recompute launch failed: %s", cudaGetErrorString(e));
+      g->launches += nedge ? 2 : 1;
+    }
+    if (g->prof_live.size() > 20000) {
+      int rc = prof_drain(g);
+      if (rc) return rc;
+    }
+    // Reverse sweep over the segment.
+    for (int m = len - 1; m >= 0; --m) {
+      const long long n = ns + m;
+      float* l = static_cast<float*>(t.L[lc]);
+      cudaError_t e = launch_add_objective(l, d, t.comp, t.pt, t.samples + (n - t.n0), two_dt, g->stream);
+      if (e == cudaSuccess)
+        e = launch_grad_accum(l, d, t.ecomp, t.ept, nedge, t.etr + (size_t)m * nedge, t.ctr + (size_t)m * nedge,
+                              t.gcb, t.gca, g->stream);
+      if (e == cudaSuccess) {
+        StepArgs a = make_step_args(g);
+        a.fin = t.L[lc];
+        a.fout = t.L[1 - lc];
+        a.n0 = n;
+        a.prb.n = 0;
+        cudaEvent_t ea = g->prof ? prof_event(g) : nullptr, eb = g->prof ? prof_event(g) : nullptr;
+        if (ea) cudaEventRecord(ea, g->stream);
+        e = launch_adj_step(a, g->stream);
+        if (eb) {
+          cudaEventRecord(eb, g->stream);
+          g->prof_live.push_back({SOPHIE_KERNEL_ADJOINT, ea, eb});
+        }
+      }
+      if (e != cudaSuccess) return fail(SOPHIE_ECUDA, "adjoint launch failed: %s", cudaGetErrorString(e));
+      g->launches += nedge ? 3 : 2;
+      lc = 1 - lc;
+    }
+  }
+  std::vector<double> gcb((size_t)nedge), gca((size_t)nedge);
+  if (nedge) {
+    CUDA_TRY(cudaMemcpyAsync(gcb.data(), t.gcb, (size_t)nedge * 8, cudaMemcpyDeviceToHost, g->stream));
+    CUDA_TRY(cudaMemcpyAsync(gca.data(), t.gca, (size_t)nedge * 8, cudaMemcpyDeviceToHost, g->stream));
+  }
+  int rc = check_err_word(g);
+  if (rc) return rc;
+  // Chain rule to cells: eps_r(edge) is the mean of its four cells.
+  for (int kk = 0; kk < nk; ++kk)
+    for (int jj = 0; jj < nj; ++jj)
+      for (int ii = 0; ii < ni; ++ii) {
+        double acc = 0.0;
+        for (int c = 0; c < 3; ++c)
+          for (int a = 0; a < 2; ++a)
+            for (int b = 0; b < 2; ++b) {
+              const int ei = ii + (c == 0 ? 0 : a);
+              const int ej = jj + (c == 0 ? a : c == 1 ? 0 : b);
+              const int ek = kk + (c == 2 ? 0 : b);
+              const int q = map[c][((size_t)ek * ext[c][1] + ej) * ext[c][0] + ei];
+              if (q >= 0) acc += 0.25 * (gcb[q] * dcb[q] + gca[q] * dca[q]);
+            }
+        grad[((size_t)kk * nj + jj) * ni + ii] = acc;
+      }
   return SOPHIE_OK;
 }
 

@@ -130,4 +130,19 @@ int energy_noalloc(const StepArgs& a, const double* eps_tab, double scale, doubl
 cudaError_t launch_mask_component(void* f, int esz, const Dims& d, int comp, cudaStream_t s);
 cudaError_t launch_or_flag(uint32_t* mat, long long pos, uint32_t bit, cudaStream_t s);
 
+// Reverse-mode sweep (yee_adjoint.cu). Adjoint fields use the float field
+// layout; a.fin holds the adjoint of the state after a step, a.fout receives
+// the adjoint of the state before it.
+cudaError_t launch_adj_step(const StepArgs& a, cudaStream_t s);
+// After the forward step a.fin -> a.fout (float storage, a.n0 = its index):
+// e_out[t] = e^n and c_out[t] = B h^{n+1/2} + s on design edge t.
+cudaError_t launch_gather(const StepArgs& a, const int* edge_comp, const long long* edge_pt, int nedge, float* e_out,
+                          float* c_out, cudaStream_t s);
+// gcb[t] += l_e(edge t) * c_in[t], gca[t] += l_e(edge t) * e_in[t] (double).
+cudaError_t launch_grad_accum(const float* l, const Dims& d, const int* edge_comp, const long long* edge_pt, int nedge,
+                              const float* e_in, const float* c_in, double* gcb, double* gca, cudaStream_t s);
+// l(comp at point pt) += two_dt * sample[0].
+cudaError_t launch_add_objective(float* l, const Dims& d, int comp, long long pt, const float* sample, double two_dt,
+                                 cudaStream_t s);
+
 }  // namespace sophie

@@ -21,7 +21,7 @@ OK, EINVAL, EUNSTABLE, ENOMEM, ECUDA, ENONFINITE, ETIMEOUT, ETOOMANYMAT, ENOTSUP
 EX, EY, EZ, HX, HY, HZ = range(6)
 GAUSS_SINE, GAUSS = 0, 1
 FP32, FP16, BF16 = 0, 1, 2
-KERNEL_PLAIN, KERNEL_BLOCKED, KERNEL_ENERGY = 0, 1, 2
+KERNEL_PLAIN, KERNEL_BLOCKED, KERNEL_ENERGY, KERNEL_ADJOINT = 0, 1, 2, 3
 
 # Exported symbols with (restype, argtypes).
 _P = ctypes.c_void_p
@@ -50,6 +50,9 @@ SIGNATURES = {
     "sophie_launch_count": (_I, [_P, ctypes.POINTER(_LL)]),
     "sophie_profile": (_I, [_P, _I]),
     "sophie_profile_read": (_I, [_P, _I, ctypes.POINTER(_LL), ctypes.POINTER(_D)]),
+    "sophie_objective_forward": (_I, [_P, _I, _I, _I, _I, _I, _I, ctypes.POINTER(_D)]),
+    "sophie_objective_grad_eps": (_I, [_P, _I, _I, _I, _I, _I, _I, _P]),
+    "sophie_objective_release": (_I, [_P]),
     "sophie_last_error": (ctypes.c_char_p, []),
 }
 
@@ -201,6 +204,24 @@ def sophie_profile_read(g: int, kernel: int):
     return n.value, ms.value
 
 
+def sophie_objective_forward(g: int, nsteps: int, comp: int, i: int, j: int, k: int,
+                             checkpoint_every: int = 0) -> float:
+    J = _D()
+    _chk(load().sophie_objective_forward(g, nsteps, comp, i, j, k, checkpoint_every, ctypes.byref(J)))
+    return J.value
+
+
+def sophie_objective_grad_eps(g: int, i0: int, j0: int, k0: int, ni: int, nj: int, nk: int) -> np.ndarray:
+    """dJ/d eps_r of the cell box, shape (nk, nj, ni)."""
+    out = np.zeros((nk, nj, ni), np.float64)
+    _chk(load().sophie_objective_grad_eps(g, i0, j0, k0, ni, nj, nk, out.ctypes.data))
+    return out
+
+
+def sophie_objective_release(g: int) -> None:
+    _chk(load().sophie_objective_release(g))
+
+
 def sophie_last_error() -> str:
     return load().sophie_last_error().decode()
 
@@ -281,3 +302,12 @@ class Grid:
 
     def profile_read(self, kernel):
         return sophie_profile_read(self.h, kernel)
+
+    def objective_forward(self, nsteps, comp, i, j, k, checkpoint_every=0):
+        return sophie_objective_forward(self.h, nsteps, comp, i, j, k, checkpoint_every)
+
+    def objective_grad_eps(self, i0, j0, k0, ni, nj, nk):
+        return sophie_objective_grad_eps(self.h, i0, j0, k0, ni, nj, nk)
+
+    def objective_release(self):
+        sophie_objective_release(self.h)
