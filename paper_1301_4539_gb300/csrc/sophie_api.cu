@@ -86,6 +86,7 @@ struct Tape {
   CUtensorMap tmR[2];
   CUtensorMap tmRM;
   void* L[2] = {nullptr, nullptr};  // adjoint fields
+  CUtensorMap tmL[2];
   int* ecomp = nullptr;             // design edges: component, index point
   long long* ept = nullptr;
   float* etr = nullptr;  // [K][nedge] e^n on the design edges
@@ -1188,6 +1189,7 @@ int sophie_objective_grad_eps(sophie_grid* g, int i0, int j0, int k0, int ni, in
   std::vector<int> hcomp;
   std::vector<long long> hpt;
   std::vector<double> dcb, dca;
+  std::vector<float> cbf;  // the float Cb the step kernels use on each design edge
   for (int c = 0; c < 3; ++c) {
     map[c].assign((size_t)ext[c][0] * ext[c][1] * ext[c][2], -1);
     for (int kk = 0; kk < ext[c][2]; ++kk)
@@ -1210,6 +1212,7 @@ int sophie_objective_grad_eps(sophie_grid* g, int i0, int j0, int k0, int ni, in
           const double beta = (sg * g->dt) / (2.0 * kEps0 * e);
           const double cb = (g->S64 / e) / (1.0 + beta);
           map[c][((size_t)kk * ext[c][1] + jj) * ext[c][0] + ii] = (int)hpt.size();
+          cbf.push_back((w & kExpFlag) ? g->ecoef_h[3 * (size_t)(w >> 3) + c].y : g->coef_h[cls_of(w, c)].y);
           hcomp.push_back(c);
           hpt.push_back(pt);
           dcb.push_back(-cb / (e * (1.0 + beta)));
@@ -1234,7 +1237,8 @@ int sophie_objective_grad_eps(sophie_grid* g, int i0, int j0, int k0, int ni, in
       if (!grow(&t.R[b], fbytes) || !grow(&t.L[b], fbytes))
         return fail(SOPHIE_ENOMEM, "adjoint workspace allocation failed");
     for (int b = 0; b < 2; ++b)
-      if (!encode_maps(d, kF32, t.R[b], g->mat, plain_box_x(kF32), plain_box_y(), &t.tmR[b], &t.tmRM))
+      if (!encode_maps(d, kF32, t.R[b], g->mat, plain_box_x(kF32), plain_box_y(), &t.tmR[b], &t.tmRM) ||
+          !encode_maps(d, kF32, t.L[b], nullptr, plain_box_x(kF32), plain_box_y(), &t.tmL[b], nullptr))
         return fail(SOPHIE_ECUDA, "cuTensorMapEncodeTiled failed");
   }
   if (nedge > t.edge_cap) {
@@ -1261,7 +1265,28 @@ int sophie_objective_grad_eps(sophie_grid* g, int i0, int j0, int k0, int ni, in
   }
   CUDA_TRY(cudaMemsetAsync(t.L[0], 0, fbytes, g->stream));
   CUDA_TRY(cudaMemsetAsync(t.L[1], 0, fbytes, g->stream));
-  const double two_dt = 2.0 * g->dt;
+  // Reverse sweep. Default form: in the variables u = Cb * l_e, mu = -S * l_h
+  // the reverse step is the forward step itself with the same coefficients
+  // (mu' = mu + S A u, u' = Ca u + Cb B mu'), so it runs on the forward step
+  // kernel with sources and probes off; the objective's direct term enters as
+  // u += Cb 2dt f (E component) or mu += -S 2dt f (H component), and the
+  // accumulated sums of u * (bracket) and u * e are divided by Cb at the end.
+  // SOPHIE_ADJOINT=direct runs the literal transposed step (yee_adjoint.cu)
+  // on (l_e, l_h) instead (a cross-check; same gradient up to rounding).
+  const char* am = getenv("SOPHIE_ADJOINT");
+  const bool direct = am && strcmp(am, "direct") == 0;
+  double obj_scale = 1.0;
+  if (!direct) {
+    if (t.comp < 3) {
+      const uint32_t w = g->mat_host[t.pt];
+      obj_scale = (w & kExpFlag) ? g->ecoef_h[3 * (size_t)(w >> 3) + t.comp].y : g->coef_h[cls_of(w, t.comp)].y;
+      if (!e_edge_interior(d, t.comp, (int)(t.pt % d.nxp), (int)(t.pt / d.nxp % d.ny1), (int)(t.pt / d.plane)))
+        obj_scale = 0.0;
+    } else {
+      obj_scale = -(double)g->S32;
+    }
+  }
+  const double two_dt = 2.0 * g->dt * obj_scale;
   int lc = 0;
   const int nseg = (t.N + t.K - 1) / t.K;
   for (int sg = nseg - 1; sg >= 0; --sg) {
@@ -1305,9 +1330,10 @@ int sophie_objective_grad_eps(sophie_grid* g, int i0, int j0, int k0, int ni, in
         a.fout = t.L[1 - lc];
         a.n0 = n;
         a.prb.n = 0;
+        a.src.n = 0;
         cudaEvent_t ea = g->prof ? prof_event(g) : nullptr, eb = g->prof ? prof_event(g) : nullptr;
         if (ea) cudaEventRecord(ea, g->stream);
-        e = launch_adj_step(a, g->stream);
+        e = direct ? launch_adj_step(a, g->stream) : launch_step_plain(a, t.tmL[lc], t.tmRM, g->ptile, g->stream);
         if (eb) {
           cudaEventRecord(eb, g->stream);
           g->prof_live.push_back({SOPHIE_KERNEL_ADJOINT, ea, eb});
@@ -1337,7 +1363,10 @@ int sophie_objective_grad_eps(sophie_grid* g, int i0, int j0, int k0, int ni, in
               const int ej = jj + (c == 0 ? a : c == 1 ? 0 : b);
               const int ek = kk + (c == 2 ? 0 : b);
               const int q = map[c][((size_t)ek * ext[c][1] + ej) * ext[c][0] + ei];
-              if (q >= 0) acc += 0.25 * (gcb[q] * dcb[q] + gca[q] * dca[q]);
+              if (q < 0) continue;
+              // sums of u * (...) = Cb * sums of l_e * (...) in the default form
+              const double un = direct ? 1.0 : (double)cbf[q];
+              acc += 0.25 * (gcb[q] * dcb[q] + gca[q] * dca[q]) / un;
             }
         grad[((size_t)kk * nj + jj) * ni + ii] = acc;
       }

@@ -59,18 +59,26 @@ def _box_cells(box):
     return [(i0 + i, j0 + j, k0 + k) for k in range(nk) for j in range(nj) for i in range(ni)]
 
 
-def test_grad_matches_fp64_oracle_gradient(oracle_mod, sophie):
+@pytest.mark.parametrize("form", ["default", "direct"])
+@pytest.mark.parametrize("probe_comp", [2, 4])
+def test_grad_matches_fp64_oracle_gradient(oracle_mod, sophie, monkeypatch, form, probe_comp):
+    """Both forms of the reverse sweep (forward step kernel on u = Cb l_e,
+    mu = -S l_h; literal transposed step on l_e, l_h), for an E and an H
+    objective, against the FP64 oracle's gradient over every design cell."""
+    if form == "direct":
+        monkeypatch.setenv("SOPHIE_ADJOINT", "direct")
     n3, eps, sig, src, probe, box = _small_case()
+    probe = (probe_comp,) + probe[1:]
     N = 130  # segments 50, 50, 30
     g, J, grad = _gpu_grad(n3, eps, sig, src, probe, box, N)
     Jo, go = _oracle_grad(oracle_mod, n3, eps, sig, src, probe, _box_cells(box), N)
     go = go.reshape(grad.shape)
-    print(f"J gpu {J:.9e} oracle {Jo:.9e}")
+    print(f"[{form}, comp {probe_comp}] J gpu {J:.9e} oracle {Jo:.9e}")
     assert abs(J - Jo) <= 1e-5 * abs(Jo)
     scale = np.max(np.abs(go))
     rel = np.linalg.norm(grad - go) / np.linalg.norm(go)
     worst = np.max(np.abs(grad - go)) / scale
-    print(f"gradient vs FP64 oracle: rel-L2 {rel:.3e}, max |diff|/max|g| {worst:.3e}")
+    print(f"[{form}, comp {probe_comp}] gradient vs FP64 oracle: rel-L2 {rel:.3e}, max |diff|/max|g| {worst:.3e}")
     assert rel <= 1e-4 and worst <= 1e-4
     assert g.n == N
 
