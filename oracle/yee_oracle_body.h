@@ -38,6 +38,9 @@
  *   beta = sigma*dt / (2*eps0*eps_r),  Ca = (1-beta)/(1+beta),
  *   Cb = (S/eps_r)/(1+beta),           S  = c*dt/dx  (double).
  * Only interior (non-PEC) edges get coefficients; wall edges keep Ca = Cb = 0.
+ * A cell with eps_r = +inf is a perfect conductor: every edge it touches is a
+ * PEC edge (Ca = Cb = 0, eps_r(edge) reported as 0), the same as a wall edge,
+ * so a layer of such cells splits the grid into independent cavities.
  * epsx/epsy/epsz (double, may be NULL) receive eps_r(edge), 0 on walls.
  */
 void FN(oracle_coefs)(int nx, int ny, int nz, double dx, double dt,
@@ -59,6 +62,12 @@ void FN(oracle_coefs)(int nx, int ny, int nz, double dx, double dt,
 #define COEF(eps4, sig4, ca, cb)                                                  \
     do {                                                                          \
         const double e_ = (eps4) * 0.25, s_ = (sig4) * 0.25;                      \
+        if (isinf(e_)) { /* an edge of a PEC cell: tangential E stays 0 */         \
+            ca = 0;                                                               \
+            cb = 0;                                                               \
+            epsv = 0.0;                                                           \
+            break;                                                                \
+        }                                                                         \
         const double beta_ = (s_ * dt) / (2.0 * EPS0 * e_);                       \
         ca = (REAL)((1.0 - beta_) / (1.0 + beta_));                               \
         cb = (REAL)((S / e_) / (1.0 + beta_));                                    \

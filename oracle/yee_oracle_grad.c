@@ -230,6 +230,7 @@ double oracle_grad_f64(int nx, int ny, int nz, double dx, double dt,
                 s4 += (double)sig_cell[cell];
             }
             const double e = e4 * 0.25, s = s4 * 0.25;
+            if (isinf(e)) continue; /* edge of a PEC cell: no eps dependence */
             const double beta = (s * dt) / (2.0 * EPS0 * e);
             const double cbv = (S / e) / (1.0 + beta);
             const double dcb = -cbv / (e * (1.0 + beta));
