@@ -100,14 +100,16 @@ int sophie_destroy_grid(sophie_grid *g);
 
 /*
  * Per-cell relative permittivity and conductivity (S/m), host arrays of
- * nx*ny*nz floats each (x fastest, then y, then z), copied. eps_r >= 1 and
- * finite; sigma >= 0 and finite (else EINVAL). Edge values are the mean of the
- * four cells sharing the edge (Sec. 2.1 coefficients, see top of file). The
- * 511 most frequent edge materials are held as classes in a table; index
- * points with an edge outside them carry their own coefficients (any number
- * of distinct materials; the explicit points cost 48 extra bytes each and are
- * updated on a slower path). Enqueued on the grid's stream; the host arrays
- * may be reused on return. Errors: EINVAL, ENOMEM, ECUDA.
+ * nx*ny*nz floats each (x fastest, then y, then z), copied. eps_r >= 1, or
+ * +inf for a perfectly conducting cell (every edge it touches is PEC, like
+ * the outer walls); sigma >= 0 and finite (else EINVAL). Edge values are the
+ * mean of the four cells sharing the edge (Sec. 2.1 coefficients, see top of
+ * file). The 511 most frequent edge materials are held as classes in a
+ * table; index points with an edge outside them carry explicit coefficients
+ * (any number of distinct materials; points with the same three edge
+ * materials share one 48-byte entry, read with the point). Enqueued on the
+ * grid's stream; the host arrays may be reused on return.
+ * Errors: EINVAL, ENOMEM, ECUDA, ETOOMANYMAT (more than 2^29 explicit entries).
  */
 int sophie_set_materials(sophie_grid *g, const float *eps_r, const float *sigma);
 
@@ -205,7 +207,8 @@ int sophie_sync(sophie_grid *g);
 
 /*
  * temporal_k: steps fused per launch (1 = plain kernel, 2..4 = temporally
- * blocked; 5..8 reserved, ENOTSUP), 0 = library default (2). tile_x: 0 or 64 = TMA-staged 64x16 tiles
+ * blocked; 5..8 reserved, ENOTSUP), 0 = autotuned (the default: the first
+ * sophie_step measures the candidates, see sophie_autotune). tile_x: 0 or 64 = TMA-staged 64x16 tiles
  * (default), 32 = 32x8 tiles with direct loads (a slower reference kernel;
  * identical results); tile_y: reserved, 0.
  * precision: SOPHIE_FP32, SOPHIE_FP16 or SOPHIE_BF16 storage of the fields
@@ -224,6 +227,19 @@ int sophie_configure(sophie_grid *g, int temporal_k, int tile_x, int tile_y, int
  * No effect on float storage. Errors: EINVAL.
  */
 int sophie_set_storage_scale(sophie_grid *g, const float *scale);
+
+/*
+ * Autotuner: times the step kernel candidates on this grid (plain kernel with
+ * z chunks of 4..64 planes per work unit; temporally blocked kernel with
+ * k = 2, 3, 4 and both work splits), each launch reading the current fields
+ * and writing the spare buffer so the state does not advance, and keeps the
+ * fastest per time step. The grid switches to temporal_k = 0 (autotuned) with
+ * that choice. *temporal_k gets the chosen k, *ms_per_step the measured device
+ * milliseconds per time step. All float-storage candidates give bitwise
+ * identical fields; with 2-byte storage (results depend on k) k stays 2 and
+ * only the tilings are tuned. Synchronises. Errors: EINVAL, ECUDA, ETIMEOUT.
+ */
+int sophie_autotune(sophie_grid *g, int *temporal_k, double *ms_per_step);
 
 /* Number of kernels this grid has launched since creation. */
 int sophie_launch_count(sophie_grid *g, long long *launches);
@@ -275,6 +291,62 @@ int sophie_objective_forward(sophie_grid *g, int nsteps, int comp, int i, int j,
                              double *J);
 int sophie_objective_grad_eps(sophie_grid *g, int i0, int j0, int k0, int ni, int nj, int nk, double *grad);
 int sophie_objective_release(sophie_grid *g);
+
+/*
+ * Batched cavities (the batching form): many independent PEC cavities of
+ * uneven sizes sharing dx and dt, advanced together. Each cavity has its own
+ * fields, materials (per-cell eps_r / sigma as for sophie_set_materials, its
+ * own class and explicit tables) and up to 4 soft sources; its fields are
+ * bitwise those of a single grid of the same size run alone. One time step of
+ * the whole batch is one persistent launch over a work list of
+ * (cavity, 32 x tile_y tile, z chunk) items taken from a global counter, and
+ * a run of n steps is recorded into a CUDA graph once and replayed while the
+ * same (start step, n, buffer parity) recurs (e.g. reset + n steps). Field
+ * storage is float. Indexing within a cavity is that of a single grid.
+ *
+ * sophie_batch_create: ncav cavities, dims = ncav x {nx, ny, nz} (each in
+ *   [1, 4096]); fields zero, vacuum, step 0. Errors: EINVAL, EUNSTABLE,
+ *   ENOMEM, ECUDA.
+ * sophie_batch_set_materials: eps and sigma hold every cavity's nx*ny*nz
+ *   cells (x fastest), cavities one after the other in index order; sigma
+ *   NULL = lossless, both NULL = vacuum everywhere. Words and tables are built
+ *   on host threads, one cavity per task. Errors: EINVAL, ENOMEM, ECUDA,
+ *   ETOOMANYMAT.
+ * sophie_batch_add_source: as sophie_add_source, for cavity cav (at most 4
+ *   per cavity).
+ * sophie_batch_step: advance all cavities by n steps (asynchronous).
+ * sophie_batch_energy: W[c] = the energy of cavity c (as sophie_energy), host
+ *   array of ncav doubles. Synchronises. Errors: EINVAL, ECUDA, ENONFINITE.
+ * sophie_batch_set_fields / get_fields: one component of one cavity, host
+ *   array laid out as for sophie_set_fields. Synchronise.
+ * sophie_batch_reset: zero all fields, step 0.
+ * sophie_batch_configure: tile_y in {0 = keep, 4, 8, 16}, zchunk = z planes
+ *   per work item (0 = keep), use_graph != 0 records runs into CUDA graphs.
+ * sophie_batch_autotune: times the step with tile_y in {4, 8, 16} and z chunks
+ *   in {4, 8, 16, 32, 96} (trial launches read the current fields and write
+ *   the spare buffer, so the state does not advance) and keeps the fastest.
+ *   Results do not depend on the choice. Synchronises.
+ * sophie_batch_info: total cells, current work items, tile_y and z chunk.
+ * sophie_batch_set_stream: a created (non-legacy) stream for later work.
+ */
+typedef struct sophie_batch sophie_batch;
+int sophie_batch_create(int ncav, const int *dims, double dx, double dt, sophie_batch **out);
+int sophie_batch_destroy(sophie_batch *b);
+int sophie_batch_set_materials(sophie_batch *b, const float *eps_r, const float *sigma);
+int sophie_batch_add_source(sophie_batch *b, int cav, int comp, int i, int j, int k, double amp, double f0,
+                            double bw, double t0, int kind);
+int sophie_batch_step(sophie_batch *b, int n);
+int sophie_batch_get_step(sophie_batch *b, long long *n);
+int sophie_batch_energy(sophie_batch *b, double *W);
+int sophie_batch_set_fields(sophie_batch *b, int cav, int comp, const float *host);
+int sophie_batch_get_fields(sophie_batch *b, int cav, int comp, float *host);
+int sophie_batch_reset(sophie_batch *b);
+int sophie_batch_set_stream(sophie_batch *b, void *cuda_stream);
+int sophie_batch_configure(sophie_batch *b, int tile_y, int zchunk, int use_graph);
+int sophie_batch_autotune(sophie_batch *b, int *tile_y, int *zchunk, double *ms_per_step);
+int sophie_batch_info(sophie_batch *b, long long *cells, long long *work_items, int *tile_y, int *zchunk);
+int sophie_batch_launch_count(sophie_batch *b, long long *launches);
+int sophie_batch_sync(sophie_batch *b);
 
 /* Message of the last error on this thread ("" if none). */
 const char *sophie_last_error(void);

@@ -42,6 +42,17 @@ int fail(int code, const char* fmt, ...) {
   return code;
 }
 
+}  // namespace
+
+namespace sophie {
+int report_error(int code, const char* msg) {
+  g_err = msg;
+  return code;
+}
+}  // namespace sophie
+
+namespace {
+
 #define CUDA_TRY(call)                                                              \
   do {                                                                              \
     cudaError_t e_ = (call);                                                        \
@@ -138,7 +149,9 @@ struct sophie_grid {
   long long n = 0;
   cudaStream_t stream = nullptr;
   bool own_stream = false;
-  int temporal_k = 2;  // default: two steps per launch (fastest at 256^3 on GB300)
+  int temporal_k = 0;  // 0: chosen by the autotuner at the first step
+  bool tuned = false;  // autotuner result valid for the current format
+  int tuned_k = 2;
   int precision = SOPHIE_FP32;
   double* e_partials = nullptr;
   double* e_out = nullptr;
@@ -181,155 +194,22 @@ bool comp_valid(const Dims& d, int c, int i, int j, int k) {
   }
 }
 
-// Coefficients of one edge from the four (eps_r, sigma) cell values, in the
-// fixed order (-,-), (+,-), (-,+), (+,+) of the two transverse offsets:
-// mean in double, beta = sigma dt/(2 eps0 eps_r), Ca = (1-beta)/(1+beta),
-// Cb = (S/eps_r)/(1+beta), both rounded once to float.
-struct EdgeKey {
-  uint64_t e, s;
-  bool operator==(const EdgeKey& o) const { return e == o.e && s == o.s; }
-};
-struct EdgeKeyHash {
-  size_t operator()(const EdgeKey& k) const {
-    return (size_t)(k.e * 0x9E3779B97F4A7C15ull ^ (k.s + 0x632BE59BD9B4E019ull + (k.e << 6)));
-  }
-};
-
-uint64_t dbits(double v) {
-  uint64_t u;
-  memcpy(&u, &v, 8);
-  return u;
-}
-
-// Coefficients (Ca, Cb) of an edge whose mean material is (e, s).
-float2 edge_coef(const sophie_grid* g, double e, double s) {
-  const double beta = (s * g->dt) / (2.0 * kEps0 * e);
-  const double ca = (1.0 - beta) / (1.0 + beta);
-  const double cb = (g->S64 / e) / (1.0 + beta);
-  return make_float2((float)ca, (float)cb);
-}
-
-// Fill g->mat_host with material words for per-cell eps/sigma (nullptr =
-// vacuum). Edge materials are means of four cells in double (summed in the
-// fixed order (-,-), (+,-), (-,+), (+,+)). The up to 511 most frequent edge
-// materials become classes; an index point with an edge outside them gets an
-// explicit entry (its three edges' (Ca, Cb) and eps_r).
+// Fill g->mat_host and the host tables for per-cell eps/sigma (nullptr =
+// vacuum); sources and probes flag their points.
 int build_material_words(sophie_grid* g, const float* eps, const float* sig) {
-  const Dims& d = g->d;
-  const int nx = d.nx, ny = d.ny, nz = d.nz;
-  auto E = [&](int i, int j, int k) -> double {
-    return eps ? (double)eps[((long long)k * ny + j) * nx + i] : 1.0;
-  };
-  auto Sg = [&](int i, int j, int k) -> double {
-    return sig ? (double)sig[((long long)k * ny + j) * nx + i] : 0.0;
-  };
-  // Mean (eps, sigma) of edge component c at index (i, j, k) (interior only).
-  auto edge_mat = [&](int c, int i, int j, int k, double& e, double& s) {
-    double e4, s4;
-    if (c == 0) {
-      e4 = ((E(i, j - 1, k - 1) + E(i, j, k - 1)) + E(i, j - 1, k)) + E(i, j, k);
-      s4 = ((Sg(i, j - 1, k - 1) + Sg(i, j, k - 1)) + Sg(i, j - 1, k)) + Sg(i, j, k);
-    } else if (c == 1) {
-      e4 = ((E(i - 1, j, k - 1) + E(i, j, k - 1)) + E(i - 1, j, k)) + E(i, j, k);
-      s4 = ((Sg(i - 1, j, k - 1) + Sg(i, j, k - 1)) + Sg(i - 1, j, k)) + Sg(i, j, k);
-    } else {
-      e4 = ((E(i - 1, j - 1, k) + E(i, j - 1, k)) + E(i - 1, j, k)) + E(i, j, k);
-      s4 = ((Sg(i - 1, j - 1, k) + Sg(i, j - 1, k)) + Sg(i - 1, j, k)) + Sg(i, j, k);
-    }
-    e = e4 * 0.25;
-    s = s4 * 0.25;
-  };
-  // Pass 1: frequency of every edge material (runs along x are counted once).
-  std::unordered_map<EdgeKey, long long, EdgeKeyHash> freq;
-  for (int c = 0; c < 3; ++c) {
-    EdgeKey last{~0ull, ~0ull};
-    long long run = 0;
-    for (int k = 0; k <= nz; ++k)
-      for (int j = 0; j <= ny; ++j)
-        for (int i = 0; i <= nx; ++i) {
-          if (!e_edge_interior(d, c, i, j, k)) continue;
-          double e, s;
-          edge_mat(c, i, j, k, e, s);
-          const EdgeKey key{dbits(e), dbits(s)};
-          if (key == last) {
-            ++run;
-            continue;
-          }
-          if (run) freq[last] += run;
-          last = key;
-          run = 1;
-        }
-    if (run) freq[last] += run;
-  }
-  // Classes: the most frequent materials (class 0 is PEC / absent).
-  std::vector<std::pair<long long, EdgeKey>> order;
-  order.reserve(freq.size());
-  for (const auto& kv : freq) order.push_back({kv.second, kv.first});
-  std::sort(order.begin(), order.end(), [](const std::pair<long long, EdgeKey>& a, const std::pair<long long, EdgeKey>& b) {
-    if (a.first != b.first) return a.first > b.first;
-    return a.second.e != b.second.e ? a.second.e < b.second.e : a.second.s < b.second.s;
-  });
-  std::unordered_map<EdgeKey, int, EdgeKeyHash> cls;
-  std::vector<float2> coef(1, make_float2(0.f, 0.f));
-  std::vector<double> epsv(1, 0.0), sigv(1, 0.0);
-  for (size_t q = 0; q < order.size() && (int)coef.size() < kMaxClasses; ++q) {
-    double e, s;
-    memcpy(&e, &order[q].second.e, 8);
-    memcpy(&s, &order[q].second.s, 8);
-    cls.emplace(order[q].second, (int)coef.size());
-    coef.push_back(edge_coef(g, e, s));
-    epsv.push_back(e);
-    sigv.push_back(s);
-  }
-  // Pass 2: words.
-  std::vector<float2> ecoef;
-  std::vector<double> eeps, esig;
+  MaterialTables t;
+  if (build_material_tables(g->d, g->dt, g->S64, eps, sig, g->mat_host, &t) != 0)
+    return fail(SOPHIE_ETOOMANYMAT, "more than 2^29 explicit material points");
   uint32_t* w = g->mat_host;
-  EdgeKey lk[3] = {{~0ull, ~0ull}, {~0ull, ~0ull}, {~0ull, ~0ull}};
-  int lc[3] = {-1, -1, -1};
-  for (int k = 0; k <= nz; ++k)
-    for (int j = 0; j <= ny; ++j) {
-      uint32_t* row = w + ((long long)k * d.ny1 + j) * d.nxp;
-      for (int i = 0; i < d.nxp; ++i) {
-        int ci[3] = {0, 0, 0};
-        double ce[3] = {0, 0, 0}, cs[3] = {0, 0, 0};
-        bool expl = false;
-        for (int c = 0; c < 3; ++c) {
-          if (!e_edge_interior(d, c, i, j, k)) continue;
-          edge_mat(c, i, j, k, ce[c], cs[c]);
-          const EdgeKey key{dbits(ce[c]), dbits(cs[c])};
-          if (!(key == lk[c])) {
-            auto it = cls.find(key);
-            lk[c] = key;
-            lc[c] = it == cls.end() ? -1 : it->second;
-          }
-          ci[c] = lc[c];
-          if (ci[c] < 0) expl = true;
-        }
-        if (!expl) {
-          row[i] = cls_word((uint32_t)ci[0], (uint32_t)ci[1], (uint32_t)ci[2]);
-        } else {
-          const size_t q = eeps.size() / 3;
-          if (q >= (1u << 29)) return fail(SOPHIE_ETOOMANYMAT, "more than 2^29 explicit material points");
-          for (int c = 0; c < 3; ++c) {
-            const bool in = e_edge_interior(d, c, i, j, k);
-            ecoef.push_back(in ? edge_coef(g, ce[c], cs[c]) : make_float2(0.f, 0.f));
-            eeps.push_back(in ? ce[c] : 0.0);
-            esig.push_back(in ? cs[c] : 0.0);
-          }
-          row[i] = kExpFlag | ((uint32_t)q << 3);
-        }
-      }
-    }
   for (const Source& s : g->src) w[s.pos] |= kSrcFlag;
   for (const Probe& p : g->prb)
     if (!p.fixed) w[p.pos] |= kPrbFlag;
-  g->coef_h = std::move(coef);
-  g->eps_h = std::move(epsv);
-  g->ecoef_h = std::move(ecoef);
-  g->eeps_h = std::move(eeps);
-  g->sig_h = std::move(sigv);
-  g->esig_h = std::move(esig);
+  g->coef_h = std::move(t.coef);
+  g->eps_h = std::move(t.eps);
+  g->sig_h = std::move(t.sig);
+  g->ecoef_h = std::move(t.ecoef);
+  g->eeps_h = std::move(t.eeps);
+  g->esig_h = std::move(t.esig);
   return SOPHIE_OK;
 }
 
@@ -368,13 +248,7 @@ int upload_materials(sophie_grid* g) {
 }
 
 double waveform(const Source& s, long long n, double dt) {
-  const double pi = 3.14159265358979323846;
-  const double sf = s.bw / (2.0 * std::sqrt(2.0 * std::log(2.0)));
-  const double st = 1.0 / (2.0 * pi * sf);
-  const double t = ((double)n + 0.5) * dt;
-  const double u = t - s.t0;
-  const double env = std::exp(-(u * u) / (2.0 * st * st));
-  return s.amp * (s.kind == 0 ? std::sin(2.0 * pi * s.f0 * u) * env : env);
+  return source_waveform(s.kind, s.amp, s.f0, s.bw, s.t0, dt, n);
 }
 
 // Make the source table cover steps [0, need) and the probe buffer [0, need).
@@ -672,6 +546,104 @@ int restore_fields(sophie_grid* g, int fmt, const float* sc) {
   return SOPHIE_OK;
 }
 
+// Time one candidate launch configuration: `launch` is enqueued `reps` times
+// reading the current buffer and writing the other one (the state does not
+// advance). Returns the mean milliseconds per launch, or < 0 on a launch error.
+template <class Fn>
+double time_candidate(sophie_grid* g, Fn&& launch, cudaEvent_t e0, cudaEvent_t e1) {
+  if (launch() != cudaSuccess) return -1.0;  // warm-up
+  cudaEventRecord(e0, g->stream);
+  if (launch() != cudaSuccess) return -1.0;
+  cudaEventRecord(e1, g->stream);
+  if (cudaEventSynchronize(e1) != cudaSuccess) return -1.0;
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  const int reps = std::max(2, std::min(40, (int)(2.0 / std::max(ms, 1e-3f))));
+  cudaEventRecord(e0, g->stream);
+  for (int r = 0; r < reps; ++r)
+    if (launch() != cudaSuccess) return -1.0;
+  cudaEventRecord(e1, g->stream);
+  if (cudaEventSynchronize(e1) != cudaSuccess) return -1.0;
+  cudaEventElapsedTime(&ms, e0, e1);
+  g->launches += reps + 2;
+  return (double)ms / reps;
+}
+
+// Autotuner: measure the plain kernel's z-chunk choices and the temporally
+// blocked kernel at k = 2..4 with both work splits on this grid, keep the
+// fastest per step. All candidates give bitwise identical float results, so
+// the choice changes only speed. With 2-byte storage, where results depend
+// on k, only the tilings are tuned and k stays 2.
+int run_autotune(sophie_grid* g, double* best_ms_per_step) {
+  if (g->use_simple) {
+    g->tuned = true;
+    g->tuned_k = 1;
+    if (best_ms_per_step) *best_ms_per_step = -1.0;
+    return SOPHIE_OK;
+  }
+  int rc = ensure_capacity(g, g->n + 1);
+  if (rc) return rc;
+  StepArgs a = make_step_args(g);
+  a.prb.n = 0;  // no probe samples from the trial launches
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  CUDA_TRY(cudaEventCreate(&e0));
+  CUDA_TRY(cudaEventCreate(&e1));
+  const Dims& d = g->d;
+  double best = 1e300;
+  PlainTiling best_p = g->ptile;
+  double best_plain = 1e300;
+  BlockedTiling best_b{};
+  int best_k = 1;
+  const int zcs[] = {4, 8, 16, 32, 64};
+  for (int zc : zcs) {
+    if (zc > 2 * d.nz && zc != zcs[0]) break;
+    const PlainTiling pt = plain_tiling(d, g->num_sms, zc);
+    const double ms = time_candidate(g, [&] { return launch_step_plain(a, g->tmF[g->cur], g->tmM, pt, g->stream); },
+                                     e0, e1);
+    if (ms < 0) {
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      return fail(SOPHIE_ECUDA, "autotune launch failed: %s", cudaGetErrorString(cudaGetLastError()));
+    }
+    if (ms < best_plain) {
+      best_plain = ms;
+      best_p = pt;
+    }
+  }
+  if (g->fmt == kF32) {
+    best = best_plain;
+    best_k = 1;
+  }
+  for (int K = 2; K <= 4; ++K) {
+    if (g->fmt != kF32 && K != 2) continue;
+    for (int aligned = 1; aligned >= 0; --aligned) {
+      const BlockedTiling bt = blocked_tiling(d, K, g->num_sms, aligned);
+      const double ms = time_candidate(
+          g, [&] { return launch_step_blocked(a, g->tmFB[g->cur], g->tmMB, bt, g->stream); }, e0, e1);
+      if (ms < 0) {
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        return fail(SOPHIE_ECUDA, "autotune launch failed: %s", cudaGetErrorString(cudaGetLastError()));
+      }
+      if (ms / K < best) {
+        best = ms / K;
+        best_k = K;
+        best_b = bt;
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  rc = check_err_word(g);
+  if (rc) return rc;
+  g->ptile = best_p;
+  if (best_k >= 2) g->btile = best_b;
+  g->tuned_k = best_k;
+  g->tuned = true;
+  if (best_ms_per_step) *best_ms_per_step = best;
+  return SOPHIE_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -797,8 +769,8 @@ int sophie_set_materials(sophie_grid* g, const float* eps, const float* sig) {
   if (!g || !eps || !sig) return fail(SOPHIE_EINVAL, "NULL argument");
   const long long ncell = (long long)g->d.nx * g->d.ny * g->d.nz;
   for (long long c = 0; c < ncell; ++c) {
-    if (!(eps[c] >= 1.0f) || !std::isfinite(eps[c]))
-      return fail(SOPHIE_EINVAL, "eps_r[%lld] = %g must be finite and >= 1", c, (double)eps[c]);
+    if (!(eps[c] >= 1.0f))
+      return fail(SOPHIE_EINVAL, "eps_r[%lld] = %g must be >= 1 (+inf: conductor)", c, (double)eps[c]);
     if (!(sig[c] >= 0.0f) || !std::isfinite(sig[c]))
       return fail(SOPHIE_EINVAL, "sigma[%lld] = %g must be finite and >= 0", c, (double)sig[c]);
   }
@@ -870,8 +842,12 @@ int sophie_step(sophie_grid* g, int n) {
   int rc = ensure_capacity(g, g->n + n);
   if (rc) return rc;
   g->gen++;
+  if (g->temporal_k == 0 && !g->tuned) {
+    rc = run_autotune(g, nullptr);
+    if (rc) return rc;
+  }
   for (int m = 0; m < n;) {
-    const int K = g->temporal_k;
+    const int K = g->temporal_k == 0 ? g->tuned_k : g->temporal_k;
     const bool blocked = !g->use_simple && K >= 2 && n - m >= K && blocked_supported(K);
     StepArgs a = make_step_args(g);
     cudaEvent_t ea = nullptr, eb = nullptr;
@@ -1054,9 +1030,25 @@ int sophie_configure(sophie_grid* g, int temporal_k, int tile_x, int tile_y, int
     int rc = restore_fields(g, precision, g->sc);
     if (rc) return rc;
   }
-  g->temporal_k = temporal_k == 0 ? 2 : temporal_k;
+  if (temporal_k != g->temporal_k || precision != g->precision || (tile_x == 32) != g->use_simple) {
+    g->tuned = false;
+    // a fixed k keeps the default tilings
+    const char* zc = getenv("SOPHIE_ZCHUNK");
+    g->ptile = plain_tiling(g->d, g->num_sms, zc ? atoi(zc) : 0);
+    g->btile = BlockedTiling{};
+  }
+  g->temporal_k = temporal_k;
   g->precision = precision;
   g->use_simple = tile_x == 32;
+  return SOPHIE_OK;
+}
+
+int sophie_autotune(sophie_grid* g, int* temporal_k, double* ms_per_step) {
+  if (!g || !temporal_k || !ms_per_step) return fail(SOPHIE_EINVAL, "NULL argument");
+  g->temporal_k = 0;
+  int rc = run_autotune(g, ms_per_step);
+  if (rc) return rc;
+  *temporal_k = g->tuned_k;
   return SOPHIE_OK;
 }
 
@@ -1199,6 +1191,8 @@ int sophie_objective_grad_eps(sophie_grid* g, int i0, int j0, int k0, int ni, in
           if (!e_edge_interior(d, c, i, j, k)) continue;
           const long long pt = point_index(d, i, j, k);
           const uint32_t w = g->mat_host[pt];
+          const float cb_edge = (w & kExpFlag) ? g->ecoef_h[3 * (size_t)(w >> 3) + c].y : g->coef_h[cls_of(w, c)].y;
+          if (cb_edge == 0.f) continue;  // edge of a conducting cell: no eps dependence
           double e, sg;
           if (w & kExpFlag) {
             const size_t q = w >> 3;
@@ -1212,7 +1206,7 @@ int sophie_objective_grad_eps(sophie_grid* g, int i0, int j0, int k0, int ni, in
           const double beta = (sg * g->dt) / (2.0 * kEps0 * e);
           const double cb = (g->S64 / e) / (1.0 + beta);
           map[c][((size_t)kk * ext[c][1] + jj) * ext[c][0] + ii] = (int)hpt.size();
-          cbf.push_back((w & kExpFlag) ? g->ecoef_h[3 * (size_t)(w >> 3) + c].y : g->coef_h[cls_of(w, c)].y);
+          cbf.push_back(cb_edge);
           hcomp.push_back(c);
           hpt.push_back(pt);
           dcb.push_back(-cb / (e * (1.0 + beta)));
@@ -1236,6 +1230,10 @@ int sophie_objective_grad_eps(sophie_grid* g, int i0, int j0, int k0, int ni, in
     for (int b = 0; b < 2; ++b)
       if (!grow(&t.R[b], fbytes) || !grow(&t.L[b], fbytes))
         return fail(SOPHIE_ENOMEM, "adjoint workspace allocation failed");
+    // Wall and padding entries are never written by the step kernels: they
+    // must start (and stay) zero in both recompute buffers.
+    CUDA_TRY(cudaMemsetAsync(t.R[0], 0, fbytes, g->stream));
+    CUDA_TRY(cudaMemsetAsync(t.R[1], 0, fbytes, g->stream));
     for (int b = 0; b < 2; ++b)
       if (!encode_maps(d, kF32, t.R[b], g->mat, plain_box_x(kF32), plain_box_y(), &t.tmR[b], &t.tmRM) ||
           !encode_maps(d, kF32, t.L[b], nullptr, plain_box_x(kF32), plain_box_y(), &t.tmL[b], nullptr))

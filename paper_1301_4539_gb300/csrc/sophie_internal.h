@@ -6,6 +6,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 namespace sophie {
 
 // Device field layout of one buffer: for z in [0,nz], comp f in [0,6),
@@ -103,6 +105,31 @@ struct BlockedTiling {
   int zsplit;  // > 0: CTA b works on tile b / zsplit, z range b % zsplit of zsplit
 };
 
+// Coefficient tables behind the material words (host copies). Class c:
+// coef[c] = (Ca, Cb), eps[c], sig[c] = the edge's mean material; class 0 is
+// PEC / absent. Explicit entry q: three consecutive (Ca, Cb) / eps / sigma
+// for the ex, ey, ez edges of the points that carry it.
+struct MaterialTables {
+  std::vector<float2> coef;
+  std::vector<double> eps, sig;
+  std::vector<float2> ecoef;
+  std::vector<double> eeps, esig;
+};
+
+// (Ca, Cb) of an edge with mean material (e, s): beta = s dt / (2 eps0 e),
+// Ca = (1-beta)/(1+beta), Cb = (S/e)/(1+beta), computed in double and
+// rounded once to float (materials.cu).
+float2 edge_coefficients(double dt, double S64, double e, double s);
+// Words (row pitch d.nxp, (nz+1)(ny+1) rows) and tables for per-cell eps_r and
+// sigma (x fastest; nullptr = vacuum; eps_r = +inf marks a perfectly
+// conducting cell, whose edges are PEC). Edge material = mean of its four
+// cells; the 511 most frequent edge materials become classes, points with an
+// edge outside them share explicit entries by their three edge materials.
+// No source or probe flags are set. Returns 0, or -1 if more than 2^29
+// explicit entries would be needed.
+int build_material_tables(const Dims& d, double dt, double S64, const float* eps, const float* sig, uint32_t* words,
+                          MaterialTables* out);
+
 // Launchers (return cudaError_t of the launch).
 cudaError_t launch_step_simple(const StepArgs& a, cudaStream_t s);
 bool encode_maps(const Dims& d, int fmt, void* fields, uint32_t* mat, int box_x, int box_y, CUtensorMap* tmF,
@@ -129,6 +156,47 @@ int energy_noalloc(const StepArgs& a, const double* eps_tab, double scale, doubl
                    const char** why);
 cudaError_t launch_mask_component(void* f, int esz, const Dims& d, int comp, cudaStream_t s);
 cudaError_t launch_or_flag(uint32_t* mat, long long pos, uint32_t bit, cudaStream_t s);
+
+// Batched cavities (yee_batch.cu, sophie_batch.cu). One descriptor per
+// cavity in device memory; float field storage.
+constexpr int kBatchMaxSrc = 4;
+struct CavityDesc {
+  Dims d;
+  void* F[2];              // the cavity's two field buffers (ping-pong)
+  const uint32_t* mat;     // material words (layout of a single grid)
+  const float2* coef;      // class table (kMaxClasses entries)
+  const double* eps_tab;   // class eps_r(edge) (energy)
+  const float2* ecoef;     // explicit entries
+  const double* eeps;
+  int nsrc;
+  int src_comp[kBatchMaxSrc];
+  long long src_pos[kBatchMaxSrc];
+  const float* src_val;    // [nsrc][src_cap] waveform values by absolute step
+  int src_cap;
+};
+// A step work item: x tile [x0, x0+32), y tile [y0, y0+TY), planes [z0, z1).
+struct BatchItem {
+  int cav, x0, y0, z0, z1;
+};
+// An energy work item: index points [p0, p1) of one cavity.
+struct EnergyItem {
+  int cav;
+  long long p0, p1;
+};
+bool batch_tile_supported(int ty);
+int batch_blocks_per_sm(int ty);
+// Memsets the work counter, then one persistent launch of `grid` CTAs.
+cudaError_t launch_batch_step(const CavityDesc* descs, const BatchItem* items, int nitems, int* counter, int cur,
+                              float S, long long nstep, int ty, int grid, cudaStream_t s);
+// out[c] = scale * energy sum of cavity c; first[c]..first[c+1] are its items.
+cudaError_t launch_batch_energy(const CavityDesc* descs, const EnergyItem* items, int nitems, const int* first,
+                                int ncav, int cur, float S, double* partials, double scale, double* out,
+                                cudaStream_t s);
+// Set the thread's last-error message (sophie_last_error) and return code.
+int report_error(int code, const char* msg);
+// amp * w((n + 1/2) dt) of a soft source (kind 0: Gaussian-modulated sine,
+// kind 1: Gaussian pulse; bw = FWHM of the envelope's amplitude spectrum).
+double source_waveform(int kind, double amp, double f0, double bw, double t0, double dt, long long n);
 
 // Reverse-mode sweep (yee_adjoint.cu). Adjoint fields use the float field
 // layout; a.fin holds the adjoint of the state after a step, a.fout receives

@@ -47,12 +47,30 @@ SIGNATURES = {
     "sophie_sync": (_I, [_P]),
     "sophie_configure": (_I, [_P, _I, _I, _I, _I]),
     "sophie_set_storage_scale": (_I, [_P, _P]),
+    "sophie_autotune": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(_D)]),
     "sophie_launch_count": (_I, [_P, ctypes.POINTER(_LL)]),
     "sophie_profile": (_I, [_P, _I]),
     "sophie_profile_read": (_I, [_P, _I, ctypes.POINTER(_LL), ctypes.POINTER(_D)]),
     "sophie_objective_forward": (_I, [_P, _I, _I, _I, _I, _I, _I, ctypes.POINTER(_D)]),
     "sophie_objective_grad_eps": (_I, [_P, _I, _I, _I, _I, _I, _I, _P]),
     "sophie_objective_release": (_I, [_P]),
+    "sophie_batch_create": (_I, [_I, _P, _D, _D, ctypes.POINTER(_P)]),
+    "sophie_batch_destroy": (_I, [_P]),
+    "sophie_batch_set_materials": (_I, [_P, _P, _P]),
+    "sophie_batch_add_source": (_I, [_P, _I, _I, _I, _I, _I, _D, _D, _D, _D, _I]),
+    "sophie_batch_step": (_I, [_P, _I]),
+    "sophie_batch_get_step": (_I, [_P, ctypes.POINTER(_LL)]),
+    "sophie_batch_energy": (_I, [_P, _P]),
+    "sophie_batch_set_fields": (_I, [_P, _I, _I, _P]),
+    "sophie_batch_get_fields": (_I, [_P, _I, _I, _P]),
+    "sophie_batch_reset": (_I, [_P]),
+    "sophie_batch_set_stream": (_I, [_P, _P]),
+    "sophie_batch_configure": (_I, [_P, _I, _I, _I]),
+    "sophie_batch_autotune": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_D)]),
+    "sophie_batch_info": (_I, [_P, ctypes.POINTER(_LL), ctypes.POINTER(_LL), ctypes.POINTER(_I),
+                               ctypes.POINTER(_I)]),
+    "sophie_batch_launch_count": (_I, [_P, ctypes.POINTER(_LL)]),
+    "sophie_batch_sync": (_I, [_P]),
     "sophie_last_error": (ctypes.c_char_p, []),
 }
 
@@ -187,6 +205,14 @@ def sophie_set_storage_scale(g: int, scale) -> None:
     _chk(load().sophie_set_storage_scale(g, sc.ctypes.data))
 
 
+def sophie_autotune(g: int):
+    """(chosen temporal_k, device ms per time step)."""
+    k = _I()
+    ms = _D()
+    _chk(load().sophie_autotune(g, ctypes.byref(k), ctypes.byref(ms)))
+    return k.value, ms.value
+
+
 def sophie_launch_count(g: int) -> int:
     n = _LL()
     _chk(load().sophie_launch_count(g, ctypes.byref(n)))
@@ -294,6 +320,9 @@ class Grid:
     def set_storage_scale(self, scale):
         sophie_set_storage_scale(self.h, scale)
 
+    def autotune(self):
+        return sophie_autotune(self.h)
+
     def launch_count(self):
         return sophie_launch_count(self.h)
 
@@ -311,3 +340,158 @@ class Grid:
 
     def objective_release(self):
         sophie_objective_release(self.h)
+
+
+# ---- batched cavities -------------------------------------------------------
+def sophie_batch_create(dims, dx: float, dt: float) -> int:
+    d = np.ascontiguousarray(dims, dtype=np.int32).reshape(-1, 3)
+    h = _P()
+    _chk(load().sophie_batch_create(len(d), d.ctypes.data, dx, dt, ctypes.byref(h)))
+    return h.value
+
+
+def sophie_batch_destroy(b: int) -> None:
+    _chk(load().sophie_batch_destroy(b))
+
+
+def sophie_batch_set_materials(b: int, eps_r, sigma=None) -> None:
+    e = None if eps_r is None else _f32(eps_r)
+    s = None if sigma is None else _f32(sigma)
+    _chk(load().sophie_batch_set_materials(b, None if e is None else e.ctypes.data,
+                                           None if s is None else s.ctypes.data))
+
+
+def sophie_batch_add_source(b: int, cav: int, comp: int, i: int, j: int, k: int, amp: float, f0: float,
+                            bw: float, t0: float, kind: int) -> None:
+    _chk(load().sophie_batch_add_source(b, cav, comp, i, j, k, amp, f0, bw, t0, kind))
+
+
+def sophie_batch_step(b: int, n: int) -> None:
+    _chk(load().sophie_batch_step(b, n))
+
+
+def sophie_batch_get_step(b: int) -> int:
+    n = _LL()
+    _chk(load().sophie_batch_get_step(b, ctypes.byref(n)))
+    return n.value
+
+
+def sophie_batch_energy(b: int, ncav: int) -> np.ndarray:
+    out = np.zeros(ncav, np.float64)
+    _chk(load().sophie_batch_energy(b, out.ctypes.data))
+    return out
+
+
+def sophie_batch_set_fields(b: int, cav: int, comp: int, host: np.ndarray) -> None:
+    a = _f32(host)
+    _chk(load().sophie_batch_set_fields(b, cav, comp, a.ctypes.data))
+
+
+def sophie_batch_get_fields(b: int, cav: int, comp: int, shape) -> np.ndarray:
+    out = np.empty(shape, np.float32)
+    _chk(load().sophie_batch_get_fields(b, cav, comp, out.ctypes.data))
+    return out
+
+
+def sophie_batch_reset(b: int) -> None:
+    _chk(load().sophie_batch_reset(b))
+
+
+def sophie_batch_set_stream(b: int, cuda_stream: int) -> None:
+    _chk(load().sophie_batch_set_stream(b, cuda_stream))
+
+
+def sophie_batch_configure(b: int, tile_y: int = 0, zchunk: int = 0, use_graph: bool = True) -> None:
+    _chk(load().sophie_batch_configure(b, tile_y, zchunk, 1 if use_graph else 0))
+
+
+def sophie_batch_autotune(b: int):
+    """(tile_y, zchunk, device ms per time step) of the fastest work split."""
+    ty, zc, ms = _I(), _I(), _D()
+    _chk(load().sophie_batch_autotune(b, ctypes.byref(ty), ctypes.byref(zc), ctypes.byref(ms)))
+    return ty.value, zc.value, ms.value
+
+
+def sophie_batch_info(b: int):
+    cells, items, ty, zc = _LL(), _LL(), _I(), _I()
+    _chk(load().sophie_batch_info(b, ctypes.byref(cells), ctypes.byref(items), ctypes.byref(ty), ctypes.byref(zc)))
+    return {"cells": cells.value, "work_items": items.value, "tile_y": ty.value, "zchunk": zc.value}
+
+
+def sophie_batch_launch_count(b: int) -> int:
+    n = _LL()
+    _chk(load().sophie_batch_launch_count(b, ctypes.byref(n)))
+    return n.value
+
+
+def sophie_batch_sync(b: int) -> None:
+    _chk(load().sophie_batch_sync(b))
+
+
+class Batch:
+    """Owning handle of a batch of cavities (marshalling only)."""
+
+    def __init__(self, dims, dx: float, dt: float):
+        self.dims = [tuple(int(v) for v in d) for d in dims]
+        self.h = sophie_batch_create(self.dims, dx, dt)
+
+    def close(self):
+        if self.h:
+            sophie_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def shape(self, cav):
+        nx, ny, nz = self.dims[cav]
+        return (nz + 1, ny + 1, nx + 1)
+
+    def set_materials(self, eps=None, sigma=None):
+        sophie_batch_set_materials(self.h, eps, sigma)
+
+    def add_source(self, cav, comp, i, j, k, amp, f0, bw, t0, kind):
+        sophie_batch_add_source(self.h, cav, comp, i, j, k, amp, f0, bw, t0, kind)
+
+    def step(self, n):
+        sophie_batch_step(self.h, n)
+
+    @property
+    def n(self):
+        return sophie_batch_get_step(self.h)
+
+    def energy(self):
+        return sophie_batch_energy(self.h, len(self.dims))
+
+    def set_field(self, cav, comp, arr):
+        sophie_batch_set_fields(self.h, cav, comp, arr)
+
+    def get_field(self, cav, comp):
+        return sophie_batch_get_fields(self.h, cav, comp, self.shape(cav))
+
+    def fields(self, cav):
+        return [self.get_field(cav, c) for c in range(6)]
+
+    def reset(self):
+        sophie_batch_reset(self.h)
+
+    def set_stream(self, s):
+        sophie_batch_set_stream(self.h, s)
+
+    def configure(self, tile_y=0, zchunk=0, use_graph=True):
+        sophie_batch_configure(self.h, tile_y, zchunk, use_graph)
+
+    def autotune(self):
+        return sophie_batch_autotune(self.h)
+
+    def info(self):
+        return sophie_batch_info(self.h)
+
+    def launch_count(self):
+        return sophie_batch_launch_count(self.h)
+
+    def sync(self):
+        sophie_batch_sync(self.h)

@@ -188,3 +188,31 @@ def design_cavity(n: int = 128, design: tuple = (48, 80), eps_range=(1.0, 4.0),
             cells.append(c)
     return dict(nx=n, ny=n, nz=n, dx=DX_DEFAULT, dt=cfl_dt(DX_DEFAULT), eps=eps, sigma=sig,
                 sources=[src], probe=probe, design=(lo, lo, lo, m, m, m), cells=cells)
+
+
+def batch_cavities(ncav: int = 4096, size_range=(16, 96), eps_range=(1.0, 12.0), block: int = 4,
+                   seed: int = 1304):
+    """The batching workload: `ncav` PEC cavities with per-axis sizes uniform in
+    size_range (inclusive), eps_r uniform in eps_range per block^3-cell block
+    (partial blocks at the high edges), sigma = 0, and one Gaussian-pulse Ez
+    source at a random interior edge of each cavity. Returns the sizes
+    (ncav x 3, nx ny nz), the cavities' eps_r one after the other (x fastest
+    within each) and the source tuples (cav, comp, i, j, k, amp, f0, bw, t0,
+    kind)."""
+    rng = np.random.default_rng(seed)
+    lo, hi = size_range
+    dims = rng.integers(lo, hi + 1, size=(ncav, 3))
+    eps_parts = []
+    sources = []
+    amp, f0, bw, t0, kind = gaussian_pulse_source()
+    for c in range(ncav):
+        nx, ny, nz = (int(v) for v in dims[c])
+        nb = [(n + block - 1) // block for n in (nz, ny, nx)]
+        blocks = rng.uniform(*eps_range, size=nb).astype(np.float32)
+        e = np.repeat(np.repeat(np.repeat(blocks, block, 0), block, 1), block, 2)[:nz, :ny, :nx]
+        eps_parts.append(np.ascontiguousarray(e).ravel())
+        i = int(rng.integers(1, max(2, nx)))
+        j = int(rng.integers(1, max(2, ny)))
+        k = int(rng.integers(0, nz))
+        sources.append((c, 2, min(i, nx - 1), min(j, ny - 1), k, amp, f0, bw, t0, kind))
+    return dims.astype(np.int32), np.concatenate(eps_parts), sources

@@ -1,0 +1,165 @@
+"""Batching form: many cavities of uneven sizes advanced together.
+
+* Every cavity of a batch equals, bitwise, the float oracle run of that cavity
+  alone (and a single-grid run of the library), for lossy materials with
+  explicit entries and conducting cells, random initial fields and sources,
+  with and without graph replay, and after the autotuner changes the split.
+* Energy of every lossless cavity is conserved once its source pulse is over
+  (the discrete energy identity; float fields, double accumulation).
+"""
+
+import numpy as np
+import pytest
+
+from gpu_helpers import DX
+from paper_1301_4539_gb300 import sophie as so
+from paper_1301_4539_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+DIMS = [(16, 17, 18), (1, 1, 5), (40, 33, 21), (96, 20, 30), (5, 70, 9), (33, 8, 64), (2, 2, 2), (64, 64, 16)]
+
+
+def _materials(dims, seed):
+    rng = np.random.default_rng(seed)
+    eps, sig = [], []
+    for (nx, ny, nz) in dims:
+        nb = [(n + 3) // 4 for n in (nz, ny, nx)]
+        blocks = rng.uniform(1.0, 12.0, size=nb).astype(np.float32)
+        e = np.repeat(np.repeat(np.repeat(blocks, 4, 0), 4, 1), 4, 2)[:nz, :ny, :nx].copy()
+        e[rng.random((nz, ny, nx)) < 0.02] = np.inf
+        eps.append(e)
+        sig.append(rng.uniform(0.0, 0.3, size=(nz, ny, nx)).astype(np.float32))
+    return eps, sig
+
+
+def _sources(dims, seed):
+    rng = np.random.default_rng(seed)
+    amp, f0, bw, t0, kind = wl.gaussian_sine_source()
+    out = []
+    for c, (nx, ny, nz) in enumerate(dims):
+        if nx < 2 or ny < 2:
+            continue
+        for q in range(1 + c % 2):
+            out.append((c, 2, int(rng.integers(1, nx)), int(rng.integers(1, ny)), int(rng.integers(0, nz)),
+                        float(rng.uniform(1, 20)), f0, bw, t0 * (1 + q), kind))
+    return out
+
+
+def test_batch_equals_oracle_and_single_grids(oracle_mod, sophie):
+    dims = DIMS
+    eps, sig = _materials(dims, 4)
+    srcs = _sources(dims, 5)
+    b = so.Batch(dims, DX, wl.cfl_dt(DX))
+    b.set_materials(np.concatenate([e.ravel() for e in eps]), np.concatenate([s.ravel() for s in sig]))
+    fields = [wl.random_fields(*d, seed=100 + c) for c, d in enumerate(dims)]
+    for c in range(len(dims)):
+        for comp in range(6):
+            b.set_field(c, comp, fields[c][comp])
+    for s in srcs:
+        b.add_source(*s)
+    N1, N2 = 13, 10
+    b.step(N1)
+    b.configure(tile_y=4, zchunk=5, use_graph=False)
+    b.step(N2)
+    assert b.n == N1 + N2
+    W = b.energy()
+    for c, (nx, ny, nz) in enumerate(dims):
+        o = oracle_mod.OracleGrid(nx, ny, nz, DX, wl.cfl_dt(DX), "f32")
+        o.set_materials(eps[c], sig[c])
+        g = so.Grid(nx, ny, nz, DX, wl.cfl_dt(DX))
+        g.set_materials(eps[c], sig[c])
+        for comp in range(6):
+            o.set_field(comp, fields[c][comp])
+            g.set_field(comp, fields[c][comp])
+        for s in srcs:
+            if s[0] == c:
+                o.add_source(*s[1:])
+                g.add_source(*s[1:])
+        o.step(N1 + N2)
+        g.step(N1 + N2)
+        for comp in range(6):
+            got = b.get_field(c, comp)
+            np.testing.assert_array_equal(got, o.f[comp], err_msg=f"cavity {c} comp {comp}")
+            np.testing.assert_array_equal(got, g.get_field(comp))
+        assert abs(W[c] - o.energy()) <= 1e-12 * abs(o.energy())
+        g.close()
+
+
+def test_graph_replay_autotune_and_reset(sophie):
+    dims = DIMS[:6]
+    eps, sig = _materials(dims, 8)
+    srcs = _sources(dims, 9)
+    b = so.Batch(dims, DX, wl.cfl_dt(DX))
+    b.set_materials(np.concatenate([e.ravel() for e in eps]), np.concatenate([s.ravel() for s in sig]))
+    for s in srcs:
+        b.add_source(*s)
+    b.step(21)  # recorded into a graph
+    ref = [b.fields(c) for c in range(len(dims))]
+    b.reset()
+    ty, zc, ms = b.autotune()
+    assert ty in (4, 8, 16) and zc >= 1 and ms > 0
+    info = b.info()
+    assert info["tile_y"] == ty and info["zchunk"] == zc and info["cells"] == sum(x * y * z for x, y, z in dims)
+    assert b.n == 0
+    for c in range(len(dims)):
+        for comp in range(6):
+            assert not b.get_field(c, comp).any()  # the trial launches left the state alone
+    b.step(21)
+    b.reset()
+    b.step(21)  # graph replay of the same run
+    for c in range(len(dims)):
+        got = b.fields(c)
+        for comp in range(6):
+            np.testing.assert_array_equal(got[comp], ref[c][comp])
+    b.configure(use_graph=False)
+    b.reset()
+    b.step(21)
+    for c in range(len(dims)):
+        for comp in range(6):
+            np.testing.assert_array_equal(b.get_field(c, comp), ref[c][comp])
+
+
+def test_energy_conserved_after_pulse(sophie):
+    """A small instance of the batching workload: 24 lossless cavities with
+    4^3-block eps_r U(1,12) and a Gaussian-pulse Ez source each; after the
+    pulse (2 t0) each cavity's energy stays constant."""
+    dims, eps, srcs = wl.batch_cavities(ncav=24, size_range=(16, 40), seed=17)
+    b = so.Batch(dims, DX, wl.cfl_dt(DX))
+    b.set_materials(eps)
+    for s in srcs:
+        b.add_source(*s)
+    t0 = srcs[0][8]
+    n_off = int(np.ceil(2 * t0 / wl.cfl_dt(DX))) + 2
+    b.step(n_off)
+    W0 = b.energy()
+    assert np.all(W0 > 0)
+    b.step(250)
+    W1 = b.energy()
+    rel = np.abs(W1 - W0) / W0
+    print(f"max relative energy change over 250 steps after the pulse: {rel.max():.3e}")
+    assert rel.max() < 2e-6
+
+
+def test_batch_errors(sophie):
+    with pytest.raises(so.SophieError):
+        so.Batch([(0, 4, 4)], DX, wl.cfl_dt(DX))
+    with pytest.raises(so.SophieError) as e:
+        so.Batch([(4, 4, 4)], DX, 2 * wl.cfl_dt(DX))
+    assert e.value.code == so.EUNSTABLE
+    b = so.Batch([(8, 8, 8), (9, 9, 9)], DX, wl.cfl_dt(DX))
+    with pytest.raises(so.SophieError):
+        b.add_source(2, 2, 3, 3, 3, 1.0, 1e10, 5e9, 1e-10, 0)  # no cavity 2
+    with pytest.raises(so.SophieError):
+        b.add_source(0, 2, 0, 3, 3, 1.0, 1e10, 5e9, 1e-10, 0)  # PEC edge
+    for q in range(4):
+        b.add_source(1, 2, 3, 3, 3, 1.0, 1e10, 5e9, 1e-10, 0)
+    with pytest.raises(so.SophieError):
+        b.add_source(1, 2, 3, 3, 3, 1.0, 1e10, 5e9, 1e-10, 0)  # a fifth source
+    with pytest.raises(so.SophieError) as e:
+        b.configure(tile_y=5)
+    assert e.value.code == so.ENOTSUP
+    with pytest.raises(so.SophieError):
+        b.set_materials(np.full(8 ** 3 + 9 ** 3, 0.5, np.float32))
+    with pytest.raises(so.SophieError):
+        so.sophie_batch_get_fields(b.h, 3, 0, (2, 2, 2))  # no cavity 3

@@ -195,3 +195,27 @@ def test_design_region_in_class_background(oracle_mod, sophie, K):
     o.step(30)
     assert_fields_equal(g, o)
     np.testing.assert_array_equal(g.read_probe(0), o.probe(0))
+
+
+@pytest.mark.parametrize("K", [1, 2, 3])
+def test_conducting_cells(oracle_mod, sophie, K):
+    """Perfectly conducting cells (eps_r = +inf): scattered cells, a full layer
+    splitting the grid, and 4^3-block random eps (explicit entries shared by
+    points with the same three edge materials); bitwise = oracle."""
+    nx, ny, nz = 41, 22, 17
+    rng = np.random.default_rng(77)
+    blocks = rng.uniform(1.0, 12.0, size=((nz + 3) // 4, (ny + 3) // 4, (nx + 3) // 4)).astype(np.float32)
+    eps = np.repeat(np.repeat(np.repeat(blocks, 4, 0), 4, 1), 4, 2)[:nz, :ny, :nx].copy()
+    eps[rng.random((nz, ny, nx)) < 0.03] = np.inf
+    eps[:, :, 20] = np.inf
+    sig = rng.uniform(0.0, 0.2, size=(nz, ny, nx)).astype(np.float32)
+    f = wl.random_fields(nx, ny, nz, 5)
+    amp, f0, bw, t0, kind = wl.gaussian_sine_source()
+    g, o = make_pair(oracle_mod, nx, ny, nz, eps, sig, f, [(2, 30, 11, 8, 3.0, f0, bw, t0, kind)],
+                     [(2, 10, 10, 10), (2, 31, 11, 8)], temporal_k=K)
+    g.step(4 * K + 1)
+    o.step(4 * K + 1)
+    assert_fields_equal(g, o)
+    for q in range(2):
+        np.testing.assert_array_equal(g.read_probe(q), o.probe(q))
+    assert abs(g.energy() - o.energy()) <= 1e-12 * abs(o.energy())
