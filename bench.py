@@ -448,7 +448,7 @@ def run_batch(ncav: int = 4096, tsteps: int = 500):
     del eps
     for s in srcs:
         b.add_source(*s)
-    ty, zc, tuned_ms = b.autotune()
+    tx, ty, zc, tuned_ms = b.autotune()
     setup_s = time.perf_counter() - t_setup
     info = b.info()
     cells = info["cells"]
@@ -474,7 +474,8 @@ def run_batch(ncav: int = 4096, tsteps: int = 500):
     return {"workload": f"{ncav} PEC cavities, sizes U{{16..96}}^3 (seed 1304), eps_r U(1,12) per 4^3 block, "
                         f"one Gaussian-pulse Ez source each, {tsteps} steps per run",
             "cells": cells, "value": rate, "unit": "Gcell-updates/s", "ms_per_run": ms,
-            "launches_per_run": tsteps, "graph": True, "tile_y": ty, "zchunk": zc,
+            "launches_per_run": tsteps, "graph": True, "tiles": [tx, ty], "zchunk": zc,
+            "kernel": "yee_plain (batch work list, TMA)" if tx == 64 else "yee_batch (direct loads)",
             "work_items": info["work_items"], "autotuned_ms_per_step": tuned_ms,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "peak_source": peak_kind,

@@ -299,8 +299,11 @@ int sophie_objective_release(sophie_grid *g);
  * own class and explicit tables) and up to 4 soft sources; its fields are
  * bitwise those of a single grid of the same size run alone. One time step of
  * the whole batch is one persistent launch over a work list of
- * (cavity, 32 x tile_y tile, z chunk) items taken from a global counter, and
- * a run of n steps is recorded into a CUDA graph once and replayed while the
+ * (cavity, tile, z chunk) items: 64 x 16 tiles run the TMA-staged plain step
+ * kernel (units walked in list order by the persistent CTAs, each unit taking
+ * its cavity's tensor maps and tables from a device descriptor), 32 x tile_y
+ * tiles a direct-load kernel whose CTAs take items from a global counter. A
+ * run of n steps is recorded into a CUDA graph once and replayed while the
  * same (start step, n, buffer parity) recurs (e.g. reset + n steps). Field
  * storage is float. Indexing within a cavity is that of a single grid.
  *
@@ -320,13 +323,16 @@ int sophie_objective_release(sophie_grid *g);
  * sophie_batch_set_fields / get_fields: one component of one cavity, host
  *   array laid out as for sophie_set_fields. Synchronise.
  * sophie_batch_reset: zero all fields, step 0.
- * sophie_batch_configure: tile_y in {0 = keep, 4, 8, 16}, zchunk = z planes
- *   per work item (0 = keep), use_graph != 0 records runs into CUDA graphs.
- * sophie_batch_autotune: times the step with tile_y in {4, 8, 16} and z chunks
- *   in {4, 8, 16, 32, 96} (trial launches read the current fields and write
- *   the spare buffer, so the state does not advance) and keeps the fastest.
- *   Results do not depend on the choice. Synchronises.
- * sophie_batch_info: total cells, current work items, tile_y and z chunk.
+ * sophie_batch_configure: tiles (tile_x, tile_y) = (64, 16) or (32, 4|8|16)
+ *   (0 = keep), zchunk = z planes per work item (0 = keep), use_graph != 0
+ *   records runs into CUDA graphs. Errors: EINVAL, ENOTSUP, ENOMEM.
+ * sophie_batch_autotune: times one step for a set of (tiles, z chunk)
+ *   candidates of both kernels (trial launches read the current fields and
+ *   write the spare buffer, so the state does not advance) and keeps the
+ *   fastest. Results do not depend on the choice. Synchronises.
+ * sophie_batch_info: total cells, current work items, tiles and z chunk.
+ * sophie_batch_sync: wait for the batch's work; ETIMEOUT if a kernel gave up
+ *   a bounded wait.
  * sophie_batch_set_stream: a created (non-legacy) stream for later work.
  */
 typedef struct sophie_batch sophie_batch;
@@ -342,9 +348,10 @@ int sophie_batch_set_fields(sophie_batch *b, int cav, int comp, const float *hos
 int sophie_batch_get_fields(sophie_batch *b, int cav, int comp, float *host);
 int sophie_batch_reset(sophie_batch *b);
 int sophie_batch_set_stream(sophie_batch *b, void *cuda_stream);
-int sophie_batch_configure(sophie_batch *b, int tile_y, int zchunk, int use_graph);
-int sophie_batch_autotune(sophie_batch *b, int *tile_y, int *zchunk, double *ms_per_step);
-int sophie_batch_info(sophie_batch *b, long long *cells, long long *work_items, int *tile_y, int *zchunk);
+int sophie_batch_configure(sophie_batch *b, int tile_x, int tile_y, int zchunk, int use_graph);
+int sophie_batch_autotune(sophie_batch *b, int *tile_x, int *tile_y, int *zchunk, double *ms_per_step);
+int sophie_batch_info(sophie_batch *b, long long *cells, long long *work_items, int *tile_x, int *tile_y,
+                      int *zchunk);
 int sophie_batch_launch_count(sophie_batch *b, long long *launches);
 int sophie_batch_sync(sophie_batch *b);
 

@@ -22,6 +22,7 @@
 
 #include "../../include/sophie.h"
 #include "sophie_internal.h"
+#include "yee_store.cuh"
 
 using namespace sophie;
 
@@ -96,7 +97,8 @@ struct sophie_batch {
   long long n = 0;
   cudaStream_t stream = nullptr;
   bool own_stream = false;
-  int tile_y = 8, zchunk = 16, grid = 0, num_sms = 1;
+  int tile_x = 64, tile_y = 16, zchunk = 16, grid = 0, num_sms = 1;  // tile_x 64: TMA kernel, 32: direct
+  int* err = nullptr;  // bounded waits of the TMA kernel that ran out
   bool use_graph = true;
   cudaGraphExec_t gexec = nullptr;
   long long g_n0 = -1;
@@ -117,47 +119,75 @@ void free_batch(sophie_batch* b) {
   if (b->stream) cudaStreamSynchronize(b->stream);
   drop_graph(b);
   void* bufs[] = {b->arena, b->words, b->coef, b->eps_tab, b->ecoef, b->eeps, b->sval, b->d_desc,
-                  b->d_items, b->d_eitems, b->d_efirst, b->e_part, b->e_out, b->counter};
+                  b->d_items, b->d_eitems, b->d_efirst, b->e_part, b->e_out, b->counter, b->err};
   for (void* p : bufs)
     if (p) cudaFree(p);
   if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
   delete b;
 }
 
-int upload_desc(sophie_batch* b) {
+void fill_desc(sophie_batch* b, int c) {
+  CavityDesc& cd = b->h_desc[c];
+  cd.d = b->dims[c];
+  cd.F[0] = b->arena + b->fofs[c];
+  cd.F[1] = b->arena + b->fofs[c] + b->fbytes[c];
+  cd.mat = b->words + b->wofs[c];
+  cd.coef = b->coef + (size_t)c * kMaxClasses;
+  cd.eps_tab = b->eps_tab + (size_t)c * kMaxClasses;
+  cd.ecoef = b->ecoef ? b->ecoef + 3 * b->eofs[c] : nullptr;
+  cd.eeps = b->eeps ? b->eeps + 3 * b->eofs[c] : nullptr;
+  cd.src.n = (int)b->src[c].size();
+  for (int q = 0; q < cd.src.n; ++q) {
+    cd.src.comp[q] = b->src[c][q].comp;
+    cd.src.pos[q] = b->src[c][q].pos;
+  }
+  cd.src.val = b->sval ? b->sval + (size_t)c * kBatchMaxSrc * b->scap : nullptr;
+  cd.src.cap = b->scap;
+}
+
+// TMA maps of every cavity (its buffers and words do not move).
+int encode_desc_maps(sophie_batch* b) {
   for (int c = 0; c < b->ncav; ++c) {
     CavityDesc& cd = b->h_desc[c];
-    cd.d = b->dims[c];
-    cd.F[0] = b->arena + b->fofs[c];
-    cd.F[1] = b->arena + b->fofs[c] + b->fbytes[c];
-    cd.mat = b->words + b->wofs[c];
-    cd.coef = b->coef + (size_t)c * kMaxClasses;
-    cd.eps_tab = b->eps_tab + (size_t)c * kMaxClasses;
-    cd.ecoef = b->ecoef ? b->ecoef + 3 * b->eofs[c] : nullptr;
-    cd.eeps = b->eeps ? b->eeps + 3 * b->eofs[c] : nullptr;
-    cd.nsrc = (int)b->src[c].size();
-    for (int q = 0; q < cd.nsrc; ++q) {
-      cd.src_comp[q] = b->src[c][q].comp;
-      cd.src_pos[q] = b->src[c][q].pos;
-    }
-    cd.src_val = b->sval ? b->sval + (size_t)c * kBatchMaxSrc * b->scap : nullptr;
-    cd.src_cap = b->scap;
+    fill_desc(b, c);
+    if (!encode_maps(cd.d, kF32, cd.F[0], const_cast<uint32_t*>(cd.mat), plain_box_x(kF32), plain_box_y(), &cd.tmF[0],
+                     &cd.tmM) ||
+        !encode_maps(cd.d, kF32, cd.F[1], nullptr, plain_box_x(kF32), plain_box_y(), &cd.tmF[1], nullptr))
+      return bfail(SOPHIE_ECUDA, "cuTensorMapEncodeTiled failed for cavity %d", c);
   }
+  return SOPHIE_OK;
+}
+
+int upload_desc(sophie_batch* b) {
+  for (int c = 0; c < b->ncav; ++c) fill_desc(b, c);
   BCUDA(cudaMemcpyAsync(b->d_desc, b->h_desc.data(), sizeof(CavityDesc) * b->ncav, cudaMemcpyHostToDevice,
                         b->stream));
   BCUDA(cudaStreamSynchronize(b->stream));
   return SOPHIE_OK;
 }
 
-// Step work list for tile height ty and z chunk zc: cavity by cavity, then z
+int upload_desc_one(sophie_batch* b, int c) {
+  fill_desc(b, c);
+  BCUDA(cudaMemcpyAsync(b->d_desc + c, &b->h_desc[c], sizeof(CavityDesc), cudaMemcpyHostToDevice, b->stream));
+  BCUDA(cudaStreamSynchronize(b->stream));
+  return SOPHIE_OK;
+}
+
+bool tiles_supported(int tx, int ty) {
+  return (tx == 64 && ty == 16) || (tx == 32 && batch_tile_supported(ty));
+}
+
+// Step work list for tx x ty tiles and z chunk zc: cavity by cavity, then z
 // chunk, y tile, x tile, so that the items taken together share planes in L2.
-int build_items(sophie_batch* b, int ty, int zc) {
+// tx = 64 (ty = 16) runs the TMA-staged plain kernel over the list, tx = 32
+// the direct-load kernel.
+int build_items(sophie_batch* b, int tx, int ty, int zc) {
   std::vector<BatchItem> it;
   for (int c = 0; c < b->ncav; ++c) {
     const Dims& d = b->dims[c];
     for (int z0 = 0; z0 < d.nz; z0 += zc)
       for (int y0 = 0; y0 < d.ny; y0 += ty)
-        for (int x0 = 0; x0 < d.nx; x0 += 32) it.push_back({c, x0, y0, z0, std::min(z0 + zc, d.nz)});
+        for (int x0 = 0; x0 < d.nx; x0 += tx) it.push_back({c, x0, y0, z0, std::min(z0 + zc, d.nz)});
   }
   if (it.size() > 0x7ffffff0u) return bfail(SOPHIE_EINVAL, "too many work items");
   drop_graph(b);
@@ -169,9 +199,10 @@ int build_items(sophie_batch* b, int ty, int zc) {
   }
   BCUDA(cudaMemcpy(b->d_items, it.data(), it.size() * sizeof(BatchItem), cudaMemcpyHostToDevice));
   b->nitems = (int)it.size();
+  b->tile_x = tx;
   b->tile_y = ty;
   b->zchunk = zc;
-  b->grid = b->num_sms * batch_blocks_per_sm(ty);
+  b->grid = tx == 64 ? 2 * b->num_sms : b->num_sms * batch_blocks_per_sm(ty);
   return SOPHIE_OK;
 }
 
@@ -229,14 +260,40 @@ int check_cav(sophie_batch* b, int cav) {
   return SOPHIE_OK;
 }
 
+// One step of every cavity reading buffer `cur` (step index nstep).
+cudaError_t launch_one(sophie_batch* b, int cur, long long nstep) {
+  if (b->tile_x == 64) {
+    StepArgs a{};
+    a.fmt = kF32;
+    for (int c = 0; c < 6; ++c) a.sc[c] = a.isc[c] = 1.f;
+    a.S = b->S32;
+    a.n0 = nstep;
+    a.err = b->err;
+    const PlainBatch pb{b->d_desc, b->d_items, b->nitems, cur};
+    return launch_step_plain_batch(a, pb, b->grid, b->stream);
+  }
+  return launch_batch_step(b->d_desc, b->d_items, b->nitems, b->counter, cur, b->S32, nstep, b->tile_y, b->grid,
+                           b->stream);
+}
+
 // Enqueue the launches of steps [b->n, b->n + n) without a graph.
 int enqueue_steps(sophie_batch* b, int n) {
   int cur = b->cur;
   for (int m = 0; m < n; ++m) {
-    const cudaError_t e = launch_batch_step(b->d_desc, b->d_items, b->nitems, b->counter, cur, b->S32, b->n + m,
-                                            b->tile_y, b->grid, b->stream);
+    const cudaError_t e = launch_one(b, cur, b->n + m);
     if (e != cudaSuccess) return bfail(SOPHIE_ECUDA, "batch step launch failed: %s", cudaGetErrorString(e));
     cur = 1 - cur;
+  }
+  return SOPHIE_OK;
+}
+
+int check_err(sophie_batch* b) {
+  int h = 0;
+  BCUDA(cudaMemcpyAsync(&h, b->err, sizeof(int), cudaMemcpyDeviceToHost, b->stream));
+  BCUDA(cudaStreamSynchronize(b->stream));
+  if (h != 0) {
+    cudaMemsetAsync(b->err, 0, sizeof(int), b->stream);
+    return bfail(SOPHIE_ETIMEOUT, "a batch kernel ran out of its bounded wait (code %d)", h);
   }
   return SOPHIE_OK;
 }
@@ -307,7 +364,11 @@ int sophie_batch_create(int ncav, const int* dims, double dx, double dt, sophie_
     if (!alloc((void**)&b->coef, (size_t)ncav * kMaxClasses * sizeof(float2))) break;
     if (!alloc((void**)&b->eps_tab, (size_t)ncav * kMaxClasses * sizeof(double))) break;
     if (!alloc((void**)&b->d_desc, (size_t)ncav * sizeof(CavityDesc))) break;
-    if (!alloc((void**)&b->counter, sizeof(int))) break;
+    if (!alloc((void**)&b->counter, sizeof(int)) || !alloc((void**)&b->err, sizeof(int))) break;
+    if (cudaMemsetAsync(b->err, 0, sizeof(int), b->stream) != cudaSuccess) {
+      rc = bfail(SOPHIE_ECUDA, "cudaMemsetAsync failed");
+      break;
+    }
     if (!alloc((void**)&b->e_out, (size_t)ncav * 8)) break;
     if (!alloc((void**)&b->d_efirst, (size_t)(ncav + 1) * 4)) break;
     if (cudaMemsetAsync(b->arena, 0, fb, b->stream) != cudaSuccess) {
@@ -340,9 +401,11 @@ int sophie_batch_create(int ncav, const int* dims, double dx, double dt, sophie_
       rc = bfail(SOPHIE_ECUDA, "initialisation failed: %s", cudaGetErrorString(cudaGetLastError()));
       break;
     }
+    rc = encode_desc_maps(b);
+    if (rc) break;
     rc = sophie_batch_set_materials(b, nullptr, nullptr);
     if (rc) break;
-    rc = build_items(b, 8, 16);
+    rc = build_items(b, 64, 16, 16);
     if (rc) break;
     rc = ensure_src_capacity(b, 1);
     if (rc) break;
@@ -472,7 +535,7 @@ int sophie_batch_add_source(sophie_batch* b, int cav, int comp, int i, int j, in
     return bfail(SOPHIE_ECUDA, "flag launch failed");
   b->launches++;
   drop_graph(b);
-  return upload_desc(b);
+  return upload_desc_one(b, cav);
 }
 
 int sophie_batch_step(sophie_batch* b, int n) {
@@ -520,10 +583,12 @@ int sophie_batch_get_step(sophie_batch* b, long long* n) {
   return SOPHIE_OK;
 }
 
-int sophie_batch_info(sophie_batch* b, long long* cells, long long* work_items, int* tile_y, int* zchunk) {
-  if (!b || !cells || !work_items || !tile_y || !zchunk) return bfail(SOPHIE_EINVAL, "NULL argument");
+int sophie_batch_info(sophie_batch* b, long long* cells, long long* work_items, int* tile_x, int* tile_y,
+                      int* zchunk) {
+  if (!b || !cells || !work_items || !tile_x || !tile_y || !zchunk) return bfail(SOPHIE_EINVAL, "NULL argument");
   *cells = b->cells;
   *work_items = b->nitems;
+  *tile_x = b->tile_x;
   *tile_y = b->tile_y;
   *zchunk = b->zchunk;
   return SOPHIE_OK;
@@ -537,7 +602,8 @@ int sophie_batch_energy(sophie_batch* b, double* W) {
   if (e != cudaSuccess) return bfail(SOPHIE_ECUDA, "batch energy launch failed: %s", cudaGetErrorString(e));
   b->launches += 2;
   BCUDA(cudaMemcpyAsync(W, b->e_out, (size_t)b->ncav * 8, cudaMemcpyDeviceToHost, b->stream));
-  BCUDA(cudaStreamSynchronize(b->stream));
+  int rc = check_err(b);
+  if (rc) return rc;
   for (int c = 0; c < b->ncav; ++c)
     if (!std::isfinite(W[c])) return bfail(SOPHIE_ENONFINITE, "energy of cavity %d is not finite", c);
   return SOPHIE_OK;
@@ -592,65 +658,69 @@ int sophie_batch_set_stream(sophie_batch* b, void* cuda_stream) {
   return SOPHIE_OK;
 }
 
-int sophie_batch_configure(sophie_batch* b, int tile_y, int zchunk, int use_graph) {
+int sophie_batch_configure(sophie_batch* b, int tile_x, int tile_y, int zchunk, int use_graph) {
   if (!b) return bfail(SOPHIE_EINVAL, "NULL batch");
-  if (tile_y != 0 && !batch_tile_supported(tile_y)) return bfail(SOPHIE_ENOTSUP, "tile_y must be 0, 4, 8 or 16");
+  const int tx = tile_x ? tile_x : b->tile_x;
+  const int ty = tile_y ? tile_y : (tile_x == 64 ? 16 : b->tile_y);
+  if (!tiles_supported(tx, ty)) return bfail(SOPHIE_ENOTSUP, "tiles %d x %d not built (64 x 16; 32 x 4, 8, 16)", tx, ty);
   if (zchunk < 0) return bfail(SOPHIE_EINVAL, "zchunk must be >= 0");
   b->use_graph = use_graph != 0;
-  const int ty = tile_y ? tile_y : b->tile_y, zc = zchunk ? zchunk : b->zchunk;
-  if (ty != b->tile_y || zc != b->zchunk) return build_items(b, ty, zc);
+  const int zc = zchunk ? zchunk : b->zchunk;
+  if (tx != b->tile_x || ty != b->tile_y || zc != b->zchunk) return build_items(b, tx, ty, zc);
   return SOPHIE_OK;
 }
 
-int sophie_batch_autotune(sophie_batch* b, int* tile_y, int* zchunk, double* ms_per_step) {
-  if (!b || !tile_y || !zchunk || !ms_per_step) return bfail(SOPHIE_EINVAL, "NULL argument");
+int sophie_batch_autotune(sophie_batch* b, int* tile_x, int* tile_y, int* zchunk, double* ms_per_step) {
+  if (!b || !tile_x || !tile_y || !zchunk || !ms_per_step) return bfail(SOPHIE_EINVAL, "NULL argument");
   int rc = ensure_src_capacity(b, b->n + 1);
   if (rc) return rc;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   BCUDA(cudaEventCreate(&e0));
   BCUDA(cudaEventCreate(&e1));
   double best = 1e300;
-  int bty = b->tile_y, bzc = b->zchunk;
-  const int tys[] = {4, 8, 16};
-  const int zcs[] = {4, 8, 16, 32, 96};
-  for (int ty : tys)
-    for (int zc : zcs) {
-      rc = build_items(b, ty, zc);
-      if (rc) break;
-      // Trial launches read the current buffer and write the spare one; the
-      // state does not advance.
-      auto launch = [&]() {
-        return launch_batch_step(b->d_desc, b->d_items, b->nitems, b->counter, b->cur, b->S32, b->n, ty, b->grid,
-                                 b->stream);
-      };
-      if (launch() != cudaSuccess) {
-        rc = bfail(SOPHIE_ECUDA, "autotune launch failed");
-        break;
-      }
-      cudaEventRecord(e0, b->stream);
-      const int reps = 3;
-      for (int r = 0; r < reps; ++r)
-        if (launch() != cudaSuccess) rc = bfail(SOPHIE_ECUDA, "autotune launch failed");
-      cudaEventRecord(e1, b->stream);
-      if (rc) break;
-      if (cudaEventSynchronize(e1) != cudaSuccess) {
-        rc = bfail(SOPHIE_ECUDA, "autotune timing failed");
-        break;
-      }
-      float ms = 0.f;
-      cudaEventElapsedTime(&ms, e0, e1);
-      b->launches += reps + 1;
-      if (ms / reps < best) {
-        best = ms / reps;
-        bty = ty;
-        bzc = zc;
-      }
+  int btx = b->tile_x, bty = b->tile_y, bzc = b->zchunk;
+  struct Cand {
+    int tx, ty, zc;
+  };
+  const Cand cands[] = {{64, 16, 4}, {64, 16, 8},  {64, 16, 16}, {64, 16, 32}, {64, 16, 96},
+                        {32, 8, 16}, {32, 16, 16}, {32, 16, 96}, {32, 4, 8}};
+  for (const Cand& cd : cands) {
+    rc = build_items(b, cd.tx, cd.ty, cd.zc);
+    if (rc) break;
+    // Trial launches read the current buffer and write the spare one; the
+    // state does not advance.
+    if (launch_one(b, b->cur, b->n) != cudaSuccess) {
+      rc = bfail(SOPHIE_ECUDA, "autotune launch failed");
+      break;
     }
+    cudaEventRecord(e0, b->stream);
+    const int reps = 3;
+    for (int r = 0; r < reps; ++r)
+      if (launch_one(b, b->cur, b->n) != cudaSuccess) rc = bfail(SOPHIE_ECUDA, "autotune launch failed");
+    cudaEventRecord(e1, b->stream);
+    if (rc) break;
+    if (cudaEventSynchronize(e1) != cudaSuccess) {
+      rc = bfail(SOPHIE_ECUDA, "autotune timing failed");
+      break;
+    }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    b->launches += reps + 1;
+    if (ms / reps < best) {
+      best = ms / reps;
+      btx = cd.tx;
+      bty = cd.ty;
+      bzc = cd.zc;
+    }
+  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (rc) return rc;
-  rc = build_items(b, bty, bzc);
+  rc = check_err(b);
   if (rc) return rc;
+  rc = build_items(b, btx, bty, bzc);
+  if (rc) return rc;
+  *tile_x = btx;
   *tile_y = bty;
   *zchunk = bzc;
   *ms_per_step = best;
@@ -665,8 +735,7 @@ int sophie_batch_launch_count(sophie_batch* b, long long* launches) {
 
 int sophie_batch_sync(sophie_batch* b) {
   if (!b) return bfail(SOPHIE_EINVAL, "NULL batch");
-  BCUDA(cudaStreamSynchronize(b->stream));
-  return SOPHIE_OK;
+  return check_err(b);
 }
 
 }  // extern "C"

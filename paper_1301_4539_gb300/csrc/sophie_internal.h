@@ -161,6 +161,8 @@ cudaError_t launch_or_flag(uint32_t* mat, long long pos, uint32_t bit, cudaStrea
 // cavity in device memory; float field storage.
 constexpr int kBatchMaxSrc = 4;
 struct CavityDesc {
+  CUtensorMap tmF[2];      // TMA maps of the two field buffers (plain kernel box)
+  CUtensorMap tmM;         // TMA map of the material words
   Dims d;
   void* F[2];              // the cavity's two field buffers (ping-pong)
   const uint32_t* mat;     // material words (layout of a single grid)
@@ -168,11 +170,7 @@ struct CavityDesc {
   const double* eps_tab;   // class eps_r(edge) (energy)
   const float2* ecoef;     // explicit entries
   const double* eeps;
-  int nsrc;
-  int src_comp[kBatchMaxSrc];
-  long long src_pos[kBatchMaxSrc];
-  const float* src_val;    // [nsrc][src_cap] waveform values by absolute step
-  int src_cap;
+  SrcTable src;            // at most kBatchMaxSrc sources; val[q*cap + step]
 };
 // A step work item: x tile [x0, x0+32), y tile [y0, y0+TY), planes [z0, z1).
 struct BatchItem {
@@ -183,6 +181,17 @@ struct EnergyItem {
   int cav;
   long long p0, p1;
 };
+// The TMA-staged plain kernel over a batch work list (64 x 16 tiles; items
+// with x0 % 64 == 0, y0 % 16 == 0). a supplies S, n0 and err; float storage.
+struct PlainBatch {
+  const CavityDesc* descs;
+  const BatchItem* items;
+  int nitems;
+  int cur;
+};
+cudaError_t launch_step_plain_batch(const StepArgs& a, const PlainBatch& pb, int grid, cudaStream_t s);
+int plain_tile_x();
+int plain_tile_y();
 bool batch_tile_supported(int ty);
 int batch_blocks_per_sm(int ty);
 // Memsets the work counter, then one persistent launch of `grid` CTAs.

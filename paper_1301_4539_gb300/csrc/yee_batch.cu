@@ -89,11 +89,12 @@ yee_batch_kernel(const CavityDesc* __restrict__ descs, const BatchItem* __restri
         float by = curl_br(hx, hxp, hz, sH[2][ty][tx - 1]);
         float bz = curl_br(hy, sH[1][ty][tx - 1], hx, sH[0][ty - 1][tx]);
         if (m & kSrcFlag) {
-          for (int q = 0; q < cd->nsrc; ++q) {
-            if (cd->src_pos[q] != pt) continue;
-            const float v = cd->src_val[(long long)q * cd->src_cap + nstep];
-            if (cd->src_comp[q] == 0) bx = __fadd_rn(bx, v);
-            else if (cd->src_comp[q] == 1) by = __fadd_rn(by, v);
+          const SrcTable* st = &cd->src;
+          for (int q = 0; q < st->n; ++q) {
+            if (st->pos[q] != pt) continue;
+            const float v = st->val[(long long)q * st->cap + nstep];
+            if (st->comp[q] == 0) bx = __fadd_rn(bx, v);
+            else if (st->comp[q] == 1) by = __fadd_rn(by, v);
             else bz = __fadd_rn(bz, v);
           }
         }

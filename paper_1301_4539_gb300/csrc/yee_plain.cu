@@ -80,10 +80,15 @@ __device__ __forceinline__ Unit unit_of(long long u, const PlainTiling& t, int n
 
 __device__ __forceinline__ void set_err(int* err, int code) { atomicOr(err, code); }
 
-template <int FMT>
+// BATCH: the work units are the items of a batch of cavities (one step of
+// every cavity); each unit takes its tensor maps, sizes, output buffer,
+// coefficient tables and sources from its cavity's descriptor. Otherwise the
+// units tile the single grid of `a` as described by `t`.
+template <int FMT, bool BATCH>
 __global__ void __launch_bounds__(kThreads, 2)
 yee_plain_kernel(const __grid_constant__ CUtensorMap tmF, const __grid_constant__ CUtensorMap tmM,
-                 const __grid_constant__ StepArgs a, PlainTiling t) {
+                 const __grid_constant__ StepArgs a, PlainTiling t, PlainBatch pb) {
+  static_assert(!BATCH || FMT == kF32, "batches store float fields");
   using C = PCfg<FMT>;
   using St = Store<FMT>;
   using T = typename C::T;
@@ -109,17 +114,33 @@ yee_plain_kernel(const __grid_constant__ CUtensorMap tmF, const __grid_constant_
     fence_mbar_init();
   }
   __syncthreads();
-  const Dims d = a.d;
+  const long long nunits = BATCH ? (long long)pb.nitems : t.units;
+  // Unit u: its tile and z range, and (batches) its cavity's descriptor.
+  auto unit_at = [&](long long u, const CavityDesc*& cd) -> Unit {
+    if constexpr (BATCH) {
+      const BatchItem it = pb.items[u];
+      cd = pb.descs + it.cav;
+      return Unit{it.x0, it.y0, it.z0, it.z1};
+    } else {
+      cd = nullptr;
+      return unit_of(u, t, a.d.nz);
+    }
+  };
 
   if (warp == kCW) {
     // ---------------- producer warp ----------------
     if (lane != 0) return;
-    prefetch_tmap(&tmF);
-    prefetch_tmap(&tmM);
+    if constexpr (!BATCH) {
+      prefetch_tmap(&tmF);
+      prefetch_tmap(&tmM);
+    }
     long long L = 0;
     bool ok = true;
-    for (long long u = blockIdx.x; u < t.units && ok; u += gridDim.x) {
-      const Unit w = unit_of(u, t, d.nz);
+    for (long long u = blockIdx.x; u < nunits && ok; u += gridDim.x) {
+      const CavityDesc* cd;
+      const Unit w = unit_at(u, cd);
+      const CUtensorMap* mF = BATCH ? &cd->tmF[pb.cur] : &tmF;
+      const CUtensorMap* mM = BATCH ? &cd->tmM : &tmM;
       const int ps = w.z0 > 0 ? w.z0 - 1 : 0;
       for (int p = ps; p <= w.z1; ++p, ++L) {
         const int s = (int)(L % kNS);
@@ -129,8 +150,8 @@ yee_plain_kernel(const __grid_constant__ CUtensorMap tmF, const __grid_constant_
           break;
         }
         mbar_arrive_expect_tx(full(s), C::kLoadBytes);
-        tma_load_4d(smem_u32(sF(s)), &tmF, w.x0 - OX, w.y0 - 1, 0, p, full(s));
-        tma_load_3d(smem_u32(sM(s)), &tmM, w.x0 - OX, w.y0 - 1, p, full(s));
+        tma_load_4d(smem_u32(sF(s)), mF, w.x0 - OX, w.y0 - 1, 0, p, full(s));
+        tma_load_3d(smem_u32(sM(s)), mM, w.x0 - OX, w.y0 - 1, p, full(s));
       }
     }
     if (!ok) {
@@ -153,11 +174,16 @@ yee_plain_kernel(const __grid_constant__ CUtensorMap tmF, const __grid_constant_
     hc = OX + 8 * warp + (lane - 2);
   }
   const float S = a.S;
-  T* const fout = static_cast<T*>(a.fout);
   long long C_ = 0;
   bool abort = false;
-  for (long long u = blockIdx.x; u < t.units && !abort; u += gridDim.x) {
-    const Unit w = unit_of(u, t, d.nz);
+  for (long long u = blockIdx.x; u < nunits && !abort; u += gridDim.x) {
+    const CavityDesc* cd;
+    const Unit w = unit_at(u, cd);
+    const Dims d = BATCH ? cd->d : a.d;
+    T* const fout = static_cast<T*>(BATCH ? cd->F[1 - pb.cur] : a.fout);
+    const float2* const coef = BATCH ? cd->coef : a.coef;
+    const float2* const ecoef = BATCH ? cd->ecoef : a.ecoef;
+    const SrcTable* const srct = BATCH ? &cd->src : &a.src;
     const int ps = w.z0 > 0 ? w.z0 - 1 : 0;
     float hxp[2][2] = {{0.f, 0.f}, {0.f, 0.f}}, hyp[2][2] = {{0.f, 0.f}, {0.f, 0.f}};
     for (int z = ps; z < w.z1; ++z, ++C_) {
@@ -263,21 +289,21 @@ yee_plain_kernel(const __grid_constant__ CUtensorMap tmF, const __grid_constant_
           float bz = curl_br(hy[r][cc], cc ? hy[r][0] : hy_im, hx[r][cc], hxj[cc]);
           if ((m & kSrcFlag) && out_plane) {
             const float3 b3 = apply_sources(make_float3(bx, by, bz),
-                                            ((long long)z * d.ny1 + y) * d.nxp + x + cc, a.n0, &a.src);
+                                            ((long long)z * d.ny1 + y) * d.nxp + x + cc, a.n0, srct);
             bx = b3.x;
             by = b3.y;
             bz = b3.z;
           }
           float2 k0, k1, k2;
           if (m & kExpFlag) {
-            const float2* e3 = a.ecoef + 3ull * (m >> 3);
+            const float2* e3 = ecoef + 3ull * (m >> 3);
             k0 = __ldg(e3);
             k1 = __ldg(e3 + 1);
             k2 = __ldg(e3 + 2);
           } else {
-            k0 = __ldg(&a.coef[cls_of(m, 0)]);
-            k1 = __ldg(&a.coef[cls_of(m, 1)]);
-            k2 = __ldg(&a.coef[cls_of(m, 2)]);
+            k0 = __ldg(&coef[cls_of(m, 0)]);
+            k1 = __ldg(&coef[cls_of(m, 1)]);
+            k2 = __ldg(&coef[cls_of(m, 2)]);
           }
           eo[0][cc] = e_upd(ex[r][cc], k0, bx);
           eo[1][cc] = e_upd(ey[r][cc], k1, by);
@@ -397,12 +423,29 @@ cudaError_t launch_plain_f(const StepArgs& a, const CUtensorMap& tmF, const CUte
                            cudaStream_t s) {
   static bool attr = false;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(yee_plain_kernel<F>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(yee_plain_kernel<F, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)PCfg<F>::kSmemBytes);
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  yee_plain_kernel<F><<<t.grid, kThreads, PCfg<F>::kSmemBytes, s>>>(tmF, tmM, a, t);
+  yee_plain_kernel<F, false><<<t.grid, kThreads, PCfg<F>::kSmemBytes, s>>>(tmF, tmM, a, t, PlainBatch{});
+  return cudaGetLastError();
+}
+
+int plain_tile_x() { return kPX; }
+int plain_tile_y() { return kPY; }
+
+cudaError_t launch_step_plain_batch(const StepArgs& a, const PlainBatch& pb, int grid, cudaStream_t s) {
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(yee_plain_kernel<kF32, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)PCfg<kF32>::kSmemBytes);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  CUtensorMap none{};
+  PlainTiling t{};
+  yee_plain_kernel<kF32, true><<<grid, kThreads, PCfg<kF32>::kSmemBytes, s>>>(none, none, a, t, pb);
   return cudaGetLastError();
 }
 

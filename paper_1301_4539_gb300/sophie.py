@@ -65,10 +65,11 @@ SIGNATURES = {
     "sophie_batch_get_fields": (_I, [_P, _I, _I, _P]),
     "sophie_batch_reset": (_I, [_P]),
     "sophie_batch_set_stream": (_I, [_P, _P]),
-    "sophie_batch_configure": (_I, [_P, _I, _I, _I]),
-    "sophie_batch_autotune": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_D)]),
+    "sophie_batch_configure": (_I, [_P, _I, _I, _I, _I]),
+    "sophie_batch_autotune": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I),
+                                   ctypes.POINTER(_D)]),
     "sophie_batch_info": (_I, [_P, ctypes.POINTER(_LL), ctypes.POINTER(_LL), ctypes.POINTER(_I),
-                               ctypes.POINTER(_I)]),
+                               ctypes.POINTER(_I), ctypes.POINTER(_I)]),
     "sophie_batch_launch_count": (_I, [_P, ctypes.POINTER(_LL)]),
     "sophie_batch_sync": (_I, [_P]),
     "sophie_last_error": (ctypes.c_char_p, []),
@@ -401,21 +402,24 @@ def sophie_batch_set_stream(b: int, cuda_stream: int) -> None:
     _chk(load().sophie_batch_set_stream(b, cuda_stream))
 
 
-def sophie_batch_configure(b: int, tile_y: int = 0, zchunk: int = 0, use_graph: bool = True) -> None:
-    _chk(load().sophie_batch_configure(b, tile_y, zchunk, 1 if use_graph else 0))
+def sophie_batch_configure(b: int, tile_x: int = 0, tile_y: int = 0, zchunk: int = 0,
+                           use_graph: bool = True) -> None:
+    _chk(load().sophie_batch_configure(b, tile_x, tile_y, zchunk, 1 if use_graph else 0))
 
 
 def sophie_batch_autotune(b: int):
-    """(tile_y, zchunk, device ms per time step) of the fastest work split."""
-    ty, zc, ms = _I(), _I(), _D()
-    _chk(load().sophie_batch_autotune(b, ctypes.byref(ty), ctypes.byref(zc), ctypes.byref(ms)))
-    return ty.value, zc.value, ms.value
+    """(tile_x, tile_y, zchunk, device ms per time step) of the fastest work split."""
+    tx, ty, zc, ms = _I(), _I(), _I(), _D()
+    _chk(load().sophie_batch_autotune(b, ctypes.byref(tx), ctypes.byref(ty), ctypes.byref(zc), ctypes.byref(ms)))
+    return tx.value, ty.value, zc.value, ms.value
 
 
 def sophie_batch_info(b: int):
-    cells, items, ty, zc = _LL(), _LL(), _I(), _I()
-    _chk(load().sophie_batch_info(b, ctypes.byref(cells), ctypes.byref(items), ctypes.byref(ty), ctypes.byref(zc)))
-    return {"cells": cells.value, "work_items": items.value, "tile_y": ty.value, "zchunk": zc.value}
+    cells, items, tx, ty, zc = _LL(), _LL(), _I(), _I(), _I()
+    _chk(load().sophie_batch_info(b, ctypes.byref(cells), ctypes.byref(items), ctypes.byref(tx), ctypes.byref(ty),
+                                  ctypes.byref(zc)))
+    return {"cells": cells.value, "work_items": items.value, "tile_x": tx.value, "tile_y": ty.value,
+            "zchunk": zc.value}
 
 
 def sophie_batch_launch_count(b: int) -> int:
@@ -481,8 +485,8 @@ class Batch:
     def set_stream(self, s):
         sophie_batch_set_stream(self.h, s)
 
-    def configure(self, tile_y=0, zchunk=0, use_graph=True):
-        sophie_batch_configure(self.h, tile_y, zchunk, use_graph)
+    def configure(self, tile_x=0, tile_y=0, zchunk=0, use_graph=True):
+        sophie_batch_configure(self.h, tile_x, tile_y, zchunk, use_graph)
 
     def autotune(self):
         return sophie_batch_autotune(self.h)

@@ -58,10 +58,13 @@ def test_batch_equals_oracle_and_single_grids(oracle_mod, sophie):
             b.set_field(c, comp, fields[c][comp])
     for s in srcs:
         b.add_source(*s)
-    N1, N2 = 13, 10
-    b.step(N1)
-    b.configure(tile_y=4, zchunk=5, use_graph=False)
-    b.step(N2)
+    N1, N2, N3 = 13, 10, 6
+    b.step(N1)  # TMA-staged kernel, 64 x 16 tiles, graph replay
+    b.configure(tile_x=32, tile_y=4, zchunk=5, use_graph=False)
+    b.step(N2)  # direct-load kernel
+    b.configure(tile_x=64, zchunk=3)
+    b.step(N3)
+    N2 += N3
     assert b.n == N1 + N2
     W = b.energy()
     for c, (nx, ny, nz) in enumerate(dims):
@@ -97,10 +100,11 @@ def test_graph_replay_autotune_and_reset(sophie):
     b.step(21)  # recorded into a graph
     ref = [b.fields(c) for c in range(len(dims))]
     b.reset()
-    ty, zc, ms = b.autotune()
-    assert ty in (4, 8, 16) and zc >= 1 and ms > 0
+    tx, ty, zc, ms = b.autotune()
+    assert (tx, ty) in ((64, 16), (32, 4), (32, 8), (32, 16)) and zc >= 1 and ms > 0
     info = b.info()
-    assert info["tile_y"] == ty and info["zchunk"] == zc and info["cells"] == sum(x * y * z for x, y, z in dims)
+    assert (info["tile_x"], info["tile_y"], info["zchunk"]) == (tx, ty, zc)
+    assert info["cells"] == sum(x * y * z for x, y, z in dims)
     assert b.n == 0
     for c in range(len(dims)):
         for comp in range(6):
@@ -157,7 +161,10 @@ def test_batch_errors(sophie):
     with pytest.raises(so.SophieError):
         b.add_source(1, 2, 3, 3, 3, 1.0, 1e10, 5e9, 1e-10, 0)  # a fifth source
     with pytest.raises(so.SophieError) as e:
-        b.configure(tile_y=5)
+        b.configure(tile_x=32, tile_y=5)
+    assert e.value.code == so.ENOTSUP
+    with pytest.raises(so.SophieError) as e:
+        b.configure(tile_x=64, tile_y=8)
     assert e.value.code == so.ENOTSUP
     with pytest.raises(so.SophieError):
         b.set_materials(np.full(8 ** 3 + 9 ** 3, 0.5, np.float32))
