@@ -303,10 +303,10 @@ def run_ours(args):
         vms, _, _, _ = timed(kk, nv, 1, False)
         variants[f"k{kk}"] = cells * args.tsteps * nv * world / (vms / 1e3) / 1e9
     # storage-precision forms (float arithmetic, 2-byte fields in HBM)
-    for pname, prec in (("fp16", so.FP16), ("bf16", so.BF16)):
+    for pname, prec in (("fp16", so.FP16), ("bf16", so.BF16), ("fp16hl", so.FP16HL)):
         g.configure(temporal_k=1, precision=prec)
         g_prec[0] = prec
-        if prec == so.FP16:
+        if prec in (so.FP16, so.FP16HL):
             g.set_storage_scale([2.0 ** 10] * 6)
         for kk in (1, 2):
             vms, _, _, _ = timed(kk, nv, 1, False)

@@ -72,6 +72,7 @@ extern "C" {
 #define SOPHIE_FP32 0
 #define SOPHIE_FP16 1
 #define SOPHIE_BF16 2
+#define SOPHIE_FP16HL 3  /* hi + lo pair of halves per value (4 B), see sophie_configure */
 
 /* Kernel ids for sophie_profile_read. */
 #define SOPHIE_KERNEL_PLAIN   0  /* one fused H+E step per launch           */
@@ -211,11 +212,14 @@ int sophie_sync(sophie_grid *g);
  * sophie_step measures the candidates, see sophie_autotune). tile_x: 0 or 64 = TMA-staged 64x16 tiles
  * (default), 32 = 32x8 tiles with direct loads (a slower reference kernel;
  * identical results); tile_y: reserved, 0.
- * precision: SOPHIE_FP32, SOPHIE_FP16 or SOPHIE_BF16 storage of the fields
- * (a change converts the current fields; synchronises). In the 2-byte modes
- * one launch loads the stored fields, computes its k steps in float and
- * rounds once when storing, so results depend on k (no longer bitwise equal
- * across k). Errors: EINVAL, ENOTSUP, ENOMEM.
+ * precision: SOPHIE_FP32, SOPHIE_FP16 or SOPHIE_BF16 storage of the fields,
+ * or SOPHIE_FP16HL: each value v = field * scale kept as two halves
+ * hi = half(v), lo = half(v - hi) (4 B, ~22 significant bits; the split
+ * storage that wins back the accuracy half storage loses). A change converts
+ * the current fields; synchronises. In the non-float modes one launch loads
+ * the stored fields, computes its k steps in float and rounds once when
+ * storing, so results depend on k (no longer bitwise equal across k).
+ * Errors: EINVAL, ENOTSUP, ENOMEM.
  */
 int sophie_configure(sophie_grid *g, int temporal_k, int tile_x, int tile_y, int precision);
 

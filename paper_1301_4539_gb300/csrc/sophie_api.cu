@@ -454,6 +454,14 @@ void to_store(int fmt, float scale, const float* in, void* out, size_t n) {
   } else if (fmt == kBF16) {
     __nv_bfloat16* o = static_cast<__nv_bfloat16*>(out);
     for (size_t i = 0; i < n; ++i) o[i] = __float2bfloat16_rn(in[i] * scale);
+  } else if (fmt == kF16HL) {
+    __half* o = static_cast<__half*>(out);  // pairs (hi, lo)
+    for (size_t i = 0; i < n; ++i) {
+      const float v = in[i] * scale;
+      const __half hi = __float2half_rn(v);
+      o[2 * i] = hi;
+      o[2 * i + 1] = __float2half_rn(v - __half2float(hi));
+    }
   } else {
     memcpy(out, in, n * 4);
   }
@@ -467,6 +475,9 @@ void from_store(int fmt, float scale, const void* in, float* out, size_t n) {
   } else if (fmt == kBF16) {
     const __nv_bfloat16* p = static_cast<const __nv_bfloat16*>(in);
     for (size_t i = 0; i < n; ++i) out[i] = __bfloat162float(p[i]) * inv;
+  } else if (fmt == kF16HL) {
+    const __half* p = static_cast<const __half*>(in);
+    for (size_t i = 0; i < n; ++i) out[i] = (__half2float(p[2 * i]) + __half2float(p[2 * i + 1])) * inv;
   } else {
     memcpy(out, in, n * 4);
   }
@@ -516,7 +527,7 @@ int restore_fields(sophie_grid* g, int fmt, const float* sc) {
     if (rc) return rc;
   }
   CUDA_TRY(cudaStreamSynchronize(g->stream));
-  const int esz = fmt == kF32 ? 4 : 2;
+  const int esz = store_bytes(fmt);
   if (esz != g->esz) {
     const size_t bytes = (size_t)d.zstride * d.nz1 * esz;
     void* nb[2] = {nullptr, nullptr};
@@ -558,7 +569,7 @@ double time_candidate(sophie_grid* g, Fn&& launch, cudaEvent_t e0, cudaEvent_t e
   if (cudaEventSynchronize(e1) != cudaSuccess) return -1.0;
   float ms = 0.f;
   cudaEventElapsedTime(&ms, e0, e1);
-  const int reps = std::max(2, std::min(40, (int)(2.0 / std::max(ms, 1e-3f))));
+  const int reps = std::max(3, std::min(100, (int)(6.0 / std::max(ms, 1e-3f))));
   cudaEventRecord(e0, g->stream);
   for (int r = 0; r < reps; ++r)
     if (launch() != cudaSuccess) return -1.0;
@@ -1022,7 +1033,7 @@ int sophie_configure(sophie_grid* g, int temporal_k, int tile_x, int tile_y, int
     return fail(SOPHIE_ENOTSUP, "temporal_k = %d not built (supported: 1..4)", temporal_k);
   if (tile_x < 0 || tile_y < 0) return fail(SOPHIE_EINVAL, "tile sizes must be >= 0");
   if (tile_x != 0 && tile_x != 32 && tile_x != 64) return fail(SOPHIE_EINVAL, "tile_x must be 0, 32 or 64");
-  if (precision < SOPHIE_FP32 || precision > SOPHIE_BF16)
+  if (precision < SOPHIE_FP32 || precision > SOPHIE_FP16HL)
     return fail(SOPHIE_ENOTSUP, "precision %d not supported", precision);
   if (tile_x == 32 && precision != SOPHIE_FP32)
     return fail(SOPHIE_ENOTSUP, "the 32x8 reference kernel stores float only");

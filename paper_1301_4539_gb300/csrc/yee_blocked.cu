@@ -530,7 +530,7 @@ cudaError_t launch_fmt(const StepArgs& a, const CUtensorMap& tmF, const CUtensor
 
 }  // namespace
 
-int blocked_box_x(int fmt) { return fmt == kF32 ? BoxCfg<kF32>::BX : BoxCfg<kF16>::BX; }
+int blocked_box_x(int fmt) { return store_bytes(fmt) == 4 ? BoxCfg<kF32>::BX : BoxCfg<kF16>::BX; }
 int blocked_box_y() { return kRY; }
 
 BlockedTiling blocked_tiling(const Dims& d, int K, int num_sms, int aligned) {
@@ -559,6 +559,7 @@ cudaError_t launch_step_blocked(const StepArgs& a, const CUtensorMap& tmF, const
     case kF32: return launch_fmt<kF32>(a, tmF, tmM, t, s);
     case kF16: return launch_fmt<kF16>(a, tmF, tmM, t, s);
     case kBF16: return launch_fmt<kBF16>(a, tmF, tmM, t, s);
+    case kF16HL: return launch_fmt<kF16HL>(a, tmF, tmM, t, s);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -217,6 +217,7 @@ cudaError_t launch_energy_scaled(const StepArgs& a, const double* eps_tab, doubl
     case kF32: return launch_energy_f<kF32>(a, eps_tab, partials, nblocks, scale, out, s);
     case kF16: return launch_energy_f<kF16>(a, eps_tab, partials, nblocks, scale, out, s);
     case kBF16: return launch_energy_f<kBF16>(a, eps_tab, partials, nblocks, scale, out, s);
+    case kF16HL: return launch_energy_f<kF16HL>(a, eps_tab, partials, nblocks, scale, out, s);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -49,7 +49,7 @@ struct PCfg {
   using T = typename Store<F>::T;
   static constexpr int OX = Store<F>::kAlign;
   static constexpr int BX = kPX + 2 * OX;
-  static constexpr bool kInPlace = F == kF32;
+  static constexpr bool kInPlace = sizeof(T) == 4;  // a float fits in the ring slot
   static constexpr uint32_t kFieldBytes = BX * kBY * 6 * sizeof(T);
   static constexpr uint32_t kMatBytes = BX * kBY * 4;
   static constexpr uint32_t kLoadBytes = kFieldBytes + kMatBytes;
@@ -357,17 +357,18 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 
 }  // namespace
 
-int plain_box_x(int fmt) { return fmt == kF32 ? PCfg<kF32>::BX : PCfg<kF16>::BX; }
+int plain_box_x(int fmt) { return store_bytes(fmt) == 4 ? PCfg<kF32>::BX : PCfg<kF16>::BX; }
 int plain_box_y() { return kBY; }
 
 bool encode_maps(const Dims& d, int fmt, void* fields, uint32_t* mat, int box_x, int box_y, CUtensorMap* tmF,
                  CUtensorMap* tmM) {
   auto fn = encode_fn();
   if (!fn) return false;
-  const cuuint64_t esz = fmt == kF32 ? 4 : 2;
-  const CUtensorMapDataType dt = fmt == kF32   ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
-                                 : fmt == kF16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
-                                               : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+  const cuuint64_t esz = store_bytes(fmt);
+  // hi+lo pairs move as 4-byte elements (zero fill = +0 + +0)
+  const CUtensorMapDataType dt = fmt == kF32 || fmt == kF16HL ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                 : fmt == kF16                ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
+                                                              : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
   if (tmF) {
     cuuint64_t gdF[4] = {(cuuint64_t)d.nxp, (cuuint64_t)d.ny1, 6, (cuuint64_t)d.nz1};
     cuuint64_t gsF[3] = {(cuuint64_t)d.nxp * esz, (cuuint64_t)d.plane * esz, (cuuint64_t)d.zstride * esz};
@@ -455,6 +456,7 @@ cudaError_t launch_step_plain(const StepArgs& a, const CUtensorMap& tmF, const C
     case kF32: return launch_plain_f<kF32>(a, tmF, tmM, t, s);
     case kF16: return launch_plain_f<kF16>(a, tmF, tmM, t, s);
     case kBF16: return launch_plain_f<kBF16>(a, tmF, tmM, t, s);
+    case kF16HL: return launch_plain_f<kF16HL>(a, tmF, tmM, t, s);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -3,6 +3,10 @@
 //   kF32  : float (4 B)
 //   kF16  : IEEE half (2 B), stored value = field * scale[comp]
 //   kBF16 : bfloat16 (2 B), stored value = field * scale[comp]
+//   kF16HL: two IEEE halves (4 B) hi = half(v), lo = half(v - hi) with
+//           v = field * scale[comp]; read back as float(hi) + float(lo), which
+//           is exact in float (22 significant bits at most), so about 2^-22
+//           relative per store instead of half's 2^-11
 // Scales are powers of two, so scaling and unscaling are exact in float
 // (barring overflow/underflow); conversion to the 2-byte formats rounds to
 // nearest even.
@@ -13,7 +17,7 @@
 
 namespace sophie {
 
-enum StoreFmt : int { kF32 = 0, kF16 = 1, kBF16 = 2 };
+enum StoreFmt : int { kF32 = 0, kF16 = 1, kBF16 = 2, kF16HL = 3 };
 
 template <int F>
 struct Store;
@@ -61,5 +65,37 @@ struct Store<kBF16> {
   }
   static __device__ __forceinline__ void st(T* p, float a, float sc) { *p = __float2bfloat16_rn(a * sc); }
 };
+
+template <>
+struct Store<kF16HL> {
+  using T = __half2;  // .x = hi, .y = lo
+  static constexpr int kAlign = 4;
+  static __device__ __forceinline__ float dec(__half2 h, float inv) {
+    return __fadd_rn(__low2float(h), __high2float(h)) * inv;
+  }
+  static __device__ __forceinline__ __half2 enc(float a, float sc) {
+    const float v = a * sc;
+    const __half hi = __float2half_rn(v);
+    const __half lo = __float2half_rn(__fsub_rn(v, __half2float(hi)));
+    return __halves2half2(hi, lo);
+  }
+  static __device__ __forceinline__ float2 ld2(const T* p, float inv) {
+    const uint2 raw = *reinterpret_cast<const uint2*>(p);
+    return make_float2(dec(*reinterpret_cast<const __half2*>(&raw.x), inv),
+                       dec(*reinterpret_cast<const __half2*>(&raw.y), inv));
+  }
+  static __device__ __forceinline__ float ld(const T* p, float inv) { return dec(*p, inv); }
+  static __device__ __forceinline__ void st2(T* p, float a, float b, float sc) {
+    const __half2 ha = enc(a, sc), hb = enc(b, sc);
+    uint2 raw;
+    raw.x = *reinterpret_cast<const unsigned int*>(&ha);
+    raw.y = *reinterpret_cast<const unsigned int*>(&hb);
+    *reinterpret_cast<uint2*>(p) = raw;
+  }
+  static __device__ __forceinline__ void st(T* p, float a, float sc) { *p = enc(a, sc); }
+};
+
+// Bytes per stored value.
+__host__ __device__ constexpr int store_bytes(int fmt) { return fmt == kF16 || fmt == kBF16 ? 2 : 4; }
 
 }  // namespace sophie
