@@ -37,8 +37,11 @@ FIELD_BYTES = 48   # read + write six float32 components per cell-update
 MAT_BYTES = 4      # one 32-bit material word read per cell per launch
 # DRAM bytes (read + write) per launch from one ncu capture of each kernel on
 # this workload (profiles/*.md); None where the kernel changed since.
-NCU_TRAFFIC = {("yee_blocked", 2): 522.851584e6 + 358.680064e6,
-               ("yee_blocked", 3): 546.369280e6 + 368.397312e6}
+NCU_TRAFFIC = {("yee_blocked", 2): 519.240960e6 + 358.025984e6,
+               ("yee_plain", 1): 514.649600e6 + 363.524352e6}
+# Batching workload: DRAM bytes per cell per launch of the batch-mode plain
+# kernel (3.811902 GB for the 54436430 cells of a 300-cavity instance).
+BATCH_TRAFFIC_PER_CELL = (2.415318e9 + 1.396584e9) / 54436430
 
 
 def parse():
@@ -479,7 +482,10 @@ def run_batch(ncav: int = 4096, tsteps: int = 500):
             "work_items": info["work_items"], "autotuned_ms_per_step": tuned_ms,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "peak_source": peak_kind,
-                         "note": "52 algorithmic bytes per cell-update; explicit coefficient reads not counted"},
+                         "traffic": BATCH_TRAFFIC_PER_CELL * cells,
+                         "note": "52 algorithmic bytes per cell-update; explicit coefficient reads not counted; "
+                                 "traffic per launch scaled by cells from an ncu capture of a 300-cavity "
+                                 "instance of the same generator"},
             "setup_s": setup_s, "energy_sum_J": float(np.sum(W))}
 
 
