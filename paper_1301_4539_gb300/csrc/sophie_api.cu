@@ -16,6 +16,7 @@
 #include <cstdio>
 #include <mutex>
 #include <string>
+#include <thread>
 #include <unordered_map>
 #include <vector>
 
@@ -198,7 +199,8 @@ bool comp_valid(const Dims& d, int c, int i, int j, int k) {
 // vacuum); sources and probes flag their points.
 int build_material_words(sophie_grid* g, const float* eps, const float* sig) {
   MaterialTables t;
-  if (build_material_tables(g->d, g->dt, g->S64, eps, sig, g->mat_host, &t) != 0)
+  const int nth = std::max(1, std::min(32, (int)std::thread::hardware_concurrency()));
+  if (build_material_tables(g->d, g->dt, g->S64, eps, sig, g->mat_host, &t, nth) != 0)
     return fail(SOPHIE_ETOOMANYMAT, "more than 2^29 explicit material points");
   uint32_t* w = g->mat_host;
   for (const Source& s : g->src) w[s.pos] |= kSrcFlag;

@@ -459,7 +459,7 @@ int sophie_batch_set_materials(sophie_batch* b, const float* eps, const float* s
       const Dims& d = b->dims[c];
       w.assign((size_t)d.plane * d.nz1, 0u);
       if (build_material_tables(d, b->dt, b->S64, eps ? eps + cofs[c] : nullptr, sig ? sig + cofs[c] : nullptr,
-                                w.data(), &tabs[c]) != 0) {
+                                w.data(), &tabs[c], 1) != 0) {
         err.store(1);
         return;
       }

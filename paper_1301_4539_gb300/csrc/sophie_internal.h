@@ -125,10 +125,12 @@ float2 edge_coefficients(double dt, double S64, double e, double s);
 // conducting cell, whose edges are PEC). Edge material = mean of its four
 // cells; the 511 most frequent edge materials become classes, points with an
 // edge outside them share explicit entries by their three edge materials.
-// No source or probe flags are set. Returns 0, or -1 if more than 2^29
-// explicit entries would be needed.
+// No source or probe flags are set. The work is split into fixed slabs of z
+// planes (explicit entries are shared within a slab) run on up to nthreads
+// host threads; the result does not depend on nthreads. Returns 0, or -1 if
+// more than 2^29 explicit entries would be needed.
 int build_material_tables(const Dims& d, double dt, double S64, const float* eps, const float* sig, uint32_t* words,
-                          MaterialTables* out);
+                          MaterialTables* out, int nthreads);
 
 // Launchers (return cudaError_t of the launch).
 cudaError_t launch_step_simple(const StepArgs& a, cudaStream_t s);

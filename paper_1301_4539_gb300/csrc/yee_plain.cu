@@ -176,14 +176,52 @@ yee_plain_kernel(const __grid_constant__ CUtensorMap tmF, const __grid_constant_
   const float S = a.S;
   long long C_ = 0;
   bool abort = false;
-  for (long long u = blockIdx.x; u < nunits && !abort; u += gridDim.x) {
+  // Batches: the current unit's cavity context lives in shared memory (two
+  // copies by unit parity: a warp can start unit u+1 while others finish the
+  // stores of unit u, never later ones, because of the per-plane barrier),
+  // keeping these values out of the consumers' registers.
+  struct UnitCtx {
+    T* fout;
+    const float2* coef;
+    const float2* ecoef;
+    const SrcTable* srct;
+    int nx, ny, nxp, ny1, plane, zstride;
+  };
+  __shared__ UnitCtx uctx[BATCH ? 2 : 1];
+  int upar = 0;
+  for (long long u = blockIdx.x; u < nunits && !abort; u += gridDim.x, upar ^= 1) {
     const CavityDesc* cd;
     const Unit w = unit_at(u, cd);
-    const Dims d = BATCH ? cd->d : a.d;
-    T* const fout = static_cast<T*>(BATCH ? cd->F[1 - pb.cur] : a.fout);
-    const float2* const coef = BATCH ? cd->coef : a.coef;
-    const float2* const ecoef = BATCH ? cd->ecoef : a.ecoef;
-    const SrcTable* const srct = BATCH ? &cd->src : &a.src;
+    if constexpr (BATCH) {
+      if (threadIdx.x == 0) {
+        UnitCtx& c = uctx[upar];
+        c.fout = static_cast<T*>(cd->F[1 - pb.cur]);
+        c.coef = cd->coef;
+        c.ecoef = cd->ecoef;
+        c.srct = &cd->src;
+        c.nx = cd->d.nx;
+        c.ny = cd->d.ny;
+        c.nxp = cd->d.nxp;
+        c.ny1 = cd->d.ny1;
+        c.plane = (int)cd->d.plane;
+        c.zstride = (int)cd->d.zstride;
+      }
+    }
+    const UnitCtx* uc = &uctx[BATCH ? upar : 0];
+    struct {
+      const StepArgs& a;
+      const UnitCtx* uc;
+      __device__ int nx() const { return BATCH ? uc->nx : a.d.nx; }
+      __device__ int ny() const { return BATCH ? uc->ny : a.d.ny; }
+      __device__ long long nxp() const { return BATCH ? uc->nxp : a.d.nxp; }
+      __device__ long long ny1() const { return BATCH ? uc->ny1 : a.d.ny1; }
+      __device__ long long plane() const { return BATCH ? uc->plane : a.d.plane; }
+      __device__ long long zstride() const { return BATCH ? uc->zstride : a.d.zstride; }
+    } d{a, uc};
+    auto fout = [&]() { return BATCH ? uc->fout : static_cast<T*>(a.fout); };
+    auto coef = [&]() { return BATCH ? uc->coef : a.coef; };
+    auto ecoef = [&]() { return BATCH ? uc->ecoef : a.ecoef; };
+    auto srct = [&]() { return BATCH ? uc->srct : &a.src; };
     const int ps = w.z0 > 0 ? w.z0 - 1 : 0;
     float hxp[2][2] = {{0.f, 0.f}, {0.f, 0.f}}, hyp[2][2] = {{0.f, 0.f}, {0.f, 0.f}};
     for (int z = ps; z < w.z1; ++z, ++C_) {
@@ -289,39 +327,40 @@ yee_plain_kernel(const __grid_constant__ CUtensorMap tmF, const __grid_constant_
           float bz = curl_br(hy[r][cc], cc ? hy[r][0] : hy_im, hx[r][cc], hxj[cc]);
           if ((m & kSrcFlag) && out_plane) {
             const float3 b3 = apply_sources(make_float3(bx, by, bz),
-                                            ((long long)z * d.ny1 + y) * d.nxp + x + cc, a.n0, srct);
+                                            ((long long)z * d.ny1() + y) * d.nxp() + x + cc, a.n0, srct());
             bx = b3.x;
             by = b3.y;
             bz = b3.z;
           }
           float2 k0, k1, k2;
           if (m & kExpFlag) {
-            const float2* e3 = ecoef + 3ull * (m >> 3);
+            const float2* e3 = ecoef() + 3ull * (m >> 3);
             k0 = __ldg(e3);
             k1 = __ldg(e3 + 1);
             k2 = __ldg(e3 + 2);
           } else {
-            k0 = __ldg(&coef[cls_of(m, 0)]);
-            k1 = __ldg(&coef[cls_of(m, 1)]);
-            k2 = __ldg(&coef[cls_of(m, 2)]);
+            const float2* ct = coef();
+            k0 = __ldg(&ct[cls_of(m, 0)]);
+            k1 = __ldg(&ct[cls_of(m, 1)]);
+            k2 = __ldg(&ct[cls_of(m, 2)]);
           }
           eo[0][cc] = e_upd(ex[r][cc], k0, bx);
           eo[1][cc] = e_upd(ey[r][cc], k1, by);
           eo[2][cc] = e_upd(ez[r][cc], k2, bz);
-          if ((m & kPrbFlag) && out_plane && y < d.ny && x + cc < d.nx)
-            record_probes(((long long)z * d.ny1 + y) * d.nxp + x + cc, a.n0, eo[0][cc], eo[1][cc], eo[2][cc],
+          if ((m & kPrbFlag) && out_plane && y < d.ny() && x + cc < d.nx())
+            record_probes(((long long)z * d.ny1() + y) * d.nxp() + x + cc, a.n0, eo[0][cc], eo[1][cc], eo[2][cc],
                           hx[r][cc], hy[r][cc], hz[r][cc], &a.prb);
         }
-        if (out_plane && y < d.ny && x < d.nx) {
-          T* o = fout + (long long)z * d.zstride + (long long)y * d.nxp + x;
+        if (out_plane && y < d.ny() && x < d.nx()) {
+          T* o = fout() + (long long)z * d.zstride() + (long long)y * d.nxp() + x;
           const float vals[6][2] = {{eo[0][0], eo[0][1]}, {eo[1][0], eo[1][1]}, {eo[2][0], eo[2][1]},
                                     {hx[r][0], hx[r][1]}, {hy[r][0], hy[r][1]}, {hz[r][0], hz[r][1]}};
-          if (x + 1 < d.nx) {
+          if (x + 1 < d.nx()) {
 #pragma unroll
-            for (int f = 0; f < 6; ++f) St::st2(o + f * d.plane, vals[f][0], vals[f][1], a.sc[f]);
+            for (int f = 0; f < 6; ++f) St::st2(o + f * d.plane(), vals[f][0], vals[f][1], a.sc[f]);
           } else {
 #pragma unroll
-            for (int f = 0; f < 6; ++f) St::st(o + f * d.plane, vals[f][0], a.sc[f]);
+            for (int f = 0; f < 6; ++f) St::st(o + f * d.plane(), vals[f][0], a.sc[f]);
           }
         }
 #pragma unroll
