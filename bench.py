@@ -26,10 +26,13 @@ import json
 import os
 import statistics
 import subprocess
+import sys
 import threading
 import time
 
 import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
 
 N_CELLS_SIDE = 256
 T_STEPS = 1000
@@ -57,6 +60,7 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-adjoint", action="store_true")
     p.add_argument("--no-batch", action="store_true")
+    p.add_argument("--no-768", action="store_true")
     p.add_argument("--batch-cavities", type=int, default=4096)
     return p.parse_args()
 
@@ -162,10 +166,29 @@ def cpu_baseline(w, budget_s: float = 15.0):
     dt = time.perf_counter() - t0
     g.energy()
     cells = n ** 3
-    return {"value": cells * m / dt / 1e9, "unit": "Gcell-updates/s", "cores": nthreads,
-            "kind": "oracle",
-            "sample": f"{n}^3 sphere cavity, float32 oracle, {m} time steps (of the {T_STEPS}-step run), "
-                      f"OMP over z-planes, {dt:.1f} s"}
+    out = {"value": cells * m / dt / 1e9, "unit": "Gcell-updates/s", "cores": nthreads,
+           "kind": "oracle",
+           "sample": f"{n}^3 sphere cavity, float32 oracle, {m} time steps (of the {T_STEPS}-step run), "
+                     f"OMP over z-planes, {dt:.1f} s"}
+    # the same oracle on one core (a separate process, so that its OpenMP
+    # runtime starts with one thread): 2 steps of the same workload
+    code = ("import sys, time; sys.path.insert(0, %r)\n"
+            "import oracle, bench\n"
+            "w = bench.workload(%d)\n"
+            "g = oracle.OracleGrid(%d, %d, %d, w['dx'], w['dt'], 'f32')\n"
+            "g.set_materials(w['eps'], w['sigma'])\n"
+            "[g.add_source(*s) for s in w['sources']]\n"
+            "g.step(1)\n"
+            "t = time.perf_counter(); g.step(2); print(time.perf_counter() - t)\n") % (ROOT, n, n, n, n)
+    try:
+        env = dict(os.environ, OMP_NUM_THREADS="1")
+        r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=300)
+        t1 = float(r.stdout.strip().splitlines()[-1])
+        out["one_core"] = {"value": cells * 2 / t1 / 1e9, "unit": "Gcell-updates/s", "cores": 1,
+                           "sample": f"2 time steps of the same workload, {t1:.1f} s"}
+    except Exception as e:  # reported, not fatal: the main baseline above stands
+        out["one_core"] = {"error": str(e)[:200]}
+    return out
 
 
 def run_reference(args):
@@ -300,7 +323,7 @@ def run_ours(args):
     # the other step kernels on the same workload (fewer runs), for comparison
     variants = {"autotuned" if not args.k else f"k{K}": value}
     nv = max(2, min(args.steps, 3))
-    for kk in (1, 2, 3):
+    for kk in (1, 2, 3, 4):
         if kk == K and args.k:
             continue
         vms, _, _, _ = timed(kk, nv, 1, False)
@@ -337,6 +360,10 @@ def run_ours(args):
     if not args.no_batch and rank == 0:
         batch = run_batch(args.batch_cavities)
 
+    precision_768 = None
+    if not args.no_768 and rank == 0:
+        precision_768 = run_precision_768(stream)
+
     if rank == 0:
         line = {"metric": "Gcell-updates/s 3D Yee FDTD", "value": value, "unit": "Gcell-updates/s",
                 "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -349,7 +376,7 @@ def run_ours(args):
                            "l2": "inputs larger than L2 (no flush)"},
                 "roofline": roof, "variants_gcells": variants, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": launches, "clocks": clocks, "energy_J": energy, "adjoint": adjoint,
-                "batch": batch}
+                "batch": batch, "precision_768": precision_768}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
@@ -429,6 +456,45 @@ def run_adjoint(stream, reps: int = 3):
                                "launches": la // reps},
             "recompute_kernel_avg_launch_ms": pms / max(lp, 1), "reps": reps,
             "forward_temporal_k": k_tuned}
+
+
+def run_precision_768(stream, tsteps: int = 200):
+    """Throughput of the storage forms on the precision workload's grid: the
+    768^3 sphere cavity (same generator, centre source, 16 probes), reset +
+    `tsteps` steps per run, device time with CUDA events. Accuracy of the same
+    forms against the FP64 oracle is measured at 256^3 by the tests."""
+    import torch
+    from paper_1301_4539_gb300 import sophie as so
+    n = 768
+    w = workload(n)
+    g = so.Grid(n, n, n, w["dx"], w["dt"])
+    g.set_stream(stream.cuda_stream)
+    g.set_materials(w["eps"], w["sigma"])
+    for src in w["sources"]:
+        g.add_source(*src)
+    for p in w["probes"]:
+        g.add_probe(*p)
+    out = {"workload": f"{n}^3 PEC sphere cavity (64 lossy spheres, centre Ez source, 16 probes), "
+                       f"{tsteps} steps per run", "unit": "Gcell-updates/s"}
+    for name, prec, k in (("fp32_autotuned", so.FP32, 0), ("fp32_k1", so.FP32, 1), ("fp16_k2", so.FP16, 2),
+                          ("bf16_k2", so.BF16, 2), ("fp16hl_k2", so.FP16HL, 2)):
+        g.configure(temporal_k=k, precision=prec)
+        g.set_storage_scale([2.0 ** 10 if prec in (so.FP16, so.FP16HL) else 1.0] * 6)
+        if k == 0:
+            out["fp32_autotuned_k"], _ = g.autotune()
+        g.reset()
+        g.step(20)
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        g.reset()
+        g.step(tsteps)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        out[name] = n ** 3 * tsteps / (ev0.elapsed_time(ev1) / 1e3) / 1e9
+    g.close()
+    return out
 
 
 def run_batch(ncav: int = 4096, tsteps: int = 500):

@@ -607,7 +607,7 @@ int run_autotune(sophie_grid* g, double* best_ms_per_step) {
   double best_plain = 1e300;
   BlockedTiling best_b{};
   int best_k = 1;
-  const int zcs[] = {4, 8, 16, 32, 64};
+  const int zcs[] = {1, 2, 4, 8, 16, 32, 64};
   for (int zc : zcs) {
     if (zc > 2 * d.nz && zc != zcs[0]) break;
     const PlainTiling pt = plain_tiling(d, g->num_sms, zc);
