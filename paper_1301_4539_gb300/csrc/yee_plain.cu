@@ -298,6 +298,21 @@ yee_plain_kernel(const __grid_constant__ CUtensorMap tmF, const __grid_constant_
       }
       abort = named_bar_or(1, kConsumers, !ok);
       if (abort) break;
+      if constexpr (BATCH) {
+        // Batches are mostly explicit points: warm L1 with the explicit
+        // coefficients of the next plane's points, read in the next
+        // iteration's E phase (the next stage is loaded and not yet released;
+        // it holds this unit's cavity).
+        const uint32_t* Mn = sM(sn);
+        const float2* ec = ecoef();
+#pragma unroll
+        for (int r = 0; r < 2; ++r)
+#pragma unroll
+          for (int cc = 0; cc < 2; ++cc) {
+            const uint32_t mn = Mn[(r0 + r) * BX + c0 + cc];
+            if (mn & kExpFlag) prefetch_l1(ec + 3ull * (mn >> 3));
+          }
+      }
       const bool out_plane = z >= w.z0;
       const uint32_t* M = sM(sc);
 #pragma unroll
