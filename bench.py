@@ -138,6 +138,26 @@ def dist_env():
     return rank, world, local
 
 
+def max_over_ranks(value: float) -> float:
+    """The largest `value` over all ranks (the slowest rank's time); the
+    value itself when no process group is running. Works with NCCL (a CUDA
+    tensor) and gloo (a host tensor)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(value)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_rate(cell_updates_per_rank: float, world: int, ms_max: float) -> float:
+    """Whole-job throughput (G cell-updates/s) of `world` independent replicas:
+    all ranks' updates over the slowest rank's device time (weak scaling)."""
+    return cell_updates_per_rank * world / (ms_max / 1e3) / 1e9
+
+
 def workload(n: int):
     from paper_1301_4539_gb300 import workloads as wl
     return wl.sphere_cavity(n)
@@ -288,10 +308,7 @@ def run_ours(args):
         if profile:
             prof = {kk: g.profile_read(kk) for kk in (so.KERNEL_PLAIN, so.KERNEL_BLOCKED, so.KERNEL_ENERGY)}
             g.profile(False)
-        if world > 1:
-            t = torch.tensor([ms], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
+        ms = max_over_ranks(ms)
         return ms, launches, prof, energy
 
     if args.k:
@@ -303,8 +320,7 @@ def run_ours(args):
     sampler.start()
     ms, launches, prof, energy = timed(0 if not args.k else K, args.steps, args.warmup, True)
     clocks = sampler.stop()
-    total_updates = cells * args.tsteps * args.steps * world
-    value = total_updates / (ms / 1e3) / 1e9
+    value = replica_rate(cells * args.tsteps * args.steps, world, ms)
 
     # dominant kernel of the timed region and its roofline
     kid = max(prof, key=lambda k: prof[k][1])
