@@ -96,7 +96,9 @@ int sophie_version(void);
  */
 int sophie_create_grid(int nx, int ny, int nz, double dx, double dt, sophie_grid **out);
 
-/* Free a grid and all its device memory; NULL is accepted. Waits for pending work. */
+/* Free a grid and all its device memory; NULL is accepted. Waits for pending
+ * work. A handle that is not live (e.g. destroyed already) gives EINVAL and
+ * nothing is freed. */
 int sophie_destroy_grid(sophie_grid *g);
 
 /*
@@ -358,6 +360,28 @@ int sophie_batch_info(sophie_batch *b, long long *cells, long long *work_items, 
                       int *zchunk);
 int sophie_batch_launch_count(sophie_batch *b, long long *launches);
 int sophie_batch_sync(sophie_batch *b);
+
+/*
+ * Diagnostics (no counterpart in the paper).
+ * sophie_check_guards: each field buffer sits between two guard regions
+ *   (one z slab of the six components, at least 1 MiB) filled with 0xA5 at
+ *   allocation; *bad_bytes gets the number of guard bytes that changed (0
+ *   unless a kernel wrote outside its buffer). Synchronises.
+ * sophie_batch_check_guards: the same for the guards around a batch's arena.
+ * sophie_selftest_wait_timeout: runs a kernel in which one thread waits, with
+ *   the bounded wait the step kernels use, for an mbarrier phase that never
+ *   completes (nothing arrives); the wait gives up after its 1 s limit and the
+ *   kernel sets the grid's error word and returns. *waited_ms gets how long
+ *   the wait took. Afterwards sophie_sync reports SOPHIE_ETIMEOUT once (and
+ *   clears the word); the grid stays usable.
+ * sophie_debug_fail_alloc: the n-th device allocation made by the library
+ *   after this call fails as if the device were out of memory (n = 0: off), to
+ *   test the ENOMEM paths.
+ */
+int sophie_check_guards(sophie_grid *g, long long *bad_bytes);
+int sophie_batch_check_guards(sophie_batch *b, long long *bad_bytes);
+int sophie_selftest_wait_timeout(sophie_grid *g, double *waited_ms);
+int sophie_debug_fail_alloc(int n);
 
 /* Message of the last error on this thread ("" if none). */
 const char *sophie_last_error(void);

@@ -14,10 +14,12 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <atomic>
 #include <mutex>
 #include <string>
 #include <thread>
 #include <unordered_map>
+#include <unordered_set>
 #include <vector>
 
 #include "../../include/sophie.h"
@@ -49,6 +51,33 @@ namespace sophie {
 int report_error(int code, const char* msg) {
   g_err = msg;
   return code;
+}
+
+namespace {
+std::atomic<long long> g_fail_alloc_at{0};  // > 0: the n-th next allocation fails
+std::mutex g_live_mu;
+std::unordered_set<const void*> g_live;  // handles returned by the create calls
+}  // namespace
+
+cudaError_t dev_malloc(void** p, size_t bytes) {
+  long long n = g_fail_alloc_at.load();
+  while (n > 0 && !g_fail_alloc_at.compare_exchange_weak(n, n - 1)) {
+  }
+  if (n == 1) {
+    *p = nullptr;
+    return cudaErrorMemoryAllocation;
+  }
+  return cudaMalloc(p, bytes);
+}
+
+void handle_register(const void* h) {
+  std::lock_guard<std::mutex> lk(g_live_mu);
+  g_live.insert(h);
+}
+
+bool handle_release(const void* h) {
+  std::lock_guard<std::mutex> lk(g_live_mu);
+  return g_live.erase(h) == 1;
 }
 }  // namespace sophie
 
@@ -123,6 +152,8 @@ struct sophie_grid {
   double dx = 0, dt = 0, S64 = 0;
   float S32 = 0;
   void* F[2] = {nullptr, nullptr};  // field buffers in storage format `fmt`
+  void* Fbase[2] = {nullptr, nullptr};  // their allocations: guard | buffer | guard
+  size_t fguard = 0;                    // guard bytes on each side
   int fmt = kF32;                   // StoreFmt
   int esz = 4;                      // bytes per stored value
   float sc[6] = {1, 1, 1, 1, 1, 1};  // stored = field * sc (2-byte formats)
@@ -231,8 +262,8 @@ int upload_materials(sophie_grid* g) {
     g->ecoef = nullptr;
     g->eeps = nullptr;
     g->exp_cap = 0;
-    if (cudaMalloc(&g->ecoef, nexp * 3 * sizeof(float2)) != cudaSuccess ||
-        cudaMalloc(&g->eeps, nexp * 3 * sizeof(double)) != cudaSuccess) {
+    if (dev_malloc((void**)&g->ecoef, nexp * 3 * sizeof(float2)) != cudaSuccess ||
+        dev_malloc((void**)&g->eeps, nexp * 3 * sizeof(double)) != cudaSuccess) {
       cudaGetLastError();
       return fail(SOPHIE_ENOMEM, "explicit material table allocation failed");
     }
@@ -264,7 +295,7 @@ int ensure_capacity(sophie_grid* g, long long need) {
       for (int m = 0; m < cap; ++m) h[s * cap + m] = (float)waveform(g->src[s], m, g->dt);
     float* dnew = nullptr;
     CUDA_TRY(cudaStreamSynchronize(g->stream));
-    if (cudaMalloc(&dnew, h.size() * 4) != cudaSuccess) {
+    if (dev_malloc((void**)&dnew, h.size() * 4) != cudaSuccess) {
       cudaGetLastError();
       return fail(SOPHIE_ENOMEM, "source table allocation failed");
     }
@@ -278,7 +309,7 @@ int ensure_capacity(sophie_grid* g, long long need) {
     while (cap < need) cap *= 2;
     float* dnew = nullptr;
     CUDA_TRY(cudaStreamSynchronize(g->stream));
-    if (cudaMalloc(&dnew, (size_t)kMaxProbes * cap * 4) != cudaSuccess) {
+    if (dev_malloc((void**)&dnew, (size_t)kMaxProbes * cap * 4) != cudaSuccess) {
       cudaGetLastError();
       return fail(SOPHIE_ENOMEM, "probe buffer allocation failed");
     }
@@ -382,6 +413,34 @@ int check_err_word(sophie_grid* g) {
   return SOPHIE_OK;
 }
 
+// Guard size around a field buffer: one z slab of six components (what an
+// off-by-one-plane access would touch), at least 1 MiB.
+size_t field_guard(const Dims& d, int esz) {
+  const size_t slab = (size_t)d.zstride * esz;
+  return (std::max(slab, (size_t)1 << 20) + 255) / 256 * 256;
+}
+
+// Allocate a field buffer of `bytes` between two guard regions filled with
+// kGuardByte; *F gets the buffer, *base the allocation.
+cudaError_t alloc_guarded(size_t bytes, size_t guard, void** F, void** base, cudaStream_t s) {
+  *F = *base = nullptr;
+  void* p = nullptr;
+  cudaError_t e = dev_malloc(&p, bytes + 2 * guard);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return e;
+  }
+  unsigned char* c = static_cast<unsigned char*>(p);
+  if ((e = cudaMemsetAsync(c, kGuardByte, guard, s)) != cudaSuccess ||
+      (e = cudaMemsetAsync(c + guard + bytes, kGuardByte, guard, s)) != cudaSuccess) {
+    cudaFree(p);
+    return e;
+  }
+  *base = p;
+  *F = c + guard;
+  return cudaSuccess;
+}
+
 void free_tape(Tape& t) {
   for (void* p : t.ck) cudaFree(p);
   t.ck.clear();
@@ -396,7 +455,7 @@ void free_grid(sophie_grid* g) {
   if (g->stream) cudaStreamSynchronize(g->stream);
   free_tape(g->tape);
   for (int b = 0; b < 2; ++b)
-    if (g->F[b]) cudaFree(g->F[b]);
+    if (g->Fbase[b]) cudaFree(g->Fbase[b]);
   if (g->mat) cudaFree(g->mat);
   if (g->mat_host) cudaFreeHost(g->mat_host);
   if (g->coef) cudaFree(g->coef);
@@ -532,20 +591,24 @@ int restore_fields(sophie_grid* g, int fmt, const float* sc) {
   const int esz = store_bytes(fmt);
   if (esz != g->esz) {
     const size_t bytes = (size_t)d.zstride * d.nz1 * esz;
+    const size_t guard = field_guard(d, esz);
     void* nb[2] = {nullptr, nullptr};
+    void* nbase[2] = {nullptr, nullptr};
     for (int b = 0; b < 2; ++b) {
-      if (cudaMalloc(&nb[b], bytes) != cudaSuccess) {
-        cudaGetLastError();
-        if (nb[0]) cudaFree(nb[0]);
+      if (alloc_guarded(bytes, guard, &nb[b], &nbase[b], g->stream) != cudaSuccess) {
+        if (nbase[0]) cudaFree(nbase[0]);
         return fail(SOPHIE_ENOMEM, "field buffer allocation failed");
       }
       CUDA_TRY(cudaMemsetAsync(nb[b], 0, bytes, g->stream));
     }
     CUDA_TRY(cudaStreamSynchronize(g->stream));
-    cudaFree(g->F[0]);
-    cudaFree(g->F[1]);
-    g->F[0] = nb[0];
-    g->F[1] = nb[1];
+    cudaFree(g->Fbase[0]);
+    cudaFree(g->Fbase[1]);
+    for (int b = 0; b < 2; ++b) {
+      g->F[b] = nb[b];
+      g->Fbase[b] = nbase[b];
+    }
+    g->fguard = guard;
     g->esz = esz;
   }
   g->fmt = fmt;
@@ -698,7 +761,7 @@ int sophie_create_grid(int nx, int ny, int nz, double dx, double dt, sophie_grid
   g->S32 = (float)g->S64;
   int rc = SOPHIE_OK;
   auto alloc = [&](void** p, size_t bytes) -> bool {
-    if (cudaMalloc(p, bytes) != cudaSuccess) {
+    if (dev_malloc(p, bytes) != cudaSuccess) {
       cudaGetLastError();
       rc = fail(SOPHIE_ENOMEM, "cudaMalloc of %zu bytes failed", bytes);
       return false;
@@ -713,7 +776,12 @@ int sophie_create_grid(int nx, int ny, int nz, double dx, double dt, sophie_grid
       break;
     }
     g->own_stream = true;
-    if (!alloc((void**)&g->F[0], fbytes) || !alloc((void**)&g->F[1], fbytes)) break;
+    g->fguard = field_guard(d, 4);
+    if (alloc_guarded(fbytes, g->fguard, &g->F[0], &g->Fbase[0], g->stream) != cudaSuccess ||
+        alloc_guarded(fbytes, g->fguard, &g->F[1], &g->Fbase[1], g->stream) != cudaSuccess) {
+      rc = fail(SOPHIE_ENOMEM, "field buffer allocation (%zu bytes + guards) failed", fbytes);
+      break;
+    }
     if (!alloc((void**)&g->mat, npts * 4)) break;
     if (!alloc((void**)&g->coef, kMaxClasses * sizeof(float2))) break;
     if (!alloc((void**)&g->eps_tab, kMaxClasses * sizeof(double))) break;
@@ -769,12 +837,63 @@ int sophie_create_grid(int nx, int ny, int nz, double dx, double dt, sophie_grid
     free_grid(g);
     return rc;
   }
+  handle_register(g);
   *out = g;
   return SOPHIE_OK;
 }
 
 int sophie_destroy_grid(sophie_grid* g) {
+  if (!g) return SOPHIE_OK;
+  if (!handle_release(g)) return fail(SOPHIE_EINVAL, "not a live grid (already destroyed?)");
   free_grid(g);
+  return SOPHIE_OK;
+}
+
+int sophie_check_guards(sophie_grid* g, long long* bad_bytes) {
+  if (!g || !bad_bytes) return fail(SOPHIE_EINVAL, "NULL argument");
+  unsigned long long* d = nullptr;
+  if (dev_malloc((void**)&d, sizeof(unsigned long long)) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(SOPHIE_ENOMEM, "guard check counter allocation failed");
+  }
+  cudaError_t e = cudaMemsetAsync(d, 0, sizeof(unsigned long long), g->stream);
+  const size_t fbytes = (size_t)g->d.zstride * g->d.nz1 * g->esz;
+  for (int b = 0; b < 2 && e == cudaSuccess; ++b) {
+    const unsigned char* base = static_cast<const unsigned char*>(g->Fbase[b]);
+    e = launch_guard_check(base, g->fguard, kGuardByte, d, g->stream);
+    if (e == cudaSuccess) e = launch_guard_check(base + g->fguard + fbytes, g->fguard, kGuardByte, d, g->stream);
+  }
+  unsigned long long h = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&h, d, sizeof(h), cudaMemcpyDeviceToHost, g->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
+  cudaFree(d);
+  if (e != cudaSuccess) return fail(SOPHIE_ECUDA, "guard check failed: %s", cudaGetErrorString(e));
+  g->launches += 4;
+  *bad_bytes = (long long)h;
+  return SOPHIE_OK;
+}
+
+int sophie_selftest_wait_timeout(sophie_grid* g, double* waited_ms) {
+  if (!g || !waited_ms) return fail(SOPHIE_EINVAL, "NULL argument");
+  unsigned long long* d = nullptr;
+  if (dev_malloc((void**)&d, sizeof(unsigned long long)) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(SOPHIE_ENOMEM, "self-test allocation failed");
+  }
+  cudaError_t e = launch_wait_timeout(g->err, d, g->stream);
+  unsigned long long ns = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&ns, d, sizeof(ns), cudaMemcpyDeviceToHost, g->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
+  cudaFree(d);
+  if (e != cudaSuccess) return fail(SOPHIE_ECUDA, "self-test launch failed: %s", cudaGetErrorString(e));
+  g->launches++;
+  *waited_ms = (double)ns * 1e-6;
+  return SOPHIE_OK;
+}
+
+int sophie_debug_fail_alloc(int n) {
+  if (n < 0) return fail(SOPHIE_EINVAL, "n must be >= 0");
+  g_fail_alloc_at.store(n);
   return SOPHIE_OK;
 }
 
@@ -1123,7 +1242,7 @@ int sophie_objective_forward(sophie_grid* g, int nsteps, int comp, int i, int j,
   CUDA_TRY(cudaStreamSynchronize(g->stream));
   while ((int)t.ck.size() < nseg) {
     void* p = nullptr;
-    if (cudaMalloc(&p, fbytes) != cudaSuccess) {
+    if (dev_malloc((void**)&p, fbytes) != cudaSuccess) {
       cudaGetLastError();
       free_tape(t);
       return fail(SOPHIE_ENOMEM, "checkpoint allocation (%d x %zu bytes) failed", nseg, fbytes);
@@ -1134,7 +1253,7 @@ int sophie_objective_forward(sophie_grid* g, int nsteps, int comp, int i, int j,
     if (t.samples) cudaFree(t.samples);
     t.samples = nullptr;
     t.samples_cap = 0;
-    if (cudaMalloc(&t.samples, (size_t)nsteps * 4) != cudaSuccess) {
+    if (dev_malloc((void**)&t.samples, (size_t)nsteps * 4) != cudaSuccess) {
       cudaGetLastError();
       return fail(SOPHIE_ENOMEM, "objective sample buffer allocation failed");
     }
@@ -1232,7 +1351,7 @@ int sophie_objective_grad_eps(sophie_grid* g, int i0, int j0, int k0, int ni, in
   auto grow = [&](void** p, size_t bytes) -> bool {
     if (*p) cudaFree(*p);
     *p = nullptr;
-    if (cudaMalloc(p, bytes) != cudaSuccess) {
+    if (dev_malloc(p, bytes) != cudaSuccess) {
       cudaGetLastError();
       *p = nullptr;
       return false;

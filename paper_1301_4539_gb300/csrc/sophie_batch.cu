@@ -72,7 +72,9 @@ struct sophie_batch {
   std::vector<size_t> fofs, fbytes;  // cavity c: buffer b at arena + fofs[c] + b * fbytes[c]
   std::vector<size_t> wofs;          // first material word of cavity c
   long long cells = 0;
-  unsigned char* arena = nullptr;
+  unsigned char* arena = nullptr;   // guard | cavities' buffers | guard
+  unsigned char* arena_base = nullptr;
+  size_t aguard = 0, abytes = 0;
   uint32_t* words = nullptr;
   float2* coef = nullptr;     // ncav x kMaxClasses
   double* eps_tab = nullptr;  // ncav x kMaxClasses
@@ -118,7 +120,7 @@ void free_batch(sophie_batch* b) {
   if (!b) return;
   if (b->stream) cudaStreamSynchronize(b->stream);
   drop_graph(b);
-  void* bufs[] = {b->arena, b->words, b->coef, b->eps_tab, b->ecoef, b->eeps, b->sval, b->d_desc,
+  void* bufs[] = {b->arena_base, b->words, b->coef, b->eps_tab, b->ecoef, b->eeps, b->sval, b->d_desc,
                   b->d_items, b->d_eitems, b->d_efirst, b->e_part, b->e_out, b->counter, b->err};
   for (void* p : bufs)
     if (p) cudaFree(p);
@@ -193,7 +195,7 @@ int build_items(sophie_batch* b, int tx, int ty, int zc) {
   drop_graph(b);
   if (b->d_items) cudaFree(b->d_items);
   b->d_items = nullptr;
-  if (cudaMalloc(&b->d_items, it.size() * sizeof(BatchItem)) != cudaSuccess) {
+  if (dev_malloc((void**)&b->d_items, it.size() * sizeof(BatchItem)) != cudaSuccess) {
     cudaGetLastError();
     return bfail(SOPHIE_ENOMEM, "work list allocation failed");
   }
@@ -221,7 +223,7 @@ int ensure_src_capacity(sophie_batch* b, long long need) {
     }
   BCUDA(cudaStreamSynchronize(b->stream));
   float* nv = nullptr;
-  if (cudaMalloc(&nv, h.size() * 4) != cudaSuccess) {
+  if (dev_malloc((void**)&nv, h.size() * 4) != cudaSuccess) {
     cudaGetLastError();
     return bfail(SOPHIE_ENOMEM, "source table allocation failed");
   }
@@ -347,7 +349,7 @@ int sophie_batch_create(int ncav, const int* dims, double dx, double dt, sophie_
   b->h_desc.resize(ncav);
   int rc = SOPHIE_OK;
   auto alloc = [&](void** p, size_t bytes) -> bool {
-    if (cudaMalloc(p, bytes) != cudaSuccess) {
+    if (dev_malloc(p, bytes) != cudaSuccess) {
       cudaGetLastError();
       rc = bfail(SOPHIE_ENOMEM, "cudaMalloc of %zu bytes failed", bytes);
       return false;
@@ -360,7 +362,15 @@ int sophie_batch_create(int ncav, const int* dims, double dx, double dt, sophie_
       break;
     }
     b->own_stream = true;
-    if (!alloc((void**)&b->arena, fb) || !alloc((void**)&b->words, wb * 4)) break;
+    b->aguard = (size_t)1 << 20;
+    b->abytes = fb;
+    if (!alloc((void**)&b->arena_base, fb + 2 * b->aguard) || !alloc((void**)&b->words, wb * 4)) break;
+    b->arena = b->arena_base + b->aguard;
+    if (cudaMemsetAsync(b->arena_base, kGuardByte, b->aguard, b->stream) != cudaSuccess ||
+        cudaMemsetAsync(b->arena + fb, kGuardByte, b->aguard, b->stream) != cudaSuccess) {
+      rc = bfail(SOPHIE_ECUDA, "cudaMemsetAsync failed");
+      break;
+    }
     if (!alloc((void**)&b->coef, (size_t)ncav * kMaxClasses * sizeof(float2))) break;
     if (!alloc((void**)&b->eps_tab, (size_t)ncav * kMaxClasses * sizeof(double))) break;
     if (!alloc((void**)&b->d_desc, (size_t)ncav * sizeof(CavityDesc))) break;
@@ -414,12 +424,35 @@ int sophie_batch_create(int ncav, const int* dims, double dx, double dt, sophie_
     free_batch(b);
     return rc;
   }
+  handle_register(b);
   *out = b;
   return SOPHIE_OK;
 }
 
 int sophie_batch_destroy(sophie_batch* b) {
+  if (!b) return SOPHIE_OK;
+  if (!handle_release(b)) return bfail(SOPHIE_EINVAL, "not a live batch (already destroyed?)");
   free_batch(b);
+  return SOPHIE_OK;
+}
+
+int sophie_batch_check_guards(sophie_batch* b, long long* bad_bytes) {
+  if (!b || !bad_bytes) return bfail(SOPHIE_EINVAL, "NULL argument");
+  unsigned long long* d = nullptr;
+  if (dev_malloc((void**)&d, sizeof(unsigned long long)) != cudaSuccess) {
+    cudaGetLastError();
+    return bfail(SOPHIE_ENOMEM, "guard check counter allocation failed");
+  }
+  cudaError_t e = cudaMemsetAsync(d, 0, sizeof(unsigned long long), b->stream);
+  if (e == cudaSuccess) e = launch_guard_check(b->arena_base, b->aguard, kGuardByte, d, b->stream);
+  if (e == cudaSuccess) e = launch_guard_check(b->arena + b->abytes, b->aguard, kGuardByte, d, b->stream);
+  unsigned long long h = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&h, d, sizeof(h), cudaMemcpyDeviceToHost, b->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  cudaFree(d);
+  if (e != cudaSuccess) return bfail(SOPHIE_ECUDA, "guard check failed: %s", cudaGetErrorString(e));
+  b->launches += 2;
+  *bad_bytes = (long long)h;
   return SOPHIE_OK;
 }
 
@@ -493,8 +526,8 @@ int sophie_batch_set_materials(sophie_batch* b, const float* eps, const float* s
     b->ecoef = nullptr;
     b->eeps = nullptr;
     b->ecap = 0;
-    if (cudaMalloc(&b->ecoef, ne * 3 * sizeof(float2)) != cudaSuccess ||
-        cudaMalloc(&b->eeps, ne * 3 * sizeof(double)) != cudaSuccess) {
+    if (dev_malloc((void**)&b->ecoef, ne * 3 * sizeof(float2)) != cudaSuccess ||
+        dev_malloc((void**)&b->eeps, ne * 3 * sizeof(double)) != cudaSuccess) {
       cudaGetLastError();
       return bfail(SOPHIE_ENOMEM, "explicit material tables (%zu entries) allocation failed", ne);
     }
@@ -639,9 +672,7 @@ int sophie_batch_get_fields(sophie_batch* b, int cav, int comp, float* host) {
 
 int sophie_batch_reset(sophie_batch* b) {
   if (!b) return bfail(SOPHIE_EINVAL, "NULL batch");
-  size_t total = 0;
-  for (int c = 0; c < b->ncav; ++c) total = std::max(total, b->fofs[c] + 2 * b->fbytes[c]);
-  BCUDA(cudaMemsetAsync(b->arena, 0, total, b->stream));
+  BCUDA(cudaMemsetAsync(b->arena, 0, b->abytes, b->stream));
   b->n = 0;
   b->cur = 0;
   return SOPHIE_OK;

@@ -205,6 +205,21 @@ cudaError_t launch_batch_energy(const CavityDesc* descs, const EnergyItem* items
                                 cudaStream_t s);
 // Set the thread's last-error message (sophie_last_error) and return code.
 int report_error(int code, const char* msg);
+
+// cudaMalloc, except that a debug hook (sophie_debug_fail_alloc) can make the
+// n-th following call fail as if the device were out of memory.
+cudaError_t dev_malloc(void** p, size_t bytes);
+// Registry of live handles (grids and batches), so that destroying a handle
+// twice is reported instead of freeing freed memory.
+void handle_register(const void* h);
+bool handle_release(const void* h);
+// Field buffers sit between two guard regions of kGuardByte (guard bytes
+// each side); launch_guard_check counts the changed bytes of a region.
+constexpr unsigned char kGuardByte = 0xA5;
+cudaError_t launch_guard_check(const void* p, size_t n, unsigned char pattern, unsigned long long* bad,
+                               cudaStream_t s);
+// Bounded-wait self-test kernel (selftest.cu): sets code 32 in *err.
+cudaError_t launch_wait_timeout(int* err, unsigned long long* waited_ns, cudaStream_t s);
 // amp * w((n + 1/2) dt) of a soft source (kind 0: Gaussian-modulated sine,
 // kind 1: Gaussian pulse; bw = FWHM of the envelope's amplitude spectrum).
 double source_waveform(int kind, double amp, double f0, double bw, double t0, double dt, long long n);

@@ -72,6 +72,10 @@ SIGNATURES = {
                                ctypes.POINTER(_I), ctypes.POINTER(_I)]),
     "sophie_batch_launch_count": (_I, [_P, ctypes.POINTER(_LL)]),
     "sophie_batch_sync": (_I, [_P]),
+    "sophie_check_guards": (_I, [_P, ctypes.POINTER(_LL)]),
+    "sophie_batch_check_guards": (_I, [_P, ctypes.POINTER(_LL)]),
+    "sophie_selftest_wait_timeout": (_I, [_P, ctypes.POINTER(_D)]),
+    "sophie_debug_fail_alloc": (_I, [_I]),
     "sophie_last_error": (ctypes.c_char_p, []),
 }
 
@@ -333,6 +337,12 @@ class Grid:
     def profile_read(self, kernel):
         return sophie_profile_read(self.h, kernel)
 
+    def check_guards(self):
+        return sophie_check_guards(self.h)
+
+    def selftest_wait_timeout(self):
+        return sophie_selftest_wait_timeout(self.h)
+
     def objective_forward(self, nsteps, comp, i, j, k, checkpoint_every=0):
         return sophie_objective_forward(self.h, nsteps, comp, i, j, k, checkpoint_every)
 
@@ -341,6 +351,29 @@ class Grid:
 
     def objective_release(self):
         sophie_objective_release(self.h)
+
+
+# ---- diagnostics -------------------------------------------------------------
+def sophie_check_guards(g: int) -> int:
+    n = _LL()
+    _chk(load().sophie_check_guards(g, ctypes.byref(n)))
+    return n.value
+
+
+def sophie_batch_check_guards(b: int) -> int:
+    n = _LL()
+    _chk(load().sophie_batch_check_guards(b, ctypes.byref(n)))
+    return n.value
+
+
+def sophie_selftest_wait_timeout(g: int) -> float:
+    ms = _D()
+    _chk(load().sophie_selftest_wait_timeout(g, ctypes.byref(ms)))
+    return ms.value
+
+
+def sophie_debug_fail_alloc(n: int) -> None:
+    _chk(load().sophie_debug_fail_alloc(n))
 
 
 # ---- batched cavities -------------------------------------------------------
@@ -496,6 +529,9 @@ class Batch:
 
     def launch_count(self):
         return sophie_batch_launch_count(self.h)
+
+    def check_guards(self):
+        return sophie_batch_check_guards(self.h)
 
     def sync(self):
         sophie_batch_sync(self.h)
