@@ -356,6 +356,12 @@ def run_ours(args):
         g_prec[0] = so.FP32
         g.configure(temporal_k=1, precision=so.FP32)
     variants["speedup_vs_plain"] = {k: v / variants["k1"] for k, v in variants.items() if k != "speedup_vs_plain"}
+    # the plain (one step per launch) kernel's own roofline on this workload
+    plain_roof = {"kernel": "yee_plain", "gcell_per_s": variants["k1"],
+                  "achieved_GBs_52B": variants["k1"] * (FIELD_BYTES + MAT_BYTES),
+                  "frac_52B": variants["k1"] * (FIELD_BYTES + MAT_BYTES) / peaks()[0],
+                  "frac_48B_fields_only": variants["k1"] * FIELD_BYTES / peaks()[0],
+                  "traffic": NCU_TRAFFIC.get(("yee_plain", 1)), "peak": peaks()[0], "unit": "GB/s"}
     g.configure(temporal_k=0 if not args.k else K, precision=so.FP32)
     if not args.k:
         g.autotune()
@@ -390,7 +396,7 @@ def run_ours(args):
                            "grid": [n, n, n], "time_steps_per_bench_step": args.tsteps,
                            "temporal_k": K, "autotuned": not args.k, "parallelism": f"replicas x{world}",
                            "l2": "inputs larger than L2 (no flush)"},
-                "roofline": roof, "variants_gcells": variants, "cpu_baseline": cpu, "e2e": e2e,
+                "roofline": roof, "plain_roofline": plain_roof, "variants_gcells": variants, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": launches, "clocks": clocks, "energy_J": energy, "adjoint": adjoint,
                 "batch": batch, "precision_768": precision_768}
         print(json.dumps(line), flush=True)

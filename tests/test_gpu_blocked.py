@@ -17,7 +17,9 @@ from paper_1301_4539_gb300 import workloads as wl
 
 pytestmark = pytest.mark.gpu
 
-SIZES = [(5, 6, 7), (17, 33, 9), (40, 21, 35), (70, 9, 20), (130, 70, 50), (61, 29, 3)]
+# (37, 116, 21) and (50, 200, 13): many y tiles, probes next to both y walls.
+SIZES = [(5, 6, 7), (17, 33, 9), (40, 21, 35), (70, 9, 20), (130, 70, 50), (61, 29, 3), (37, 116, 21),
+         (50, 200, 13)]
 
 
 @pytest.mark.parametrize("K", [2, 3, 4])
@@ -32,6 +34,8 @@ def test_blocked_equals_oracle(oracle_mod, sophie, K, n3):
         srcs.append((1, max(1, nx // 3), 0, max(1, nz // 2), 7.0, f0, bw, 6e-12, 1))
     prbs = wl.probe_edges(nx, ny, nz, 6, seed=nx + K) + [(3, 0, 0, 0), (4, nx - 1, ny, max(0, nz - 1)),
                                                          (5, 0, 0, nz)]
+    if ny > 8 and nx > 2 and nz > 2:  # rows next to the y walls (inside the wall tiles)
+        prbs += [(0, nx // 2, ny - 1, nz // 2), (2, nx // 2, ny - 2, nz // 2), (1, 1, 0, 1), (3, nx // 2, ny - 1, 1)]
     g, o = make_pair(oracle_mod, nx, ny, nz, eps, sig, f, srcs, prbs, temporal_k=K)
     steps = 3 * K + 2  # blocked launches plus a plain remainder
     g.step(steps)
