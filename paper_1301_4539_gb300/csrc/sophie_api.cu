@@ -23,17 +23,19 @@
 #include <vector>
 
 #include "../../include/sophie.h"
+#include "grid_state.h"
 #include "sophie_internal.h"
 #include "yee_store.cuh"
 
 using namespace sophie;
+using namespace sophie::grid;
 
 namespace {
-
-constexpr double kC0 = 299792458.0;
-constexpr double kEps0 = 8.8541878128e-12;
-
 thread_local std::string g_err;
+}  // namespace
+
+namespace sophie {
+namespace grid {
 
 int fail(int code, const char* fmt, ...) {
   char buf[512];
@@ -45,9 +47,8 @@ int fail(int code, const char* fmt, ...) {
   return code;
 }
 
-}  // namespace
+}  // namespace grid
 
-namespace sophie {
 int report_error(int code, const char* msg) {
   g_err = msg;
   return code;
@@ -81,126 +82,9 @@ bool handle_release(const void* h) {
 }
 }  // namespace sophie
 
-namespace {
 
-#define CUDA_TRY(call)                                                              \
-  do {                                                                              \
-    cudaError_t e_ = (call);                                                        \
-    if (e_ != cudaSuccess)                                                          \
-      return fail(SOPHIE_ECUDA, "%s failed: %s", #call, cudaGetErrorString(e_));    \
-  } while (0)
-
-struct Source {
-  int comp, i, j, k, kind;
-  double amp, f0, bw, t0;
-  long long pos;
-};
-
-struct Probe {
-  int comp, i, j, k;
-  long long pos;
-  // Index on a plane no kernel updates (i == nx, j == ny or k == nz): a PEC
-  // edge or a wall-normal face whose value never changes. Its samples are
-  // filled from the field at read time instead of by the step kernels.
-  bool fixed;
-  long long n_added;
-};
-
-struct ProfEntry {
-  int kernel;
-  cudaEvent_t a, b;
-};
-
-// Recorded forward pass of a probe objective (sophie_objective_forward) and
-// the workspace of its reverse sweep (sophie_objective_grad_eps).
-struct Tape {
-  bool valid = false;
-  long long gen = -1;  // grid generation the record belongs to
-  long long n0 = 0;    // first step of the recorded pass
-  int N = 0, K = 50;   // steps, checkpoint interval
-  int comp = 2;        // objective component and index point
-  long long pt = 0;
-  std::vector<void*> ck;     // states at n0 + s*K, s = 0 .. ceil(N/K)-1
-  float* samples = nullptr;  // objective samples f^{n0+1} .. f^{n0+N}
-  int samples_cap = 0;
-  void* R[2] = {nullptr, nullptr};  // segment recompute (float fields)
-  CUtensorMap tmR[2];
-  CUtensorMap tmRM;
-  void* L[2] = {nullptr, nullptr};  // adjoint fields
-  CUtensorMap tmL[2];
-  int* ecomp = nullptr;             // design edges: component, index point
-  long long* ept = nullptr;
-  float* etr = nullptr;  // [K][nedge] e^n on the design edges
-  float* ctr = nullptr;  // [K][nedge] B h^{n+1/2} + s on the design edges
-  double* gcb = nullptr;  // dJ/dCb, dJ/dCa per design edge
-  double* gca = nullptr;
-  int edge_cap = 0, tr_cap = 0;
-};
-
-}  // namespace
-
-struct sophie_grid {
-  Dims d{};
-  CUtensorMap tmF[2];  // TMA maps of the two field buffers
-  CUtensorMap tmM;     // TMA map of the material words
-  PlainTiling ptile{};
-  CUtensorMap tmFB[2];  // TMA maps with the temporally blocked kernel's box
-  CUtensorMap tmMB;
-  BlockedTiling btile{};
-  int num_sms = 0;
-  bool use_simple = false;  // tile_x == 32: untiled-load reference kernel
-  double dx = 0, dt = 0, S64 = 0;
-  float S32 = 0;
-  void* F[2] = {nullptr, nullptr};  // field buffers in storage format `fmt`
-  void* Fbase[2] = {nullptr, nullptr};  // their allocations: guard | buffer | guard
-  size_t fguard = 0;                    // guard bytes on each side
-  int fmt = kF32;                   // StoreFmt
-  int esz = 4;                      // bytes per stored value
-  float sc[6] = {1, 1, 1, 1, 1, 1};  // stored = field * sc (2-byte formats)
-  int cur = 0;
-  uint32_t* mat = nullptr;     // device material words
-  uint32_t* mat_host = nullptr;  // pinned staging for uploads
-  float2* coef = nullptr;      // device class table (Ca, Cb)
-  double* eps_tab = nullptr;   // device class table eps_r(edge)
-  std::vector<float2> coef_h;
-  std::vector<double> eps_h;
-  std::vector<float2> ecoef_h;    // explicit points: (Ca, Cb) of ex, ey, ez
-  std::vector<double> eeps_h;     // explicit points: eps_r of ex, ey, ez
-  std::vector<double> sig_h;      // sigma(edge) of each class (host; gradients)
-  std::vector<double> esig_h;     // explicit points: sigma of ex, ey, ez
-  float2* ecoef = nullptr;        // device copies
-  double* eeps = nullptr;
-  size_t exp_cap = 0;
-  cudaEvent_t mat_upload_done = nullptr;
-  std::vector<Source> src;
-  std::vector<Probe> prb;
-  float* sval = nullptr;  // device [kMaxSources][scap]
-  int scap = 0;
-  float* pbuf = nullptr;  // device [kMaxProbes][pcap]
-  int pcap = 0;
-  long long n = 0;
-  cudaStream_t stream = nullptr;
-  bool own_stream = false;
-  int temporal_k = 0;  // 0: chosen by the autotuner at the first step
-  bool tuned = false;  // autotuner result valid for the current format
-  int tuned_k = 2;
-  int precision = SOPHIE_FP32;
-  double* e_partials = nullptr;
-  double* e_out = nullptr;
-  int e_blocks = 0;
-  int* err = nullptr;
-  long long launches = 0;
-  bool prof = false;
-  std::vector<ProfEntry> prof_live;
-  std::vector<cudaEvent_t> ev_pool;
-  long long prof_count[4] = {0, 0, 0, 0};
-  double prof_ms[4] = {0, 0, 0, 0};
-  long long gen = 0;       // bumped by every change of fields, materials or sources
-  bool obj_rec = false;    // the step kernels also sample the objective point
-  Tape tape;
-};
-
-namespace {
+namespace sophie {
+namespace grid {
 
 long long point_index(const Dims& d, int i, int j, int k) {
   return ((long long)k * d.ny1 + j) * d.nxp + i;
@@ -225,6 +109,11 @@ bool comp_valid(const Dims& d, int c, int i, int j, int k) {
     default: return i < d.nx && j < d.ny;
   }
 }
+
+}  // namespace grid
+}  // namespace sophie
+
+namespace {
 
 // Fill g->mat_host and the host tables for per-cell eps/sigma (nullptr =
 // vacuum); sources and probes flag their points.
@@ -285,6 +174,10 @@ double waveform(const Source& s, long long n, double dt) {
 }
 
 // Make the source table cover steps [0, need) and the probe buffer [0, need).
+}  // namespace
+
+namespace sophie {
+namespace grid {
 int ensure_capacity(sophie_grid* g, long long need) {
   if (need > (1ll << 30)) return fail(SOPHIE_EINVAL, "step count too large");
   if (need > g->scap) {
@@ -324,6 +217,10 @@ int ensure_capacity(sophie_grid* g, long long need) {
   }
   return SOPHIE_OK;
 }
+}  // namespace grid
+}  // namespace sophie
+
+namespace {
 
 // Rebuild one source's waveform column after it was added.
 int refresh_source_table(sophie_grid* g, int s) {
@@ -335,6 +232,10 @@ int refresh_source_table(sophie_grid* g, int s) {
   return SOPHIE_OK;
 }
 
+}  // namespace
+
+namespace sophie {
+namespace grid {
 cudaEvent_t prof_event(sophie_grid* g) {
   if (!g->ev_pool.empty()) {
     cudaEvent_t e = g->ev_pool.back();
@@ -412,6 +313,10 @@ int check_err_word(sophie_grid* g) {
   }
   return SOPHIE_OK;
 }
+}  // namespace grid
+}  // namespace sophie
+
+namespace {
 
 // Guard size around a field buffer: one z slab of six components (what an
 // off-by-one-plane access would touch), at least 1 MiB.
@@ -441,6 +346,10 @@ cudaError_t alloc_guarded(size_t bytes, size_t guard, void** F, void** base, cud
   return cudaSuccess;
 }
 
+}  // namespace
+
+namespace sophie {
+namespace grid {
 void free_tape(Tape& t) {
   for (void* p : t.ck) cudaFree(p);
   t.ck.clear();
@@ -449,6 +358,10 @@ void free_tape(Tape& t) {
     if (p) cudaFree(p);
   t = Tape{};
 }
+}  // namespace grid
+}  // namespace sophie
+
+namespace {
 
 void free_grid(sophie_grid* g) {
   if (!g) return;
@@ -1210,296 +1123,6 @@ int sophie_profile_read(sophie_grid* g, int kernel, long long* launches, double*
   if (rc) return rc;
   *launches = g->prof_count[kernel];
   *ms = g->prof_ms[kernel];
-  return SOPHIE_OK;
-}
-
-int sophie_objective_release(sophie_grid* g) {
-  if (!g) return fail(SOPHIE_EINVAL, "NULL grid");
-  CUDA_TRY(cudaStreamSynchronize(g->stream));
-  free_tape(g->tape);
-  return SOPHIE_OK;
-}
-
-int sophie_objective_forward(sophie_grid* g, int nsteps, int comp, int i, int j, int k, int checkpoint_every,
-                             double* J) {
-  if (!g || !J) return fail(SOPHIE_EINVAL, "NULL argument");
-  if (nsteps < 1) return fail(SOPHIE_EINVAL, "nsteps must be >= 1");
-  if (checkpoint_every < 0) return fail(SOPHIE_EINVAL, "checkpoint_every must be >= 0");
-  if (comp < 0 || comp > 5 || !comp_valid(g->d, comp, i, j, k))
-    return fail(SOPHIE_EINVAL, "objective point (%d,%d,%d) outside comp %d's range", i, j, k, comp);
-  if (i == g->d.nx || j == g->d.ny || k == g->d.nz)
-    return fail(SOPHIE_EINVAL, "objective point on a plane no step updates");
-  if (g->fmt != kF32) return fail(SOPHIE_ENOTSUP, "gradients need float field storage");
-  if ((int)g->prb.size() >= kMaxProbes) return fail(SOPHIE_ENOTSUP, "all %d probe slots are in use", kMaxProbes);
-  Tape& t = g->tape;
-  t.valid = false;
-  const int K = checkpoint_every == 0 ? 50 : checkpoint_every;
-  const int nseg = (nsteps + K - 1) / K;
-  const Dims& d = g->d;
-  const size_t fbytes = (size_t)d.zstride * d.nz1 * 4;
-  int rc = ensure_capacity(g, g->n + nsteps);
-  if (rc) return rc;
-  CUDA_TRY(cudaStreamSynchronize(g->stream));
-  while ((int)t.ck.size() < nseg) {
-    void* p = nullptr;
-    if (dev_malloc((void**)&p, fbytes) != cudaSuccess) {
-      cudaGetLastError();
-      free_tape(t);
-      return fail(SOPHIE_ENOMEM, "checkpoint allocation (%d x %zu bytes) failed", nseg, fbytes);
-    }
-    t.ck.push_back(p);
-  }
-  if (t.samples_cap < nsteps) {
-    if (t.samples) cudaFree(t.samples);
-    t.samples = nullptr;
-    t.samples_cap = 0;
-    if (dev_malloc((void**)&t.samples, (size_t)nsteps * 4) != cudaSuccess) {
-      cudaGetLastError();
-      return fail(SOPHIE_ENOMEM, "objective sample buffer allocation failed");
-    }
-    t.samples_cap = nsteps;
-  }
-  t.comp = comp;
-  t.pt = point_index(d, i, j, k);
-  t.n0 = g->n;
-  t.N = nsteps;
-  t.K = K;
-  if (launch_or_flag(g->mat, t.pt, kPrbFlag, g->stream) != cudaSuccess)
-    return fail(SOPHIE_ECUDA, "flag launch failed");
-  g->launches++;
-  const int slot = (int)g->prb.size();
-  g->obj_rec = true;
-  for (int sg = 0; sg < nseg; ++sg) {
-    const cudaError_t e = cudaMemcpyAsync(t.ck[sg], g->F[g->cur], fbytes, cudaMemcpyDeviceToDevice, g->stream);
-    if (e != cudaSuccess) {
-      g->obj_rec = false;
-      return fail(SOPHIE_ECUDA, "checkpoint copy failed: %s", cudaGetErrorString(e));
-    }
-    rc = sophie_step(g, std::min(K, nsteps - sg * K));
-    if (rc) {
-      g->obj_rec = false;
-      return rc;
-    }
-  }
-  g->obj_rec = false;
-  float* slot_p = g->pbuf + (size_t)slot * g->pcap + t.n0;
-  CUDA_TRY(cudaMemcpyAsync(t.samples, slot_p, (size_t)nsteps * 4, cudaMemcpyDeviceToDevice, g->stream));
-  CUDA_TRY(cudaMemsetAsync(slot_p, 0, (size_t)nsteps * 4, g->stream));
-  std::vector<float> f((size_t)nsteps);
-  CUDA_TRY(cudaMemcpyAsync(f.data(), t.samples, (size_t)nsteps * 4, cudaMemcpyDeviceToHost, g->stream));
-  rc = check_err_word(g);
-  if (rc) return rc;
-  double acc = 0.0;
-  for (int n = 0; n < nsteps; ++n) acc += (double)f[n] * (double)f[n];
-  *J = g->dt * acc;
-  if (!std::isfinite(*J)) return fail(SOPHIE_ENONFINITE, "objective is not finite");
-  t.valid = true;
-  t.gen = g->gen;
-  return SOPHIE_OK;
-}
-
-int sophie_objective_grad_eps(sophie_grid* g, int i0, int j0, int k0, int ni, int nj, int nk, double* grad) {
-  if (!g || !grad) return fail(SOPHIE_EINVAL, "NULL argument");
-  Tape& t = g->tape;
-  if (!t.valid || t.gen != g->gen)
-    return fail(SOPHIE_EINVAL, "no objective recorded since the last change of the grid");
-  const Dims& d = g->d;
-  if (ni < 1 || nj < 1 || nk < 1 || i0 < 0 || j0 < 0 || k0 < 0 || i0 + ni > d.nx || j0 + nj > d.ny ||
-      k0 + nk > d.nz)
-    return fail(SOPHIE_EINVAL, "design box outside the grid's cells");
-  // Design edges: interior edges of the box's cells; box index -> edge index.
-  const int ext[3][3] = {{ni, nj + 1, nk + 1}, {ni + 1, nj, nk + 1}, {ni + 1, nj + 1, nk}};
-  std::vector<int> map[3];
-  std::vector<int> hcomp;
-  std::vector<long long> hpt;
-  std::vector<double> dcb, dca;
-  std::vector<float> cbf;  // the float Cb the step kernels use on each design edge
-  for (int c = 0; c < 3; ++c) {
-    map[c].assign((size_t)ext[c][0] * ext[c][1] * ext[c][2], -1);
-    for (int kk = 0; kk < ext[c][2]; ++kk)
-      for (int jj = 0; jj < ext[c][1]; ++jj)
-        for (int ii = 0; ii < ext[c][0]; ++ii) {
-          const int i = i0 + ii, j = j0 + jj, k = k0 + kk;
-          if (!e_edge_interior(d, c, i, j, k)) continue;
-          const long long pt = point_index(d, i, j, k);
-          const uint32_t w = g->mat_host[pt];
-          const float cb_edge = (w & kExpFlag) ? g->ecoef_h[3 * (size_t)(w >> 3) + c].y : g->coef_h[cls_of(w, c)].y;
-          if (cb_edge == 0.f) continue;  // edge of a conducting cell: no eps dependence
-          double e, sg;
-          if (w & kExpFlag) {
-            const size_t q = w >> 3;
-            e = g->eeps_h[3 * q + c];
-            sg = g->esig_h[3 * q + c];
-          } else {
-            e = g->eps_h[cls_of(w, c)];
-            sg = g->sig_h[cls_of(w, c)];
-          }
-          // Cb = (S/e)/(1+beta), Ca = (1-beta)/(1+beta), beta = sigma dt/(2 eps0 e)
-          const double beta = (sg * g->dt) / (2.0 * kEps0 * e);
-          const double cb = (g->S64 / e) / (1.0 + beta);
-          map[c][((size_t)kk * ext[c][1] + jj) * ext[c][0] + ii] = (int)hpt.size();
-          cbf.push_back(cb_edge);
-          hcomp.push_back(c);
-          hpt.push_back(pt);
-          dcb.push_back(-cb / (e * (1.0 + beta)));
-          dca.push_back(2.0 * beta / (e * (1.0 + beta) * (1.0 + beta)));
-        }
-  }
-  const int nedge = (int)hpt.size();
-  const size_t fbytes = (size_t)d.zstride * d.nz1 * 4;
-  CUDA_TRY(cudaStreamSynchronize(g->stream));
-  auto grow = [&](void** p, size_t bytes) -> bool {
-    if (*p) cudaFree(*p);
-    *p = nullptr;
-    if (dev_malloc(p, bytes) != cudaSuccess) {
-      cudaGetLastError();
-      *p = nullptr;
-      return false;
-    }
-    return true;
-  };
-  if (!t.R[0]) {
-    for (int b = 0; b < 2; ++b)
-      if (!grow(&t.R[b], fbytes) || !grow(&t.L[b], fbytes))
-        return fail(SOPHIE_ENOMEM, "adjoint workspace allocation failed");
-    // Wall and padding entries are never written by the step kernels: they
-    // must start (and stay) zero in both recompute buffers.
-    CUDA_TRY(cudaMemsetAsync(t.R[0], 0, fbytes, g->stream));
-    CUDA_TRY(cudaMemsetAsync(t.R[1], 0, fbytes, g->stream));
-    for (int b = 0; b < 2; ++b)
-      if (!encode_maps(d, kF32, t.R[b], g->mat, plain_box_x(kF32), plain_box_y(), &t.tmR[b], &t.tmRM) ||
-          !encode_maps(d, kF32, t.L[b], nullptr, plain_box_x(kF32), plain_box_y(), &t.tmL[b], nullptr))
-        return fail(SOPHIE_ECUDA, "cuTensorMapEncodeTiled failed");
-  }
-  if (nedge > t.edge_cap) {
-    if (!grow((void**)&t.ecomp, (size_t)nedge * 4) || !grow((void**)&t.ept, (size_t)nedge * 8) ||
-        !grow((void**)&t.gcb, (size_t)nedge * 8) || !grow((void**)&t.gca, (size_t)nedge * 8)) {
-      t.edge_cap = 0;
-      return fail(SOPHIE_ENOMEM, "design edge table allocation failed");
-    }
-    t.edge_cap = nedge;
-    t.tr_cap = 0;
-  }
-  if ((long long)nedge * t.K > t.tr_cap) {
-    if (!grow((void**)&t.etr, (size_t)nedge * t.K * 4) || !grow((void**)&t.ctr, (size_t)nedge * t.K * 4)) {
-      t.tr_cap = 0;
-      return fail(SOPHIE_ENOMEM, "design edge trace allocation failed");
-    }
-    t.tr_cap = nedge * t.K;
-  }
-  if (nedge) {
-    CUDA_TRY(cudaMemcpyAsync(t.ecomp, hcomp.data(), (size_t)nedge * 4, cudaMemcpyHostToDevice, g->stream));
-    CUDA_TRY(cudaMemcpyAsync(t.ept, hpt.data(), (size_t)nedge * 8, cudaMemcpyHostToDevice, g->stream));
-    CUDA_TRY(cudaMemsetAsync(t.gcb, 0, (size_t)nedge * 8, g->stream));
-    CUDA_TRY(cudaMemsetAsync(t.gca, 0, (size_t)nedge * 8, g->stream));
-  }
-  CUDA_TRY(cudaMemsetAsync(t.L[0], 0, fbytes, g->stream));
-  CUDA_TRY(cudaMemsetAsync(t.L[1], 0, fbytes, g->stream));
-  // Reverse sweep. Default form: in the variables u = Cb * l_e, mu = -S * l_h
-  // the reverse step is the forward step itself with the same coefficients
-  // (mu' = mu + S A u, u' = Ca u + Cb B mu'), so it runs on the forward step
-  // kernel with sources and probes off; the objective's direct term enters as
-  // u += Cb 2dt f (E component) or mu += -S 2dt f (H component), and the
-  // accumulated sums of u * (bracket) and u * e are divided by Cb at the end.
-  // SOPHIE_ADJOINT=direct runs the literal transposed step (yee_adjoint.cu)
-  // on (l_e, l_h) instead (a cross-check; same gradient up to rounding).
-  const char* am = getenv("SOPHIE_ADJOINT");
-  const bool direct = am && strcmp(am, "direct") == 0;
-  double obj_scale = 1.0;
-  if (!direct) {
-    if (t.comp < 3) {
-      const uint32_t w = g->mat_host[t.pt];
-      obj_scale = (w & kExpFlag) ? g->ecoef_h[3 * (size_t)(w >> 3) + t.comp].y : g->coef_h[cls_of(w, t.comp)].y;
-      if (!e_edge_interior(d, t.comp, (int)(t.pt % d.nxp), (int)(t.pt / d.nxp % d.ny1), (int)(t.pt / d.plane)))
-        obj_scale = 0.0;
-    } else {
-      obj_scale = -(double)g->S32;
-    }
-  }
-  const double two_dt = 2.0 * g->dt * obj_scale;
-  int lc = 0;
-  const int nseg = (t.N + t.K - 1) / t.K;
-  for (int sg = nseg - 1; sg >= 0; --sg) {
-    const long long ns = t.n0 + (long long)sg * t.K;
-    const int len = std::min(t.K, t.N - sg * t.K);
-    // Recompute the segment from its checkpoint, keeping the design-edge values.
-    CUDA_TRY(cudaMemcpyAsync(t.R[0], t.ck[sg], fbytes, cudaMemcpyDeviceToDevice, g->stream));
-    for (int m = 0; m < len; ++m) {
-      StepArgs a = make_step_args(g);
-      a.fin = t.R[m & 1];
-      a.fout = t.R[(m + 1) & 1];
-      a.n0 = ns + m;
-      a.prb.n = 0;
-      cudaEvent_t ea = g->prof ? prof_event(g) : nullptr, eb = g->prof ? prof_event(g) : nullptr;
-      if (ea) cudaEventRecord(ea, g->stream);
-      cudaError_t e = launch_step_plain(a, t.tmR[m & 1], t.tmRM, g->ptile, g->stream);
-      if (eb) {
-        cudaEventRecord(eb, g->stream);
-        g->prof_live.push_back({SOPHIE_KERNEL_PLAIN, ea, eb});
-      }
-      if (e == cudaSuccess)
-        e = launch_gather(a, t.ecomp, t.ept, nedge, t.etr + (size_t)m * nedge, t.ctr + (size_t)m * nedge, g->stream);
-      if (e != cudaSuccess) return fail(SOPHIE_ECUDA, "recompute launch failed: %s", cudaGetErrorString(e));
-      g->launches += nedge ? 2 : 1;
-    }
-    if (g->prof_live.size() > 20000) {
-      int rc = prof_drain(g);
-      if (rc) return rc;
-    }
-    // Reverse sweep over the segment.
-    for (int m = len - 1; m >= 0; --m) {
-      const long long n = ns + m;
-      float* l = static_cast<float*>(t.L[lc]);
-      cudaError_t e = launch_add_objective(l, d, t.comp, t.pt, t.samples + (n - t.n0), two_dt, g->stream);
-      if (e == cudaSuccess)
-        e = launch_grad_accum(l, d, t.ecomp, t.ept, nedge, t.etr + (size_t)m * nedge, t.ctr + (size_t)m * nedge,
-                              t.gcb, t.gca, g->stream);
-      if (e == cudaSuccess) {
-        StepArgs a = make_step_args(g);
-        a.fin = t.L[lc];
-        a.fout = t.L[1 - lc];
-        a.n0 = n;
-        a.prb.n = 0;
-        a.src.n = 0;
-        cudaEvent_t ea = g->prof ? prof_event(g) : nullptr, eb = g->prof ? prof_event(g) : nullptr;
-        if (ea) cudaEventRecord(ea, g->stream);
-        e = direct ? launch_adj_step(a, g->stream) : launch_step_plain(a, t.tmL[lc], t.tmRM, g->ptile, g->stream);
-        if (eb) {
-          cudaEventRecord(eb, g->stream);
-          g->prof_live.push_back({SOPHIE_KERNEL_ADJOINT, ea, eb});
-        }
-      }
-      if (e != cudaSuccess) return fail(SOPHIE_ECUDA, "adjoint launch failed: %s", cudaGetErrorString(e));
-      g->launches += nedge ? 3 : 2;
-      lc = 1 - lc;
-    }
-  }
-  std::vector<double> gcb((size_t)nedge), gca((size_t)nedge);
-  if (nedge) {
-    CUDA_TRY(cudaMemcpyAsync(gcb.data(), t.gcb, (size_t)nedge * 8, cudaMemcpyDeviceToHost, g->stream));
-    CUDA_TRY(cudaMemcpyAsync(gca.data(), t.gca, (size_t)nedge * 8, cudaMemcpyDeviceToHost, g->stream));
-  }
-  int rc = check_err_word(g);
-  if (rc) return rc;
-  // Chain rule to cells: eps_r(edge) is the mean of its four cells.
-  for (int kk = 0; kk < nk; ++kk)
-    for (int jj = 0; jj < nj; ++jj)
-      for (int ii = 0; ii < ni; ++ii) {
-        double acc = 0.0;
-        for (int c = 0; c < 3; ++c)
-          for (int a = 0; a < 2; ++a)
-            for (int b = 0; b < 2; ++b) {
-              const int ei = ii + (c == 0 ? 0 : a);
-              const int ej = jj + (c == 0 ? a : c == 1 ? 0 : b);
-              const int ek = kk + (c == 2 ? 0 : b);
-              const int q = map[c][((size_t)ek * ext[c][1] + ej) * ext[c][0] + ei];
-              if (q < 0) continue;
-              // sums of u * (...) = Cb * sums of l_e * (...) in the default form
-              const double un = direct ? 1.0 : (double)cbf[q];
-              acc += 0.25 * (gcb[q] * dcb[q] + gca[q] * dca[q]) / un;
-            }
-        grad[((size_t)kk * nj + jj) * ni + ii] = acc;
-      }
   return SOPHIE_OK;
 }
 
