@@ -355,6 +355,12 @@ def run_ours(args):
             variants[f"{pname}_k{kk}"] = cells * args.tsteps * nv * world / (vms / 1e3) / 1e9
         g_prec[0] = so.FP32
         g.configure(temporal_k=1, precision=so.FP32)
+    # zero-field skipping (opt-in; not part of the headline): the same runs from
+    # zero fields with the work units outside the known-nonzero box skipped
+    g.set_zero_skip(True)
+    vms, _, _, _ = timed(2, nv, 1, False)
+    variants["k2_zero_skip"] = cells * args.tsteps * nv * world / (vms / 1e3) / 1e9
+    g.set_zero_skip(False)
     variants["speedup_vs_plain"] = {k: v / variants["k1"] for k, v in variants.items() if k != "speedup_vs_plain"}
     # the plain (one step per launch) kernel's own roofline on this workload
     plain_roof = {"kernel": "yee_plain", "gcell_per_s": variants["k1"],

@@ -247,6 +247,20 @@ int sophie_set_storage_scale(sophie_grid *g, const float *scale);
  */
 int sophie_autotune(sophie_grid *g, int *temporal_k, double *ms_per_step);
 
+/*
+ * Zero-field skipping (early-time sparsity; the paper skips sub-domains whose
+ * fields are all zero on their boundary, Sec. 4). With enable != 0 the step
+ * kernels skip the work units whose outputs lie outside a box known to hold
+ * every nonzero field value: after create or sophie_reset the box holds the
+ * source points, and each step grows it by one index point per side (the
+ * scheme moves a value by at most one point per axis and step); after the
+ * caller writes fields (sophie_set_fields, a storage change) it is the whole
+ * grid until the next reset. The skipped outputs are zero and stay zero, so
+ * every field, probe and energy value is the same as without skipping.
+ * Off by default. Errors: EINVAL.
+ */
+int sophie_set_zero_skip(sophie_grid *g, int enable);
+
 /* Number of kernels this grid has launched since creation. */
 int sophie_launch_count(sophie_grid *g, long long *launches);
 

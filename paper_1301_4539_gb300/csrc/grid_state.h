@@ -143,6 +143,12 @@ struct sophie_grid {
   std::vector<cudaEvent_t> ev_pool;
   long long prof_count[4] = {0, 0, 0, 0};
   double prof_ms[4] = {0, 0, 0, 0};
+  // Zero-field skipping (sophie_set_zero_skip): outside zbox (index points
+  // [zbox[0], zbox[1]) x ... , empty if zbox[0] >= zbox[1]) every field is zero,
+  // unless box_all (fields were written by the caller).
+  bool zskip = false;
+  bool box_all = false;
+  int zbox[6] = {0, 0, 0, 0, 0, 0};
   long long gen = 0;       // bumped by every change of fields, materials or sources
   bool obj_rec = false;    // the step kernels also sample the objective point
   sophie::grid::Tape tape;

@@ -300,6 +300,12 @@ StepArgs make_step_args(sophie_grid* g) {
   a.prb.buf = g->pbuf;
   a.prb.cap = g->pcap;
   a.err = g->err;
+  a.box[0] = 0;
+  a.box[1] = g->d.nxp;
+  a.box[2] = 0;
+  a.box[3] = g->d.ny1;
+  a.box[4] = 0;
+  a.box[5] = g->d.nz1;
   return a;
 }
 
@@ -459,6 +465,7 @@ void from_store(int fmt, float scale, const void* in, float* out, size_t n) {
 
 int set_component(sophie_grid* g, int comp, const float* host) {
   g->gen++;
+  g->box_all = true;  // caller's fields: nothing is known to be zero
   const Dims& d = g->d;
   const size_t n = (size_t)(d.nx + 1) * d.ny1 * d.nz1;
   std::vector<unsigned char> tmp;
@@ -631,6 +638,44 @@ int run_autotune(sophie_grid* g, double* best_ms_per_step) {
   g->tuned = true;
   if (best_ms_per_step) *best_ms_per_step = best;
   return SOPHIE_OK;
+}
+
+}  // namespace
+
+namespace {
+
+// Add index point (i, j, k) to the known-nonzero box.
+void box_add_point(sophie_grid* g, int i, int j, int k) {
+  int* b = g->zbox;
+  if (b[0] >= b[1]) {
+    b[0] = i; b[1] = i + 1; b[2] = j; b[3] = j + 1; b[4] = k; b[5] = k + 1;
+    return;
+  }
+  b[0] = std::min(b[0], i); b[1] = std::max(b[1], i + 1);
+  b[2] = std::min(b[2], j); b[3] = std::max(b[3], j + 1);
+  b[4] = std::min(b[4], k); b[5] = std::max(b[5], k + 1);
+}
+
+// The box grown by r index points per side (one step moves nonzero values by
+// at most one point per axis), clamped to the grid's points.
+void box_grown(const sophie_grid* g, int r, int* out) {
+  const int* b = g->zbox;
+  if (b[0] >= b[1]) {
+    for (int q = 0; q < 6; ++q) out[q] = 0;
+    return;
+  }
+  const int hi[3] = {g->d.nx + 1, g->d.ny + 1, g->d.nz + 1};
+  for (int a = 0; a < 3; ++a) {
+    out[2 * a] = std::max(0, b[2 * a] - r);
+    out[2 * a + 1] = std::min(hi[a], b[2 * a + 1] + r);
+  }
+}
+
+// Reset the box to the source points (fields zero).
+void box_from_sources(sophie_grid* g) {
+  for (int q = 0; q < 6; ++q) g->zbox[q] = 0;
+  g->box_all = false;
+  for (const Source& s : g->src) box_add_point(g, s.i, s.j, s.k);
 }
 
 }  // namespace
@@ -852,6 +897,7 @@ int sophie_add_source(sophie_grid* g, int comp, int i, int j, int k, double amp,
   Source s{comp, i, j, k, kind, amp, f0, bw, t0, point_index(g->d, i, j, k)};
   g->gen++;
   g->src.push_back(s);
+  if (!g->box_all) box_add_point(g, i, j, k);
   int rc = refresh_source_table(g, (int)g->src.size() - 1);
   if (rc) {
     g->src.pop_back();
@@ -895,28 +941,47 @@ int sophie_step(sophie_grid* g, int n) {
     const int K = g->temporal_k == 0 ? g->tuned_k : g->temporal_k;
     const bool blocked = !g->use_simple && K >= 2 && n - m >= K && blocked_supported(K);
     StepArgs a = make_step_args(g);
+    const int adv_steps = blocked ? K : 1;
+    // Zero-field skipping: this launch covers only the tiles and planes of the
+    // known-nonzero box grown by its steps (nothing at all if the box is empty).
+    const bool sub = g->zskip && !g->box_all && !g->use_simple;
+    PlainTiling pt_sub{};
+    BlockedTiling bt_sub{};
+    bool none = false;
+    if (sub) {
+      box_grown(g, adv_steps, a.box);
+      if (blocked) {
+        bt_sub = blocked_tiling_box(g->d, K, g->num_sms, a.box);
+        none = bt_sub.grid == 0;
+      } else {
+        pt_sub = plain_tiling_box(g->d, g->num_sms, a.box);
+        none = pt_sub.grid == 0;
+      }
+    }
     cudaEvent_t ea = nullptr, eb = nullptr;
-    if (g->prof) {
+    if (g->prof && !none) {
       ea = prof_event(g);
       eb = prof_event(g);
       cudaEventRecord(ea, g->stream);
     }
-    cudaError_t e;
-    if (blocked) {
+    cudaError_t e = cudaSuccess;
+    if (none) {
+      // every field is zero in both buffers: nothing to compute
+    } else if (blocked) {
       if (g->btile.K != K) {
         // SOPHIE_BLOCKED_ALIGNED=0 cuts the work into equal contiguous ranges
         // instead of equal z ranges per tile (tuning knob; same results).
         const char* al = getenv("SOPHIE_BLOCKED_ALIGNED");
         g->btile = blocked_tiling(g->d, K, g->num_sms, al ? atoi(al) : 1);
       }
-      e = launch_step_blocked(a, g->tmFB[g->cur], g->tmMB, g->btile, g->stream);
+      e = launch_step_blocked(a, g->tmFB[g->cur], g->tmMB, sub ? bt_sub : g->btile, g->stream);
     } else if (g->use_simple) {
       e = launch_step_simple(a, g->stream);
     } else {
-      e = launch_step_plain(a, g->tmF[g->cur], g->tmM, g->ptile, g->stream);
+      e = launch_step_plain(a, g->tmF[g->cur], g->tmM, sub ? pt_sub : g->ptile, g->stream);
     }
     if (e != cudaSuccess) return fail(SOPHIE_ECUDA, "step launch failed: %s", cudaGetErrorString(e));
-    if (g->prof) {
+    if (g->prof && !none) {
       cudaEventRecord(eb, g->stream);
       g->prof_live.push_back({blocked ? SOPHIE_KERNEL_BLOCKED : SOPHIE_KERNEL_PLAIN, ea, eb});
       if (g->prof_live.size() > 20000) {
@@ -924,9 +989,15 @@ int sophie_step(sophie_grid* g, int n) {
         if (rc) return rc;
       }
     }
-    g->launches++;
+    if (!none) g->launches++;
     g->cur = 1 - g->cur;
-    const int adv = blocked ? K : 1;
+    const int adv = adv_steps;
+    if (!g->box_all) {
+      int grown[6];
+      box_grown(g, adv, grown);
+      if (g->zbox[0] < g->zbox[1])
+        for (int q = 0; q < 6; ++q) g->zbox[q] = grown[q];
+    }
     g->n += adv;
     m += adv;
   }
@@ -1040,6 +1111,7 @@ int sophie_reset(sophie_grid* g) {
   g->n = 0;
   g->cur = 0;
   g->gen++;
+  box_from_sources(g);
   for (Probe& p : g->prb) p.n_added = 0;
   return SOPHIE_OK;
 }
@@ -1085,6 +1157,12 @@ int sophie_configure(sophie_grid* g, int temporal_k, int tile_x, int tile_y, int
   g->temporal_k = temporal_k;
   g->precision = precision;
   g->use_simple = tile_x == 32;
+  return SOPHIE_OK;
+}
+
+int sophie_set_zero_skip(sophie_grid* g, int enable) {
+  if (!g) return fail(SOPHIE_EINVAL, "NULL grid");
+  g->zskip = enable != 0;
   return SOPHIE_OK;
 }
 

@@ -89,13 +89,24 @@ struct StepArgs {
   SrcTable src;
   PrbTable prb;
   int* err;      // device error word (bounded waits that ran out)
+  // Output box of this launch, index points [box[0], box[1]) x [box[2], box[3])
+  // x [box[4], box[5]): work units whose outputs lie outside it are skipped
+  // (the fields there are known to be zero and stay zero; see sophie.h,
+  // sophie_set_zero_skip). The full grid when skipping is off.
+  int box[6];
 };
+
+// Whether the output block [x0, x1) x [y0, y1) x [z0, z1) meets the launch box.
+__host__ __device__ __forceinline__ bool box_meets(const int* b, int x0, int x1, int y0, int y1, int z0, int z1) {
+  return x0 < b[1] && x1 > b[0] && y0 < b[3] && y1 > b[2] && z0 < b[5] && z1 > b[4];
+}
 
 // Work decomposition of the TMA step kernels: (x tile, y tile, z chunk) units
 // walked by `grid` persistent CTAs.
 struct PlainTiling {
   int tiles_x, tiles_y, zchunk, grid;
   long long units;
+  int tx0, ty0, z0, z1;  // the tiles start at tile (tx0, ty0); output planes [z0, z1)
 };
 
 // Temporally blocked kernel: K steps per launch over (tiles_x x tiles_y)
@@ -103,6 +114,7 @@ struct PlainTiling {
 struct BlockedTiling {
   int K, tiles_x, tiles_y, grid;
   int zsplit;  // > 0: CTA b works on tile b / zsplit, z range b % zsplit of zsplit
+  int tx0, ty0, zlo, zhi;  // the tiles start at tile (tx0, ty0); output planes [zlo, zhi)
 };
 
 // Coefficient tables behind the material words (host copies). Class c:
@@ -139,6 +151,11 @@ bool encode_maps(const Dims& d, int fmt, void* fields, uint32_t* mat, int box_x,
 int plain_box_x(int fmt);
 int plain_box_y();
 PlainTiling plain_tiling(const Dims& d, int num_sms, int zchunk_override);
+// Tilings of the sub-box of output points [box[0], box[1]) x ... x [box[4],
+// box[5]) only (zero-field skipping): the tiles meeting it, and its planes.
+// grid == 0 means there is nothing to compute.
+PlainTiling plain_tiling_box(const Dims& d, int num_sms, const int* box);
+BlockedTiling blocked_tiling_box(const Dims& d, int K, int num_sms, const int* box);
 cudaError_t launch_step_plain(const StepArgs& a, const CUtensorMap& tmF, const CUtensorMap& tmM,
                               const PlainTiling& t, cudaStream_t s);
 BlockedTiling blocked_tiling(const Dims& d, int K, int num_sms, int aligned);

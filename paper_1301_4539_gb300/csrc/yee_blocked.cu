@@ -29,6 +29,8 @@
 //  * Work: the (tile, z plane) items are split into equal contiguous ranges,
 //    one per CTA; a range that starts above z = 0 first replays 3K-2 planes
 //    so that every level's state is exact from its first output plane.
+#include <algorithm>
+
 #include "sophie_internal.h"
 #include "tma_util.cuh"
 #include "yee_rare.cuh"
@@ -93,15 +95,15 @@ __device__ __forceinline__ void set_err(int* err, int code) { atomicOr(err, code
 // equal contiguous ranges, tile after tile.
 struct UnitIter {
   long long i, hi;
-  int nz;
-  __device__ UnitIter(const BlockedTiling& t, int nz_) : nz(nz_) {
+  int nz, zlo;  // planes [zlo, zlo + nz) of every tile
+  __device__ UnitIter(const BlockedTiling& t) : nz(t.zhi - t.zlo), zlo(t.zlo) {
     if (t.zsplit > 0) {
       const long long tile = blockIdx.x / t.zsplit;
       const int part = blockIdx.x % t.zsplit;
-      i = tile * nz_ + (long long)nz_ * part / t.zsplit;
-      hi = tile * nz_ + (long long)nz_ * (part + 1) / t.zsplit;
+      i = tile * nz + (long long)nz * part / t.zsplit;
+      hi = tile * nz + (long long)nz * (part + 1) / t.zsplit;
     } else {
-      const long long n = (long long)t.tiles_x * t.tiles_y * nz_;
+      const long long n = (long long)t.tiles_x * t.tiles_y * nz;
       i = n * blockIdx.x / gridDim.x;
       hi = n * (blockIdx.x + 1) / gridDim.x;
     }
@@ -110,13 +112,32 @@ struct UnitIter {
   __device__ bool next(long long& tile, int& z0, int& z1) {
     if (i >= hi) return false;
     tile = i / nz;
-    z0 = (int)(i % nz);
+    const int r0 = (int)(i % nz);
     const long long room = hi - i;
-    z1 = (int)((long long)z0 + room < nz ? z0 + room : nz);
-    i += z1 - z0;
+    const int r1 = (int)((long long)r0 + room < nz ? r0 + room : nz);
+    i += r1 - r0;
+    z0 = zlo + r0;
+    z1 = zlo + r1;
     return true;
   }
 };
+
+// Tile coordinates of tile index `tile` of the tiling.
+__device__ __forceinline__ void tile_xy(const BlockedTiling& t, long long tile, int& tx, int& ty) {
+  tx = t.tx0 + (int)(tile % t.tiles_x);
+  ty = t.ty0 + (int)(tile / t.tiles_x);
+}
+
+// Whether unit (tile, planes [z0, z1)) has outputs inside the launch box.
+template <int K>
+__device__ __forceinline__ bool unit_live(const StepArgs& a, const BlockedTiling& t, long long tile, int z0,
+                                          int z1) {
+  constexpr int TX = kRX - 2 * K, TY = kRY - 2 * K, PHI = K & 1;
+  int tx, ty;
+  tile_xy(t, tile, tx, ty);
+  const int x0 = tx * TX - PHI, y0 = ty * TY;
+  return box_meets(a.box, x0, x0 + TX, y0, y0 + TY, z0, z1);
+}
 
 // First iteration of a unit: level 1 updates plane s-1; planes below 0 are
 // zero and exact, otherwise 3K-2 planes are replayed before z0.
@@ -134,15 +155,18 @@ struct Loader {
   UnitIter it;
   int p = 0, pend = -1, bx = 0, ry = 0;
   long long issued = 0;
-  __device__ Loader(const BlockedTiling& t, int nz) : it(t, nz) {}
+  __device__ Loader(const BlockedTiling& t) : it(t) {}
   // Issue the next plane into its stage; false when the sequence is exhausted.
-  __device__ bool issue(const BlockedTiling& t, const CUtensorMap* tmF, const CUtensorMap* tmM,
+  __device__ bool issue(const StepArgs& a, const BlockedTiling& t, const CUtensorMap* tmF, const CUtensorMap* tmM,
                         unsigned char* base, uint32_t bar0) {
     if (p > pend) {
       long long tile;
       int z0, z1;
-      if (!it.next(tile, z0, z1)) return false;
-      const int tx = (int)(tile % t.tiles_x), ty = (int)(tile / t.tiles_x);
+      do {
+        if (!it.next(tile, z0, z1)) return false;
+      } while (!unit_live<K>(a, t, tile, z0, z1));  // the consumers skip the same units
+      int tx, ty;
+      tile_xy(t, tile, tx, ty);
       const int rx = tx * Cfg<K, F>::TX - Cfg<K, F>::PHI - K;
       ry = ty * Cfg<K, F>::TY - K;
       bx = rx & ~(BoxCfg<F>::GX - 1);
@@ -198,24 +222,26 @@ yee_blocked_kernel(const __grid_constant__ CUtensorMap tmF, const __grid_constan
   }
   __syncthreads();
   const Dims d = a.d;
-  Loader<K, FMT> ld(t, d.nz);
+  Loader<K, FMT> ld(t);
   if (threadIdx.x == 0) {
     prefetch_tmap(&tmF);
     prefetch_tmap(&tmM);
     for (int s = 0; s < kNS; ++s)
-      if (!ld.issue(t, &tmF, &tmM, base, bar0)) break;
+      if (!ld.issue(a, t, &tmF, &tmM, base, bar0)) break;
   }
 
   const float S = a.S;
   const int wn = warp + 1 < kW ? warp + 1 : warp;  // seam partner below (clamped at the edge)
   const int wp = warp > 0 ? warp - 1 : warp;       // seam partner above
-  UnitIter it(t, d.nz);
+  UnitIter it(t);
   long long tile;
   int z0, z1;
   long long Cn = 0;  // consumed-plane counter (ring position)
   bool abort = false;
   while (!abort && it.next(tile, z0, z1)) {
-    const int tx = (int)(tile % t.tiles_x), ty = (int)(tile / t.tiles_x);
+    if (!unit_live<K>(a, t, tile, z0, z1)) continue;  // known zeros: no planes loaded for it
+    int tx, ty;
+    tile_xy(t, tile, tx, ty);
     const int rx = tx * C::TX - C::PHI - K, ry = ty * C::TY - K;
     const int ox = rx & (B::GX - 1);  // even: region start inside the TMA box
     const int col0 = ox + 2 * lane;
@@ -355,7 +381,7 @@ yee_blocked_kernel(const __grid_constant__ CUtensorMap tmF, const __grid_constan
           const long long released = Cn + 1 + (s == s1 ? 1 : 0);
           fence_proxy_async_smem();
           while (ld.issued < released + kNS)
-            if (!ld.issue(t, &tmF, &tmM, base, bar0)) break;
+            if (!ld.issue(a, t, &tmF, &tmM, base, bar0)) break;
         }
         float hxa[2], hza[2];  // H of the row above this warp's rows
         {
@@ -539,6 +565,8 @@ BlockedTiling blocked_tiling(const Dims& d, int K, int num_sms, int aligned) {
   t.K = K;
   t.tiles_x = (d.nx + phi + TX - 1) / TX;
   t.tiles_y = (d.ny + TY - 1) / TY;
+  t.tx0 = t.ty0 = t.zlo = 0;
+  t.zhi = d.nz;
   const long long tiles = (long long)t.tiles_x * t.tiles_y;
   if (aligned && tiles <= num_sms) {
     t.zsplit = (int)(num_sms / tiles < d.nz ? num_sms / tiles : d.nz);
@@ -548,6 +576,37 @@ BlockedTiling blocked_tiling(const Dims& d, int K, int num_sms, int aligned) {
     t.zsplit = 0;
     t.grid = (int)(items < num_sms ? items : num_sms);
   }
+  return t;
+}
+
+BlockedTiling blocked_tiling_box(const Dims& d, int K, int num_sms, const int* box) {
+  BlockedTiling t{};
+  t.K = K;
+  const int TX = kRX - 2 * K, TY = kRY - 2 * K, phi = K & 1;
+  const int z0 = std::max(box[4], 0), z1 = std::min(box[5], d.nz);
+  const int x1 = std::min(box[1], d.nx), y1 = std::min(box[3], d.ny);
+  if (box[0] >= x1 || box[2] >= y1 || z0 >= z1) return t;  // nothing live: grid 0
+  // tile tx covers output x [tx TX - phi, tx TX - phi + TX)
+  const int tx0 = (box[0] + phi) / TX, tx1 = (x1 - 1 + phi) / TX + 1;
+  const int ty0 = box[2] / TY, ty1 = (y1 - 1) / TY + 1;
+  Dims sub = d;
+  sub.nz = z1 - z0;
+  t = blocked_tiling(sub, K, num_sms, 1);
+  t.tiles_x = tx1 - tx0;
+  t.tiles_y = ty1 - ty0;
+  const long long tiles = (long long)t.tiles_x * t.tiles_y;
+  if (tiles <= num_sms) {
+    t.zsplit = (int)(num_sms / tiles < sub.nz ? num_sms / tiles : sub.nz);
+    t.grid = (int)(tiles * t.zsplit);
+  } else {
+    const long long items = tiles * sub.nz;
+    t.zsplit = 0;
+    t.grid = (int)(items < num_sms ? items : num_sms);
+  }
+  t.tx0 = tx0;
+  t.ty0 = ty0;
+  t.zlo = z0;
+  t.zhi = z1;
   return t;
 }
 

@@ -65,16 +65,16 @@ struct Unit {
   int x0, y0, z0, z1;
 };
 
-__device__ __forceinline__ Unit unit_of(long long u, const PlainTiling& t, int nz) {
+__device__ __forceinline__ Unit unit_of(long long u, const PlainTiling& t) {
   Unit w;
-  const int tx = (int)(u % t.tiles_x);
+  const int tx = t.tx0 + (int)(u % t.tiles_x);
   const long long q = u / t.tiles_x;
-  const int ty = (int)(q % t.tiles_y);
+  const int ty = t.ty0 + (int)(q % t.tiles_y);
   const int zc = (int)(q / t.tiles_y);
   w.x0 = tx * kPX;
   w.y0 = ty * kPY;
-  w.z0 = zc * t.zchunk;
-  w.z1 = min(w.z0 + t.zchunk, nz);
+  w.z0 = t.z0 + zc * t.zchunk;
+  w.z1 = min(w.z0 + t.zchunk, t.z1);
   return w;
 }
 
@@ -123,7 +123,7 @@ yee_plain_kernel(const __grid_constant__ CUtensorMap tmF, const __grid_constant_
       return Unit{it.x0, it.y0, it.z0, it.z1};
     } else {
       cd = nullptr;
-      return unit_of(u, t, a.d.nz);
+      return unit_of(u, t);
     }
   };
 
@@ -139,6 +139,9 @@ yee_plain_kernel(const __grid_constant__ CUtensorMap tmF, const __grid_constant_
     for (long long u = blockIdx.x; u < nunits && ok; u += gridDim.x) {
       const CavityDesc* cd;
       const Unit w = unit_at(u, cd);
+      if constexpr (!BATCH) {
+        if (!box_meets(a.box, w.x0, w.x0 + kPX, w.y0, w.y0 + kPY, w.z0, w.z1)) continue;  // known zeros
+      }
       const CUtensorMap* mF = BATCH ? &cd->tmF[pb.cur] : &tmF;
       const CUtensorMap* mM = BATCH ? &cd->tmM : &tmM;
       const int ps = w.z0 > 0 ? w.z0 - 1 : 0;
@@ -192,6 +195,9 @@ yee_plain_kernel(const __grid_constant__ CUtensorMap tmF, const __grid_constant_
   for (long long u = blockIdx.x; u < nunits && !abort; u += gridDim.x, upar ^= 1) {
     const CavityDesc* cd;
     const Unit w = unit_at(u, cd);
+    if constexpr (!BATCH) {
+      if (!box_meets(a.box, w.x0, w.x0 + kPX, w.y0, w.y0 + kPY, w.z0, w.z1)) continue;  // as the producer
+    }
     if constexpr (BATCH) {
       if (threadIdx.x == 0) {
         UnitCtx& c = uctx[upar];
@@ -451,6 +457,8 @@ PlainTiling plain_tiling(const Dims& d, int num_sms, int zchunk_override) {
   const int tiles_x = (d.nx + kPX - 1) / kPX, tiles_y = (d.ny + kPY - 1) / kPY;
   const int slots = 2 * num_sms;
   const int cands[] = {4, 6, 8, 12, 16, 24, 32, 48, 64, 96, 128, 256, 512, 1024};
+  best.tx0 = best.ty0 = best.z0 = 0;
+  best.z1 = d.nz;
   for (int zc : cands) {
     if (zchunk_override > 0) zc = zchunk_override;
     if (zc > d.nz && zc != cands[0] && zchunk_override <= 0) continue;
@@ -485,6 +493,26 @@ cudaError_t launch_plain_f(const StepArgs& a, const CUtensorMap& tmF, const CUte
   }
   yee_plain_kernel<F, false><<<t.grid, kThreads, PCfg<F>::kSmemBytes, s>>>(tmF, tmM, a, t, PlainBatch{});
   return cudaGetLastError();
+}
+
+PlainTiling plain_tiling_box(const Dims& d, int num_sms, const int* box) {
+  PlainTiling t{};
+  const int z0 = std::max(box[4], 0), z1 = std::min(box[5], d.nz);
+  const int x1 = std::min(box[1], d.nx), y1 = std::min(box[3], d.ny);
+  if (box[0] >= x1 || box[2] >= y1 || z0 >= z1) return t;  // nothing live: grid 0
+  const int tx0 = box[0] / kPX, tx1 = (x1 + kPX - 1) / kPX;
+  const int ty0 = box[2] / kPY, ty1 = (y1 + kPY - 1) / kPY;
+  // the same cost model as plain_tiling on a grid of the sub-box's extent
+  Dims sub = d;
+  sub.nx = (tx1 - tx0) * kPX;
+  sub.ny = (ty1 - ty0) * kPY;
+  sub.nz = z1 - z0;
+  t = plain_tiling(sub, num_sms, 0);
+  t.tx0 = tx0;
+  t.ty0 = ty0;
+  t.z0 = z0;
+  t.z1 = z1;
+  return t;
 }
 
 int plain_tile_x() { return kPX; }

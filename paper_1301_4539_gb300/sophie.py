@@ -48,6 +48,7 @@ SIGNATURES = {
     "sophie_configure": (_I, [_P, _I, _I, _I, _I]),
     "sophie_set_storage_scale": (_I, [_P, _P]),
     "sophie_autotune": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(_D)]),
+    "sophie_set_zero_skip": (_I, [_P, _I]),
     "sophie_launch_count": (_I, [_P, ctypes.POINTER(_LL)]),
     "sophie_profile": (_I, [_P, _I]),
     "sophie_profile_read": (_I, [_P, _I, ctypes.POINTER(_LL), ctypes.POINTER(_D)]),
@@ -218,6 +219,10 @@ def sophie_autotune(g: int):
     return k.value, ms.value
 
 
+def sophie_set_zero_skip(g: int, enable: bool) -> None:
+    _chk(load().sophie_set_zero_skip(g, 1 if enable else 0))
+
+
 def sophie_launch_count(g: int) -> int:
     n = _LL()
     _chk(load().sophie_launch_count(g, ctypes.byref(n)))
@@ -327,6 +332,9 @@ class Grid:
 
     def autotune(self):
         return sophie_autotune(self.h)
+
+    def set_zero_skip(self, enable=True):
+        sophie_set_zero_skip(self.h, enable)
 
     def launch_count(self):
         return sophie_launch_count(self.h)
