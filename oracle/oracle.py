@@ -62,6 +62,12 @@ def load() -> ctypes.CDLL:
                 getattr(lib, f"oracle_step_{suf}").restype = None
                 getattr(lib, f"oracle_energy_{suf}").argtypes = [I, I, I, R, D] + [P] * 6 + [P] * 3
                 getattr(lib, f"oracle_energy_{suf}").restype = D
+            for suf, R in (("f64", D), ("f32", F)):
+                getattr(lib, f"oracle_step_nu_{suf}").argtypes = (
+                    [I, I, I, R] + [P] * 6 + [P] * 6 + [P] * 6 + [I, P, P, L, I, P, P, L, I])
+                getattr(lib, f"oracle_step_nu_{suf}").restype = None
+                getattr(lib, f"oracle_energy_nu_{suf}").argtypes = [I, I, I, R, D] + [P] * 6 + [P] * 3 + [P] * 6
+                getattr(lib, f"oracle_energy_nu_{suf}").restype = D
             lib.oracle_grad_f64.argtypes = [I, I, I, D, D, P, P] + [P] * 6 + [I, P, P, I, I, I, I, I, I, P, P]
             lib.oracle_grad_f64.restype = D
             lib.oracle_waveform.argtypes = [I, D, D, D, D, D, L, L, P]
@@ -111,6 +117,7 @@ class OracleGrid:
         self.sources = []  # (comp, i, j, k, amp, f0, bw, t0, kind)
         self.probes = []   # (comp, i, j, k)
         self.probe_trace = []
+        self.ratios = None  # non-uniform mesh: (rx, ry, rz, rxd, ryd, rzd)
         self.set_materials(np.ones((nz, ny, nx), np.float32), np.zeros((nz, ny, nx), np.float32))
 
     # -- inputs ---------------------------------------------------------------
@@ -125,6 +132,24 @@ class OracleGrid:
         fn = getattr(load(), f"oracle_coefs_{self.precision}")
         fn(nx, ny, nz, self.dx, self.dt, _ptr(eps_cell), _ptr(sig_cell),
            *[_ptr(c) for c in self.coef], *[_ptr(e) for e in self.eps_edge])
+
+    def set_spacing(self, wx=None, wy=None, wz=None) -> None:
+        """Cell widths (metres) along x (nx), y (ny), z (nz); None = uniform dx.
+        The update then scales every difference by dx / (width it spans):
+        primary widths in the H update, dual (mean of the two adjacent cells)
+        in the E update (yee_oracle_body.h, non-uniform mesh)."""
+        if wx is None and wy is None and wz is None:
+            self.ratios = None
+            return
+        out = []
+        for w, n in ((wx, self.nx), (wy, self.ny), (wz, self.nz)):
+            w = np.full(n, self.dx) if w is None else np.asarray(w, np.float64)
+            assert w.shape == (n,) and np.all(w > 0)
+            prim = self.dx / w
+            ext = np.concatenate([[0.0], w, [0.0]])
+            dual = self.dx / ((ext[:-1] + ext[1:]) / 2.0)
+            out.append((prim.astype(self.dtype), dual.astype(self.dtype)))
+        self.ratios = tuple(a for a, _ in out) + tuple(b for _, b in out)
 
     def set_field(self, comp: int, arr: np.ndarray) -> None:
         self.f[comp][...] = arr
@@ -151,10 +176,16 @@ class OracleGrid:
         nprb = len(self.probes)
         prb = np.array(self.probes or [[0, 0, 0, 0]], np.int32).reshape(-1)
         pout = np.zeros((max(nprb, 1), nsteps), self.dtype)
-        fn = getattr(load(), f"oracle_step_{self.precision}")
-        fn(self.nx, self.ny, self.nz, self.S, *[_ptr(a) for a in self.f],
-           *[_ptr(c) for c in self.coef], nsrc, _ptr(src), _ptr(sval), nsteps,
-           nprb, _ptr(prb), _ptr(pout), nsteps, nsteps)
+        if self.ratios is None:
+            fn = getattr(load(), f"oracle_step_{self.precision}")
+            fn(self.nx, self.ny, self.nz, self.S, *[_ptr(a) for a in self.f],
+               *[_ptr(c) for c in self.coef], nsrc, _ptr(src), _ptr(sval), nsteps,
+               nprb, _ptr(prb), _ptr(pout), nsteps, nsteps)
+        else:
+            fn = getattr(load(), f"oracle_step_nu_{self.precision}")
+            fn(self.nx, self.ny, self.nz, self.S, *[_ptr(a) for a in self.f],
+               *[_ptr(c) for c in self.coef], *[_ptr(r) for r in self.ratios], nsrc, _ptr(src),
+               _ptr(sval), nsteps, nprb, _ptr(prb), _ptr(pout), nsteps, nsteps)
         for q in range(nprb):
             self.probe_trace[q].extend(pout[q].astype(np.float64).tolist())
         self.n += nsteps
@@ -174,7 +205,7 @@ class OracleGrid:
         The probe is component pcomp at index (pi, pj, pk), sampled after every
         step. Advances the state by nsteps steps (float64 grids only).
         """
-        assert self.precision == "f64"
+        assert self.precision == "f64" and self.ratios is None  # uniform meshes only
         cells = np.ascontiguousarray(cells, np.int32).reshape(-1, 3)
         grad = np.zeros(len(cells), np.float64)
         nsrc, src, sval = self._source_table(nsteps)
@@ -188,6 +219,10 @@ class OracleGrid:
         return J, grad
 
     def energy(self) -> float:
+        if self.ratios is not None:
+            fn = getattr(load(), f"oracle_energy_nu_{self.precision}")
+            return fn(self.nx, self.ny, self.nz, self.S, self.dx, *[_ptr(a) for a in self.f],
+                      *[_ptr(e) for e in self.eps_edge], *[_ptr(r) for r in self.ratios])
         fn = getattr(load(), f"oracle_energy_{self.precision}")
         return fn(self.nx, self.ny, self.nz, self.S, self.dx, *[_ptr(a) for a in self.f],
                   *[_ptr(e) for e in self.eps_edge])

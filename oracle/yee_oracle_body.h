@@ -311,6 +311,211 @@ double FN(oracle_energy)(int nx, int ny, int nz, REAL S, double dx,
     return 0.5 * EPS0 * dx * dx * dx * (we + wh);
 }
 
+/*
+ * Non-uniform mesh (1-D coefficient arrays per axis, the geometric
+ * coefficients dx(i), dy(j), dz(k) of Sec. 2.2's loop). With a reference step
+ * dx0 (the grid's dx, S = c dt / dx0) and cell widths wx(i), the ratio arrays
+ *   rx(i)  = dx0 / wx(i)                          i in [0, nx)  (primary)
+ *   rxd(i) = dx0 / ((wx(i-1) + wx(i)) / 2)        i in [0, nx]  (dual; wx(-1) = wx(nx) = 0)
+ * (and likewise y, z) scale each difference of a curl bracket by the width it
+ * spans: primary widths for the H update (differences of E across a face),
+ * dual widths for the E update (differences of H across an edge's dual face):
+ *   br = FMA(r_a, a1 - a0, -(r_b * (b1 - b0)))
+ *   h  = FMA(S, br, h),   e = FMA(Cb, br [+ s], Ca*e)
+ * With all ratios 1 this is exactly the uniform expression (1*x is exact and
+ * FMA(1, x, -y) rounds x - y once).
+ */
+static void FN(update_h_nu)(int nx, int ny, int nz, REAL S,
+                            const REAL *ex, const REAL *ey, const REAL *ez,
+                            REAL *hx, REAL *hy, REAL *hz,
+                            const REAL *rx, const REAL *ry, const REAL *rz)
+{
+    const long sy = nx + 1, sz = (long)(nx + 1) * (ny + 1);
+#pragma omp parallel for schedule(static)
+    for (int k = 0; k < nz; ++k)
+        for (int j = 0; j < ny; ++j)
+            for (int i = 0; i <= nx; ++i) {
+                const long p = k * sz + j * sy + i;
+                const REAL br = FMA(rz[k], ey[p + sz] - ey[p], -(ry[j] * (ez[p + sy] - ez[p])));
+                hx[p] = FMA(S, br, hx[p]);
+            }
+#pragma omp parallel for schedule(static)
+    for (int k = 0; k < nz; ++k)
+        for (int j = 0; j <= ny; ++j)
+            for (int i = 0; i < nx; ++i) {
+                const long p = k * sz + j * sy + i;
+                const REAL br = FMA(rx[i], ez[p + 1] - ez[p], -(rz[k] * (ex[p + sz] - ex[p])));
+                hy[p] = FMA(S, br, hy[p]);
+            }
+#pragma omp parallel for schedule(static)
+    for (int k = 0; k <= nz; ++k)
+        for (int j = 0; j < ny; ++j)
+            for (int i = 0; i < nx; ++i) {
+                const long p = k * sz + j * sy + i;
+                const REAL br = FMA(ry[j], ex[p + sy] - ex[p], -(rx[i] * (ey[p + 1] - ey[p])));
+                hz[p] = FMA(S, br, hz[p]);
+            }
+}
+
+#define BRN_X(p) FMA(ryd[j], hz[p] - hz[(p) - sy], -(rzd[k] * (hy[p] - hy[(p) - sz])))
+#define BRN_Y(p) FMA(rzd[k], hx[p] - hx[(p) - sz], -(rxd[i] * (hz[p] - hz[(p) - 1])))
+#define BRN_Z(p) FMA(rxd[i], hy[p] - hy[(p) - 1], -(ryd[j] * (hx[p] - hx[(p) - sy])))
+
+/* Non-uniform E update; sources as in update_e (inside the bracket). */
+static void FN(update_e_nu)(int nx, int ny, int nz,
+                            REAL *ex, REAL *ey, REAL *ez,
+                            const REAL *hx, const REAL *hy, const REAL *hz,
+                            const REAL *cax, const REAL *cbx, const REAL *cay,
+                            const REAL *cby, const REAL *caz, const REAL *cbz,
+                            const REAL *rxd, const REAL *ryd, const REAL *rzd,
+                            int nsrc, const int *src, const REAL *sval, REAL *eold)
+{
+    const long sy = nx + 1, sz = (long)(nx + 1) * (ny + 1);
+    for (int s = 0; s < nsrc; ++s) {
+        const int c = src[4 * s];
+        const long p = (long)src[4 * s + 3] * sz + (long)src[4 * s + 2] * sy + src[4 * s + 1];
+        eold[s] = (c == 0 ? ex : c == 1 ? ey : ez)[p];
+    }
+#pragma omp parallel for schedule(static)
+    for (int k = 1; k < nz; ++k)
+        for (int j = 1; j < ny; ++j)
+            for (int i = 0; i < nx; ++i) {
+                const long p = k * sz + j * sy + i;
+                ex[p] = FMA(cbx[p], BRN_X(p), cax[p] * ex[p]);
+            }
+#pragma omp parallel for schedule(static)
+    for (int k = 1; k < nz; ++k)
+        for (int j = 0; j < ny; ++j)
+            for (int i = 1; i < nx; ++i) {
+                const long p = k * sz + j * sy + i;
+                ey[p] = FMA(cby[p], BRN_Y(p), cay[p] * ey[p]);
+            }
+#pragma omp parallel for schedule(static)
+    for (int k = 0; k < nz; ++k)
+        for (int j = 1; j < ny; ++j)
+            for (int i = 1; i < nx; ++i) {
+                const long p = k * sz + j * sy + i;
+                ez[p] = FMA(cbz[p], BRN_Z(p), caz[p] * ez[p]);
+            }
+    for (int s = 0; s < nsrc; ++s) {
+        const int c = src[4 * s];
+        const int i = src[4 * s + 1], j = src[4 * s + 2], k = src[4 * s + 3];
+        const long p = (long)k * sz + (long)j * sy + i;
+        int first = 1;
+        for (int q = 0; q < s; ++q)
+            if (src[4 * q] == c && src[4 * q + 1] == i && src[4 * q + 2] == j && src[4 * q + 3] == k)
+                first = 0;
+        if (!first) continue;
+        REAL br = (c == 0 ? BRN_X(p) : c == 1 ? BRN_Y(p) : BRN_Z(p));
+        for (int q = s; q < nsrc; ++q)
+            if (src[4 * q] == c && src[4 * q + 1] == i && src[4 * q + 2] == j && src[4 * q + 3] == k)
+                br = br + sval[q];
+        const REAL *ca = c == 0 ? cax : c == 1 ? cay : caz;
+        const REAL *cb = c == 0 ? cbx : c == 1 ? cby : cbz;
+        REAL *e = c == 0 ? ex : c == 1 ? ey : ez;
+        e[p] = FMA(cb[p], br, ca[p] * eold[s]);
+    }
+}
+
+/* Steps on a non-uniform mesh; arguments as oracle_step plus the six ratio
+ * arrays (rx[nx], ry[ny], rz[nz], rxd[nx+1], ryd[ny+1], rzd[nz+1]). */
+void FN(oracle_step_nu)(int nx, int ny, int nz, REAL S,
+                        REAL *ex, REAL *ey, REAL *ez, REAL *hx, REAL *hy, REAL *hz,
+                        const REAL *cax, const REAL *cbx, const REAL *cay,
+                        const REAL *cby, const REAL *caz, const REAL *cbz,
+                        const REAL *rx, const REAL *ry, const REAL *rz,
+                        const REAL *rxd, const REAL *ryd, const REAL *rzd,
+                        int nsrc, const int *src, const REAL *sval, long sstride,
+                        int nprb, const int *prb, REAL *pout, long pstride, int nsteps)
+{
+    const long sy = nx + 1, sz = (long)(nx + 1) * (ny + 1);
+    REAL eold[64];
+    REAL sv[64];
+    if (nsrc > 64) nsrc = 64;
+    for (int m = 0; m < nsteps; ++m) {
+        FN(update_h_nu)(nx, ny, nz, S, ex, ey, ez, hx, hy, hz, rx, ry, rz);
+        for (int s = 0; s < nsrc; ++s) sv[s] = sval[s * sstride + m];
+        FN(update_e_nu)(nx, ny, nz, ex, ey, ez, hx, hy, hz, cax, cbx, cay, cby, caz, cbz,
+                        rxd, ryd, rzd, nsrc, src, sv, eold);
+        for (int q = 0; q < nprb; ++q) {
+            const int c = prb[4 * q];
+            const long p = (long)prb[4 * q + 3] * sz + (long)prb[4 * q + 2] * sy + prb[4 * q + 1];
+            const REAL *f = c == 0 ? ex : c == 1 ? ey : c == 2 ? ez : c == 3 ? hx : c == 4 ? hy : hz;
+            pout[q * pstride + m] = f[p];
+        }
+    }
+}
+
+/*
+ * Discrete energy on a non-uniform mesh: every term is weighted by its
+ * volume in units of dx0^3 -- an edge's length times its dual face, a face's
+ * area times its dual edge -- formed in double from the ratio arrays:
+ *   ex(i,j,k): 1 / (rx(i) ryd(j) rzd(k)),   hx(i,j,k): 1 / (rxd(i) ry(j) rz(k)), ...
+ * h^{n+1/2} is formed with the non-uniform H update.
+ */
+double FN(oracle_energy_nu)(int nx, int ny, int nz, REAL S, double dx,
+                            const REAL *ex, const REAL *ey, const REAL *ez,
+                            const REAL *hx, const REAL *hy, const REAL *hz,
+                            const double *epsx, const double *epsy, const double *epsz,
+                            const REAL *rx, const REAL *ry, const REAL *rz,
+                            const REAL *rxd, const REAL *ryd, const REAL *rzd)
+{
+    const long sy = nx + 1, sz = (long)(nx + 1) * (ny + 1);
+    double we = 0.0, wh = 0.0;
+    for (int k = 1; k < nz; ++k)
+        for (int j = 1; j < ny; ++j)
+            for (int i = 0; i < nx; ++i) {
+                const long p = k * sz + j * sy + i;
+                const double v = 1.0 / (((double)rx[i] * (double)ryd[j]) * (double)rzd[k]);
+                we += v * (epsx[p] * ((double)ex[p] * (double)ex[p]));
+            }
+    for (int k = 1; k < nz; ++k)
+        for (int j = 0; j < ny; ++j)
+            for (int i = 1; i < nx; ++i) {
+                const long p = k * sz + j * sy + i;
+                const double v = 1.0 / (((double)rxd[i] * (double)ry[j]) * (double)rzd[k]);
+                we += v * (epsy[p] * ((double)ey[p] * (double)ey[p]));
+            }
+    for (int k = 0; k < nz; ++k)
+        for (int j = 1; j < ny; ++j)
+            for (int i = 1; i < nx; ++i) {
+                const long p = k * sz + j * sy + i;
+                const double v = 1.0 / (((double)rxd[i] * (double)ryd[j]) * (double)rz[k]);
+                we += v * (epsz[p] * ((double)ez[p] * (double)ez[p]));
+            }
+    for (int k = 0; k < nz; ++k)
+        for (int j = 0; j < ny; ++j)
+            for (int i = 0; i <= nx; ++i) {
+                const long p = k * sz + j * sy + i;
+                const REAL br = FMA(rz[k], ey[p + sz] - ey[p], -(ry[j] * (ez[p + sy] - ez[p])));
+                const REAL hn = FMA(S, br, hx[p]);
+                const double v = 1.0 / (((double)rxd[i] * (double)ry[j]) * (double)rz[k]);
+                wh += v * ((double)hx[p] * (double)hn);
+            }
+    for (int k = 0; k < nz; ++k)
+        for (int j = 0; j <= ny; ++j)
+            for (int i = 0; i < nx; ++i) {
+                const long p = k * sz + j * sy + i;
+                const REAL br = FMA(rx[i], ez[p + 1] - ez[p], -(rz[k] * (ex[p + sz] - ex[p])));
+                const REAL hn = FMA(S, br, hy[p]);
+                const double v = 1.0 / (((double)rx[i] * (double)ryd[j]) * (double)rz[k]);
+                wh += v * ((double)hy[p] * (double)hn);
+            }
+    for (int k = 0; k <= nz; ++k)
+        for (int j = 0; j < ny; ++j)
+            for (int i = 0; i < nx; ++i) {
+                const long p = k * sz + j * sy + i;
+                const REAL br = FMA(ry[j], ex[p + sy] - ex[p], -(rx[i] * (ey[p + 1] - ey[p])));
+                const REAL hn = FMA(S, br, hz[p]);
+                const double v = 1.0 / (((double)rx[i] * (double)ry[j]) * (double)rzd[k]);
+                wh += v * ((double)hz[p] * (double)hn);
+            }
+    return 0.5 * EPS0 * dx * dx * dx * (we + wh);
+}
+
+#undef BRN_X
+#undef BRN_Y
+#undef BRN_Z
 #undef BR_X
 #undef BR_Y
 #undef BR_Z
