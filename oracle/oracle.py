@@ -137,7 +137,9 @@ class OracleGrid:
         """Cell widths (metres) along x (nx), y (ny), z (nz); None = uniform dx.
         The update then scales every difference by dx / (width it spans):
         primary widths in the H update, dual (mean of the two adjacent cells)
-        in the E update (yee_oracle_body.h, non-uniform mesh)."""
+        in the E update (yee_oracle_body.h, non-uniform mesh). At a wall node
+        the dual width is the end cell's own width, as the uniform energy
+        weights the wall faces by a whole cell; no update reads those two."""
         if wx is None and wy is None and wz is None:
             self.ratios = None
             return
@@ -146,7 +148,7 @@ class OracleGrid:
             w = np.full(n, self.dx) if w is None else np.asarray(w, np.float64)
             assert w.shape == (n,) and np.all(w > 0)
             prim = self.dx / w
-            ext = np.concatenate([[0.0], w, [0.0]])
+            ext = np.concatenate([w[:1], w, w[-1:]])
             dual = self.dx / ((ext[:-1] + ext[1:]) / 2.0)
             out.append((prim.astype(self.dtype), dual.astype(self.dtype)))
         self.ratios = tuple(a for a, _ in out) + tuple(b for _, b in out)

@@ -316,14 +316,16 @@ double FN(oracle_energy)(int nx, int ny, int nz, REAL S, double dx,
  * coefficients dx(i), dy(j), dz(k) of Sec. 2.2's loop). With a reference step
  * dx0 (the grid's dx, S = c dt / dx0) and cell widths wx(i), the ratio arrays
  *   rx(i)  = dx0 / wx(i)                          i in [0, nx)  (primary)
- *   rxd(i) = dx0 / ((wx(i-1) + wx(i)) / 2)        i in [0, nx]  (dual; wx(-1) = wx(nx) = 0)
+ *   rxd(i) = dx0 / ((wx(i-1) + wx(i)) / 2)        i in [0, nx]  (dual; wx(-1) = wx(0), wx(nx) = wx(nx-1))
  * (and likewise y, z) scale each difference of a curl bracket by the width it
  * spans: primary widths for the H update (differences of E across a face),
  * dual widths for the E update (differences of H across an edge's dual face):
  *   br = FMA(r_a, a1 - a0, -(r_b * (b1 - b0)))
  *   h  = FMA(S, br, h),   e = FMA(Cb, br [+ s], Ca*e)
  * With all ratios 1 this is exactly the uniform expression (1*x is exact and
- * FMA(1, x, -y) rounds x - y once).
+ * FMA(1, x, -y) rounds x - y once). The wall-node duals rxd(0), rxd(nx) are
+ * read by no update (the E edges there are PEC); they weigh the wall-normal
+ * faces in the energy, a whole end cell as in the uniform energy.
  */
 static void FN(update_h_nu)(int nx, int ny, int nz, REAL S,
                             const REAL *ex, const REAL *ey, const REAL *ez,
