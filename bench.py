@@ -61,6 +61,7 @@ def parse():
     p.add_argument("--no-adjoint", action="store_true")
     p.add_argument("--no-batch", action="store_true")
     p.add_argument("--no-768", action="store_true")
+    p.add_argument("--no-graded", action="store_true")
     p.add_argument("--batch-cavities", type=int, default=4096)
     return p.parse_args()
 
@@ -392,6 +393,10 @@ def run_ours(args):
     if not args.no_768 and rank == 0:
         precision_768 = run_precision_768(stream)
 
+    graded = None
+    if not args.no_graded and rank == 0:
+        graded = run_graded(stream, variants["k1"])
+
     if rank == 0:
         line = {"metric": "Gcell-updates/s 3D Yee FDTD", "value": value, "unit": "Gcell-updates/s",
                 "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -404,7 +409,7 @@ def run_ours(args):
                            "l2": "inputs larger than L2 (no flush)"},
                 "roofline": roof, "plain_roofline": plain_roof, "variants_gcells": variants, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": launches, "clocks": clocks, "energy_J": energy, "adjoint": adjoint,
-                "batch": batch, "precision_768": precision_768}
+                "batch": batch, "precision_768": precision_768, "graded_mesh": graded}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
@@ -523,6 +528,56 @@ def run_precision_768(stream, tsteps: int = 200):
         out[name] = n ** 3 * tsteps / (ev0.elapsed_time(ev1) / 1e3) / 1e9
     g.close()
     return out
+
+
+def run_graded(stream, uniform_k1: float, n: int = 256, tsteps: int = 1000, reps: int = 3):
+    """The non-uniform mesh on its workload: the 256^3 sphere cavity on a mesh
+    refined around the source (every axis dx down to dx/2, Gaussian profile;
+    dt at the refined Courant limit), reset + `tsteps` steps per run, device
+    time with CUDA events; the plain kernel's scaled-difference variant
+    (temporal blocking takes uniform meshes only). Roofline of that kernel:
+    the same 52 B per cell as the uniform plain kernel (the ratio arrays are
+    a few KB, read from L1) over its event-timed launches."""
+    import torch
+    from paper_1301_4539_gb300 import sophie as so
+    from paper_1301_4539_gb300 import workloads as wl
+    w = wl.sphere_cavity_graded(n)
+    g = so.Grid(n, n, n, w["dx"], w["dt"])
+    g.set_stream(stream.cuda_stream)
+    g.set_materials(w["eps"], w["sigma"])
+    g.set_spacing(*w["widths"])
+    for src in w["sources"]:
+        g.add_source(*src)
+    for p in w["probes"]:
+        g.add_probe(*p)
+    k, _ = g.autotune()
+    g.reset()
+    g.step(50)
+    g.profile(True)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    energy = None
+    for _ in range(reps):
+        g.reset()
+        g.step(tsteps)
+        energy = g.energy()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    kl, kms = g.profile_read(so.KERNEL_PLAIN)
+    g.profile(False)
+    g.close()
+    rate = n ** 3 * tsteps * reps / (ms / 1e3) / 1e9
+    achieved = n ** 3 * (FIELD_BYTES + MAT_BYTES) / (kms / max(kl, 1) / 1e3) / 1e9
+    return {"workload": f"{n}^3 PEC sphere cavity on a graded mesh (widths 1 mm to 0.5 mm towards the centre "
+                        f"along every axis, dt {w['dt']:.4g} s), {tsteps} steps per run",
+            "gcell_per_s": rate, "unit": "Gcell-updates/s", "temporal_k": k, "vs_uniform_k1": rate / uniform_k1,
+            "roofline": {"kernel": "yee_plain (non-uniform)", "bound": "hbm", "achieved": achieved,
+                         "peak": peaks()[0], "unit": "GB/s", "frac": achieved / peaks()[0],
+                         "avg_launch_ms": kms / max(kl, 1), "launches": kl},
+            "energy_J": energy}
 
 
 def run_batch(ncav: int = 4096, tsteps: int = 500):

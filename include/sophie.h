@@ -221,7 +221,7 @@ int sophie_sync(sophie_grid *g);
  * the current fields; synchronises. In the non-float modes one launch loads
  * the stored fields, computes its k steps in float and rounds once when
  * storing, so results depend on k (no longer bitwise equal across k).
- * Errors: EINVAL, ENOTSUP, ENOMEM.
+ * Errors: EINVAL, ENOTSUP (also temporal_k >= 2 on a non-uniform mesh), ENOMEM.
  */
 int sophie_configure(sophie_grid *g, int temporal_k, int tile_x, int tile_y, int precision);
 
@@ -261,6 +261,35 @@ int sophie_autotune(sophie_grid *g, int *temporal_k, double *ms_per_step);
  */
 int sophie_set_zero_skip(sophie_grid *g, int enable);
 
+/*
+ * Non-uniform mesh (Sec. 2.2: the loop's geometric coefficients are 1-D
+ * arrays dx(i), dy(j), dz(k)). wx (nx doubles), wy (ny), wz (nz): the cell
+ * widths in metres along each axis, host arrays copied by the call; NULL
+ * keeps that axis uniform with step dx, and all three NULL return the grid
+ * to the uniform mesh. With the grid's dx as the reference step (S = c dt/dx
+ * as before), every difference of a curl bracket is scaled by dx / (the
+ * width it spans), rounded to float once per width:
+ *   H update: primary widths, e.g. hx: rz(k) (ey(k+1) - ey(k)) - ry(j) (ez(j+1) - ez(j))
+ *   E update: dual widths (the mean of the two cells beside the node; the
+ *             end cell's width at a wall node, which only weighs the static
+ *             wall-normal faces in the energy),
+ *             e.g. ex: ryd(j) (hz(j) - hz(j-1)) - rzd(k) (hy(k) - hy(k-1))
+ * evaluated as br = fma(ra, a1 - a0, -(rb * (b1 - b0))); with every width
+ * equal to dx the fields and energies are bitwise those of the uniform mesh. Material
+ * coefficients (Ca, Cb) are unchanged (the ratios carry the geometry), and
+ * sophie_energy weights each term by its edge or face volume in units of
+ * dx^3, so the lossless energy stays conserved.
+ * Steps run on the plain step kernel (either tile choice, every storage
+ * format) with k = 1; zero-field skipping applies as usual. Stability needs
+ * c dt sqrt(1/min(wx)^2 + 1/min(wy)^2 + 1/min(wz)^2) <= 1.
+ * A probe objective record (sophie_objective_forward) is invalidated; probe
+ * objectives need the uniform mesh.
+ * Errors: EINVAL (NULL grid, a width not finite and > 0), EUNSTABLE (dt above
+ * that limit), ENOTSUP (the grid is configured with temporal_k >= 2, which
+ * the temporally blocked kernel does not support on this mesh), ENOMEM, ECUDA.
+ */
+int sophie_set_spacing(sophie_grid *g, const double *wx, const double *wy, const double *wz);
+
 /* Number of kernels this grid has launched since creation. */
 int sophie_launch_count(sophie_grid *g, long long *launches);
 
@@ -291,7 +320,8 @@ int sophie_profile_read(sophie_grid *g, int kernel, long long *launches, double 
  * sophie_objective_release or sophie_destroy_grid.
  * Errors: EINVAL (NULL, nsteps < 1, point outside comp's range or on a plane
  * i == nx, j == ny or k == nz), ENOTSUP (half or bfloat16 storage; all probe
- * slots in use, the objective needs one), ENOMEM (checkpoints), ECUDA,
+ * slots in use, the objective needs one; a non-uniform mesh), ENOMEM
+ * (checkpoints), ECUDA,
  * ETIMEOUT, ENONFINITE.
  *
  * sophie_objective_grad_eps returns dJ/d eps_r(cell) for the box of cells

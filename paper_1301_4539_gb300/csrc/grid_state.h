@@ -149,7 +149,13 @@ struct sophie_grid {
   bool zskip = false;
   bool box_all = false;
   int zbox[6] = {0, 0, 0, 0, 0, 0};
-  long long gen = 0;       // bumped by every change of fields, materials or sources
+  // Non-uniform mesh (sophie_set_spacing): one device allocation holding the
+  // six float ratio arrays rx, ry, rz, rxd, ryd, rzd back to back, then the
+  // padded (primary, dual) pair arrays of x, y, z (StepArgs::rpair); null
+  // when the mesh is uniform.
+  float* rat = nullptr;
+  long long rpair_off[3] = {0, 0, 0};  // float offset of each pair array's index 0
+  long long gen = 0;       // bumped by every change of fields, materials, sources or mesh
   bool obj_rec = false;    // the step kernels also sample the objective point
   sophie::grid::Tape tape;
 };

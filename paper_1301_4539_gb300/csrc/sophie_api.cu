@@ -298,6 +298,13 @@ StepArgs make_step_args(sophie_grid* g) {
     a.prb.n += 1;
   }
   a.prb.buf = g->pbuf;
+  if (g->rat) {
+    const Dims& d = g->d;
+    const long long off[6] = {0, d.nx, d.nx + d.ny, d.nx + d.ny + d.nz, 2ll * d.nx + d.ny + d.nz + 1,
+                              2ll * (d.nx + d.ny) + d.nz + 2};
+    for (int q = 0; q < 6; ++q) a.rat[q] = g->rat + off[q];
+    for (int q = 0; q < 3; ++q) a.rpair[q] = reinterpret_cast<const float2*>(g->rat + g->rpair_off[q]);
+  }
   a.prb.cap = g->pcap;
   a.err = g->err;
   a.box[0] = 0;
@@ -386,6 +393,7 @@ void free_grid(sophie_grid* g) {
   if (g->e_partials) cudaFree(g->e_partials);
   if (g->e_out) cudaFree(g->e_out);
   if (g->err) cudaFree(g->err);
+  if (g->rat) cudaFree(g->rat);
   if (g->mat_upload_done) cudaEventDestroy(g->mat_upload_done);
   for (ProfEntry& p : g->prof_live) {
     cudaEventDestroy(p.a);
@@ -606,11 +614,11 @@ int run_autotune(sophie_grid* g, double* best_ms_per_step) {
       best_p = pt;
     }
   }
-  if (g->fmt == kF32) {
+  if (g->fmt == kF32 || g->rat) {
     best = best_plain;
     best_k = 1;
   }
-  for (int K = 2; K <= 4; ++K) {
+  for (int K = 2; K <= 4 && !g->rat; ++K) {  // the blocked kernel takes uniform meshes only
     if (g->fmt != kF32 && K != 2) continue;
     for (int aligned = 1; aligned >= 0; --aligned) {
       const BlockedTiling bt = blocked_tiling(d, K, g->num_sms, aligned);
@@ -939,7 +947,7 @@ int sophie_step(sophie_grid* g, int n) {
   }
   for (int m = 0; m < n;) {
     const int K = g->temporal_k == 0 ? g->tuned_k : g->temporal_k;
-    const bool blocked = !g->use_simple && K >= 2 && n - m >= K && blocked_supported(K);
+    const bool blocked = !g->use_simple && !g->rat && K >= 2 && n - m >= K && blocked_supported(K);
     StepArgs a = make_step_args(g);
     const int adv_steps = blocked ? K : 1;
     // Zero-field skipping: this launch covers only the tiles and planes of the
@@ -1137,6 +1145,8 @@ int sophie_configure(sophie_grid* g, int temporal_k, int tile_x, int tile_y, int
   if (temporal_k < 0 || temporal_k > 8) return fail(SOPHIE_EINVAL, "temporal_k must be in 0..8");
   if (temporal_k >= 2 && !blocked_supported(temporal_k))
     return fail(SOPHIE_ENOTSUP, "temporal_k = %d not built (supported: 1..4)", temporal_k);
+  if (temporal_k >= 2 && g->rat)
+    return fail(SOPHIE_ENOTSUP, "the temporally blocked kernel takes uniform meshes only");
   if (tile_x < 0 || tile_y < 0) return fail(SOPHIE_EINVAL, "tile sizes must be >= 0");
   if (tile_x != 0 && tile_x != 32 && tile_x != 64) return fail(SOPHIE_EINVAL, "tile_x must be 0, 32 or 64");
   if (precision < SOPHIE_FP32 || precision > SOPHIE_FP16HL)
@@ -1163,6 +1173,87 @@ int sophie_configure(sophie_grid* g, int temporal_k, int tile_x, int tile_y, int
 int sophie_set_zero_skip(sophie_grid* g, int enable) {
   if (!g) return fail(SOPHIE_EINVAL, "NULL grid");
   g->zskip = enable != 0;
+  return SOPHIE_OK;
+}
+
+int sophie_set_spacing(sophie_grid* g, const double* wx, const double* wy, const double* wz) {
+  if (!g) return fail(SOPHIE_EINVAL, "NULL grid");
+  const Dims& d = g->d;
+  if (!wx && !wy && !wz) {
+    if (g->rat) {
+      CUDA_TRY(cudaStreamSynchronize(g->stream));
+      cudaFree(g->rat);
+      g->rat = nullptr;
+      g->gen++;
+      g->tuned = false;
+    }
+    return SOPHIE_OK;
+  }
+  if (g->temporal_k >= 2)
+    return fail(SOPHIE_ENOTSUP, "the grid runs the temporally blocked kernel (temporal_k = %d), "
+                "which takes uniform meshes only", g->temporal_k);
+  const double* w[3] = {wx, wy, wz};
+  const int n[3] = {d.nx, d.ny, d.nz};
+  double inv2 = 0.0;
+  for (int a = 0; a < 3; ++a) {
+    double wmin = g->dx;
+    if (w[a]) {
+      wmin = HUGE_VAL;
+      for (int i = 0; i < n[a]; ++i) {
+        if (!(w[a][i] > 0) || !std::isfinite(w[a][i]))
+          return fail(SOPHIE_EINVAL, "width %d along axis %d is %g (must be finite and > 0)", i, a, w[a][i]);
+        wmin = std::min(wmin, w[a][i]);
+      }
+    }
+    inv2 += 1.0 / (wmin * wmin);
+  }
+  if (kC0 * g->dt * std::sqrt(inv2) > 1.0 + 1e-12)
+    return fail(SOPHIE_EUNSTABLE, "dt above the Courant limit of the smallest cells");
+  // Ratios dx / width (primary) and dx / ((w[i-1] + w[i]) / 2) (dual; at a
+  // wall node the end cell's own width, so the wall-normal faces weigh a whole
+  // cell in the energy as on the uniform mesh), each computed in double and
+  // rounded once.
+  std::vector<float> h;
+  h.reserve(2 * (size_t)(d.nx + d.ny + d.nz) + 3);
+  auto width = [&](int a, int i) { return w[a] ? w[a][i] : g->dx; };
+  for (int a = 0; a < 3; ++a)
+    for (int i = 0; i < n[a]; ++i) h.push_back((float)(g->dx / width(a, i)));
+  for (int a = 0; a < 3; ++a)
+    for (int i = 0; i <= n[a]; ++i) {
+      const double lo = width(a, i > 0 ? i - 1 : 0), hi = width(a, i < n[a] ? i : n[a] - 1);
+      h.push_back((float)(g->dx / ((lo + hi) / 2.0)));
+    }
+  // Pair arrays: (r(i), rd(i)) at pair index i, zero outside [0, n) resp.
+  // [0, n]; each starts on a 16-byte boundary with kRatioPad pairs before it.
+  const size_t nplain = h.size();
+  const long long doff[3] = {d.nx + d.ny + d.nz, 2ll * d.nx + d.ny + d.nz + 1, 2ll * (d.nx + d.ny) + d.nz + 2};
+  long long rpo[3];
+  size_t pos = (nplain + 3) / 4 * 4;
+  for (int a = 0; a < 3; ++a) {
+    const long long pairs = kRatioPad + n[a] + kRatioTail;
+    rpo[a] = (long long)pos + 2 * kRatioPad;
+    h.resize(pos + 2 * (size_t)pairs, 0.f);
+    const long long poff = a == 0 ? 0 : a == 1 ? d.nx : d.nx + d.ny;
+    for (int i = 0; i <= n[a]; ++i) {
+      if (i < n[a]) h[(size_t)(rpo[a] + 2 * i)] = h[(size_t)(poff + i)];
+      h[(size_t)(rpo[a] + 2 * i + 1)] = h[(size_t)(doff[a] + i)];
+    }
+    pos = (h.size() + 3) / 4 * 4;
+  }
+  CUDA_TRY(cudaStreamSynchronize(g->stream));
+  if (g->rat) {
+    cudaFree(g->rat);
+    g->rat = nullptr;
+  }
+  if (dev_malloc((void**)&g->rat, h.size() * sizeof(float)) != cudaSuccess) {
+    cudaGetLastError();
+    g->rat = nullptr;
+    return fail(SOPHIE_ENOMEM, "ratio array allocation failed");
+  }
+  for (int a = 0; a < 3; ++a) g->rpair_off[a] = rpo[a];
+  CUDA_TRY(cudaMemcpy(g->rat, h.data(), h.size() * sizeof(float), cudaMemcpyHostToDevice));
+  g->gen++;
+  g->tuned = false;
   return SOPHIE_OK;
 }
 

@@ -94,7 +94,27 @@ struct StepArgs {
   // (the fields there are known to be zero and stay zero; see sophie.h,
   // sophie_set_zero_skip). The full grid when skipping is off.
   int box[6];
+  // Non-uniform mesh (sophie_set_spacing): device arrays of the float ratios
+  // reference step / cell width, rat[0..2] = rx[nx], ry[ny], rz[nz] (primary
+  // widths) and rat[3..5] = rxd[nx+1], ryd[ny+1], rzd[nz+1] (dual widths, the
+  // mean of the two cells beside a node; the end cell's at a wall node). All
+  // null on a uniform mesh.
+  const float* rat[6];
+  // The same ratios as (primary, dual) pairs per index, one array per axis,
+  // zero-padded so that rpair[a][i] is readable for i in [-kRatioPad,
+  // n_a + kRatioTail) and 16-byte aligned at even i (two pairs per 16-byte
+  // load); entries outside an array's range are 0.
+  const float2* rpair[3];
 };
+
+constexpr int kRatioPad = 8;    // pairs before index 0
+constexpr int kRatioTail = 72;  // pairs from index n on (a 64-wide tile plus halo beyond the last cell)
+
+// Ratio of a non-uniform mesh at index i, 0 outside [0, n) (such points only
+// feed values that are discarded or multiplied by a zero coefficient).
+__device__ __forceinline__ float ratio_at(const float* r, int i, int n) {
+  return (unsigned)i < (unsigned)n ? r[i] : 0.f;
+}
 
 // Whether the output block [x0, x1) x [y0, y1) x [z0, z1) meets the launch box.
 __host__ __device__ __forceinline__ bool box_meets(const int* b, int x0, int x1, int y0, int y1, int z0, int z1) {

@@ -35,6 +35,7 @@ int sophie_objective_forward(sophie_grid* g, int nsteps, int comp, int i, int j,
   if (i == g->d.nx || j == g->d.ny || k == g->d.nz)
     return fail(SOPHIE_EINVAL, "objective point on a plane no step updates");
   if (g->fmt != kF32) return fail(SOPHIE_ENOTSUP, "gradients need float field storage");
+  if (g->rat) return fail(SOPHIE_ENOTSUP, "gradients need a uniform mesh");
   if ((int)g->prb.size() >= kMaxProbes) return fail(SOPHIE_ENOTSUP, "all %d probe slots are in use", kMaxProbes);
   Tape& t = g->tape;
   t.valid = false;

@@ -26,6 +26,8 @@ __device__ __forceinline__ float ld_f(const float* f, const Dims& d, int c, int 
   return f[(long long)z * d.zstride + (long long)c * d.plane + (long long)y * d.nxp + x];
 }
 
+// NU: non-uniform mesh, every difference scaled by its ratio (a.rat).
+template <bool NU>
 __global__ void __launch_bounds__((kSTX + 1) * (kSTY + 1))
 yee_step_simple_kernel(StepArgs a) {
   __shared__ float sE[3][kSTY + 2][kSTX + 2];
@@ -41,12 +43,23 @@ yee_step_simple_kernel(StepArgs a) {
   const float S = a.S;
   const bool owner = tx >= 1 && ty >= 1 && x < d.nx && y < d.ny;
   float hxp = 0.f, hyp = 0.f;  // new hx, hy of the plane below (own column)
+  // h^{n+1/2} at plane z0-1 is only needed for hx, hy of this column; it is
+  // recomputed in the first loop pass below (no store).
   const int zs = z0 > 0 ? z0 - 1 : 0;
-  if (z0 > 0) {
-    // h^{n+1/2} at plane z0-1 is only needed for hx, hy of this column; it is
-    // recomputed in the first loop pass below (no store).
+  // Ratios of this thread's column and row (1 and unused on a uniform mesh).
+  float rx = 1.f, ry = 1.f, rxd = 1.f, ryd = 1.f;
+  if constexpr (NU) {
+    rx = ratio_at(a.rat[0], x, d.nx);
+    ry = ratio_at(a.rat[1], y, d.ny);
+    rxd = ratio_at(a.rat[3], x, d.nx + 1);
+    ryd = ratio_at(a.rat[4], y, d.ny + 1);
   }
   for (int z = zs; z < z1; ++z) {
+    float rz = 1.f, rzd = 1.f;
+    if constexpr (NU) {
+      rz = __ldg(a.rat[2] + z);
+      rzd = __ldg(a.rat[5] + z);
+    }
     for (int c = 0; c < 3; ++c) {
       sE[c][ty][tx] = ld_f(fin, d, c, x, y, z);
       if (tx == kSTX) sE[c][ty][tx + 1] = ld_f(fin, d, c, x + 1, y, z);
@@ -59,9 +72,9 @@ yee_step_simple_kernel(StepArgs a) {
     float hz = ld_f(fin, d, 5, x, y, z);
     const float ey1 = ld_f(fin, d, 1, x, y, z + 1);
     const float ex1 = ld_f(fin, d, 0, x, y, z + 1);
-    hx = h_upd(hx, S, ey1, ey0, sE[2][ty + 1][tx], ez0);
-    hy = h_upd(hy, S, sE[2][ty][tx + 1], ez0, ex1, ex0);
-    hz = h_upd(hz, S, sE[0][ty + 1][tx], ex0, sE[1][ty][tx + 1], ey0);
+    hx = h_upd_r<NU>(hx, S, rz, ey1, ey0, ry, sE[2][ty + 1][tx], ez0);
+    hy = h_upd_r<NU>(hy, S, rx, sE[2][ty][tx + 1], ez0, rz, ex1, ex0);
+    hz = h_upd_r<NU>(hz, S, ry, sE[0][ty + 1][tx], ex0, rx, sE[1][ty][tx + 1], ey0);
     sH[0][ty][tx] = hx;
     sH[1][ty][tx] = hy;
     sH[2][ty][tx] = hz;
@@ -74,9 +87,9 @@ yee_step_simple_kernel(StepArgs a) {
       const float2 cx = ex_pt ? e3[0] : a.coef[cls_of(m, 0)];
       const float2 cy = ex_pt ? e3[1] : a.coef[cls_of(m, 1)];
       const float2 cz = ex_pt ? e3[2] : a.coef[cls_of(m, 2)];
-      float bx = curl_br(hz, sH[2][ty - 1][tx], hy, hyp);
-      float by = curl_br(hx, hxp, hz, sH[2][ty][tx - 1]);
-      float bz = curl_br(hy, sH[1][ty][tx - 1], hx, sH[0][ty - 1][tx]);
+      float bx = bracket<NU>(ryd, hz, sH[2][ty - 1][tx], rzd, hy, hyp);
+      float by = bracket<NU>(rzd, hx, hxp, rxd, hz, sH[2][ty][tx - 1]);
+      float bz = bracket<NU>(rxd, hy, sH[1][ty][tx - 1], ryd, hx, sH[0][ty - 1][tx]);
       if (m & kSrcFlag) {
         for (int s = 0; s < a.src.n; ++s) {
           if (a.src.pos[s] != pt) continue;
@@ -109,8 +122,9 @@ yee_step_simple_kernel(StepArgs a) {
 }
 
 // ---------------------------------------------------------------------------
-// Discrete energy, Sec. 2.1 antisymmetric form (see sophie_energy in sophie.h).
-// Grid-stride over index points; fixed-order block tree; deterministic.
+// Discrete energy, Sec. 2.1 antisymmetric form (see sophie_energy in sophie.h),
+// volume-weighted on a non-uniform mesh. Grid-stride over index points;
+// fixed-order block tree; deterministic.
 constexpr int kEThreads = 256;
 
 __device__ __forceinline__ double block_sum(double v, double* sh) {
@@ -126,7 +140,7 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
 }
 
 
-template <int F>
+template <int F, bool NU>
 __global__ void __launch_bounds__(kEThreads)
 energy_partial_kernel(const __grid_constant__ StepArgs a, const double* eps_tab, double* partials) {
   __shared__ double sh[kEThreads / 32];
@@ -143,7 +157,10 @@ energy_partial_kernel(const __grid_constant__ StepArgs a, const double* eps_tab,
     const long long r = pt / d.nxp;
     const int y = (int)(r % d.ny1);
     const int z = (int)(r / d.ny1);
-    acc += point_energy<F>(f, d, isc, S, mat[pt], eps_tab, a.eeps, x, y, z);
+    if constexpr (NU)
+      acc += point_energy_nu<F>(f, d, isc, S, mat[pt], eps_tab, a.eeps, a.rat, x, y, z);
+    else
+      acc += point_energy<F>(f, d, isc, S, mat[pt], eps_tab, a.eeps, x, y, z);
   }
   const double t = block_sum(acc, sh);
   if (threadIdx.x == 0) partials[blockIdx.x] = t;
@@ -189,7 +206,10 @@ __global__ void or_flag_kernel(uint32_t* mat, long long pos, uint32_t bit) { mat
 
 cudaError_t launch_step_simple(const StepArgs& a, cudaStream_t s) {
   dim3 grid((a.d.nx + kSTX - 1) / kSTX, (a.d.ny + kSTY - 1) / kSTY, (a.d.nz + kSZ - 1) / kSZ);
-  yee_step_simple_kernel<<<grid, (kSTX + 1) * (kSTY + 1), 0, s>>>(a);
+  if (a.rat[0])
+    yee_step_simple_kernel<true><<<grid, (kSTX + 1) * (kSTY + 1), 0, s>>>(a);
+  else
+    yee_step_simple_kernel<false><<<grid, (kSTX + 1) * (kSTY + 1), 0, s>>>(a);
   return cudaGetLastError();
 }
 
@@ -204,7 +224,10 @@ int energy_blocks(const Dims& d) {
 template <int F>
 cudaError_t launch_energy_f(const StepArgs& a, const double* eps_tab, double* partials, int nblocks, double scale,
                             double* out, cudaStream_t s) {
-  energy_partial_kernel<F><<<nblocks, kEThreads, 0, s>>>(a, eps_tab, partials);
+  if (a.rat[0])
+    energy_partial_kernel<F, true><<<nblocks, kEThreads, 0, s>>>(a, eps_tab, partials);
+  else
+    energy_partial_kernel<F, false><<<nblocks, kEThreads, 0, s>>>(a, eps_tab, partials);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   energy_final_kernel<<<1, kEThreads, 0, s>>>(partials, nblocks, scale, out);

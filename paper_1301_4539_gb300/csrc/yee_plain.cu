@@ -84,11 +84,15 @@ __device__ __forceinline__ void set_err(int* err, int code) { atomicOr(err, code
 // every cavity); each unit takes its tensor maps, sizes, output buffer,
 // coefficient tables and sources from its cavity's descriptor. Otherwise the
 // units tile the single grid of `a` as described by `t`.
-template <int FMT, bool BATCH>
+// NU: non-uniform mesh; every difference is scaled by the ratio of the width
+// it spans (a.rat): a lane keeps the ratios of its two columns and two rows,
+// the plane's ratio is read per plane.
+template <int FMT, bool BATCH, bool NU>
 __global__ void __launch_bounds__(kThreads, 2)
 yee_plain_kernel(const __grid_constant__ CUtensorMap tmF, const __grid_constant__ CUtensorMap tmM,
                  const __grid_constant__ StepArgs a, PlainTiling t, PlainBatch pb) {
   static_assert(!BATCH || FMT == kF32, "batches store float fields");
+  static_assert(!(BATCH && NU), "batches are uniform meshes");
   using C = PCfg<FMT>;
   using St = Store<FMT>;
   using T = typename C::T;
@@ -231,6 +235,27 @@ yee_plain_kernel(const __grid_constant__ CUtensorMap tmF, const __grid_constant_
     const int ps = w.z0 > 0 ? w.z0 - 1 : 0;
     float hxp[2][2] = {{0.f, 0.f}, {0.f, 0.f}}, hyp[2][2] = {{0.f, 0.f}, {0.f, 0.f}};
     for (int z = ps; z < w.z1; ++z, ++C_) {
+      // Ratios of this lane's columns, rows, halo point and plane (1, unused,
+      // on a uniform mesh): (primary, dual) pairs of the padded arrays, the
+      // two columns (rows) in one 16-byte load, read per plane from L1 (once
+      // for the H phase, again for the E phase) rather than held in
+      // registers across the loop.
+      float rxv[2] = {1.f, 1.f}, rxdv[2] = {1.f, 1.f}, ryv[2] = {1.f, 1.f}, rydv[2] = {1.f, 1.f};
+      float rxh = 1.f, ryh = 1.f, rz = 1.f, rzd = 1.f;
+      const int xl = w.x0 + 2 * lane, yl = w.y0 + 2 * warp;  // even: 16-byte aligned pairs
+      if constexpr (NU) {
+        const float4 px = *reinterpret_cast<const float4*>(a.rpair[0] + xl);
+        const float4 py = *reinterpret_cast<const float4*>(a.rpair[1] + yl);
+        rxv[0] = px.x;
+        rxv[1] = px.z;
+        ryv[0] = py.x;
+        ryv[1] = py.z;
+        if (hr >= 0) {
+          rxh = a.rpair[0][w.x0 - OX + hc].x;
+          ryh = a.rpair[1][w.y0 - 1 + hr].x;
+        }
+        rz = a.rpair[2][z].x;
+      }
       const int sc = (int)(C_ % kNS), sn = (int)((C_ + 1) % kNS);
       const bool ok = mbar_wait(full(sc), (uint32_t)((C_ / kNS) & 1)) &&
                       mbar_wait(full(sn), (uint32_t)(((C_ + 1) / kNS) & 1));
@@ -277,12 +302,12 @@ yee_plain_kernel(const __grid_constant__ CUtensorMap tmF, const __grid_constant_
           }
           const float ez_ip1 = St::ld(&F[FI(2, row, c0 + 2)], a.isc[2]);
           const float ey_ip1 = St::ld(&F[FI(1, row, c0 + 2)], a.isc[1]);
-          hx[r][0] = h_upd(vhx.x, S, ney.x, ey[r][0], ezj[0], ez[r][0]);
-          hx[r][1] = h_upd(vhx.y, S, ney.y, ey[r][1], ezj[1], ez[r][1]);
-          hy[r][0] = h_upd(vhy.x, S, ez[r][1], ez[r][0], nex.x, ex[r][0]);
-          hy[r][1] = h_upd(vhy.y, S, ez_ip1, ez[r][1], nex.y, ex[r][1]);
-          hz[r][0] = h_upd(vhz.x, S, exj[0], ex[r][0], ey[r][1], ey[r][0]);
-          hz[r][1] = h_upd(vhz.y, S, exj[1], ex[r][1], ey_ip1, ey[r][1]);
+          hx[r][0] = h_upd_r<NU>(vhx.x, S, rz, ney.x, ey[r][0], ryv[r], ezj[0], ez[r][0]);
+          hx[r][1] = h_upd_r<NU>(vhx.y, S, rz, ney.y, ey[r][1], ryv[r], ezj[1], ez[r][1]);
+          hy[r][0] = h_upd_r<NU>(vhy.x, S, rxv[0], ez[r][1], ez[r][0], rz, nex.x, ex[r][0]);
+          hy[r][1] = h_upd_r<NU>(vhy.y, S, rxv[1], ez_ip1, ez[r][1], rz, nex.y, ex[r][1]);
+          hz[r][0] = h_upd_r<NU>(vhz.x, S, ryv[r], exj[0], ex[r][0], rxv[0], ey[r][1], ey[r][0]);
+          hz[r][1] = h_upd_r<NU>(vhz.y, S, ryv[r], exj[1], ex[r][1], rxv[1], ey_ip1, ey[r][1]);
           *reinterpret_cast<float2*>(hp(0, row, c0)) = make_float2(hx[r][0], hx[r][1]);
           *reinterpret_cast<float2*>(hp(1, row, c0)) = make_float2(hy[r][0], hy[r][1]);
           *reinterpret_cast<float2*>(hp(2, row, c0)) = make_float2(hz[r][0], hz[r][1]);
@@ -291,12 +316,15 @@ yee_plain_kernel(const __grid_constant__ CUtensorMap tmF, const __grid_constant_
           const float e0 = St::ld(&F[FI(0, hr, hc)], a.isc[0]);
           const float e1 = St::ld(&F[FI(1, hr, hc)], a.isc[1]);
           const float e2 = St::ld(&F[FI(2, hr, hc)], a.isc[2]);
-          const float nx_ = h_upd(St::ld(&F[FI(3, hr, hc)], a.isc[3]), S, St::ld(&Fn[FI(1, hr, hc)], a.isc[1]), e1,
-                                  St::ld(&F[FI(2, hr + 1, hc)], a.isc[2]), e2);
-          const float ny_ = h_upd(St::ld(&F[FI(4, hr, hc)], a.isc[4]), S, St::ld(&F[FI(2, hr, hc + 1)], a.isc[2]),
-                                  e2, St::ld(&Fn[FI(0, hr, hc)], a.isc[0]), e0);
-          const float nz_ = h_upd(St::ld(&F[FI(5, hr, hc)], a.isc[5]), S, St::ld(&F[FI(0, hr + 1, hc)], a.isc[0]),
-                                  e0, St::ld(&F[FI(1, hr, hc + 1)], a.isc[1]), e1);
+          const float nx_ = h_upd_r<NU>(St::ld(&F[FI(3, hr, hc)], a.isc[3]), S, rz,
+                                        St::ld(&Fn[FI(1, hr, hc)], a.isc[1]), e1, ryh,
+                                        St::ld(&F[FI(2, hr + 1, hc)], a.isc[2]), e2);
+          const float ny_ = h_upd_r<NU>(St::ld(&F[FI(4, hr, hc)], a.isc[4]), S, rxh,
+                                        St::ld(&F[FI(2, hr, hc + 1)], a.isc[2]), e2, rz,
+                                        St::ld(&Fn[FI(0, hr, hc)], a.isc[0]), e0);
+          const float nz_ = h_upd_r<NU>(St::ld(&F[FI(5, hr, hc)], a.isc[5]), S, ryh,
+                                        St::ld(&F[FI(0, hr + 1, hc)], a.isc[0]), e0, rxh,
+                                        St::ld(&F[FI(1, hr, hc + 1)], a.isc[1]), e1);
           *hp(0, hr, hc) = nx_;
           *hp(1, hr, hc) = ny_;
           *hp(2, hr, hc) = nz_;
@@ -321,6 +349,15 @@ yee_plain_kernel(const __grid_constant__ CUtensorMap tmF, const __grid_constant_
       }
       const bool out_plane = z >= w.z0;
       const uint32_t* M = sM(sc);
+      if constexpr (NU) {
+        const float4 px = *reinterpret_cast<const float4*>(a.rpair[0] + xl);
+        const float4 py = *reinterpret_cast<const float4*>(a.rpair[1] + yl);
+        rxdv[0] = px.y;
+        rxdv[1] = px.w;
+        rydv[0] = py.y;
+        rydv[1] = py.w;
+        rzd = a.rpair[2][z].y;
+      }
 #pragma unroll
       for (int r = 0; r < 2; ++r) {
         const int row = r0 + r;
@@ -343,9 +380,9 @@ yee_plain_kernel(const __grid_constant__ CUtensorMap tmF, const __grid_constant_
 #pragma unroll
         for (int cc = 0; cc < 2; ++cc) {
           const uint32_t m = cc ? m2.y : m2.x;
-          float bx = curl_br(hz[r][cc], hzj[cc], hy[r][cc], hyp[r][cc]);
-          float by = curl_br(hx[r][cc], hxp[r][cc], hz[r][cc], cc ? hz[r][0] : hz_im);
-          float bz = curl_br(hy[r][cc], cc ? hy[r][0] : hy_im, hx[r][cc], hxj[cc]);
+          float bx = bracket<NU>(rydv[r], hz[r][cc], hzj[cc], rzd, hy[r][cc], hyp[r][cc]);
+          float by = bracket<NU>(rzd, hx[r][cc], hxp[r][cc], rxdv[cc], hz[r][cc], cc ? hz[r][0] : hz_im);
+          float bz = bracket<NU>(rxdv[cc], hy[r][cc], cc ? hy[r][0] : hy_im, rydv[r], hx[r][cc], hxj[cc]);
           if ((m & kSrcFlag) && out_plane) {
             const float3 b3 = apply_sources(make_float3(bx, by, bz),
                                             ((long long)z * d.ny1() + y) * d.nxp() + x + cc, a.n0, srct());
@@ -481,18 +518,24 @@ PlainTiling plain_tiling(const Dims& d, int num_sms, int zchunk_override) {
   return best;
 }
 
-template <int F>
-cudaError_t launch_plain_f(const StepArgs& a, const CUtensorMap& tmF, const CUtensorMap& tmM, const PlainTiling& t,
-                           cudaStream_t s) {
+template <int F, bool NU>
+cudaError_t launch_plain_fn(const StepArgs& a, const CUtensorMap& tmF, const CUtensorMap& tmM, const PlainTiling& t,
+                            cudaStream_t s) {
   static bool attr = false;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(yee_plain_kernel<F, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(yee_plain_kernel<F, false, NU>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)PCfg<F>::kSmemBytes);
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  yee_plain_kernel<F, false><<<t.grid, kThreads, PCfg<F>::kSmemBytes, s>>>(tmF, tmM, a, t, PlainBatch{});
+  yee_plain_kernel<F, false, NU><<<t.grid, kThreads, PCfg<F>::kSmemBytes, s>>>(tmF, tmM, a, t, PlainBatch{});
   return cudaGetLastError();
+}
+
+template <int F>
+cudaError_t launch_plain_f(const StepArgs& a, const CUtensorMap& tmF, const CUtensorMap& tmM, const PlainTiling& t,
+                           cudaStream_t s) {
+  return a.rat[0] ? launch_plain_fn<F, true>(a, tmF, tmM, t, s) : launch_plain_fn<F, false>(a, tmF, tmM, t, s);
 }
 
 PlainTiling plain_tiling_box(const Dims& d, int num_sms, const int* box) {
@@ -521,14 +564,14 @@ int plain_tile_y() { return kPY; }
 cudaError_t launch_step_plain_batch(const StepArgs& a, const PlainBatch& pb, int grid, cudaStream_t s) {
   static bool attr = false;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(yee_plain_kernel<kF32, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)PCfg<kF32>::kSmemBytes);
+    cudaError_t e = cudaFuncSetAttribute(yee_plain_kernel<kF32, true, false>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PCfg<kF32>::kSmemBytes);
     if (e != cudaSuccess) return e;
     attr = true;
   }
   CUtensorMap none{};
   PlainTiling t{};
-  yee_plain_kernel<kF32, true><<<grid, kThreads, PCfg<kF32>::kSmemBytes, s>>>(none, none, a, t, pb);
+  yee_plain_kernel<kF32, true, false><<<grid, kThreads, PCfg<kF32>::kSmemBytes, s>>>(none, none, a, t, pb);
   return cudaGetLastError();
 }
 

@@ -49,6 +49,7 @@ SIGNATURES = {
     "sophie_set_storage_scale": (_I, [_P, _P]),
     "sophie_autotune": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(_D)]),
     "sophie_set_zero_skip": (_I, [_P, _I]),
+    "sophie_set_spacing": (_I, [_P, _P, _P, _P]),
     "sophie_launch_count": (_I, [_P, ctypes.POINTER(_LL)]),
     "sophie_profile": (_I, [_P, _I]),
     "sophie_profile_read": (_I, [_P, _I, ctypes.POINTER(_LL), ctypes.POINTER(_D)]),
@@ -223,6 +224,13 @@ def sophie_set_zero_skip(g: int, enable: bool) -> None:
     _chk(load().sophie_set_zero_skip(g, 1 if enable else 0))
 
 
+def sophie_set_spacing(g: int, wx, wy, wz) -> None:
+    """Cell widths along x, y, z (metres; None = uniform dx on that axis)."""
+    arrs = [None if w is None else np.ascontiguousarray(w, np.float64) for w in (wx, wy, wz)]
+    ptrs = [None if a is None else a.ctypes.data for a in arrs]
+    _chk(load().sophie_set_spacing(g, *ptrs))
+
+
 def sophie_launch_count(g: int) -> int:
     n = _LL()
     _chk(load().sophie_launch_count(g, ctypes.byref(n)))
@@ -335,6 +343,13 @@ class Grid:
 
     def set_zero_skip(self, enable=True):
         sophie_set_zero_skip(self.h, enable)
+
+    def set_spacing(self, wx=None, wy=None, wz=None):
+        """Non-uniform mesh: cell widths (nx, ny, nz arrays, metres); all None = uniform."""
+        for w, n in ((wx, self.nx), (wy, self.ny), (wz, self.nz)):
+            if w is not None and np.shape(w) != (n,):
+                raise ValueError(f"width array of shape {np.shape(w)}, expected ({n},)")
+        sophie_set_spacing(self.h, wx, wy, wz)
 
     def launch_count(self):
         return sophie_launch_count(self.h)

@@ -15,6 +15,8 @@ stand in for them):
     U(4,24) cells, eps_r U(1,12), sigma U(0,0.05) S/m), later spheres overwrite
     earlier ones, a Gaussian-modulated-sine Ez source at the centre (10 GHz,
     5 GHz bandwidth) and 16 random interior Ez probes.
+  * Graded sphere cavity: the same on a non-uniform mesh refined towards the
+    centre along every axis (widths dx down to dx/2, Gaussian profile).
 """
 
 from __future__ import annotations
@@ -129,6 +131,35 @@ def sphere_cavity(n: int = 256, seed_materials: int = 1301, seed_probes: int = 1
     probes = probe_edges(n, n, n, nprobes, seed_probes)
     return dict(nx=n, ny=n, nz=n, dx=DX_DEFAULT, dt=cfl_dt(DX_DEFAULT), eps=eps_a,
                 sigma=sig_a, sources=[src], probes=probes)
+
+
+def graded_widths(n: int, dx: float = DX_DEFAULT, fine: float = 0.5, spread: float = 0.125):
+    """Cell widths of an axis refined around its centre: dx far from it, fine*dx
+    at it, a Gaussian profile of width spread*n cells in between."""
+    i = np.arange(n, dtype=np.float64) + 0.5
+    return dx * (1.0 - (1.0 - fine) * np.exp(-(((i - n / 2.0) / (spread * n)) ** 2)))
+
+
+def random_widths(n: int, seed: int, dx: float = DX_DEFAULT, lo: float = 0.6, hi: float = 1.6):
+    """Cell widths drawn uniformly in [lo*dx, hi*dx) (independent per cell)."""
+    return dx * np.random.default_rng(seed).uniform(lo, hi, n)
+
+
+def mesh_dt(wx, wy, wz, frac: float = 0.99) -> float:
+    """Time step at a fraction of the Courant limit of a mesh's smallest cells,
+    1 / (c sqrt(1/min(wx)^2 + 1/min(wy)^2 + 1/min(wz)^2))."""
+    inv2 = sum(1.0 / float(np.min(w)) ** 2 for w in (wx, wy, wz))
+    return frac / (C0 * math.sqrt(inv2))
+
+
+def sphere_cavity_graded(n: int = 256, fine: float = 0.5):
+    """The sphere-cavity workload on a mesh refined around the source: every
+    axis graded by graded_widths (dx = 1 mm far out, fine*dx at the centre),
+    dt at 0.99 of the refined mesh's Courant limit."""
+    w = sphere_cavity(n)
+    widths = [graded_widths(n, w["dx"], fine) for _ in range(3)]
+    w.update(widths=widths, dt=mesh_dt(*widths))
+    return w
 
 
 def random_fields(nx: int, ny: int, nz: int, seed: int, scale: float = 1.0):
