@@ -62,6 +62,7 @@ def parse():
     p.add_argument("--no-batch", action="store_true")
     p.add_argument("--no-768", action="store_true")
     p.add_argument("--no-graded", action="store_true")
+    p.add_argument("--graded-tsteps", type=int, default=1000, help="time steps per run of the graded-mesh workload")
     p.add_argument("--batch-cavities", type=int, default=4096)
     return p.parse_args()
 
@@ -395,7 +396,7 @@ def run_ours(args):
 
     graded = None
     if not args.no_graded and rank == 0:
-        graded = run_graded(stream, variants["k1"])
+        graded = run_graded(stream, variants["k1"], tsteps=args.graded_tsteps, autotune=not args.k)
 
     if rank == 0:
         line = {"metric": "Gcell-updates/s 3D Yee FDTD", "value": value, "unit": "Gcell-updates/s",
@@ -530,7 +531,7 @@ def run_precision_768(stream, tsteps: int = 200):
     return out
 
 
-def run_graded(stream, uniform_k1: float, n: int = 256, tsteps: int = 1000, reps: int = 3):
+def run_graded(stream, uniform_k1: float, n: int = 256, tsteps: int = 1000, reps: int = 3, autotune: bool = True):
     """The non-uniform mesh on its workload: the 256^3 sphere cavity on a mesh
     refined around the source (every axis dx down to dx/2, Gaussian profile;
     dt at the refined Courant limit), reset + `tsteps` steps per run, device
@@ -550,7 +551,11 @@ def run_graded(stream, uniform_k1: float, n: int = 256, tsteps: int = 1000, reps
         g.add_source(*src)
     for p in w["probes"]:
         g.add_probe(*p)
-    k, _ = g.autotune()
+    if autotune:
+        k, _ = g.autotune()
+    else:
+        k = 1
+        g.configure(temporal_k=1)
     g.reset()
     g.step(50)
     g.profile(True)

@@ -16,9 +16,12 @@
  * with, per edge, eps_r and sigma the mean of the four cells sharing the edge,
  *   beta = sigma*dt/(2*eps0*eps_r), Ca = (1-beta)/(1+beta),
  *   Cb = (S/eps_r)/(1+beta)   (computed in double, rounded once to float),
- * and s the source term (only on source edges). Fields are float32; every
- * update is evaluated without fused multiply-add, in the operand order
- *   h + S*((a1-a0) - (b1-b0))   and   Ca*e + Cb*((a1-a0) - (b1-b0)).
+ * and s the source term (only on source edges). Fields are float32; with
+ * br = (a1-a0) - (b1-b0) (plus s on a source edge), every update is one
+ * fused multiply-add with every other operation rounded separately:
+ *   h = fma(S, br, h)   and   e = fma(Cb, br, Ca*e),
+ * so the results are fixed by the expression alone, whatever the kernel.
+ * (On a non-uniform mesh br scales its two differences, sophie_set_spacing.)
  *
  * Storage indices (the "field layout" below). For a grid of nx*ny*nz cells,
  * every component is addressed on the (nx+1)*(ny+1)*(nz+1) index box, x

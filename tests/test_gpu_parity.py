@@ -1,9 +1,9 @@
 """CUDA path vs the CPU oracle, element by element, on seeded inputs.
 
 Bar: the float32 fields and probe samples are bitwise equal to the oracle's
-float32 run (both evaluate the same expression tree without fused
-multiply-add, and the per-edge coefficients are the same double expression
-rounded once); relative L2 <= 1e-5 is the tolerance the method fixes, and is
+float32 run (both evaluate the same expression tree, one fused
+multiply-add per update and every other operation rounded separately, and
+the per-edge coefficients are the same double expression rounded once); relative L2 <= 1e-5 is the tolerance the method fixes, and is
 also checked. The energy (double accumulation of the same float values)
 agrees to 1e-12 relative.
 """
