@@ -40,11 +40,12 @@ FIELD_BYTES = 48   # read + write six float32 components per cell-update
 MAT_BYTES = 4      # one 32-bit material word read per cell per launch
 # DRAM bytes (read + write) per launch from one ncu capture of each kernel on
 # this workload (profiles/*.md); None where the kernel changed since.
-NCU_TRAFFIC = {("yee_blocked", 2): 519.240960e6 + 358.025984e6,
-               ("yee_plain", 1): 514.649600e6 + 363.524352e6}
+NCU_TRAFFIC = {("yee_blocked", 2): 518.453248e6 + 358.631680e6,
+               ("yee_plain", 1): 513.512192e6 + 362.430976e6,
+               ("yee_plain_nu", 1): 517.370368e6 + 363.933184e6}  # graded 256^3 cavity
 # Batching workload: DRAM bytes per cell per launch of the batch-mode plain
-# kernel (3.811902 GB for the 54436430 cells of a 300-cavity instance).
-BATCH_TRAFFIC_PER_CELL = (2.415318e9 + 1.396584e9) / 54436430
+# kernel (4.093696 GB for the 54436430 cells of a 300-cavity instance).
+BATCH_TRAFFIC_PER_CELL = (2.742592e9 + 1.351104e9) / 54436430
 
 
 def parse():
@@ -581,6 +582,7 @@ def run_graded(stream, uniform_k1: float, n: int = 256, tsteps: int = 1000, reps
             "gcell_per_s": rate, "unit": "Gcell-updates/s", "temporal_k": k, "vs_uniform_k1": rate / uniform_k1,
             "roofline": {"kernel": "yee_plain (non-uniform)", "bound": "hbm", "achieved": achieved,
                          "peak": peaks()[0], "unit": "GB/s", "frac": achieved / peaks()[0],
+                         "traffic": NCU_TRAFFIC.get(("yee_plain_nu", 1)),
                          "avg_launch_ms": kms / max(kl, 1), "launches": kl},
             "energy_J": energy}
 
