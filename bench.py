@@ -40,8 +40,8 @@ FIELD_BYTES = 48   # read + write six float32 components per cell-update
 MAT_BYTES = 4      # one 32-bit material word read per cell per launch
 # DRAM bytes (read + write) per launch from one ncu capture of each kernel on
 # this workload (profiles/*.md); None where the kernel changed since.
-NCU_TRAFFIC = {("yee_blocked", 2): 518.453248e6 + 358.631680e6,
-               ("yee_plain", 1): 513.512192e6 + 362.430976e6,
+NCU_TRAFFIC = {("yee_blocked", 2): None,  # packed float pairs since the last capture
+               ("yee_plain", 1): None,
                ("yee_plain_nu", 1): 517.370368e6 + 363.933184e6}  # graded 256^3 cavity
 # Batching workload: DRAM bytes per cell per launch of the batch-mode plain
 # kernel (4.093696 GB for the 54436430 cells of a 300-cavity instance).

@@ -357,12 +357,16 @@ yee_blocked_kernel(const __grid_constant__ CUtensorMap tmF, const __grid_constan
             exj[0] = bex[0]; exj[1] = bex[1];
             ezj[0] = bez[0]; ezj[1] = bez[1];
           }
-          hx[r][0] = h_upd(in.hx[r][0], S, eyn[r][0], in.ey[r][0], ezj[0], in.ez[r][0]);
-          hx[r][1] = h_upd(in.hx[r][1], S, eyn[r][1], in.ey[r][1], ezj[1], in.ez[r][1]);
-          hy[r][0] = h_upd(in.hy[r][0], S, in.ez[r][1], in.ez[r][0], exn[r][0], in.ex[r][0]);
-          hy[r][1] = h_upd(in.hy[r][1], S, ez_ip1, in.ez[r][1], exn[r][1], in.ex[r][1]);
-          hz[r][0] = h_upd(in.hz[r][0], S, exj[0], in.ex[r][0], in.ey[r][1], in.ey[r][0]);
-          hz[r][1] = h_upd(in.hz[r][1], S, exj[1], in.ex[r][1], ey_ip1, in.ey[r][1]);
+          // the lane's two x positions as packed pairs
+          auto P = [](const float (&v)[2]) { return make_float2(v[0], v[1]); };
+          const float2 hx2 = h_upd2(P(in.hx[r]), S, P(eyn[r]), P(in.ey[r]), P(ezj), P(in.ez[r]));
+          const float2 hy2 = h_upd2(P(in.hy[r]), S, make_float2(in.ez[r][1], ez_ip1), P(in.ez[r]), P(exn[r]),
+                                    P(in.ex[r]));
+          const float2 hz2 = h_upd2(P(in.hz[r]), S, P(exj), P(in.ex[r]), make_float2(in.ey[r][1], ey_ip1),
+                                    P(in.ey[r]));
+          hx[r][0] = hx2.x; hx[r][1] = hx2.y;
+          hy[r][0] = hy2.x; hy[r][1] = hy2.y;
+          hz[r][0] = hz2.x; hz[r][1] = hz2.y;
         }
         float* hpl = hp + (lv - 1) * (kW * 2 * kRX);
         *reinterpret_cast<float2*>(&hpl[(warp * 2 + 0) * kRX + 2 * lane]) = make_float2(hx[kR - 1][0], hx[kR - 1][1]);
@@ -403,16 +407,22 @@ yee_blocked_kernel(const __grid_constant__ CUtensorMap tmF, const __grid_constan
           for (int r = 0; r < kR; ++r) {
             const float hz_im1 = __shfl_up_sync(0xffffffffu, hz[r][1], 1);
             const float hy_im1 = __shfl_up_sync(0xffffffffu, hy[r][1], 1);
+            const int rj = r > 0 ? r - 1 : 0;
+            const float2 hzj = r > 0 ? make_float2(hz[rj][0], hz[rj][1]) : make_float2(hza[0], hza[1]);
+            const float2 hxj = r > 0 ? make_float2(hx[rj][0], hx[rj][1]) : make_float2(hxa[0], hxa[1]);
+            // brackets of the lane's two x positions as packed pairs
+            const float2 bx = curl_br2(make_float2(hz[r][0], hz[r][1]), hzj, make_float2(hy[r][0], hy[r][1]),
+                                       make_float2(hyprev(lv, r, 0), hyprev(lv, r, 1)));
+            const float2 by = curl_br2(make_float2(hx[r][0], hx[r][1]), make_float2(hxprev(lv, r, 0), hxprev(lv, r, 1)),
+                                       make_float2(hz[r][0], hz[r][1]), make_float2(hz_im1, hz[r][0]));
+            const float2 bz = curl_br2(make_float2(hy[r][0], hy[r][1]), make_float2(hy_im1, hy[r][0]),
+                                       make_float2(hx[r][0], hx[r][1]), hxj);
 #pragma unroll
             for (int cc = 0; cc < 2; ++cc) {
-              const float hzj = r > 0 ? hz[r > 0 ? r - 1 : 0][cc] : hza[cc];
-              const float hxj = r > 0 ? hx[r > 0 ? r - 1 : 0][cc] : hxa[cc];
-              const float hzi = cc ? hz[r][0] : hz_im1;
-              const float hyi = cc ? hy[r][0] : hy_im1;
               const uint32_t m = in.m[r][cc];
-              out.ex[r][cc] = e_upd(in.ex[r][cc], *reinterpret_cast<const float2*>(scoefb + cls_off_x(m)), curl_br(hz[r][cc], hzj, hy[r][cc], hyprev(lv, r, cc)));
-              out.ey[r][cc] = e_upd(in.ey[r][cc], *reinterpret_cast<const float2*>(scoefb + cls_off_y(m)), curl_br(hx[r][cc], hxprev(lv, r, cc), hz[r][cc], hzi));
-              out.ez[r][cc] = e_upd(in.ez[r][cc], *reinterpret_cast<const float2*>(scoefb + cls_off_z(m)), curl_br(hy[r][cc], hyi, hx[r][cc], hxj));
+              out.ex[r][cc] = e_upd(in.ex[r][cc], *reinterpret_cast<const float2*>(scoefb + cls_off_x(m)), cc ? bx.y : bx.x);
+              out.ey[r][cc] = e_upd(in.ey[r][cc], *reinterpret_cast<const float2*>(scoefb + cls_off_y(m)), cc ? by.y : by.x);
+              out.ez[r][cc] = e_upd(in.ez[r][cc], *reinterpret_cast<const float2*>(scoefb + cls_off_z(m)), cc ? bz.y : bz.x);
               out.m[r][cc] = m;
             }
           }

@@ -302,12 +302,23 @@ yee_plain_kernel(const __grid_constant__ CUtensorMap tmF, const __grid_constant_
           }
           const float ez_ip1 = St::ld(&F[FI(2, row, c0 + 2)], a.isc[2]);
           const float ey_ip1 = St::ld(&F[FI(1, row, c0 + 2)], a.isc[1]);
-          hx[r][0] = h_upd_r<NU>(vhx.x, S, rz, ney.x, ey[r][0], ryv[r], ezj[0], ez[r][0]);
-          hx[r][1] = h_upd_r<NU>(vhx.y, S, rz, ney.y, ey[r][1], ryv[r], ezj[1], ez[r][1]);
-          hy[r][0] = h_upd_r<NU>(vhy.x, S, rxv[0], ez[r][1], ez[r][0], rz, nex.x, ex[r][0]);
-          hy[r][1] = h_upd_r<NU>(vhy.y, S, rxv[1], ez_ip1, ez[r][1], rz, nex.y, ex[r][1]);
-          hz[r][0] = h_upd_r<NU>(vhz.x, S, ryv[r], exj[0], ex[r][0], rxv[0], ey[r][1], ey[r][0]);
-          hz[r][1] = h_upd_r<NU>(vhz.y, S, ryv[r], exj[1], ex[r][1], rxv[1], ey_ip1, ey[r][1]);
+          if constexpr (NU) {
+            hx[r][0] = h_upd_r<NU>(vhx.x, S, rz, ney.x, ey[r][0], ryv[r], ezj[0], ez[r][0]);
+            hx[r][1] = h_upd_r<NU>(vhx.y, S, rz, ney.y, ey[r][1], ryv[r], ezj[1], ez[r][1]);
+            hy[r][0] = h_upd_r<NU>(vhy.x, S, rxv[0], ez[r][1], ez[r][0], rz, nex.x, ex[r][0]);
+            hy[r][1] = h_upd_r<NU>(vhy.y, S, rxv[1], ez_ip1, ez[r][1], rz, nex.y, ex[r][1]);
+            hz[r][0] = h_upd_r<NU>(vhz.x, S, ryv[r], exj[0], ex[r][0], rxv[0], ey[r][1], ey[r][0]);
+            hz[r][1] = h_upd_r<NU>(vhz.y, S, ryv[r], exj[1], ex[r][1], rxv[1], ey_ip1, ey[r][1]);
+          } else {
+            // the lane's two x positions as packed pairs
+            auto P = [](const float (&v)[2]) { return make_float2(v[0], v[1]); };
+            const float2 hx2 = h_upd2(vhx, S, ney, P(ey[r]), P(ezj), P(ez[r]));
+            const float2 hy2 = h_upd2(vhy, S, make_float2(ez[r][1], ez_ip1), P(ez[r]), nex, P(ex[r]));
+            const float2 hz2 = h_upd2(vhz, S, P(exj), P(ex[r]), make_float2(ey[r][1], ey_ip1), P(ey[r]));
+            hx[r][0] = hx2.x; hx[r][1] = hx2.y;
+            hy[r][0] = hy2.x; hy[r][1] = hy2.y;
+            hz[r][0] = hz2.x; hz[r][1] = hz2.y;
+          }
           *reinterpret_cast<float2*>(hp(0, row, c0)) = make_float2(hx[r][0], hx[r][1]);
           *reinterpret_cast<float2*>(hp(1, row, c0)) = make_float2(hy[r][0], hy[r][1]);
           *reinterpret_cast<float2*>(hp(2, row, c0)) = make_float2(hz[r][0], hz[r][1]);
@@ -377,12 +388,28 @@ yee_plain_kernel(const __grid_constant__ CUtensorMap tmF, const __grid_constant_
         const int y = w.y0 + 2 * warp + r;
         const int x = w.x0 + 2 * lane;
         float eo[3][2];
+        float2 bx2, by2, bz2;  // uniform mesh: the brackets of both x positions, packed
+        if constexpr (!NU) {
+          bx2 = curl_br2(make_float2(hz[r][0], hz[r][1]), make_float2(hzj[0], hzj[1]),
+                         make_float2(hy[r][0], hy[r][1]), make_float2(hyp[r][0], hyp[r][1]));
+          by2 = curl_br2(make_float2(hx[r][0], hx[r][1]), make_float2(hxp[r][0], hxp[r][1]),
+                         make_float2(hz[r][0], hz[r][1]), make_float2(hz_im, hz[r][0]));
+          bz2 = curl_br2(make_float2(hy[r][0], hy[r][1]), make_float2(hy_im, hy[r][0]),
+                         make_float2(hx[r][0], hx[r][1]), make_float2(hxj[0], hxj[1]));
+        }
 #pragma unroll
         for (int cc = 0; cc < 2; ++cc) {
           const uint32_t m = cc ? m2.y : m2.x;
-          float bx = bracket<NU>(rydv[r], hz[r][cc], hzj[cc], rzd, hy[r][cc], hyp[r][cc]);
-          float by = bracket<NU>(rzd, hx[r][cc], hxp[r][cc], rxdv[cc], hz[r][cc], cc ? hz[r][0] : hz_im);
-          float bz = bracket<NU>(rxdv[cc], hy[r][cc], cc ? hy[r][0] : hy_im, rydv[r], hx[r][cc], hxj[cc]);
+          float bx, by, bz;
+          if constexpr (NU) {
+            bx = bracket<NU>(rydv[r], hz[r][cc], hzj[cc], rzd, hy[r][cc], hyp[r][cc]);
+            by = bracket<NU>(rzd, hx[r][cc], hxp[r][cc], rxdv[cc], hz[r][cc], cc ? hz[r][0] : hz_im);
+            bz = bracket<NU>(rxdv[cc], hy[r][cc], cc ? hy[r][0] : hy_im, rydv[r], hx[r][cc], hxj[cc]);
+          } else {
+            bx = cc ? bx2.y : bx2.x;
+            by = cc ? by2.y : by2.x;
+            bz = cc ? bz2.y : bz2.x;
+          }
           if ((m & kSrcFlag) && out_plane) {
             const float3 b3 = apply_sources(make_float3(bx, by, bz),
                                             ((long long)z * d.ny1() + y) * d.nxp() + x + cc, a.n0, srct());

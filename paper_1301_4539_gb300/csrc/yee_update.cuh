@@ -58,4 +58,28 @@ __device__ __forceinline__ float e_upd(float e, float2 c, float br) {
   return __fmaf_rn(c.y, br, __fmul_rn(c.x, e));
 }
 
+// Two adjacent points at once with Blackwell's packed f32x2 operations: each
+// half of a packed operation is rounded exactly like its scalar counterpart
+// (no flush to zero), so these give bitwise the results of curl_br and h_upd
+// on (.x, .y) with half the float instructions.
+__device__ __forceinline__ float2 fsub2_rn(float2 a, float2 b) {
+  float2 r;
+  asm("{\n\t.reg .b64 pa, pb, pr;\n\t"
+      "mov.b64 pa, {%2, %3};\n\t"
+      "mov.b64 pb, {%4, %5};\n\t"
+      "sub.rn.f32x2 pr, pa, pb;\n\t"
+      "mov.b64 {%0, %1}, pr;\n\t}"
+      : "=f"(r.x), "=f"(r.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+  return r;
+}
+
+__device__ __forceinline__ float2 curl_br2(float2 a1, float2 a0, float2 b1, float2 b0) {
+  return fsub2_rn(fsub2_rn(a1, a0), fsub2_rn(b1, b0));
+}
+
+__device__ __forceinline__ float2 h_upd2(float2 h, float S, float2 a1, float2 a0, float2 b1, float2 b0) {
+  return __ffma2_rn(make_float2(S, S), curl_br2(a1, a0, b1, b0), h);
+}
+
 }  // namespace sophie
