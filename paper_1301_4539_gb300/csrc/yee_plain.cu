@@ -57,7 +57,10 @@ struct PCfg {
   static constexpr uint32_t kHbOff = kNS * kStageBytes;
   static constexpr uint32_t kHbBytes = kInPlace ? 0 : 2 * 3 * kBY * BX * 4;
   static constexpr uint32_t kBarOff = kHbOff + kHbBytes;
-  static constexpr uint32_t kSmemBytes = kBarOff + 2 * kNS * 8 + 128;
+  // class table (Ca, Cb) of a single grid, indexed by the material word's
+  // pre-scaled byte offsets (batches read their cavities' tables from L1)
+  static constexpr uint32_t kCoefOff = (kBarOff + 2 * kNS * 8 + 15) / 16 * 16;
+  static constexpr uint32_t kSmemBytes = kCoefOff + kMaxClasses * 8 + 128;
   static_assert(kFieldBytes % 128 == 0, "material box must start 128-byte aligned");
 };
 
@@ -108,6 +111,10 @@ yee_plain_kernel(const __grid_constant__ CUtensorMap tmF, const __grid_constant_
   auto sF = [&](int s) { return reinterpret_cast<T*>(base + s * C::kStageBytes); };
   auto sM = [&](int s) { return reinterpret_cast<const uint32_t*>(base + s * C::kStageBytes + C::kFieldBytes); };
   float* const hbuf = reinterpret_cast<float*>(base + C::kHbOff);
+  const unsigned char* const scoefb = base + C::kCoefOff;
+  if constexpr (!BATCH)
+    for (int c = threadIdx.x; c < kMaxClasses; c += kThreads)
+      reinterpret_cast<float2*>(base + C::kCoefOff)[c] = a.coef[c];
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
@@ -302,16 +309,23 @@ yee_plain_kernel(const __grid_constant__ CUtensorMap tmF, const __grid_constant_
           }
           const float ez_ip1 = St::ld(&F[FI(2, row, c0 + 2)], a.isc[2]);
           const float ey_ip1 = St::ld(&F[FI(1, row, c0 + 2)], a.isc[1]);
+          // the lane's two x positions as packed pairs
+          auto P = [](const float (&v)[2]) { return make_float2(v[0], v[1]); };
           if constexpr (NU) {
-            hx[r][0] = h_upd_r<NU>(vhx.x, S, rz, ney.x, ey[r][0], ryv[r], ezj[0], ez[r][0]);
-            hx[r][1] = h_upd_r<NU>(vhx.y, S, rz, ney.y, ey[r][1], ryv[r], ezj[1], ez[r][1]);
-            hy[r][0] = h_upd_r<NU>(vhy.x, S, rxv[0], ez[r][1], ez[r][0], rz, nex.x, ex[r][0]);
-            hy[r][1] = h_upd_r<NU>(vhy.y, S, rxv[1], ez_ip1, ez[r][1], rz, nex.y, ex[r][1]);
-            hz[r][0] = h_upd_r<NU>(vhz.x, S, ryv[r], exj[0], ex[r][0], rxv[0], ey[r][1], ey[r][0]);
-            hz[r][1] = h_upd_r<NU>(vhz.y, S, ryv[r], exj[1], ex[r][1], rxv[1], ey_ip1, ey[r][1]);
+            // the b ratios negated (curl_br2_nu)
+            const float2 S2 = make_float2(S, S);
+            const float2 rz2 = make_float2(rz, rz), ry2 = make_float2(ryv[r], ryv[r]);
+            const float2 rx2 = make_float2(rxv[0], rxv[1]);
+            const float2 hx2 = __ffma2_rn(S2, curl_br2_nu(rz2, ney, P(ey[r]), make_float2(-ryv[r], -ryv[r]), P(ezj),
+                                                          P(ez[r])), vhx);
+            const float2 hy2 = __ffma2_rn(S2, curl_br2_nu(rx2, make_float2(ez[r][1], ez_ip1), P(ez[r]),
+                                                          make_float2(-rz, -rz), nex, P(ex[r])), vhy);
+            const float2 hz2 = __ffma2_rn(S2, curl_br2_nu(ry2, P(exj), P(ex[r]), make_float2(-rxv[0], -rxv[1]),
+                                                          make_float2(ey[r][1], ey_ip1), P(ey[r])), vhz);
+            hx[r][0] = hx2.x; hx[r][1] = hx2.y;
+            hy[r][0] = hy2.x; hy[r][1] = hy2.y;
+            hz[r][0] = hz2.x; hz[r][1] = hz2.y;
           } else {
-            // the lane's two x positions as packed pairs
-            auto P = [](const float (&v)[2]) { return make_float2(v[0], v[1]); };
             const float2 hx2 = h_upd2(vhx, S, ney, P(ey[r]), P(ezj), P(ez[r]));
             const float2 hy2 = h_upd2(vhy, S, make_float2(ez[r][1], ez_ip1), P(ez[r]), nex, P(ex[r]));
             const float2 hz2 = h_upd2(vhz, S, P(exj), P(ex[r]), make_float2(ey[r][1], ey_ip1), P(ey[r]));
@@ -388,8 +402,17 @@ yee_plain_kernel(const __grid_constant__ CUtensorMap tmF, const __grid_constant_
         const int y = w.y0 + 2 * warp + r;
         const int x = w.x0 + 2 * lane;
         float eo[3][2];
-        float2 bx2, by2, bz2;  // uniform mesh: the brackets of both x positions, packed
-        if constexpr (!NU) {
+        float2 bx2, by2, bz2;  // the brackets of both x positions, packed
+        if constexpr (NU) {
+          const float2 ryd2 = make_float2(rydv[r], rydv[r]), rzd2 = make_float2(rzd, rzd);
+          const float2 rxd2 = make_float2(rxdv[0], rxdv[1]);
+          bx2 = curl_br2_nu(ryd2, make_float2(hz[r][0], hz[r][1]), make_float2(hzj[0], hzj[1]),
+                            make_float2(-rzd, -rzd), make_float2(hy[r][0], hy[r][1]), make_float2(hyp[r][0], hyp[r][1]));
+          by2 = curl_br2_nu(rzd2, make_float2(hx[r][0], hx[r][1]), make_float2(hxp[r][0], hxp[r][1]),
+                            make_float2(-rxdv[0], -rxdv[1]), make_float2(hz[r][0], hz[r][1]), make_float2(hz_im, hz[r][0]));
+          bz2 = curl_br2_nu(rxd2, make_float2(hy[r][0], hy[r][1]), make_float2(hy_im, hy[r][0]),
+                            make_float2(-rydv[r], -rydv[r]), make_float2(hx[r][0], hx[r][1]), make_float2(hxj[0], hxj[1]));
+        } else {
           bx2 = curl_br2(make_float2(hz[r][0], hz[r][1]), make_float2(hzj[0], hzj[1]),
                          make_float2(hy[r][0], hy[r][1]), make_float2(hyp[r][0], hyp[r][1]));
           by2 = curl_br2(make_float2(hx[r][0], hx[r][1]), make_float2(hxp[r][0], hxp[r][1]),
@@ -400,16 +423,9 @@ yee_plain_kernel(const __grid_constant__ CUtensorMap tmF, const __grid_constant_
 #pragma unroll
         for (int cc = 0; cc < 2; ++cc) {
           const uint32_t m = cc ? m2.y : m2.x;
-          float bx, by, bz;
-          if constexpr (NU) {
-            bx = bracket<NU>(rydv[r], hz[r][cc], hzj[cc], rzd, hy[r][cc], hyp[r][cc]);
-            by = bracket<NU>(rzd, hx[r][cc], hxp[r][cc], rxdv[cc], hz[r][cc], cc ? hz[r][0] : hz_im);
-            bz = bracket<NU>(rxdv[cc], hy[r][cc], cc ? hy[r][0] : hy_im, rydv[r], hx[r][cc], hxj[cc]);
-          } else {
-            bx = cc ? bx2.y : bx2.x;
-            by = cc ? by2.y : by2.x;
-            bz = cc ? bz2.y : bz2.x;
-          }
+          float bx = cc ? bx2.y : bx2.x;
+          float by = cc ? by2.y : by2.x;
+          float bz = cc ? bz2.y : bz2.x;
           if ((m & kSrcFlag) && out_plane) {
             const float3 b3 = apply_sources(make_float3(bx, by, bz),
                                             ((long long)z * d.ny1() + y) * d.nxp() + x + cc, a.n0, srct());
@@ -423,11 +439,15 @@ yee_plain_kernel(const __grid_constant__ CUtensorMap tmF, const __grid_constant_
             k0 = __ldg(e3);
             k1 = __ldg(e3 + 1);
             k2 = __ldg(e3 + 2);
-          } else {
+          } else if constexpr (BATCH) {
             const float2* ct = coef();
             k0 = __ldg(&ct[cls_of(m, 0)]);
             k1 = __ldg(&ct[cls_of(m, 1)]);
             k2 = __ldg(&ct[cls_of(m, 2)]);
+          } else {
+            k0 = *reinterpret_cast<const float2*>(scoefb + cls_off_x(m));
+            k1 = *reinterpret_cast<const float2*>(scoefb + cls_off_y(m));
+            k2 = *reinterpret_cast<const float2*>(scoefb + cls_off_z(m));
           }
           eo[0][cc] = e_upd(ex[r][cc], k0, bx);
           eo[1][cc] = e_upd(ey[r][cc], k1, by);

@@ -82,4 +82,10 @@ __device__ __forceinline__ float2 h_upd2(float2 h, float S, float2 a1, float2 a0
   return __ffma2_rn(make_float2(S, S), curl_br2(a1, a0, b1, b0), h);
 }
 
+// Packed form of curl_br_nu with the b ratio passed negated, nrb = -rb:
+// (-rb) * d rounds to exactly -(rb * d), so the bracket is the same value.
+__device__ __forceinline__ float2 curl_br2_nu(float2 ra, float2 a1, float2 a0, float2 nrb, float2 b1, float2 b0) {
+  return __ffma2_rn(ra, fsub2_rn(a1, a0), __fmul2_rn(nrb, fsub2_rn(b1, b0)));
+}
+
 }  // namespace sophie
