@@ -215,8 +215,11 @@ void for_slabs(int nslab, int nthreads, F&& f) {
 int build_material_tables(const Dims& d, double dt, double S64, const float* eps, const float* sig, uint32_t* words,
                           MaterialTables* out, int nthreads) {
   const EdgeMaterials m{d, eps, sig};
-  // Fixed slabs of z planes: the tables do not depend on the thread count.
-  const int nslab = std::min(d.nz1, 64);
+  // Slabs of z planes fixed by the grid alone (the tables do not depend on the
+  // thread count): at most 64, each at least 16 planes thick, so that the
+  // points of a slab that share three edge materials (e.g. the planes of one
+  // material block) share one explicit entry and its cache lines.
+  const int nslab = std::max(1, std::min(64, d.nz1 / 16));
   auto slab_k = [&](int s) { return (int)((long long)d.nz1 * s / nslab); };
   // Pass 1: frequencies per slab, merged.
   std::vector<FreqMap> fs(nslab);

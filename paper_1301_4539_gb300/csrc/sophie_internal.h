@@ -157,9 +157,10 @@ float2 edge_coefficients(double dt, double S64, double e, double s);
 // conducting cell, whose edges are PEC). Edge material = mean of its four
 // cells; the 511 most frequent edge materials become classes, points with an
 // edge outside them share explicit entries by their three edge materials.
-// No source or probe flags are set. The work is split into fixed slabs of z
-// planes (explicit entries are shared within a slab) run on up to nthreads
-// host threads; the result does not depend on nthreads. Returns 0, or -1 if
+// No source or probe flags are set. The work is split into slabs of z planes
+// fixed by the grid (at most 64, at least 16 planes each; explicit entries
+// are shared within a slab) run on up to nthreads host threads; the result
+// does not depend on nthreads. Returns 0, or -1 if
 // more than 2^29 explicit entries would be needed.
 int build_material_tables(const Dims& d, double dt, double S64, const float* eps, const float* sig, uint32_t* words,
                           MaterialTables* out, int nthreads);
