@@ -42,7 +42,7 @@ MAT_BYTES = 4      # one 32-bit material word read per cell per launch
 # this workload (profiles/*.md); None where the kernel changed since.
 NCU_TRAFFIC = {("yee_blocked", 2): 522.520064e6 + 359.298816e6,
                ("yee_plain", 1): 504.597248e6 + 361.924608e6,
-               ("yee_plain_nu", 1): None}  # graded 256^3 cavity; changed since its capture
+               ("yee_plain_nu", 1): 509.975552e6 + 364.398848e6}  # graded 256^3 cavity
 # Batching workload: DRAM bytes per cell per launch of the batch-mode plain
 # kernel (4.093696 GB for the 54436430 cells of a 300-cavity instance).
 BATCH_TRAFFIC_PER_CELL = (2.742592e9 + 1.351104e9) / 54436430
