@@ -240,7 +240,9 @@ int sophie_set_storage_scale(sophie_grid *g, const float *scale);
 /*
  * Autotuner: times the step kernel candidates on this grid (plain kernel with
  * z chunks of 1..64 planes per work unit; temporally blocked kernel with
- * k = 2, 3, 4 and both work splits), each launch reading the current fields
+ * k = 2, 3, 4, each with the modelled split of every tile's planes into z
+ * ranges, its neighbours and twice it, in two unit orders, and a split into
+ * equal contiguous work ranges), each launch reading the current fields
  * and writing the spare buffer so the state does not advance, and keeps the
  * fastest per time step. The grid switches to temporal_k = 0 (autotuned) with
  * that choice. *temporal_k gets the chosen k, *ms_per_step the measured device

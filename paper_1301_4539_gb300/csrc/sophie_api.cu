@@ -574,7 +574,7 @@ double time_candidate(sophie_grid* g, Fn&& launch, cudaEvent_t e0, cudaEvent_t e
 }
 
 // Autotuner: measure the plain kernel's z-chunk choices and the temporally
-// blocked kernel at k = 2..4 with both work splits on this grid, keep the
+// blocked kernel at k = 2..4 with several work splits on this grid, keep the
 // fastest per step. All candidates give bitwise identical float results, so
 // the choice changes only speed. With 2-byte storage, where results depend
 // on k, only the tilings are tuned and k stays 2.
@@ -620,8 +620,17 @@ int run_autotune(sophie_grid* g, double* best_ms_per_step) {
   }
   for (int K = 2; K <= 4 && !g->rat; ++K) {  // the blocked kernel takes uniform meshes only
     if (g->fmt != kF32 && K != 2) continue;
-    for (int aligned = 1; aligned >= 0; --aligned) {
-      const BlockedTiling bt = blocked_tiling(d, K, g->num_sms, aligned);
+    // the cost model's aligned split in both unit orders, its neighbours and
+    // twice it, and the contiguous split
+    std::vector<BlockedTiling> cands;
+    const BlockedTiling model = blocked_tiling(d, K, g->num_sms, 1);
+    cands.push_back(model);
+    cands.push_back(blocked_tiling_split(d, K, g->num_sms, model.zsplit, 1 - model.order));
+    for (int zs : {model.zsplit + 1, model.zsplit - 1, 2 * model.zsplit})
+      if (zs >= 1 && zs <= d.nz)
+        for (int order = 0; order < 2; ++order) cands.push_back(blocked_tiling_split(d, K, g->num_sms, zs, order));
+    cands.push_back(blocked_tiling(d, K, g->num_sms, 0));
+    for (const BlockedTiling& bt : cands) {
       const double ms = time_candidate(
           g, [&] { return launch_step_blocked(a, g->tmFB[g->cur], g->tmMB, bt, g->stream); }, e0, e1);
       if (ms < 0) {
@@ -978,9 +987,11 @@ int sophie_step(sophie_grid* g, int n) {
     } else if (blocked) {
       if (g->btile.K != K) {
         // SOPHIE_BLOCKED_ALIGNED=0 cuts the work into equal contiguous ranges
-        // instead of equal z ranges per tile (tuning knob; same results).
+        // instead of equal z ranges per tile, 2 / 3 force the tile-major /
+        // range-major unit order (tuning knob; same results).
         const char* al = getenv("SOPHIE_BLOCKED_ALIGNED");
-        g->btile = blocked_tiling(g->d, K, g->num_sms, al ? atoi(al) : 1);
+        const int mode = al ? atoi(al) : 1;
+        g->btile = blocked_tiling(g->d, K, g->num_sms, mode >= 0 && mode <= 3 ? mode : 1);
       }
       e = launch_step_blocked(a, g->tmFB[g->cur], g->tmMB, sub ? bt_sub : g->btile, g->stream);
     } else if (g->use_simple) {

@@ -130,10 +130,17 @@ struct PlainTiling {
 };
 
 // Temporally blocked kernel: K steps per launch over (tiles_x x tiles_y)
-// regions; `grid` CTAs split the (tile, plane) items into equal ranges.
+// regions, walked by `grid` CTAs.
 struct BlockedTiling {
   int K, tiles_x, tiles_y, grid;
-  int zsplit;  // > 0: CTA b works on tile b / zsplit, z range b % zsplit of zsplit
+  // > 0: every tile's planes are cut into the same zsplit z ranges and CTA b
+  // takes units b, b + grid, ... in the order `order`: 0 tile-major (unit u is
+  // range u % zsplit of tile u / zsplit: the CTAs working at the same time hold
+  // all ranges of a run of neighbouring tiles), 1 range-major (range u / tiles
+  // of tile u % tiles: they hold one range of many neighbouring tiles).
+  // 0: the (tile, plane) items are cut into grid equal contiguous ranges.
+  int zsplit;
+  int order;
   int tx0, ty0, zlo, zhi;  // the tiles start at tile (tx0, ty0); output planes [zlo, zhi)
 };
 
@@ -179,7 +186,12 @@ PlainTiling plain_tiling_box(const Dims& d, int num_sms, const int* box);
 BlockedTiling blocked_tiling_box(const Dims& d, int K, int num_sms, const int* box);
 cudaError_t launch_step_plain(const StepArgs& a, const CUtensorMap& tmF, const CUtensorMap& tmM,
                               const PlainTiling& t, cudaStream_t s);
+// aligned: 0 contiguous split; 1 the modelled aligned split in its default
+// unit order; 2 / 3 the same split tile-major / range-major.
 BlockedTiling blocked_tiling(const Dims& d, int K, int num_sms, int aligned);
+// The aligned split with exactly zsplit z ranges (clamped to [1, nz]) taken
+// in unit order `order` (BlockedTiling::order).
+BlockedTiling blocked_tiling_split(const Dims& d, int K, int num_sms, int zsplit, int order);
 bool blocked_supported(int K);
 int blocked_box_x(int fmt);
 int blocked_box_y();

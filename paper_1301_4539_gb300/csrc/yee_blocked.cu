@@ -89,27 +89,35 @@ struct St {
 __device__ __forceinline__ void set_err(int* err, int code) { atomicOr(err, code); }
 
 // The (tile, plane) items of this CTA, walked as units. With zsplit > 0
-// every tile's z column is cut into the same zsplit ranges, so regions of
-// neighbouring tiles stream the same planes at the same time (their
+// every tile's z column is cut into the same zsplit ranges and CTA b takes
+// units b, b + grid, ... in tile-major or range-major order (BlockedTiling):
+// either way the CTAs working at the same time include neighbouring tiles at
+// the same range, whose regions stream the same planes together (their
 // overlapping halos then come from L2). Otherwise the items are cut into
 // equal contiguous ranges, tile after tile.
 struct UnitIter {
-  long long i, hi;
-  int nz, zlo;  // planes [zlo, zlo + nz) of every tile
-  __device__ UnitIter(const BlockedTiling& t) : nz(t.zhi - t.zlo), zlo(t.zlo) {
-    if (t.zsplit > 0) {
-      const long long tile = blockIdx.x / t.zsplit;
-      const int part = blockIdx.x % t.zsplit;
-      i = tile * nz + (long long)nz * part / t.zsplit;
-      hi = tile * nz + (long long)nz * (part + 1) / t.zsplit;
-    } else {
-      const long long n = (long long)t.tiles_x * t.tiles_y * nz;
-      i = n * blockIdx.x / gridDim.x;
-      hi = n * (blockIdx.x + 1) / gridDim.x;
-    }
+  long long i, hi;        // contiguous split: items [i, hi)
+  long long u, units, tiles;  // aligned split: next unit, unit count, tiles
+  int nz, zlo, zsplit, order;  // planes [zlo, zlo + nz) of every tile
+  __device__ UnitIter(const BlockedTiling& t) : nz(t.zhi - t.zlo), zlo(t.zlo), zsplit(t.zsplit), order(t.order) {
+    tiles = (long long)t.tiles_x * t.tiles_y;
+    u = blockIdx.x;
+    units = tiles * (zsplit > 0 ? zsplit : 0);
+    const long long n = tiles * nz;
+    i = n * blockIdx.x / gridDim.x;
+    hi = n * (blockIdx.x + 1) / gridDim.x;
   }
   // Next unit: tile index and planes [z0, z1). False when done.
   __device__ bool next(long long& tile, int& z0, int& z1) {
+    if (zsplit > 0) {
+      if (u >= units) return false;
+      const long long r = order ? u / tiles : u % zsplit;
+      tile = order ? u % tiles : u / zsplit;
+      z0 = zlo + (int)((long long)nz * r / zsplit);
+      z1 = zlo + (int)((long long)nz * (r + 1) / zsplit);
+      u += gridDim.x;
+      return true;
+    }
     if (i >= hi) return false;
     tile = i / nz;
     const int r0 = (int)(i % nz);
@@ -569,6 +577,35 @@ cudaError_t launch_fmt(const StepArgs& a, const CUtensorMap& tmF, const CUtensor
 int blocked_box_x(int fmt) { return store_bytes(fmt) == 4 ? BoxCfg<kF32>::BX : BoxCfg<kF16>::BX; }
 int blocked_box_y() { return kRY; }
 
+// Work split of `tiles` tiles of nz planes over at most num_sms CTAs (one per
+// SM). Aligned: the number of z ranges minimising the planes the busiest CTA
+// streams, rounds x (range + the 4K-3 planes of level fill and drain).
+static void choose_split(long long tiles, int nz, int K, int num_sms, int aligned, BlockedTiling& t) {
+  if (!aligned) {
+    const long long items = tiles * nz;
+    t.zsplit = 0;
+    t.grid = (int)(items < num_sms ? items : num_sms);
+    return;
+  }
+  double best = 1e300;
+  const int smax = std::max(1, std::min(nz / 8, 1024));
+  for (int s = 1; s <= smax; ++s) {
+    const long long units = tiles * s;
+    const long long grid = units < num_sms ? units : num_sms;
+    const long long rounds = (units + grid - 1) / grid;
+    const double cost = (double)rounds * ((nz + s - 1) / s + (s > 1 ? 4 * K - 3 : K - 1));
+    if (cost < best - 1e-9) {
+      best = cost;
+      t.zsplit = s;
+      t.grid = (int)grid;
+    }
+  }
+  // one round of units: tile-major (measured faster at 256^3); several:
+  // range-major (measured faster at 512^3 to 768^3); aligned = 2 / 3 force
+  // tile-major / range-major
+  t.order = aligned >= 2 ? aligned - 2 : tiles * t.zsplit > t.grid ? 1 : 0;
+}
+
 BlockedTiling blocked_tiling(const Dims& d, int K, int num_sms, int aligned) {
   BlockedTiling t{};
   const int TX = kRX - 2 * K, TY = kRY - 2 * K, phi = K & 1;
@@ -577,15 +614,17 @@ BlockedTiling blocked_tiling(const Dims& d, int K, int num_sms, int aligned) {
   t.tiles_y = (d.ny + TY - 1) / TY;
   t.tx0 = t.ty0 = t.zlo = 0;
   t.zhi = d.nz;
+  choose_split((long long)t.tiles_x * t.tiles_y, d.nz, K, num_sms, aligned, t);
+  return t;
+}
+
+BlockedTiling blocked_tiling_split(const Dims& d, int K, int num_sms, int zsplit, int order) {
+  BlockedTiling t = blocked_tiling(d, K, num_sms, 1);
   const long long tiles = (long long)t.tiles_x * t.tiles_y;
-  if (aligned && tiles <= num_sms) {
-    t.zsplit = (int)(num_sms / tiles < d.nz ? num_sms / tiles : d.nz);
-    t.grid = (int)(tiles * t.zsplit);
-  } else {
-    const long long items = tiles * d.nz;
-    t.zsplit = 0;
-    t.grid = (int)(items < num_sms ? items : num_sms);
-  }
+  t.zsplit = std::max(1, std::min(zsplit, d.nz));
+  t.order = order ? 1 : 0;
+  const long long units = tiles * t.zsplit;
+  t.grid = (int)(units < num_sms ? units : num_sms);
   return t;
 }
 
@@ -599,20 +638,9 @@ BlockedTiling blocked_tiling_box(const Dims& d, int K, int num_sms, const int* b
   // tile tx covers output x [tx TX - phi, tx TX - phi + TX)
   const int tx0 = (box[0] + phi) / TX, tx1 = (x1 - 1 + phi) / TX + 1;
   const int ty0 = box[2] / TY, ty1 = (y1 - 1) / TY + 1;
-  Dims sub = d;
-  sub.nz = z1 - z0;
-  t = blocked_tiling(sub, K, num_sms, 1);
   t.tiles_x = tx1 - tx0;
   t.tiles_y = ty1 - ty0;
-  const long long tiles = (long long)t.tiles_x * t.tiles_y;
-  if (tiles <= num_sms) {
-    t.zsplit = (int)(num_sms / tiles < sub.nz ? num_sms / tiles : sub.nz);
-    t.grid = (int)(tiles * t.zsplit);
-  } else {
-    const long long items = tiles * sub.nz;
-    t.zsplit = 0;
-    t.grid = (int)(items < num_sms ? items : num_sms);
-  }
+  choose_split((long long)t.tiles_x * t.tiles_y, z1 - z0, K, num_sms, 1, t);
   t.tx0 = tx0;
   t.ty0 = ty0;
   t.zlo = z0;

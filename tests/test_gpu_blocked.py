@@ -46,6 +46,29 @@ def test_blocked_equals_oracle(oracle_mod, sophie, K, n3):
     assert abs(g.energy() - o.energy()) <= 1e-12 * abs(o.energy())
 
 
+@pytest.mark.parametrize("aligned", ["2", "3", "0"])
+@pytest.mark.parametrize("K", [2, 3])
+def test_blocked_many_tiles_several_units_per_cta(oracle_mod, sophie, monkeypatch, K, aligned):
+    """More tiles than SMs: the aligned split gives each CTA several (z range,
+    tile) units taken with a stride of the grid (700x420x40 at K=2: 180 tiles,
+    2 ranges), tile-major (2) or range-major (3); the contiguous split (0)
+    ranges that straddle tiles."""
+    monkeypatch.setenv("SOPHIE_BLOCKED_ALIGNED", aligned)
+    nx, ny, nz = 700, 420, 40
+    eps, sig = wl.random_materials(nx, ny, nz, seed=71, nmat=6, sigma=(0.0, 0.5))
+    f = wl.random_fields(nx, ny, nz, seed=72)
+    amp, f0, bw, t0, kind = wl.gaussian_sine_source()
+    srcs = [(2, 350, 210, 20, 30.0, f0, bw, 4e-12, 0)]
+    prbs = wl.probe_edges(nx, ny, nz, 6, seed=73) + [(0, 599, 419, 39), (2, 61, 27, 0)]
+    g, o = make_pair(oracle_mod, nx, ny, nz, eps, sig, f, srcs, prbs, temporal_k=K)
+    steps = 2 * K + 1
+    g.step(steps)
+    o.step(steps)
+    assert_fields_equal(g, o)
+    for q in range(len(prbs)):
+        np.testing.assert_array_equal(g.read_probe(q), o.probe(q))
+
+
 @pytest.mark.parametrize("K", [2, 3, 4])
 def test_blocked_equals_plain_long(sophie, K):
     nx, ny, nz = 100, 90, 80
