@@ -40,7 +40,7 @@ FIELD_BYTES = 48   # read + write six float32 components per cell-update
 MAT_BYTES = 4      # one 32-bit material word read per cell per launch
 # DRAM bytes (read + write) per launch from one ncu capture of each kernel on
 # this workload (profiles/*.md); None where the kernel changed since.
-NCU_TRAFFIC = {("yee_blocked", 2): 522.520064e6 + 359.298816e6,
+NCU_TRAFFIC = {("yee_blocked", 2): None,  # work split changed since the last capture
                ("yee_plain", 1): 504.597248e6 + 361.924608e6,
                ("yee_plain_nu", 1): 509.975552e6 + 364.398848e6}  # graded 256^3 cavity
 # Batching workload: DRAM bytes per cell per launch of the batch-mode plain
