@@ -214,7 +214,9 @@ int sophie_sync(sophie_grid *g);
 /*
  * temporal_k: steps fused per launch (1 = plain kernel, 2..4 = temporally
  * blocked; 5..8 reserved, ENOTSUP), 0 = autotuned (the default: the first
- * sophie_step measures the candidates, see sophie_autotune). tile_x: 0 or 64 = TMA-staged 64x16 tiles
+ * sophie_step measures the candidates, see sophie_autotune). With a fixed k
+ * the first sophie_step still measures that k's work splits (and the plain
+ * kernel's z chunks) and keeps the fastest; results are the same. tile_x: 0 or 64 = TMA-staged 64x16 tiles
  * (default), 32 = 32x8 tiles with direct loads (a slower reference kernel;
  * identical results); tile_y: reserved, 0.
  * precision: SOPHIE_FP32, SOPHIE_FP16 or SOPHIE_BF16 storage of the fields,

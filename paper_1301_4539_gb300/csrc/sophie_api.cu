@@ -577,7 +577,10 @@ double time_candidate(sophie_grid* g, Fn&& launch, cudaEvent_t e0, cudaEvent_t e
 // blocked kernel at k = 2..4 with several work splits on this grid, keep the
 // fastest per step. All candidates give bitwise identical float results, so
 // the choice changes only speed. With 2-byte storage, where results depend
-// on k, only the tilings are tuned and k stays 2.
+// on k, only the tilings are tuned and k stays 2. With a fixed temporal_k only
+// the tilings of that k are tuned (and the plain kernel's, which also runs
+// the remainder steps). The tuning knobs SOPHIE_ZCHUNK and
+// SOPHIE_BLOCKED_ALIGNED, when set, replace the candidates they fix.
 int run_autotune(sophie_grid* g, double* best_ms_per_step) {
   if (g->use_simple) {
     g->tuned = true;
@@ -598,7 +601,11 @@ int run_autotune(sophie_grid* g, double* best_ms_per_step) {
   double best_plain = 1e300;
   BlockedTiling best_b{};
   int best_k = 1;
-  const int zcs[] = {1, 2, 4, 8, 16, 32, 64};
+  const int kfix = g->temporal_k;  // 0: k is tuned too
+  const char* zenv = getenv("SOPHIE_ZCHUNK");
+  const char* aenv = getenv("SOPHIE_BLOCKED_ALIGNED");
+  std::vector<int> zcs = {1, 2, 4, 8, 16, 32, 64};
+  if (zenv) zcs = {atoi(zenv) > 0 ? atoi(zenv) : 0};
   for (int zc : zcs) {
     if (zc > 2 * d.nz && zc != zcs[0]) break;
     const PlainTiling pt = plain_tiling(d, g->num_sms, zc);
@@ -614,22 +621,28 @@ int run_autotune(sophie_grid* g, double* best_ms_per_step) {
       best_p = pt;
     }
   }
-  if (g->fmt == kF32 || g->rat) {
+  if (kfix == 1 || (kfix == 0 && (g->fmt == kF32 || g->rat))) {
     best = best_plain;
     best_k = 1;
   }
-  for (int K = 2; K <= 4 && !g->rat; ++K) {  // the blocked kernel takes uniform meshes only
-    if (g->fmt != kF32 && K != 2) continue;
+  const int k_lo = kfix ? kfix : 2, k_hi = kfix ? kfix : 4;
+  for (int K = k_lo; K <= k_hi && K >= 2 && !g->rat; ++K) {  // the blocked kernel takes uniform meshes only
+    if (!kfix && g->fmt != kF32 && K != 2) continue;
     // the cost model's aligned split in both unit orders, its neighbours and
     // twice it, and the contiguous split
     std::vector<BlockedTiling> cands;
     const BlockedTiling model = blocked_tiling(d, K, g->num_sms, 1);
-    cands.push_back(model);
-    cands.push_back(blocked_tiling_split(d, K, g->num_sms, model.zsplit, 1 - model.order));
-    for (int zs : {model.zsplit + 1, model.zsplit - 1, 2 * model.zsplit})
-      if (zs >= 1 && zs <= d.nz)
-        for (int order = 0; order < 2; ++order) cands.push_back(blocked_tiling_split(d, K, g->num_sms, zs, order));
-    cands.push_back(blocked_tiling(d, K, g->num_sms, 0));
+    if (aenv) {
+      const int mode = atoi(aenv);
+      cands.push_back(blocked_tiling(d, K, g->num_sms, mode >= 0 && mode <= 3 ? mode : 1));
+    } else {
+      cands.push_back(model);
+      cands.push_back(blocked_tiling_split(d, K, g->num_sms, model.zsplit, 1 - model.order));
+      for (int zs : {model.zsplit + 1, model.zsplit - 1, 2 * model.zsplit})
+        if (zs >= 1 && zs <= d.nz)
+          for (int order = 0; order < 2; ++order) cands.push_back(blocked_tiling_split(d, K, g->num_sms, zs, order));
+      cands.push_back(blocked_tiling(d, K, g->num_sms, 0));
+    }
     for (const BlockedTiling& bt : cands) {
       const double ms = time_candidate(
           g, [&] { return launch_step_blocked(a, g->tmFB[g->cur], g->tmMB, bt, g->stream); }, e0, e1);
@@ -647,6 +660,12 @@ int run_autotune(sophie_grid* g, double* best_ms_per_step) {
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
+  // The trial launches wrote the spare buffer everywhere. Zero-field skipping
+  // relies on both buffers being zero outside the known-nonzero box (skipped
+  // units are never written), so clear it: the next step writes every unit it
+  // computes in full, and every other entry is zero in the state anyway.
+  if (!g->box_all)
+    CUDA_TRY(cudaMemsetAsync(g->F[1 - g->cur], 0, (size_t)d.zstride * d.nz1 * g->esz, g->stream));
   rc = check_err_word(g);
   if (rc) return rc;
   g->ptile = best_p;
@@ -950,7 +969,7 @@ int sophie_step(sophie_grid* g, int n) {
   int rc = ensure_capacity(g, g->n + n);
   if (rc) return rc;
   g->gen++;
-  if (g->temporal_k == 0 && !g->tuned) {
+  if (!g->tuned) {  // k and tilings, or (fixed temporal_k) the tilings only
     rc = run_autotune(g, nullptr);
     if (rc) return rc;
   }
@@ -1170,7 +1189,7 @@ int sophie_configure(sophie_grid* g, int temporal_k, int tile_x, int tile_y, int
   }
   if (temporal_k != g->temporal_k || precision != g->precision || (tile_x == 32) != g->use_simple) {
     g->tuned = false;
-    // a fixed k keeps the default tilings
+    // the modelled tilings until the next step measures them
     const char* zc = getenv("SOPHIE_ZCHUNK");
     g->ptile = plain_tiling(g->d, g->num_sms, zc ? atoi(zc) : 0);
     g->btile = BlockedTiling{};
