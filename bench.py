@@ -42,7 +42,8 @@ MAT_BYTES = 4      # one 32-bit material word read per cell per launch
 # this workload (profiles/*.md); None where the kernel changed since.
 NCU_TRAFFIC = {("yee_blocked", 2): 521.866496e6 + 358.466560e6,
                ("yee_plain", 1): 505.030912e6 + 361.748480e6,
-               ("yee_plain_nu", 1): 509.975552e6 + 364.398848e6}  # graded 256^3 cavity
+               ("yee_plain_nu", 1): 510.027264e6 + 364.156416e6,  # graded 256^3 cavity
+               ("yee_blocked_nu", 2): 512.795648e6 + 356.909824e6}
 # Batching workload: DRAM bytes per cell per launch of the batch-mode plain
 # kernel (4.093696 GB for the 54436430 cells of a 300-cavity instance).
 BATCH_TRAFFIC_PER_CELL = (2.742592e9 + 1.351104e9) / 54436430
@@ -399,7 +400,7 @@ def run_ours(args):
 
     graded = None
     if not args.no_graded and rank == 0:
-        graded = run_graded(stream, variants["k1"], tsteps=args.graded_tsteps, autotune=not args.k)
+        graded = run_graded(stream, variants["k1"], tsteps=args.graded_tsteps, k=args.k)
 
     if rank == 0:
         line = {"metric": "Gcell-updates/s 3D Yee FDTD", "value": value, "unit": "Gcell-updates/s",
@@ -534,13 +535,13 @@ def run_precision_768(stream, tsteps: int = 200):
     return out
 
 
-def run_graded(stream, uniform_k1: float, n: int = 256, tsteps: int = 1000, reps: int = 3, autotune: bool = True):
+def run_graded(stream, uniform_k1: float, n: int = 256, tsteps: int = 1000, reps: int = 3, k: int = 0):
     """The non-uniform mesh on its workload: the 256^3 sphere cavity on a mesh
     refined around the source (every axis dx down to dx/2, Gaussian profile;
     dt at the refined Courant limit), reset + `tsteps` steps per run, device
-    time with CUDA events; the plain kernel's scaled-difference variant
-    (temporal blocking takes uniform meshes only). Roofline of that kernel:
-    the same 52 B per cell as the uniform plain kernel (the ratio arrays are
+    time with CUDA events, autotuned (k = 0) or at a fixed k, and the plain
+    kernel (k = 1) beside it. Roofline of the dominant kernel of each: the
+    same 52 B per cell and launch as on the uniform mesh (the ratio arrays are
     a few KB, read from L1) over its event-timed launches."""
     import torch
     from paper_1301_4539_gb300 import sophie as so
@@ -554,39 +555,50 @@ def run_graded(stream, uniform_k1: float, n: int = 256, tsteps: int = 1000, reps
         g.add_source(*src)
     for p in w["probes"]:
         g.add_probe(*p)
-    if autotune:
-        k, _ = g.autotune()
-    else:
-        k = 1
-        g.configure(temporal_k=1)
-    g.reset()
-    g.step(50)
-    g.profile(True)
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize()
-    ev0.record(stream)
-    energy = None
-    for _ in range(reps):
+
+    def one(kk):
+        if kk == 0:
+            kk, _ = g.autotune()
+        else:
+            g.configure(temporal_k=kk)
         g.reset()
-        g.step(tsteps)
-        energy = g.energy()
-    ev1.record(stream)
-    torch.cuda.synchronize()
-    ms = ev0.elapsed_time(ev1)
-    kl, kms = g.profile_read(so.KERNEL_PLAIN)
-    g.profile(False)
+        g.step(50)  # (a fixed k tunes its tilings at the first step)
+        g.profile(True)
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        energy = None
+        torch.cuda.nvtx.range_push("timed")
+        for _ in range(reps):
+            g.reset()
+            g.step(tsteps)
+            energy = g.energy()
+        torch.cuda.nvtx.range_pop()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        ms = ev0.elapsed_time(ev1)
+        prof = {kid: g.profile_read(kid) for kid in (so.KERNEL_PLAIN, so.KERNEL_BLOCKED)}
+        g.profile(False)
+        kid = max(prof, key=lambda q: prof[q][1])
+        kl, kms = prof[kid]
+        name = "yee_blocked (non-uniform)" if kid == so.KERNEL_BLOCKED else "yee_plain (non-uniform)"
+        achieved = n ** 3 * (FIELD_BYTES + MAT_BYTES) / (kms / max(kl, 1) / 1e3) / 1e9
+        traffic = (NCU_TRAFFIC.get(("yee_plain_nu", 1)) if kid == so.KERNEL_PLAIN
+                   else NCU_TRAFFIC.get(("yee_blocked_nu", kk)))
+        return kk, n ** 3 * tsteps * reps / (ms / 1e3) / 1e9, energy, {
+            "kernel": name, "steps_per_launch": kk if kid == so.KERNEL_BLOCKED else 1, "bound": "hbm",
+            "achieved": achieved, "peak": peaks()[0], "unit": "GB/s", "frac": achieved / peaks()[0],
+            "traffic": traffic, "avg_launch_ms": kms / max(kl, 1), "launches": kl}
+
+    kk, rate, energy, roof = one(k)
+    k1, rate1, _, roof1 = one(1) if kk != 1 else (kk, rate, energy, roof)
     g.close()
-    rate = n ** 3 * tsteps * reps / (ms / 1e3) / 1e9
-    achieved = n ** 3 * (FIELD_BYTES + MAT_BYTES) / (kms / max(kl, 1) / 1e3) / 1e9
     return {"workload": f"{n}^3 PEC sphere cavity on a graded mesh (widths 1 mm to 0.5 mm towards the centre "
                         f"along every axis, dt {w['dt']:.4g} s), {tsteps} steps per run",
-            "gcell_per_s": rate, "unit": "Gcell-updates/s", "temporal_k": k, "vs_uniform_k1": rate / uniform_k1,
-            "roofline": {"kernel": "yee_plain (non-uniform)", "bound": "hbm", "achieved": achieved,
-                         "peak": peaks()[0], "unit": "GB/s", "frac": achieved / peaks()[0],
-                         "traffic": NCU_TRAFFIC.get(("yee_plain_nu", 1)),
-                         "avg_launch_ms": kms / max(kl, 1), "launches": kl},
-            "energy_J": energy}
+            "gcell_per_s": rate, "unit": "Gcell-updates/s", "temporal_k": kk, "autotuned": k == 0,
+            "roofline": roof, "k1_gcell_per_s": rate1, "k1_roofline": roof1,
+            "k1_vs_uniform_k1": rate1 / uniform_k1, "energy_J": energy}
 
 
 def run_batch(ncav: int = 4096, tsteps: int = 500):

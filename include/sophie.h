@@ -226,7 +226,7 @@ int sophie_sync(sophie_grid *g);
  * the current fields; synchronises. In the non-float modes one launch loads
  * the stored fields, computes its k steps in float and rounds once when
  * storing, so results depend on k (no longer bitwise equal across k).
- * Errors: EINVAL, ENOTSUP (also temporal_k >= 2 on a non-uniform mesh), ENOMEM.
+ * Errors: EINVAL, ENOTSUP, ENOMEM.
  */
 int sophie_configure(sophie_grid *g, int temporal_k, int tile_x, int tile_y, int precision);
 
@@ -286,14 +286,14 @@ int sophie_set_zero_skip(sophie_grid *g, int enable);
  * coefficients (Ca, Cb) are unchanged (the ratios carry the geometry), and
  * sophie_energy weights each term by its edge or face volume in units of
  * dx^3, so the lossless energy stays conserved.
- * Steps run on the plain step kernel (either tile choice, every storage
- * format) with k = 1; zero-field skipping applies as usual. Stability needs
- * c dt sqrt(1/min(wx)^2 + 1/min(wy)^2 + 1/min(wz)^2) <= 1.
+ * Every step kernel (plain with either tile choice, temporally blocked k =
+ * 2..4; every storage format) and zero-field skipping apply as on the
+ * uniform mesh, with the same results across k for float storage.
+ * Stability needs c dt sqrt(1/min(wx)^2 + 1/min(wy)^2 + 1/min(wz)^2) <= 1.
  * A probe objective record (sophie_objective_forward) is invalidated; probe
  * objectives need the uniform mesh.
  * Errors: EINVAL (NULL grid, a width not finite and > 0), EUNSTABLE (dt above
- * that limit), ENOTSUP (the grid is configured with temporal_k >= 2, which
- * the temporally blocked kernel does not support on this mesh), ENOMEM, ECUDA.
+ * that limit), ENOMEM, ECUDA.
  */
 int sophie_set_spacing(sophie_grid *g, const double *wx, const double *wy, const double *wz);
 

@@ -621,12 +621,12 @@ int run_autotune(sophie_grid* g, double* best_ms_per_step) {
       best_p = pt;
     }
   }
-  if (kfix == 1 || (kfix == 0 && (g->fmt == kF32 || g->rat))) {
+  if (kfix == 1 || (kfix == 0 && g->fmt == kF32)) {
     best = best_plain;
     best_k = 1;
   }
   const int k_lo = kfix ? kfix : 2, k_hi = kfix ? kfix : 4;
-  for (int K = k_lo; K <= k_hi && K >= 2 && !g->rat; ++K) {  // the blocked kernel takes uniform meshes only
+  for (int K = k_lo; K <= k_hi && K >= 2; ++K) {
     if (!kfix && g->fmt != kF32 && K != 2) continue;
     // the cost model's aligned split in both unit orders, its neighbours and
     // twice it, and the contiguous split
@@ -975,7 +975,7 @@ int sophie_step(sophie_grid* g, int n) {
   }
   for (int m = 0; m < n;) {
     const int K = g->temporal_k == 0 ? g->tuned_k : g->temporal_k;
-    const bool blocked = !g->use_simple && !g->rat && K >= 2 && n - m >= K && blocked_supported(K);
+    const bool blocked = !g->use_simple && K >= 2 && n - m >= K && blocked_supported(K);
     StepArgs a = make_step_args(g);
     const int adv_steps = blocked ? K : 1;
     // Zero-field skipping: this launch covers only the tiles and planes of the
@@ -1175,8 +1175,6 @@ int sophie_configure(sophie_grid* g, int temporal_k, int tile_x, int tile_y, int
   if (temporal_k < 0 || temporal_k > 8) return fail(SOPHIE_EINVAL, "temporal_k must be in 0..8");
   if (temporal_k >= 2 && !blocked_supported(temporal_k))
     return fail(SOPHIE_ENOTSUP, "temporal_k = %d not built (supported: 1..4)", temporal_k);
-  if (temporal_k >= 2 && g->rat)
-    return fail(SOPHIE_ENOTSUP, "the temporally blocked kernel takes uniform meshes only");
   if (tile_x < 0 || tile_y < 0) return fail(SOPHIE_EINVAL, "tile sizes must be >= 0");
   if (tile_x != 0 && tile_x != 32 && tile_x != 64) return fail(SOPHIE_EINVAL, "tile_x must be 0, 32 or 64");
   if (precision < SOPHIE_FP32 || precision > SOPHIE_FP16HL)
@@ -1219,9 +1217,6 @@ int sophie_set_spacing(sophie_grid* g, const double* wx, const double* wy, const
     }
     return SOPHIE_OK;
   }
-  if (g->temporal_k >= 2)
-    return fail(SOPHIE_ENOTSUP, "the grid runs the temporally blocked kernel (temporal_k = %d), "
-                "which takes uniform meshes only", g->temporal_k);
   const double* w[3] = {wx, wy, wz};
   const int n[3] = {d.nx, d.ny, d.nz};
   double inv2 = 0.0;

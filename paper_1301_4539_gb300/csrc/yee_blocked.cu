@@ -193,7 +193,10 @@ struct Loader {
   }
 };
 
-template <int K, int FMT>
+// NU: non-uniform mesh; every bracket in the scaled form (yee_update.cuh),
+// the ratios of the lane's columns, its rows and the level's plane read per
+// level from the padded pair arrays (L1) rather than held in registers.
+template <int K, int FMT, bool NU>
 __global__ void __launch_bounds__(kThreads, 1)
 yee_blocked_kernel(const __grid_constant__ CUtensorMap tmF, const __grid_constant__ CUtensorMap tmM,
                    const __grid_constant__ StepArgs a, BlockedTiling t) {
@@ -344,6 +347,22 @@ yee_blocked_kernel(const __grid_constant__ CUtensorMap tmF, const __grid_constan
       for (int lv = 1; lv <= K; ++lv) {
         const int p = s - lv;  // plane updated by this level
         const long long nstep = a.n0 + lv - 1;
+        // Non-uniform mesh: (primary, dual) ratios of the lane's two columns
+        // (x is even: one aligned 16-byte load) and of the level's plane;
+        // rows are read where they are used. Region and plane indices stay
+        // within the arrays' zero padding (at least -K-1 and below n + 72).
+        float4 rxp = make_float4(1.f, 1.f, 1.f, 1.f);
+        float2 rzp = make_float2(1.f, 1.f);
+        if constexpr (NU) {
+          rxp = *reinterpret_cast<const float4*>(a.rpair[0] + x);
+          rzp = a.rpair[2][p];
+        }
+        auto rrow = [&](int r) -> float2 {  // (ry, ryd) of row r of this thread
+          if constexpr (NU)
+            return a.rpair[1][ry + warp * kR + r];
+          else
+            return make_float2(1.f, 1.f);
+        };
         // H of this level at plane p-1 (see hxK above)
         auto hxprev = [&](int lvl, int r, int c) -> float {
           return lvl < K ? carry[lvl - 1 < NC ? lvl - 1 : 0].hx[r][c] : hxK[r][c];
@@ -367,11 +386,24 @@ yee_blocked_kernel(const __grid_constant__ CUtensorMap tmF, const __grid_constan
           }
           // the lane's two x positions as packed pairs
           auto P = [](const float (&v)[2]) { return make_float2(v[0], v[1]); };
-          const float2 hx2 = h_upd2(P(in.hx[r]), S, P(eyn[r]), P(in.ey[r]), P(ezj), P(in.ez[r]));
-          const float2 hy2 = h_upd2(P(in.hy[r]), S, make_float2(in.ez[r][1], ez_ip1), P(in.ez[r]), P(exn[r]),
-                                    P(in.ex[r]));
-          const float2 hz2 = h_upd2(P(in.hz[r]), S, P(exj), P(in.ex[r]), make_float2(in.ey[r][1], ey_ip1),
-                                    P(in.ey[r]));
+          float2 hx2, hy2, hz2;
+          if constexpr (NU) {
+            // scaled brackets with the b ratios negated (curl_br2_nu)
+            const float2 S2 = make_float2(S, S);
+            const float ryr = rrow(r).x;
+            hx2 = __ffma2_rn(S2, curl_br2_nu(make_float2(rzp.x, rzp.x), P(eyn[r]), P(in.ey[r]),
+                                             make_float2(-ryr, -ryr), P(ezj), P(in.ez[r])), P(in.hx[r]));
+            hy2 = __ffma2_rn(S2, curl_br2_nu(make_float2(rxp.x, rxp.z), make_float2(in.ez[r][1], ez_ip1),
+                                             P(in.ez[r]), make_float2(-rzp.x, -rzp.x), P(exn[r]), P(in.ex[r])),
+                             P(in.hy[r]));
+            hz2 = __ffma2_rn(S2, curl_br2_nu(make_float2(ryr, ryr), P(exj), P(in.ex[r]),
+                                             make_float2(-rxp.x, -rxp.z), make_float2(in.ey[r][1], ey_ip1),
+                                             P(in.ey[r])), P(in.hz[r]));
+          } else {
+            hx2 = h_upd2(P(in.hx[r]), S, P(eyn[r]), P(in.ey[r]), P(ezj), P(in.ez[r]));
+            hy2 = h_upd2(P(in.hy[r]), S, make_float2(in.ez[r][1], ez_ip1), P(in.ez[r]), P(exn[r]), P(in.ex[r]));
+            hz2 = h_upd2(P(in.hz[r]), S, P(exj), P(in.ex[r]), make_float2(in.ey[r][1], ey_ip1), P(in.ey[r]));
+          }
           hx[r][0] = hx2.x; hx[r][1] = hx2.y;
           hy[r][0] = hy2.x; hy[r][1] = hy2.y;
           hz[r][0] = hz2.x; hz[r][1] = hz2.y;
@@ -419,12 +451,26 @@ yee_blocked_kernel(const __grid_constant__ CUtensorMap tmF, const __grid_constan
             const float2 hzj = r > 0 ? make_float2(hz[rj][0], hz[rj][1]) : make_float2(hza[0], hza[1]);
             const float2 hxj = r > 0 ? make_float2(hx[rj][0], hx[rj][1]) : make_float2(hxa[0], hxa[1]);
             // brackets of the lane's two x positions as packed pairs
-            const float2 bx = curl_br2(make_float2(hz[r][0], hz[r][1]), hzj, make_float2(hy[r][0], hy[r][1]),
-                                       make_float2(hyprev(lv, r, 0), hyprev(lv, r, 1)));
-            const float2 by = curl_br2(make_float2(hx[r][0], hx[r][1]), make_float2(hxprev(lv, r, 0), hxprev(lv, r, 1)),
-                                       make_float2(hz[r][0], hz[r][1]), make_float2(hz_im1, hz[r][0]));
-            const float2 bz = curl_br2(make_float2(hy[r][0], hy[r][1]), make_float2(hy_im1, hy[r][0]),
-                                       make_float2(hx[r][0], hx[r][1]), hxj);
+            float2 bx, by, bz;
+            if constexpr (NU) {
+              const float rydr = rrow(r).y;
+              bx = curl_br2_nu(make_float2(rydr, rydr), make_float2(hz[r][0], hz[r][1]), hzj,
+                               make_float2(-rzp.y, -rzp.y), make_float2(hy[r][0], hy[r][1]),
+                               make_float2(hyprev(lv, r, 0), hyprev(lv, r, 1)));
+              by = curl_br2_nu(make_float2(rzp.y, rzp.y), make_float2(hx[r][0], hx[r][1]),
+                               make_float2(hxprev(lv, r, 0), hxprev(lv, r, 1)), make_float2(-rxp.y, -rxp.w),
+                               make_float2(hz[r][0], hz[r][1]), make_float2(hz_im1, hz[r][0]));
+              bz = curl_br2_nu(make_float2(rxp.y, rxp.w), make_float2(hy[r][0], hy[r][1]),
+                               make_float2(hy_im1, hy[r][0]), make_float2(-rydr, -rydr), make_float2(hx[r][0], hx[r][1]),
+                               hxj);
+            } else {
+              bx = curl_br2(make_float2(hz[r][0], hz[r][1]), hzj, make_float2(hy[r][0], hy[r][1]),
+                            make_float2(hyprev(lv, r, 0), hyprev(lv, r, 1)));
+              by = curl_br2(make_float2(hx[r][0], hx[r][1]), make_float2(hxprev(lv, r, 0), hxprev(lv, r, 1)),
+                            make_float2(hz[r][0], hz[r][1]), make_float2(hz_im1, hz[r][0]));
+              bz = curl_br2(make_float2(hy[r][0], hy[r][1]), make_float2(hy_im1, hy[r][0]),
+                            make_float2(hx[r][0], hx[r][1]), hxj);
+            }
 #pragma unroll
             for (int cc = 0; cc < 2; ++cc) {
               const uint32_t m = in.m[r][cc];
@@ -446,9 +492,11 @@ yee_blocked_kernel(const __grid_constant__ CUtensorMap tmF, const __grid_constan
               const float hxj = r > 0 ? hx[r > 0 ? r - 1 : 0][cc] : hxa[cc];
               const float hzi = cc ? hz[r][0] : hz_im1;
               const float hyi = cc ? hy[r][0] : hy_im1;
-              float bx = curl_br(hz[r][cc], hzj, hy[r][cc], hyprev(lv, r, cc));
-              float by = curl_br(hx[r][cc], hxprev(lv, r, cc), hz[r][cc], hzi);
-              float bz = curl_br(hy[r][cc], hyi, hx[r][cc], hxj);
+              const float2 rr = rrow(r);  // ratios of the row, of the column (dual), scaled form if NU
+              const float rxdc = cc ? rxp.w : rxp.y;
+              float bx = bracket<NU>(rr.y, hz[r][cc], hzj, rzp.y, hy[r][cc], hyprev(lv, r, cc));
+              float by = bracket<NU>(rzp.y, hx[r][cc], hxprev(lv, r, cc), rxdc, hz[r][cc], hzi);
+              float bz = bracket<NU>(rxdc, hy[r][cc], hyi, rr.y, hx[r][cc], hxj);
               const uint32_t m = in.m[r][cc];
               if (m & kSrcFlag) {
                 const float3 b3 = apply_sources(make_float3(bx, by, bz),
@@ -547,18 +595,24 @@ yee_blocked_kernel(const __grid_constant__ CUtensorMap tmF, const __grid_constan
   }
 }
 
-template <int K, int F>
-cudaError_t launch_k(const StepArgs& a, const CUtensorMap& tmF, const CUtensorMap& tmM, const BlockedTiling& t,
-                     cudaStream_t s) {
+template <int K, int F, bool NU>
+cudaError_t launch_kn(const StepArgs& a, const CUtensorMap& tmF, const CUtensorMap& tmM, const BlockedTiling& t,
+                      cudaStream_t s) {
   static bool attr = false;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(yee_blocked_kernel<K, F>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(yee_blocked_kernel<K, F, NU>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)Cfg<K, F>::kSmem);
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  yee_blocked_kernel<K, F><<<t.grid, kThreads, Cfg<K, F>::kSmem, s>>>(tmF, tmM, a, t);
+  yee_blocked_kernel<K, F, NU><<<t.grid, kThreads, Cfg<K, F>::kSmem, s>>>(tmF, tmM, a, t);
   return cudaGetLastError();
+}
+
+template <int K, int F>
+cudaError_t launch_k(const StepArgs& a, const CUtensorMap& tmF, const CUtensorMap& tmM, const BlockedTiling& t,
+                     cudaStream_t s) {
+  return a.rat[0] ? launch_kn<K, F, true>(a, tmF, tmM, t, s) : launch_kn<K, F, false>(a, tmF, tmM, t, s);
 }
 
 template <int F>

@@ -2,19 +2,21 @@
 
 * Random widths on every axis, lossy materials with conducting cells, random
   initial fields, a source and probes: fields and probe samples bitwise equal
-  to the float oracle's, for the TMA-staged kernel (every storage format's
-  float variant is float) and the direct-load kernel, on grids spanning
+  to the float oracle's, for the TMA-staged plain kernel, the direct-load
+  kernel and the temporally blocked kernel at K = 2, 3, 4, on grids spanning
   several tiles with ragged tails; energy within 1e-12 of the oracle's.
 * All widths equal to dx: bitwise the uniform run; clearing the widths
   returns to the uniform kernels.
 * Lossless, sourceless graded mesh: the volume-weighted energy is conserved.
-* Zero-field skipping on a graded mesh: bitwise the run without skipping.
-* Split hi+lo half storage on a graded mesh stays within 1e-4 of float.
+* Zero-field skipping on a graded mesh (plain, direct-load, K = 2, 3):
+  bitwise the oracle.
+* Split hi+lo half storage on a graded mesh stays within 1e-4 of float
+  (K = 1, 2).
 * The graded 256^3 sphere cavity (the non-uniform bench workload, its launch
   configuration): 300 steps, fields and probes bitwise equal to the float
   oracle, energy within the summation-order bound.
 * Argument errors: bad widths, a time step above the mesh's Courant limit,
-  the temporally blocked kernel and probe objectives on this mesh.
+  probe objectives on this mesh.
 """
 
 import numpy as np
@@ -28,7 +30,7 @@ from paper_1301_4539_gb300 import workloads as wl
 pytestmark = pytest.mark.gpu
 
 
-def _graded_pair(oracle_mod, nx, ny, nz, seed, tile_x=64, lossy=True, fields=True, source=True, probes=True):
+def _graded_pair(oracle_mod, nx, ny, nz, seed, tile_x=64, lossy=True, fields=True, source=True, probes=True, K=1):
     wx, wy, wz = (wl.random_widths(n, seed + a) for a, n in enumerate((nx, ny, nz)))
     dt = wl.mesh_dt(wx, wy, wz)
     eps, sig = wl.random_materials(nx, ny, nz, seed, nmat=6, sigma=(0.0, 0.4) if lossy else (0.0, 0.0))
@@ -36,7 +38,7 @@ def _graded_pair(oracle_mod, nx, ny, nz, seed, tile_x=64, lossy=True, fields=Tru
         eps = eps.copy()
         eps[np.random.default_rng(seed).random(eps.shape) < 0.01] = np.inf  # conducting cells
     g = so.Grid(nx, ny, nz, DX, dt)
-    g.configure(temporal_k=1, tile_x=tile_x)
+    g.configure(temporal_k=K, tile_x=tile_x)
     o = oracle_mod.OracleGrid(nx, ny, nz, DX, dt, "f32")
     for t in (g, o):
         t.set_materials(eps, sig)
@@ -60,10 +62,12 @@ def _graded_pair(oracle_mod, nx, ny, nz, seed, tile_x=64, lossy=True, fields=Tru
     return g, o, prbs, (wx, wy, wz)
 
 
-@pytest.mark.parametrize("tile_x", [64, 32])
+@pytest.mark.parametrize("kernel", ["plain", "direct", "k2", "k3", "k4"])
 @pytest.mark.parametrize("n3,steps", [((70, 37, 19), 23), ((130, 21, 40), 11), ((64, 16, 8), 7), ((3, 90, 5), 9)])
-def test_graded_mesh_equals_oracle(oracle_mod, sophie, tile_x, n3, steps):
-    g, o, prbs, _ = _graded_pair(oracle_mod, *n3, seed=sum(n3), tile_x=tile_x)
+def test_graded_mesh_equals_oracle(oracle_mod, sophie, kernel, n3, steps):
+    tile_x = 32 if kernel == "direct" else 64
+    K = int(kernel[1]) if kernel.startswith("k") else 1
+    g, o, prbs, _ = _graded_pair(oracle_mod, *n3, seed=sum(n3), tile_x=tile_x, K=K)
     g.step(steps)
     o.step(steps)
     assert_fields_equal(g, o)
@@ -110,9 +114,9 @@ def test_energy_conserved_on_graded_mesh(oracle_mod, sophie):
     assert drift < 5e-6
 
 
-@pytest.mark.parametrize("tile_x", [64, 32])
-def test_zero_skip_on_graded_mesh(oracle_mod, sophie, tile_x):
-    g, o, prbs, _ = _graded_pair(oracle_mod, 150, 70, 60, seed=5, tile_x=tile_x, fields=False)
+@pytest.mark.parametrize("tile_x,K", [(64, 1), (32, 1), (64, 2), (64, 3)])
+def test_zero_skip_on_graded_mesh(oracle_mod, sophie, tile_x, K):
+    g, o, prbs, _ = _graded_pair(oracle_mod, 150, 70, 60, seed=5, tile_x=tile_x, fields=False, K=K)
     g.set_zero_skip(True)
     done = 0
     for n in (3, 20, 45):
@@ -124,9 +128,10 @@ def test_zero_skip_on_graded_mesh(oracle_mod, sophie, tile_x):
         np.testing.assert_array_equal(g.read_probe(q), o.probe(q))
 
 
-def test_fp16hl_storage_on_graded_mesh(oracle_mod, sophie):
+@pytest.mark.parametrize("K", [1, 2])
+def test_fp16hl_storage_on_graded_mesh(oracle_mod, sophie, K):
     g, o, _, _ = _graded_pair(oracle_mod, 80, 48, 36, seed=8, fields=False)
-    g.configure(temporal_k=1, precision=so.FP16HL)
+    g.configure(temporal_k=K, precision=so.FP16HL)
     g.set_storage_scale([2.0 ** 6] * 6)
     g.step(150)
     o.step(150)
@@ -136,8 +141,7 @@ def test_fp16hl_storage_on_graded_mesh(oracle_mod, sophie):
 
 
 def test_graded_sphere_cavity_full_size(oracle_mod, sophie):
-    """The graded 256^3 sphere cavity in the bench's configuration (autotuned:
-    the plain kernel, since the blocked one takes uniform meshes only)."""
+    """The graded 256^3 sphere cavity in the bench's configuration (autotuned)."""
     w = wl.sphere_cavity_graded(256)
     n = w["nx"]
     steps = 300
@@ -182,15 +186,8 @@ def test_spacing_errors(sophie):
         g.set_spacing(None, w)
     assert e.value.code == so.EUNSTABLE
     g.set_spacing(np.full(nx, 2 * DX))  # coarser cells are fine
-    with pytest.raises(so.SophieError) as e:
-        g.configure(temporal_k=2)
-    assert e.value.code == so.ENOTSUP
+    g.configure(temporal_k=2)  # the blocked kernel takes the mesh too
     with pytest.raises(so.SophieError) as e:
         g.objective_forward(10, 2, 5, 5, 5)
-    assert e.value.code == so.ENOTSUP
-    g.set_spacing()
-    g.configure(temporal_k=2)
-    with pytest.raises(so.SophieError) as e:
-        g.set_spacing(np.full(nx, 2 * DX))
     assert e.value.code == so.ENOTSUP
     g.close()
