@@ -6,7 +6,8 @@ up front; this entry point serves them by keeping its reduction scratch in a
 static device array instead of allocating. Here it is called through the C ABI
 and must give the same energy as sophie_energy (the allocating entry point),
 within the 1e-12 relative tolerance the energy tests use, on two calls in a
-row (the static scratch keeps the previous call's contents).
+row (the static scratch keeps the previous call's contents), on a uniform and
+on a non-uniform mesh.
 """
 
 import ctypes
@@ -22,22 +23,26 @@ pytestmark = pytest.mark.gpu
 DX = 1e-3
 
 
-def _grid():
+def _grid(graded=False):
     nx, ny, nz = 70, 45, 38
-    g = so.Grid(nx, ny, nz, DX, wl.cfl_dt(DX))
+    widths = [wl.random_widths(n, seed=30 + a) for a, n in enumerate((nx, ny, nz))]
+    g = so.Grid(nx, ny, nz, DX, wl.mesh_dt(*widths) if graded else wl.cfl_dt(DX))
     eps, sig = wl.sphere_materials(nx, ny, nz, nspheres=6, seed=21, radius=(3, 10))
     g.set_materials(eps, sig)
+    if graded:  # the volume-weighted energy of a non-uniform mesh
+        g.set_spacing(*widths)
     f = wl.random_fields(nx, ny, nz, seed=22)
     for c in range(6):
         g.set_field(c, f[c])
     return g
 
 
-def test_energy_noalloc_matches_energy(sophie):
+@pytest.mark.parametrize("graded", [False, True])
+def test_energy_noalloc_matches_energy(sophie, graded):
     import torch
 
     lib = so.load()
-    g = _grid()
+    g = _grid(graded)
     out = torch.zeros(2, dtype=torch.float64, device="cuda")  # caller-owned result slots
     torch.cuda.synchronize()
     for call in range(2):
