@@ -34,11 +34,59 @@ struct TripleKey {
   EdgeKey k[3];
   bool operator==(const TripleKey& o) const { return k[0] == o.k[0] && k[1] == o.k[1] && k[2] == o.k[2]; }
 };
-struct TripleKeyHash {
-  size_t operator()(const TripleKey& t) const {
-    EdgeKeyHash h;
-    return h(t.k[0]) * 31u + h(t.k[1]) * 17u + h(t.k[2]);
+
+// Explicit entries of a slab by their three edge materials: open addressing
+// with linear probing over entry numbers (slot = number + 1, 0 = empty), the
+// keys kept in insertion order, so an entry's number is its insertion rank.
+// The key bits are mixed with the splitmix64 finalizer (Steele, Lea and
+// Flood, OOPSLA 2014): doubles from float data end in many zero bits, which a
+// power-of-two table would otherwise see as one cluster.
+class TripleIndex {
+ public:
+  // Number of `k`, inserting it as the next number if new (`inserted`).
+  uint32_t find_or_insert(const TripleKey& k, bool& inserted) {
+    if (2 * (keys_.size() + 1) > slot_.size()) grow();
+    size_t h = hash(k) & mask_;
+    for (;;) {
+      const uint32_t v = slot_[h];
+      if (v == 0) {
+        keys_.push_back(k);
+        slot_[h] = (uint32_t)keys_.size();
+        inserted = true;
+        return (uint32_t)keys_.size() - 1;
+      }
+      if (keys_[v - 1] == k) {
+        inserted = false;
+        return v - 1;
+      }
+      h = (h + 1) & mask_;
+    }
   }
+
+ private:
+  void grow() {
+    const size_t n = slot_.empty() ? 1024 : 2 * slot_.size();
+    slot_.assign(n, 0);
+    mask_ = n - 1;
+    for (size_t q = 0; q < keys_.size(); ++q) {
+      size_t h = hash(keys_[q]) & mask_;
+      while (slot_[h] != 0) h = (h + 1) & mask_;
+      slot_[h] = (uint32_t)q + 1;
+    }
+  }
+  static uint64_t mix(uint64_t z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+  }
+  static size_t hash(const TripleKey& k) {
+    uint64_t h = 0;
+    for (int c = 0; c < 3; ++c) h = mix(mix(h ^ k.k[c].e) ^ k.k[c].s);
+    return (size_t)h;
+  }
+  std::vector<TripleKey> keys_;
+  std::vector<uint32_t> slot_;
+  size_t mask_ = 0;
 };
 
 uint64_t dbits(double v) {
@@ -51,14 +99,6 @@ double from_bits(uint64_t u) {
   double v;
   memcpy(&v, &u, 8);
   return v;
-}
-
-bool edge_interior(const Dims& d, int c, int i, int j, int k) {
-  switch (c) {
-    case 0: return i >= 0 && i < d.nx && j >= 1 && j < d.ny && k >= 1 && k < d.nz;
-    case 1: return i >= 1 && i < d.nx && j >= 0 && j < d.ny && k >= 1 && k < d.nz;
-    default: return i >= 1 && i < d.nx && j >= 1 && j < d.ny && k >= 0 && k < d.nz;
-  }
 }
 
 }  // namespace
@@ -82,50 +122,80 @@ float2 edge_coefficients(double dt, double S64, double e, double s) {
 
 namespace {
 
-// Edge materials of one grid: mean (eps, sigma) of an interior edge, four
-// cells summed in the fixed order (-,-), (+,-), (-,+), (+,+) of the two
-// transverse offsets. A cell with eps = +inf (perfect conductor) makes the
-// mean infinite: PEC edge.
+// Per-cell materials of one grid (x fastest; null eps = vacuum, null sigma =
+// lossless). The material of an interior edge is the mean (eps, sigma) of its
+// four cells, summed in double in the fixed order (-,-), (+,-), (-,+), (+,+)
+// of the two transverse offsets (edge_row_means). A cell with eps = +inf
+// (perfect conductor) makes the mean infinite: PEC edge.
 struct EdgeMaterials {
   const Dims& d;
   const float* eps;
   const float* sig;
-  double E(int i, int j, int k) const { return eps ? (double)eps[((long long)k * d.ny + j) * d.nx + i] : 1.0; }
-  double Sg(int i, int j, int k) const { return sig ? (double)sig[((long long)k * d.ny + j) * d.nx + i] : 0.0; }
-  void mean(int c, int i, int j, int k, double& e, double& s) const {
-    double e4, s4;
-    if (c == 0) {
-      e4 = ((E(i, j - 1, k - 1) + E(i, j, k - 1)) + E(i, j - 1, k)) + E(i, j, k);
-      s4 = ((Sg(i, j - 1, k - 1) + Sg(i, j, k - 1)) + Sg(i, j - 1, k)) + Sg(i, j, k);
-    } else if (c == 1) {
-      e4 = ((E(i - 1, j, k - 1) + E(i, j, k - 1)) + E(i - 1, j, k)) + E(i, j, k);
-      s4 = ((Sg(i - 1, j, k - 1) + Sg(i, j, k - 1)) + Sg(i - 1, j, k)) + Sg(i, j, k);
-    } else {
-      e4 = ((E(i - 1, j - 1, k) + E(i, j - 1, k)) + E(i - 1, j, k)) + E(i, j, k);
-      s4 = ((Sg(i - 1, j - 1, k) + Sg(i, j - 1, k)) + Sg(i - 1, j, k)) + Sg(i, j, k);
-    }
-    e = e4 * 0.25;
-    s = s4 * 0.25;
-  }
 };
 
 using FreqMap = std::unordered_map<EdgeKey, long long, EdgeKeyHash>;
 using ClassMap = std::unordered_map<EdgeKey, int, EdgeKeyHash>;
 
+// Valid i range [i0, i1) of component c's interior edges on row (j, k);
+// empty when the row has none.
+void edge_row_range(const Dims& d, int c, int j, int k, int& i0, int& i1) {
+  const bool ok = c == 0 ? (j >= 1 && j < d.ny && k >= 1 && k < d.nz)
+                  : c == 1 ? (j < d.ny && k >= 1 && k < d.nz)
+                           : (j >= 1 && j < d.ny && k < d.nz);
+  i0 = c == 0 ? 0 : 1;
+  i1 = ok ? d.nx : i0;
+}
+
+// Edge means of component c along row (j, k) for i in [i0, i1), written to
+// e[i], s[i]: each the four-cell sum in the order above, times 1/4. The four cell rows are the (-,-), (+,-), (-,+), (+,+) offsets of
+// the two transverse axes; along x an offset is a shift of the row pointer.
+void edge_row_means(const EdgeMaterials& m, int c, int j, int k, int i0, int i1, double* e, double* s) {
+  const Dims& d = m.d;
+  // cell rows (j', k') and x shifts of the four terms, in summation order
+  int jr[4], kr[4], sh[4];
+  if (c == 0) {  // (i, j-1, k-1), (i, j, k-1), (i, j-1, k), (i, j, k)
+    const int J[4] = {j - 1, j, j - 1, j}, K[4] = {k - 1, k - 1, k, k}, X[4] = {0, 0, 0, 0};
+    for (int q = 0; q < 4; ++q) { jr[q] = J[q]; kr[q] = K[q]; sh[q] = X[q]; }
+  } else if (c == 1) {  // (i-1, j, k-1), (i, j, k-1), (i-1, j, k), (i, j, k)
+    const int J[4] = {j, j, j, j}, K[4] = {k - 1, k - 1, k, k}, X[4] = {-1, 0, -1, 0};
+    for (int q = 0; q < 4; ++q) { jr[q] = J[q]; kr[q] = K[q]; sh[q] = X[q]; }
+  } else {  // (i-1, j-1, k), (i, j-1, k), (i-1, j, k), (i, j, k)
+    const int J[4] = {j - 1, j - 1, j, j}, K[4] = {k, k, k, k}, X[4] = {-1, 0, -1, 0};
+    for (int q = 0; q < 4; ++q) { jr[q] = J[q]; kr[q] = K[q]; sh[q] = X[q]; }
+  }
+  auto rowp = [&](const float* a, int q) { return a + ((long long)kr[q] * d.ny + jr[q]) * d.nx + sh[q]; };
+  if (m.eps) {
+    const float *a0 = rowp(m.eps, 0), *a1 = rowp(m.eps, 1), *a2 = rowp(m.eps, 2), *a3 = rowp(m.eps, 3);
+    for (int i = i0; i < i1; ++i)
+      e[i] = ((((double)a0[i] + (double)a1[i]) + (double)a2[i]) + (double)a3[i]) * 0.25;
+  } else {
+    for (int i = i0; i < i1; ++i) e[i] = (((1.0 + 1.0) + 1.0) + 1.0) * 0.25;
+  }
+  if (m.sig) {
+    const float *b0 = rowp(m.sig, 0), *b1 = rowp(m.sig, 1), *b2 = rowp(m.sig, 2), *b3 = rowp(m.sig, 3);
+    for (int i = i0; i < i1; ++i)
+      s[i] = ((((double)b0[i] + (double)b1[i]) + (double)b2[i]) + (double)b3[i]) * 0.25;
+  } else {
+    for (int i = i0; i < i1; ++i) s[i] = (((0.0 + 0.0) + 0.0) + 0.0) * 0.25;
+  }
+}
+
 // Frequency of every edge material on planes [k0, k1) (runs along x at once).
 void count_slab(const EdgeMaterials& m, int k0, int k1, FreqMap& freq) {
   const Dims& d = m.d;
+  std::vector<double> e(d.nx + 1), s(d.nx + 1);
   for (int c = 0; c < 3; ++c) {
     EdgeKey last{~0ull, ~0ull};
     long long run = 0;
     for (int k = k0; k < k1; ++k)
-      for (int j = 0; j <= d.ny; ++j)
-        for (int i = 0; i <= d.nx; ++i) {
-          if (!edge_interior(d, c, i, j, k)) continue;
-          double e, s;
-          m.mean(c, i, j, k, e, s);
-          if (std::isinf(e)) continue;
-          const EdgeKey key{dbits(e), dbits(s)};
+      for (int j = 0; j <= d.ny; ++j) {
+        int i0, i1;
+        edge_row_range(d, c, j, k, i0, i1);
+        if (i0 >= i1) continue;
+        edge_row_means(m, c, j, k, i0, i1, e.data(), s.data());
+        for (int i = i0; i < i1; ++i) {
+          if (std::isinf(e[i])) continue;
+          const EdgeKey key{dbits(e[i]), dbits(s[i])};
           if (key == last) {
             ++run;
             continue;
@@ -134,6 +204,7 @@ void count_slab(const EdgeMaterials& m, int k0, int k1, FreqMap& freq) {
           last = key;
           run = 1;
         }
+      }
     if (run) freq[last] += run;
   }
 }
@@ -143,20 +214,29 @@ void count_slab(const EdgeMaterials& m, int k0, int k1, FreqMap& freq) {
 bool words_slab(const EdgeMaterials& m, double dt, double S64, const ClassMap& cls, int k0, int k1,
                 uint32_t* words, MaterialTables& t) {
   const Dims& d = m.d;
-  std::unordered_map<TripleKey, uint32_t, TripleKeyHash> expl;
+  TripleIndex expl;
   EdgeKey lk[3] = {{~0ull, ~0ull}, {~0ull, ~0ull}, {~0ull, ~0ull}};
   int lc[3] = {-1, -1, -1};
+  std::vector<double> eb[3], sb[3];
+  for (int c = 0; c < 3; ++c) {
+    eb[c].resize(d.nx + 1);
+    sb[c].resize(d.nx + 1);
+  }
   for (int k = k0; k < k1; ++k)
     for (int j = 0; j <= d.ny; ++j) {
       uint32_t* row = words + ((long long)k * d.ny1 + j) * d.nxp;
+      int r0[3], r1[3];
+      for (int c = 0; c < 3; ++c) {
+        edge_row_range(d, c, j, k, r0[c], r1[c]);
+        if (r0[c] < r1[c]) edge_row_means(m, c, j, k, r0[c], r1[c], eb[c].data(), sb[c].data());
+      }
       for (int i = 0; i < d.nxp; ++i) {
         int ci[3] = {0, 0, 0};
         TripleKey tk{{{0, 0}, {0, 0}, {0, 0}}};
         bool explicit_pt = false;
         for (int c = 0; c < 3; ++c) {
-          if (!edge_interior(d, c, i, j, k)) continue;
-          double e, s;
-          m.mean(c, i, j, k, e, s);
+          if (i < r0[c] || i >= r1[c]) continue;
+          const double e = eb[c][i], s = sb[c][i];
           if (std::isinf(e)) continue;  // PEC: class 0
           const EdgeKey key{dbits(e), dbits(s)};
           tk.k[c] = key;
@@ -172,14 +252,10 @@ bool words_slab(const EdgeMaterials& m, double dt, double S64, const ClassMap& c
           row[i] = cls_word((uint32_t)ci[0], (uint32_t)ci[1], (uint32_t)ci[2]);
           continue;
         }
-        auto it = expl.find(tk);
-        uint32_t q;
-        if (it != expl.end()) {
-          q = it->second;
-        } else {
-          q = (uint32_t)(t.eeps.size() / 3);
-          if (q >= (1u << 29)) return false;
-          expl.emplace(tk, q);
+        bool inserted = false;
+        const uint32_t q = expl.find_or_insert(tk, inserted);
+        if (q >= (1u << 29)) return false;
+        if (inserted) {
           for (int c = 0; c < 3; ++c) {
             const bool in = tk.k[c].e != 0 || tk.k[c].s != 0;
             const double e = from_bits(tk.k[c].e), s = from_bits(tk.k[c].s);
@@ -211,6 +287,25 @@ void for_slabs(int nslab, int nthreads, F&& f) {
 }
 
 }  // namespace
+
+long long first_bad_material(const float* eps, const float* sig, long long n, int nthreads) {
+  nthreads = std::max(1, nthreads);
+  std::vector<long long> bad(nthreads, -1);
+  std::vector<std::thread> th;
+  for (int t = 0; t < nthreads; ++t)
+    th.emplace_back([&, t] {
+      const long long c0 = n * t / nthreads, c1 = n * (t + 1) / nthreads;
+      for (long long c = c0; c < c1; ++c)
+        if ((eps && !(eps[c] >= 1.0f)) || (sig && (!(sig[c] >= 0.0f) || !std::isfinite(sig[c])))) {
+          bad[t] = c;
+          break;
+        }
+    });
+  for (std::thread& x : th) x.join();
+  for (long long c : bad)
+    if (c >= 0) return c;
+  return -1;
+}
 
 int build_material_tables(const Dims& d, double dt, double S64, const float* eps, const float* sig, uint32_t* words,
                           MaterialTables* out, int nthreads) {

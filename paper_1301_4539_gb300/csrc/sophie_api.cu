@@ -894,11 +894,11 @@ int sophie_debug_fail_alloc(int n) {
 int sophie_set_materials(sophie_grid* g, const float* eps, const float* sig) {
   if (!g || !eps || !sig) return fail(SOPHIE_EINVAL, "NULL argument");
   const long long ncell = (long long)g->d.nx * g->d.ny * g->d.nz;
-  for (long long c = 0; c < ncell; ++c) {
+  const long long c = first_bad_material(eps, sig, ncell, std::max(1, std::min(32, (int)std::thread::hardware_concurrency())));
+  if (c >= 0) {
     if (!(eps[c] >= 1.0f))
       return fail(SOPHIE_EINVAL, "eps_r[%lld] = %g must be >= 1 (+inf: conductor)", c, (double)eps[c]);
-    if (!(sig[c] >= 0.0f) || !std::isfinite(sig[c]))
-      return fail(SOPHIE_EINVAL, "sigma[%lld] = %g must be finite and >= 0", c, (double)sig[c]);
+    return fail(SOPHIE_EINVAL, "sigma[%lld] = %g must be finite and >= 0", c, (double)sig[c]);
   }
   // The staging buffer may still feed an earlier upload.
   CUDA_TRY(cudaEventSynchronize(g->mat_upload_done));

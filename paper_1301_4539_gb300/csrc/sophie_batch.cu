@@ -459,14 +459,11 @@ int sophie_batch_check_guards(sophie_batch* b, long long* bad_bytes) {
 int sophie_batch_set_materials(sophie_batch* b, const float* eps, const float* sig) {
   if (!b) return bfail(SOPHIE_EINVAL, "NULL batch");
   if (!eps && sig) return bfail(SOPHIE_EINVAL, "sigma given without eps_r");
-  if (eps) {
-    for (long long q = 0; q < b->cells; ++q)
-      if (!(eps[q] >= 1.0f)) return bfail(SOPHIE_EINVAL, "eps_r[%lld] = %g must be >= 1 (+inf: conductor)", q, (double)eps[q]);
-  }
-  if (sig) {
-    for (long long q = 0; q < b->cells; ++q)
-      if (!(sig[q] >= 0.0f) || !std::isfinite(sig[q]))
-        return bfail(SOPHIE_EINVAL, "sigma[%lld] = %g must be finite and >= 0", q, (double)sig[q]);
+  const long long q = first_bad_material(eps, sig, b->cells, std::max(1, (int)std::thread::hardware_concurrency()));
+  if (q >= 0) {
+    if (eps && !(eps[q] >= 1.0f))
+      return bfail(SOPHIE_EINVAL, "eps_r[%lld] = %g must be >= 1 (+inf: conductor)", q, (double)eps[q]);
+    return bfail(SOPHIE_EINVAL, "sigma[%lld] = %g must be finite and >= 0", q, (double)sig[q]);
   }
   BCUDA(cudaStreamSynchronize(b->stream));
   const int nc = b->ncav;

@@ -171,6 +171,10 @@ float2 edge_coefficients(double dt, double S64, double e, double s);
 // more than 2^29 explicit entries would be needed.
 int build_material_tables(const Dims& d, double dt, double S64, const float* eps, const float* sig, uint32_t* words,
                           MaterialTables* out, int nthreads);
+// Index of the first of n cells with eps_r < 1 (or NaN) or sigma negative or
+// not finite (a null array is not checked), or -1; checked on nthreads host
+// threads.
+long long first_bad_material(const float* eps, const float* sig, long long n, int nthreads);
 
 // Launchers (return cudaError_t of the launch).
 cudaError_t launch_step_simple(const StepArgs& a, cudaStream_t s);
