@@ -40,7 +40,7 @@ FIELD_BYTES = 48   # read + write six float32 components per cell-update
 MAT_BYTES = 4      # one 32-bit material word read per cell per launch
 # DRAM bytes (read + write) per launch from one ncu capture of each kernel on
 # this workload (profiles/*.md); None where the kernel changed since.
-NCU_TRAFFIC = {("yee_blocked", 2): 521.866496e6 + 358.466560e6,
+NCU_TRAFFIC = {("yee_blocked", 2): 521.599744e6 + 358.377472e6,
                ("yee_plain", 1): 505.030912e6 + 361.748480e6,
                ("yee_plain_nu", 1): 510.027264e6 + 364.156416e6,  # graded 256^3 cavity
                ("yee_blocked_nu", 2): 512.795648e6 + 356.909824e6}
