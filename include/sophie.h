@@ -434,6 +434,28 @@ int sophie_batch_check_guards(sophie_batch *b, long long *bad_bytes);
 int sophie_selftest_wait_timeout(sophie_grid *g, double *waited_ms);
 int sophie_debug_fail_alloc(int n);
 
+/*
+ * The host half of sophie_set_materials on its own, without a grid or a GPU
+ * (for checking the material words on any machine). For an nx*ny*nz grid
+ * with dx, dt and per-cell eps_r / sigma as for sophie_set_materials, built
+ * on nthreads host threads (the result does not depend on it):
+ *   words      (host, (nz+1)(ny+1)nxp uint32, nxp = nx+1 rounded up to a
+ *              multiple of 8): the material word of every index point,
+ *              x fastest (no source or probe flags): bit 2 set = explicit
+ *              point with entry index = word >> 3, else bits 3..11 / 12..20 /
+ *              21..29 = the class of the ex / ey / ez edge (0 = PEC / none);
+ *   class_coef (host, 512 x (Ca, Cb) float), class_eps (512 double eps_r):
+ *              the class table (class 0 = (0, 0), eps 0);
+ *   exp_coef   (host, exp_cap x 3 x (Ca, Cb) float), exp_eps (exp_cap x 3):
+ *              the explicit entries (edges ex, ey, ez of each), filled up to
+ *              exp_cap; *n_explicit = the number of entries.
+ * Errors: EINVAL (NULL, sizes, bad materials as for sophie_set_materials),
+ * ETOOMANYMAT.
+ */
+int sophie_debug_material_tables(int nx, int ny, int nz, double dx, double dt, const float *eps_r, const float *sigma,
+                                 int nthreads, unsigned int *words, float *class_coef, double *class_eps,
+                                 float *exp_coef, double *exp_eps, long long exp_cap, long long *n_explicit);
+
 /* Message of the last error on this thread ("" if none). */
 const char *sophie_last_error(void);
 

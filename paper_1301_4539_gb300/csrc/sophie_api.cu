@@ -885,6 +885,48 @@ int sophie_selftest_wait_timeout(sophie_grid* g, double* waited_ms) {
   return SOPHIE_OK;
 }
 
+int sophie_debug_material_tables(int nx, int ny, int nz, double dx, double dt, const float* eps, const float* sig,
+                                 int nthreads, unsigned int* words, float* class_coef, double* class_eps,
+                                 float* exp_coef, double* exp_eps, long long exp_cap, long long* n_explicit) {
+  if (!eps || !sig || !words || !class_coef || !class_eps || !n_explicit || exp_cap < 0 ||
+      (exp_cap > 0 && (!exp_coef || !exp_eps)))
+    return fail(SOPHIE_EINVAL, "NULL argument");
+  if (nx < 1 || ny < 1 || nz < 1 || nx > 4096 || ny > 4096 || nz > 4096)
+    return fail(SOPHIE_EINVAL, "grid sizes must be in [1, 4096]");
+  if (!(dx > 0) || !(dt > 0) || !std::isfinite(dx) || !std::isfinite(dt))
+    return fail(SOPHIE_EINVAL, "dx and dt must be finite and > 0");
+  if (nthreads < 1) return fail(SOPHIE_EINVAL, "nthreads must be >= 1");
+  const long long ncell = (long long)nx * ny * nz;
+  const long long c = first_bad_material(eps, sig, ncell, nthreads);
+  if (c >= 0) return fail(SOPHIE_EINVAL, "bad material at cell %lld", c);
+  Dims d{};
+  d.nx = nx;
+  d.ny = ny;
+  d.nz = nz;
+  d.nxp = ((nx + 1) + 7) / 8 * 8;
+  d.ny1 = ny + 1;
+  d.nz1 = nz + 1;
+  d.plane = (long long)d.ny1 * d.nxp;
+  d.zstride = 6 * d.plane;
+  MaterialTables t;
+  if (build_material_tables(d, dt, kC0 * dt / dx, eps, sig, words, &t, nthreads) != 0)
+    return fail(SOPHIE_ETOOMANYMAT, "more than 2^29 explicit material points");
+  for (int q = 0; q < kMaxClasses; ++q) {
+    const bool has = q < (int)t.coef.size();
+    class_coef[2 * q] = has ? t.coef[q].x : 0.f;
+    class_coef[2 * q + 1] = has ? t.coef[q].y : 0.f;
+    class_eps[q] = has ? t.eps[q] : 0.0;
+  }
+  const long long ne = (long long)t.eeps.size() / 3;
+  for (long long q = 0; q < std::min(ne, exp_cap) * 3; ++q) {
+    exp_coef[2 * q] = t.ecoef[q].x;
+    exp_coef[2 * q + 1] = t.ecoef[q].y;
+    exp_eps[q] = t.eeps[q];
+  }
+  *n_explicit = ne;
+  return SOPHIE_OK;
+}
+
 int sophie_debug_fail_alloc(int n) {
   if (n < 0) return fail(SOPHIE_EINVAL, "n must be >= 0");
   g_fail_alloc_at.store(n);

@@ -78,6 +78,8 @@ SIGNATURES = {
     "sophie_batch_check_guards": (_I, [_P, ctypes.POINTER(_LL)]),
     "sophie_selftest_wait_timeout": (_I, [_P, ctypes.POINTER(_D)]),
     "sophie_debug_fail_alloc": (_I, [_I]),
+    "sophie_debug_material_tables": (_I, [_I, _I, _I, _D, _D, _P, _P, _I, _P, _P, _P, _P, _P, _LL,
+                                          ctypes.POINTER(_LL)]),
     "sophie_last_error": (ctypes.c_char_p, []),
 }
 
@@ -397,6 +399,26 @@ def sophie_selftest_wait_timeout(g: int) -> float:
 
 def sophie_debug_fail_alloc(n: int) -> None:
     _chk(load().sophie_debug_fail_alloc(n))
+
+
+def sophie_debug_material_tables(eps, sig, dx: float, dt: float, nthreads: int = 1, exp_cap: int = 1 << 20):
+    """Host material build without a GPU: (words, class_coef, class_eps,
+    exp_coef, exp_eps) for per-cell eps_r / sigma of shape (nz, ny, nx)."""
+    eps = np.ascontiguousarray(eps, np.float32)
+    sig = np.ascontiguousarray(sig, np.float32)
+    nz, ny, nx = eps.shape
+    nxp = ((nx + 1) + 7) // 8 * 8
+    words = np.zeros((nz + 1, ny + 1, nxp), np.uint32)
+    ccoef = np.zeros((512, 2), np.float32)
+    ceps = np.zeros(512, np.float64)
+    ecoef = np.zeros((exp_cap, 3, 2), np.float32)
+    eeps = np.zeros((exp_cap, 3), np.float64)
+    n = _LL()
+    _chk(load().sophie_debug_material_tables(nx, ny, nz, dx, dt, eps.ctypes.data, sig.ctypes.data, nthreads,
+                                              words.ctypes.data, ccoef.ctypes.data, ceps.ctypes.data,
+                                              ecoef.ctypes.data, eeps.ctypes.data, exp_cap, ctypes.byref(n)))
+    k = min(n.value, exp_cap)
+    return words, ccoef, ceps, ecoef[:k], eeps[:k]
 
 
 # ---- batched cavities -------------------------------------------------------
