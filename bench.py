@@ -37,6 +37,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 N_CELLS_SIDE = 256
 T_STEPS = 1000
 FIELD_BYTES = 48   # read + write six float32 components per cell-update
+NOMINAL_HBM_GBS = 7900.0  # GB300 HBM3e, nominal (the measured copy bandwidth is the primary peak)
 MAT_BYTES = 4      # one 32-bit material word read per cell per launch
 # DRAM bytes (read + write) per launch from one ncu capture of each kernel on
 # this workload (profiles/*.md); None where the kernel changed since.
@@ -340,7 +341,7 @@ def run_ours(args):
             "traffic": NCU_TRAFFIC.get((kname, K if kid == so.KERNEL_BLOCKED else 1)), "kernel": kname,
             "steps_per_launch": K if kid == so.KERNEL_BLOCKED else 1, "avg_launch_ms": avg_ms,
             "peak_source": peak_kind, "algorithmic_bytes_per_launch": bytes_per_launch,
-            "kernel_share_of_timed_region": kms / ms}
+            "kernel_share_of_timed_region": kms / ms, "frac_of_nominal": achieved / NOMINAL_HBM_GBS}
 
     # the other step kernels on the same workload (fewer runs), for comparison
     variants = {"autotuned" if not args.k else f"k{K}": value}
@@ -368,6 +369,18 @@ def run_ours(args):
     variants["k2_zero_skip"] = cells * args.tsteps * nv * world / (vms / 1e3) / 1e9
     g.set_zero_skip(False)
     variants["speedup_vs_plain"] = {k: v / variants["k1"] for k, v in variants.items() if k != "speedup_vs_plain"}
+    # each form as a fraction of the HBM roof: its algorithmic bytes per
+    # cell-update (fields + material word, read and written once per launch of
+    # K steps: float and hi+lo 48 + 4, half and bfloat16 24 + 4, over K) times
+    # the rate, over the measured (and the nominal) copy bandwidth
+    variants_roof = {}
+    for name, rate in variants.items():
+        if name == "speedup_vs_plain":
+            continue
+        kk = K if name == "autotuned" else int(name.split("_")[0][1:]) if name[0] == "k" else int(name[-1])
+        per = (28.0 if name.startswith(("fp16_", "bf16_")) else 52.0) / kk
+        variants_roof[name] = {"bytes_per_cell_update": per, "frac": rate * per / peaks()[0],
+                               "frac_of_nominal": rate * per / NOMINAL_HBM_GBS}
     # the plain (one step per launch) kernel's own roofline on this workload
     plain_roof = {"kernel": "yee_plain", "gcell_per_s": variants["k1"],
                   "achieved_GBs_52B": variants["k1"] * (FIELD_BYTES + MAT_BYTES),
@@ -412,7 +425,8 @@ def run_ours(args):
                            "grid": [n, n, n], "time_steps_per_bench_step": args.tsteps,
                            "temporal_k": K, "autotuned": not args.k, "parallelism": f"replicas x{world}",
                            "l2": "inputs larger than L2 (no flush)"},
-                "roofline": roof, "plain_roofline": plain_roof, "variants_gcells": variants, "cpu_baseline": cpu, "e2e": e2e,
+                "roofline": roof, "plain_roofline": plain_roof, "variants_gcells": variants,
+                "variants_roofline": variants_roof, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": launches, "clocks": clocks, "energy_J": energy, "adjoint": adjoint,
                 "batch": batch, "precision_768": precision_768, "graded_mesh": graded}
         print(json.dumps(line), flush=True)
