@@ -168,6 +168,20 @@ def workload(n: int):
     return wl.sphere_cavity(n)
 
 
+def cpu_model() -> str:
+    """The host CPU as the OS reports it (model name, else implementer/part, else the architecture)."""
+    import platform
+    try:
+        info = open("/proc/cpuinfo").read().splitlines()
+        for key in ("model name", "CPU part"):
+            for line in info:
+                if line.startswith(key):
+                    return f"{platform.machine()} {key}: {line.split(':', 1)[1].strip()}"
+    except OSError:
+        pass
+    return platform.machine()
+
+
 def cpu_baseline(w, budget_s: float = 15.0):
     """Time the float32 oracle on the host cores on a bounded sample of the workload."""
     import oracle
@@ -192,7 +206,7 @@ def cpu_baseline(w, budget_s: float = 15.0):
     g.energy()
     cells = n ** 3
     out = {"value": cells * m / dt / 1e9, "unit": "Gcell-updates/s", "cores": nthreads,
-           "kind": "oracle",
+           "kind": "oracle", "cpu": cpu_model(), "cpu_count": os.cpu_count(),
            "sample": f"{n}^3 sphere cavity, float32 oracle, {m} time steps (of the {T_STEPS}-step run), "
                      f"OMP over z-planes, {dt:.1f} s"}
     # the same oracle on one core (a separate process, so that its OpenMP
@@ -255,6 +269,7 @@ def run_reference(args):
                                    f"source, 16 probes); {m} time steps per bench step",
                        "grid": [n, n, n], "time_steps_per_bench_step": m},
             "cpu_baseline": {"value": val, "unit": "Gcell-updates/s", "cores": nthreads, "kind": "oracle",
+                             "cpu": cpu_model(), "cpu_count": os.cpu_count(),
                              "sample": f"{m} time steps of the {n}^3 sphere cavity per bench step"},
             "e2e": {"value": val, "unit": "Gcell-updates/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
@@ -283,6 +298,8 @@ def run_ours(args):
     pids = [g.add_probe(*p) for p in w["probes"]]
     g_prec = [so.FP32]
 
+    step_ms = []  # per bench step of the last timed() call
+
     def timed(k, steps, warmup, profile):
         """Device time of `steps` whole runs (reset, tsteps steps, energy) at k steps per launch."""
         g.configure(temporal_k=k, precision=g_prec[0])
@@ -299,6 +316,7 @@ def run_ours(args):
         torch.cuda.synchronize()
         ev0.record(stream)
         energy = None
+        marks = []  # an event after each bench step: per-step times for best / median
         torch.cuda.nvtx.range_push("timed")  # lets ncu capture only timed launches (--nvtx-include timed/)
         for si in range(steps):
             if profile and si == steps - 1:
@@ -306,10 +324,17 @@ def run_ours(args):
             g.reset()
             g.step(args.tsteps)
             energy = g.energy()
+            marks.append(torch.cuda.Event(enable_timing=True))
+            marks[-1].record(stream)
         torch.cuda.nvtx.range_pop()
         ev1.record(stream)
         torch.cuda.synchronize()
         ms = ev0.elapsed_time(ev1)
+        step_ms.clear()
+        prev = ev0
+        for m in marks:
+            step_ms.append(prev.elapsed_time(m))
+            prev = m
         launches = g.launch_count() - l0
         prof = None
         if profile:
@@ -327,6 +352,9 @@ def run_ours(args):
     sampler.start()
     ms, launches, prof, energy = timed(0 if not args.k else K, args.steps, args.warmup, True)
     clocks = sampler.stop()
+    head_steps = sorted(step_ms)
+    bench_step_ms = {"best": head_steps[0], "median": head_steps[len(head_steps) // 2], "all": list(step_ms),
+                     "note": "device time of each bench step; the last one carries the per-launch events"}
     value = replica_rate(cells * args.tsteps * args.steps, world, ms)
 
     # dominant kernel of the timed region and its roofline
@@ -427,7 +455,7 @@ def run_ours(args):
                            "temporal_k": K, "autotuned": not args.k, "parallelism": f"replicas x{world}",
                            "l2": "inputs larger than L2 (no flush)"},
                 "roofline": roof, "plain_roofline": plain_roof, "variants_gcells": variants,
-                "variants_roofline": variants_roof, "cpu_baseline": cpu, "e2e": e2e,
+                "variants_roofline": variants_roof, "bench_step_ms": bench_step_ms, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": launches, "clocks": clocks, "energy_J": energy, "adjoint": adjoint,
                 "batch": batch, "precision_768": precision_768, "graded_mesh": graded}
         print(json.dumps(line), flush=True)
