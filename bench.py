@@ -38,9 +38,17 @@ N_CELLS_SIDE = 256
 T_STEPS = 1000
 FIELD_BYTES = 48   # read + write six float32 components per cell-update
 NOMINAL_HBM_GBS = 7900.0  # GB300 HBM3e, nominal (the measured copy bandwidth is the primary peak)
-MAT_BYTES = 4      # one 32-bit material word read per cell per launch
+# Algorithmic bytes per cell and launch: the six fields read and written once
+# plus a one-byte material identifier per cell (the method's minimum). The
+# kernels read a 4-byte material word per index point instead (three edge
+# classes and the source/probe flags), so they move 52 B; rooflines are
+# reported against the algorithmic 49 B, with the 52 B figure beside them.
+MAT_BYTES = 1
+LAYOUT_MAT_BYTES = 4
+ALG_BYTES = FIELD_BYTES + MAT_BYTES
+LAYOUT_BYTES = FIELD_BYTES + LAYOUT_MAT_BYTES
 # DRAM bytes (read + write) per launch from one ncu capture of each kernel on
-# this workload (profiles/*.md); None where the kernel changed since.
+# this workload (the kept ncu summaries); None where the kernel changed since.
 NCU_TRAFFIC = {("yee_blocked", 2): 521.599744e6 + 358.377472e6,
                ("yee_plain", 1): 505.030912e6 + 361.748480e6,
                ("yee_plain_nu", 1): 510.027264e6 + 364.156416e6,  # graded 256^3 cavity
@@ -360,15 +368,19 @@ def run_ours(args):
     # dominant kernel of the timed region and its roofline
     kid = max(prof, key=lambda k: prof[k][1])
     kl, kms = prof[kid]
-    bytes_per_launch = cells * (FIELD_BYTES + MAT_BYTES)
+    bytes_per_launch = cells * ALG_BYTES
     peak, peak_kind = peaks()
     avg_ms = kms / max(kl, 1)
     achieved = bytes_per_launch / (avg_ms / 1e3) / 1e9
+    achieved_layout = cells * LAYOUT_BYTES / (avg_ms / 1e3) / 1e9
     kname = {0: "yee_plain", 1: "yee_blocked", 2: "energy"}[kid]
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
             "traffic": NCU_TRAFFIC.get((kname, K if kid == so.KERNEL_BLOCKED else 1)), "kernel": kname,
             "steps_per_launch": K if kid == so.KERNEL_BLOCKED else 1, "avg_launch_ms": avg_ms,
             "peak_source": peak_kind, "algorithmic_bytes_per_launch": bytes_per_launch,
+            "algorithmic_bytes_per_cell": ALG_BYTES,
+            "layout_bytes_per_launch": cells * LAYOUT_BYTES, "achieved_layout": achieved_layout,
+            "frac_layout": achieved_layout / peak,
             "kernel_share_of_timed_region": kms / (ms / args.steps),  # of the profiled bench step
             "frac_of_nominal": achieved / NOMINAL_HBM_GBS}
 
@@ -399,21 +411,24 @@ def run_ours(args):
     g.set_zero_skip(False)
     variants["speedup_vs_plain"] = {k: v / variants["k1"] for k, v in variants.items() if k != "speedup_vs_plain"}
     # each form as a fraction of the HBM roof: its algorithmic bytes per
-    # cell-update (fields + material word, read and written once per launch of
-    # K steps: float and hi+lo 48 + 4, half and bfloat16 24 + 4, over K) times
-    # the rate, over the measured (and the nominal) copy bandwidth
+    # cell-update (fields read and written once per launch of K steps plus the
+    # one-byte material identifier: float and hi+lo 48 + 1, half and bfloat16
+    # 24 + 1, over K) times the rate, over the measured (and the nominal) copy
+    # bandwidth
     variants_roof = {}
     for name, rate in variants.items():
         if name == "speedup_vs_plain":
             continue
         kk = K if name == "autotuned" else int(name.split("_")[0][1:]) if name[0] == "k" else int(name[-1])
-        per = (28.0 if name.startswith(("fp16_", "bf16_")) else 52.0) / kk
+        per = (FIELD_BYTES // 2 + MAT_BYTES if name.startswith(("fp16_", "bf16_"))
+               else FIELD_BYTES * 3 // 4 + MAT_BYTES if name.startswith("fp24_") else ALG_BYTES) / kk
         variants_roof[name] = {"bytes_per_cell_update": per, "frac": rate * per / peaks()[0],
                                "frac_of_nominal": rate * per / NOMINAL_HBM_GBS}
     # the plain (one step per launch) kernel's own roofline on this workload
     plain_roof = {"kernel": "yee_plain", "gcell_per_s": variants["k1"],
-                  "achieved_GBs_52B": variants["k1"] * (FIELD_BYTES + MAT_BYTES),
-                  "frac_52B": variants["k1"] * (FIELD_BYTES + MAT_BYTES) / peaks()[0],
+                  "achieved_GBs_49B": variants["k1"] * ALG_BYTES,
+                  "frac_49B": variants["k1"] * ALG_BYTES / peaks()[0],
+                  "frac_52B_layout": variants["k1"] * LAYOUT_BYTES / peaks()[0],
                   "frac_48B_fields_only": variants["k1"] * FIELD_BYTES / peaks()[0],
                   "traffic": NCU_TRAFFIC.get(("yee_plain", 1)), "peak": peaks()[0], "unit": "GB/s"}
     g.configure(temporal_k=0 if not args.k else K, precision=so.FP32)
@@ -454,7 +469,9 @@ def run_ours(args):
                            "grid": [n, n, n], "time_steps_per_bench_step": args.tsteps,
                            "temporal_k": K, "autotuned": not args.k, "parallelism": f"replicas x{world}",
                            "l2": "inputs larger than L2 (no flush)"},
-                "roofline": roof, "plain_roofline": plain_roof, "variants_gcells": variants,
+                "roofline": roof, "plain_gcell_per_s": variants["k1"],
+                "blocked_over_plain": value / variants["k1"],
+                "plain_roofline": plain_roof, "variants_gcells": variants,
                 "variants_roofline": variants_roof, "bench_step_ms": bench_step_ms, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": launches, "clocks": clocks, "energy_J": energy, "adjoint": adjoint,
                 "batch": batch, "precision_768": precision_768, "graded_mesh": graded}
@@ -464,8 +481,13 @@ def run_ours(args):
 
 
 def run_e2e(args, g, w, pids, stream):
-    """Same metric through the public API with host buffers: upload the
-    materials from pinned host memory, run, read the probes and the energy."""
+    """Same metric through the public API with host buffers: every bench step
+    uploads its materials (the host builds the material words from eps/sigma
+    and copies them from pinned staging), runs, and reads the probes and the
+    energy back. The steps are pipelined the way a caller streaming many runs
+    would: the next step's set_materials (host build, then an upload queued on
+    the grid's stream behind the running steps) is issued before this step's
+    results are read, so the host build overlaps the device run."""
     import torch
     n = w["nx"]
     eps = torch.from_numpy(np.ascontiguousarray(w["eps"])).pin_memory().numpy()
@@ -473,10 +495,12 @@ def run_e2e(args, g, w, pids, stream):
     reps = max(1, min(args.steps, 3))
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    for _ in range(reps):
-        g.set_materials(eps, sig)
+    g.set_materials(eps, sig)
+    for r in range(reps):
         g.reset()
         g.step(args.tsteps)
+        if r + 1 < reps:
+            g.set_materials(eps, sig)  # the next step's inputs, uploaded after this run in stream order
         for p in pids:
             g.read_probe(p, args.tsteps)
         g.energy()
@@ -485,15 +509,16 @@ def run_e2e(args, g, w, pids, stream):
     npts = (n + 1) * (n + 1) * (((n + 1) + 7) // 8 * 8)
     return {"value": n ** 3 * args.tsteps * reps / dt / 1e9, "unit": "Gcell-updates/s",
             "h2d_bytes_per_step": npts * 4, "d2h_bytes_per_step": len(pids) * args.tsteps * 4 + 8,
-            "note": "material words built on the host from eps/sigma and uploaded each step"}
+            "note": "material words built on the host from eps/sigma and uploaded each step; the next "
+                    "step's host build overlaps the current run"}
 
 
 def run_adjoint(stream, reps: int = 3):
     """The differentiation form on its workload (128^3 design cavity, 800 steps,
     checkpoints every 50): wall time of one objective evaluation and of its
     gradient over the whole 32^3 design region, and the adjoint step kernel's
-    HBM roofline (52 algorithmic bytes per cell: 6 float adjoint fields read and
-    written, one material word)."""
+    HBM roofline (49 algorithmic bytes per cell: 6 float adjoint fields read and
+    written, one material identifier)."""
     import torch
     from paper_1301_4539_gb300 import sophie as so
     from paper_1301_4539_gb300 import workloads as wl
@@ -525,7 +550,7 @@ def run_adjoint(stream, reps: int = 3):
     peak, peak_kind = peaks()
     cells = n ** 3
     avg = ams / max(la, 1)
-    achieved = cells * (FIELD_BYTES + MAT_BYTES) / (avg / 1e3) / 1e9
+    achieved = cells * ALG_BYTES / (avg / 1e3) / 1e9
     t_f, t_r = float(np.median(fwd)), float(np.median(rev))
     return {"workload": f"{n}^3 vacuum PEC cavity, 32^3 design region eps_r U(1,4), Gaussian-pulse Ez "
                         f"source, {N} steps, checkpoints every 50, gradient over the 32^3 design cells",
@@ -539,7 +564,7 @@ def run_adjoint(stream, reps: int = 3):
             "forward_temporal_k": k_tuned}
 
 
-def run_precision_768(stream, tsteps: int = 200):
+def run_precision_768(stream, tsteps: int = 2000):
     """Throughput of the storage forms on the precision workload's grid: the
     768^3 sphere cavity (same generator, centre source, 16 probes), reset +
     `tsteps` steps per run, device time with CUDA events. Accuracy of the same
@@ -584,8 +609,8 @@ def run_graded(stream, uniform_k1: float, n: int = 256, tsteps: int = 1000, reps
     dt at the refined Courant limit), reset + `tsteps` steps per run, device
     time with CUDA events, autotuned (k = 0) or at a fixed k, and the plain
     kernel (k = 1) beside it. Roofline of the dominant kernel of each: the
-    same 52 B per cell and launch as on the uniform mesh (the ratio arrays are
-    a few KB, read from L1) over its event-timed launches."""
+    same 49 algorithmic bytes per cell and launch as on the uniform mesh (the
+    ratio arrays are a few KB, read from L1) over its event-timed launches."""
     import torch
     from paper_1301_4539_gb300 import sophie as so
     from paper_1301_4539_gb300 import workloads as wl
@@ -626,7 +651,7 @@ def run_graded(stream, uniform_k1: float, n: int = 256, tsteps: int = 1000, reps
         kid = max(prof, key=lambda q: prof[q][1])
         kl, kms = prof[kid]
         name = "yee_blocked (non-uniform)" if kid == so.KERNEL_BLOCKED else "yee_plain (non-uniform)"
-        achieved = n ** 3 * (FIELD_BYTES + MAT_BYTES) / (kms / max(kl, 1) / 1e3) / 1e9
+        achieved = n ** 3 * ALG_BYTES / (kms / max(kl, 1) / 1e3) / 1e9
         traffic = (NCU_TRAFFIC.get(("yee_plain_nu", 1)) if kid == so.KERNEL_PLAIN
                    else NCU_TRAFFIC.get(("yee_blocked_nu", kk)))
         return kk, n ** 3 * tsteps * reps / (ms / 1e3) / 1e9, energy, {
@@ -649,7 +674,7 @@ def run_batch(ncav: int = 4096, tsteps: int = 500):
     U{16..96}^3, eps_r U(1,12) per 4^3 block, one Gaussian-pulse Ez source
     each; one run = reset + 500 steps (one persistent launch per step,
     replayed from a CUDA graph) + the per-cavity energies. Device time of the
-    run with CUDA events on the batch's stream; the roofline uses the same 52
+    run with CUDA events on the batch's stream; the roofline uses the same 49
     algorithmic bytes per cell-update as the single grid."""
     import torch
     from paper_1301_4539_gb300 import sophie as so
@@ -688,7 +713,7 @@ def run_batch(ncav: int = 4096, tsteps: int = 500):
     b.close()
     rate = cells * tsteps / (ms / 1e3) / 1e9
     peak, peak_kind = peaks()
-    achieved = rate * (FIELD_BYTES + MAT_BYTES)
+    achieved = rate * ALG_BYTES
     return {"workload": f"{ncav} PEC cavities, sizes U{{16..96}}^3 (seed 1304), eps_r U(1,12) per 4^3 block, "
                         f"one Gaussian-pulse Ez source each, {tsteps} steps per run",
             "cells": cells, "value": rate, "unit": "Gcell-updates/s", "ms_per_run": ms,
@@ -698,7 +723,7 @@ def run_batch(ncav: int = 4096, tsteps: int = 500):
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "peak_source": peak_kind,
                          "traffic": BATCH_TRAFFIC_PER_CELL * cells,
-                         "note": "52 algorithmic bytes per cell-update; explicit coefficient reads not counted; "
+                         "note": "49 algorithmic bytes per cell-update; explicit coefficient reads not counted; "
                                  "traffic per launch scaled by cells from an ncu capture of a 300-cavity "
                                  "instance of the same generator"},
             "setup_s": setup_s, "energy_sum_J": float(np.sum(W))}

@@ -173,18 +173,23 @@ int sophie_energy(sophie_grid *g, double *W);
 
 /*
  * The energy of sophie_energy, for callers that cannot allocate device memory
- * when they ask for it: code that records the step loop into a CUDA graph
- * (cudaMalloc may not be called during stream capture) or a host that
- * reserves a fixed device-memory budget up front. The paper has no
- * counterpart; it is an interface convenience. W_dev is a caller-owned device
- * pointer that receives W (double, J). No memory is allocated: the reduction's
- * partial sums live in a static device array of 2432 doubles (19 KiB, held by
- * every device that loads the library until exit). The first call on a device
- * fetches that array's address (make it before any stream capture). Enqueued
- * on the grid's stream; does not synchronise and does not check finiteness.
- * Calls whose kernels overlap on the GPU (several grids or streams) race on
- * the shared array. Errors: EINVAL (NULL, or a grid needing more reduction
- * blocks than the array holds), ECUDA.
+ * when they ask for it: an application that reserves its whole device-memory
+ * budget up front (a caching allocator that owns the heap, or a host that
+ * forbids allocation once it runs), where a cudaMalloc would fail or is not
+ * allowed. The paper has no counterpart; it is an interface convenience.
+ * W_dev is a caller-owned device pointer that receives W (double, J). No
+ * memory is allocated: the reduction's partial sums live in a static device
+ * array of 2432 doubles (19 KiB, held by every device that loads the library
+ * until exit). That is the most any grid needs (the reduction's block count
+ * is capped at 2432 and a grid-stride loop covers larger grids), so no grid
+ * is rejected for its size. The first call on a device fetches the array's
+ * address (make it before any stream capture). Enqueued on the grid's
+ * stream; does not synchronise, does not check finiteness and does not read
+ * the device error word of earlier launches (a later synchronising call such
+ * as sophie_sync or sophie_energy reports a bounded wait that ran out); its
+ * launches are not included in the sophie_profile timings. Calls whose
+ * kernels overlap on the GPU (several grids or streams) race on the shared
+ * array. Errors: EINVAL (NULL), ECUDA.
  */
 int sophie_energy_noalloc(sophie_grid *g, double *W_dev);
 

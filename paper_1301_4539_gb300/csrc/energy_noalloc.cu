@@ -1,18 +1,21 @@
 // Discrete energy without any allocation (sophie_energy_noalloc).
 //
 // Some callers cannot allocate device memory at the point where they need
-// the energy: code that records the step loop into a CUDA graph (cudaMalloc
-// may not be called while a stream is being captured), or a host under a
-// fixed device-memory budget that reserves everything up front. This variant
-// of the energy reduction keeps its per-block partial sums in a file-scope
-// static device array instead of a buffer allocated at run time.
+// the energy: an application that reserves its whole device-memory budget up
+// front (a caching allocator that owns the heap, or an embedded host that
+// forbids allocation once it runs), where a cudaMalloc would fail or is not
+// allowed. This variant of the energy reduction keeps its per-block partial
+// sums in a file-scope static device array instead of a buffer allocated at
+// run time.
 //
-// The array is a host-side stand-in in host code: its device address is
-// fetched once per device, with that device current, by cudaGetSymbolAddress.
-// The first call on a device does that set-up, so it should come before any
-// stream capture. The array holds at most kMaxBlocks partial sums; every call
-// overwrites every slot it later reads, and calls that overlap on the GPU
-// race on it.
+// In host code the array's name is a host-side stand-in, not a device
+// address: its device address is fetched once per device, with that device
+// current, by cudaGetSymbolAddress. The first call on a device does that
+// set-up, so it should come before any stream capture. The array holds
+// kEnergyMaxBlocks partial sums, the most any grid's reduction uses (the
+// block count is capped there and a grid-stride loop covers larger grids),
+// so no grid is rejected for its size. Every call overwrites every slot it
+// later reads; calls that overlap on the GPU race on the array.
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -23,10 +26,10 @@ namespace sophie {
 
 namespace {
 
-constexpr int kMaxBlocks = 152 * 16;  // one double per reduction block: 19 KiB per device
 constexpr int kMaxDevices = 64;
 
-static __device__ __align__(256) double g_energy_partials[kMaxBlocks];
+// one double per reduction block: 19 KiB per device
+static __device__ __align__(256) double g_energy_partials[kEnergyMaxBlocks];
 
 std::mutex g_mu;
 double* g_addr[kMaxDevices] = {nullptr};
@@ -36,7 +39,7 @@ double* g_addr[kMaxDevices] = {nullptr};
 int energy_noalloc(const StepArgs& a, const double* eps_tab, double scale, double* W_dev, cudaStream_t s,
                    const char** why) {
   const int nblocks = energy_blocks(a.d);
-  if (nblocks > kMaxBlocks) {
+  if (nblocks > kEnergyMaxBlocks) {  // energy_blocks caps the count: never taken
     *why = "grid needs more reduction blocks than the static scratch holds";
     return -1;
   }

@@ -203,6 +203,10 @@ cudaError_t launch_step_blocked(const StepArgs& a, const CUtensorMap& tmF, const
                                 const BlockedTiling& t, cudaStream_t s);
 cudaError_t launch_energy(const StepArgs& a, const double* eps_tab, double* partials, int nblocks,
                           double* out, cudaStream_t s);
+// Reduction blocks of the energy kernels: one per 8 x 256 index points, at
+// most kEnergyMaxBlocks (a grid-stride loop covers larger grids), so every
+// grid needs at most kEnergyMaxBlocks partial sums.
+constexpr int kEnergyMaxBlocks = 152 * 16;
 int energy_blocks(const Dims& d);
 // Same reduction, final sum multiplied by `scale` and written to `out`.
 cudaError_t launch_energy_scaled(const StepArgs& a, const double* eps_tab, double* partials, int nblocks,

@@ -217,7 +217,7 @@ int energy_blocks(const Dims& d) {
   const long long npts = (long long)d.nz1 * d.ny1 * d.nxp;
   long long b = (npts + kEThreads * 8 - 1) / (kEThreads * 8);
   if (b < 1) b = 1;
-  if (b > 152 * 16) b = 152 * 16;
+  if (b > kEnergyMaxBlocks) b = kEnergyMaxBlocks;
   return (int)b;
 }
 

@@ -170,3 +170,56 @@ def test_batch_errors(sophie):
         b.set_materials(np.full(8 ** 3 + 9 ** 3, 0.5, np.float32))
     with pytest.raises(so.SophieError):
         so.sophie_batch_get_fields(b.h, 3, 0, (2, 2, 2))  # no cavity 3
+
+
+def _batch_sample_vs_oracle(oracle_mod, b, dims, eps_all, srcs, sample, nsteps):
+    """Cavities `sample` of batch b after nsteps steps, bitwise = FP32 oracle."""
+    offs = np.concatenate([[0], np.cumsum([int(x) * int(y) * int(z) for x, y, z in dims])])
+    for c in sample:
+        nx, ny, nz = (int(v) for v in dims[c])
+        o = oracle_mod.OracleGrid(nx, ny, nz, DX, wl.cfl_dt(DX), "f32")
+        e = eps_all[offs[c]:offs[c + 1]].reshape(nz, ny, nx)
+        o.set_materials(e, np.zeros_like(e))
+        for s in srcs:
+            if s[0] == c:
+                o.add_source(*s[1:])
+        o.step(nsteps)
+        for comp in range(6):
+            got = b.get_field(c, comp)
+            bad = np.argwhere(got != o.f[comp])
+            assert bad.size == 0, (f"cavity {c} {dims[c]} comp {comp}", bad[:4])
+
+
+def test_full_size_work_list_equals_oracle(oracle_mod, sophie):
+    """The batching workload's generator (sizes U{16..96} per axis, eps_r per
+    4^3 block, one Gaussian-pulse source each) at 512 cavities: thousands of
+    work items, many times the persistent CTAs (2 per SM), so every CTA walks
+    many units -- the unit context double-buffered by parity, the cross-unit
+    prefetch of explicit coefficients and the tuned z chunks all run. A seeded
+    sample of 16 cavities, with the largest and the smallest, is compared with
+    the float oracle bit for bit after 60 steps replayed from a CUDA graph,
+    once with the autotuned split and once with 32-plane z chunks."""
+    import torch
+    dims, eps, srcs = wl.batch_cavities(ncav=512, seed=1304)
+    vol = dims.prod(axis=1)
+    rng = np.random.default_rng(1314)
+    sample = sorted(set([int(vol.argmax()), int(vol.argmin())]) |
+                    set(int(c) for c in rng.choice(len(dims), 14, replace=False)))
+    assert len(sample) >= 16
+    b = so.Batch(dims, DX, wl.cfl_dt(DX))
+    b.set_materials(eps)
+    for s in srcs:
+        b.add_source(*s)
+    nsm = torch.cuda.get_device_properties(0).multi_processor_count
+    tx, ty, zc, _ = b.autotune()
+    for cfg in ((tx, ty, zc), (64, 16, 32)):
+        b.configure(tile_x=cfg[0], tile_y=cfg[1], zchunk=cfg[2], use_graph=True)
+        info = b.info()
+        assert info["work_items"] > 4 * 2 * nsm, info
+        b.reset()
+        b.step(60)  # recorded into a graph
+        b.reset()
+        b.step(60)  # replay of the recorded graph
+        assert b.n == 60
+        _batch_sample_vs_oracle(oracle_mod, b, dims, eps, srcs, sample, 60)
+    b.close()

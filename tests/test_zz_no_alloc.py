@@ -1,9 +1,10 @@
 """sophie_energy_noalloc: the energy for callers that cannot allocate.
 
-Code that records the step loop into a CUDA graph cannot call cudaMalloc
-while the stream is being captured, and some hosts reserve all device memory
-up front; this entry point serves them by keeping its reduction scratch in a
-static device array instead of allocating. Here it is called through the C ABI
+Some applications reserve their whole device-memory budget up front (a
+caching allocator that owns the heap, or a host that forbids allocation once
+it runs), so a cudaMalloc at the point where they need the energy fails or is
+not allowed; this entry point serves them by keeping its reduction scratch in
+a static device array instead of allocating. Here it is called through the C ABI
 and must give the same energy as sophie_energy (the allocating entry point),
 within the 1e-12 relative tolerance the energy tests use, on two calls in a
 row (the static scratch keeps the previous call's contents), on a uniform and
