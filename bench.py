@@ -46,6 +46,8 @@ NOMINAL_HBM_GBS = 7900.0  # GB300 HBM3e, nominal (the measured copy bandwidth is
 MAT_BYTES = 1
 LAYOUT_MAT_BYTES = 4
 ALG_BYTES = FIELD_BYTES + MAT_BYTES
+# Field bytes per cell-update (six values read and written) of each storage form.
+STORAGE_FIELD_BYTES = {"fp32": 48, "fp16": 24, "bf16": 24, "fp16hl": 48, "fp24": 36}
 LAYOUT_BYTES = FIELD_BYTES + LAYOUT_MAT_BYTES
 # DRAM bytes (read + write) per launch from one ncu capture of each kernel on
 # this workload (the kept ncu summaries); None where the kernel changed since.
@@ -75,6 +77,8 @@ def parse():
     p.add_argument("--no-graded", action="store_true")
     p.add_argument("--graded-tsteps", type=int, default=1000, help="time steps per run of the graded-mesh workload")
     p.add_argument("--batch-cavities", type=int, default=4096)
+    p.add_argument("--precision", default="fp32", choices=list(STORAGE_FIELD_BYTES),
+                   help="field storage of the timed runs (arithmetic is float in every form)")
     return p.parse_args()
 
 
@@ -304,7 +308,11 @@ def run_ours(args):
     for s in w["sources"]:
         g.add_source(*s)
     pids = [g.add_probe(*p) for p in w["probes"]]
-    g_prec = [so.FP32]
+    storage = {"fp32": so.FP32, "fp16": so.FP16, "bf16": so.BF16, "fp16hl": so.FP16HL, "fp24": so.FP24}
+    g_prec = [storage[args.precision]]
+    if args.precision in ("fp16", "fp16hl"):
+        g.configure(temporal_k=1, precision=g_prec[0])
+        g.set_storage_scale([2.0 ** 10] * 6)
 
     step_ms = []  # per bench step of the last timed() call
 
@@ -368,18 +376,21 @@ def run_ours(args):
     # dominant kernel of the timed region and its roofline
     kid = max(prof, key=lambda k: prof[k][1])
     kl, kms = prof[kid]
-    bytes_per_launch = cells * ALG_BYTES
+    alg_bytes = STORAGE_FIELD_BYTES[args.precision] + MAT_BYTES
+    bytes_per_launch = cells * alg_bytes
     peak, peak_kind = peaks()
     avg_ms = kms / max(kl, 1)
     achieved = bytes_per_launch / (avg_ms / 1e3) / 1e9
-    achieved_layout = cells * LAYOUT_BYTES / (avg_ms / 1e3) / 1e9
+    layout_bytes = STORAGE_FIELD_BYTES[args.precision] + LAYOUT_MAT_BYTES
+    achieved_layout = cells * layout_bytes / (avg_ms / 1e3) / 1e9
     kname = {0: "yee_plain", 1: "yee_blocked", 2: "energy"}[kid]
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": NCU_TRAFFIC.get((kname, K if kid == so.KERNEL_BLOCKED else 1)), "kernel": kname,
+            "traffic": NCU_TRAFFIC.get((kname, K if kid == so.KERNEL_BLOCKED else 1)) if args.precision == "fp32"
+            else None, "kernel": kname,
             "steps_per_launch": K if kid == so.KERNEL_BLOCKED else 1, "avg_launch_ms": avg_ms,
             "peak_source": peak_kind, "algorithmic_bytes_per_launch": bytes_per_launch,
-            "algorithmic_bytes_per_cell": ALG_BYTES,
-            "layout_bytes_per_launch": cells * LAYOUT_BYTES, "achieved_layout": achieved_layout,
+            "algorithmic_bytes_per_cell": alg_bytes,
+            "layout_bytes_per_launch": cells * layout_bytes, "achieved_layout": achieved_layout,
             "frac_layout": achieved_layout / peak,
             "kernel_share_of_timed_region": kms / (ms / args.steps),  # of the profiled bench step
             "frac_of_nominal": achieved / NOMINAL_HBM_GBS}
@@ -392,8 +403,8 @@ def run_ours(args):
             continue
         vms, _, _, _ = timed(kk, nv, 1, False)
         variants[f"k{kk}"] = cells * args.tsteps * nv * world / (vms / 1e3) / 1e9
-    # storage-precision forms (float arithmetic, 2-byte fields in HBM)
-    for pname, prec in (("fp16", so.FP16), ("bf16", so.BF16), ("fp16hl", so.FP16HL)):
+    # storage-precision forms (float arithmetic; 2-, 3- or 4-byte values in HBM)
+    for pname, prec in (("fp16", so.FP16), ("bf16", so.BF16), ("fp16hl", so.FP16HL), ("fp24", so.FP24)):
         g.configure(temporal_k=1, precision=prec)
         g_prec[0] = prec
         if prec in (so.FP16, so.FP16HL):
@@ -412,9 +423,9 @@ def run_ours(args):
     variants["speedup_vs_plain"] = {k: v / variants["k1"] for k, v in variants.items() if k != "speedup_vs_plain"}
     # each form as a fraction of the HBM roof: its algorithmic bytes per
     # cell-update (fields read and written once per launch of K steps plus the
-    # one-byte material identifier: float and hi+lo 48 + 1, half and bfloat16
-    # 24 + 1, over K) times the rate, over the measured (and the nominal) copy
-    # bandwidth
+    # one-byte material identifier: float and hi+lo 48 + 1, 24-bit 36 + 1,
+    # half and bfloat16 24 + 1, over K) times the rate, over the measured (and
+    # the nominal) copy bandwidth
     variants_roof = {}
     for name, rate in variants.items():
         if name == "speedup_vs_plain":
@@ -431,6 +442,7 @@ def run_ours(args):
                   "frac_52B_layout": variants["k1"] * LAYOUT_BYTES / peaks()[0],
                   "frac_48B_fields_only": variants["k1"] * FIELD_BYTES / peaks()[0],
                   "traffic": NCU_TRAFFIC.get(("yee_plain", 1)), "peak": peaks()[0], "unit": "GB/s"}
+    g_prec[0] = so.FP32
     g.configure(temporal_k=0 if not args.k else K, precision=so.FP32)
     if not args.k:
         g.autotune()
@@ -468,6 +480,7 @@ def run_ours(args):
                                        f"source, 16 probes), {args.tsteps} time steps per bench step",
                            "grid": [n, n, n], "time_steps_per_bench_step": args.tsteps,
                            "temporal_k": K, "autotuned": not args.k, "parallelism": f"replicas x{world}",
+                           "storage": args.precision,
                            "l2": "inputs larger than L2 (no flush)"},
                 "roofline": roof, "plain_gcell_per_s": variants["k1"],
                 "blocked_over_plain": value / variants["k1"],
@@ -583,7 +596,7 @@ def run_precision_768(stream, tsteps: int = 2000):
     out = {"workload": f"{n}^3 PEC sphere cavity (64 lossy spheres, centre Ez source, 16 probes), "
                        f"{tsteps} steps per run", "unit": "Gcell-updates/s"}
     for name, prec, k in (("fp32_autotuned", so.FP32, 0), ("fp32_k1", so.FP32, 1), ("fp16_k2", so.FP16, 2),
-                          ("bf16_k2", so.BF16, 2), ("fp16hl_k2", so.FP16HL, 2)):
+                          ("bf16_k2", so.BF16, 2), ("fp16hl_k2", so.FP16HL, 2), ("fp24_k2", so.FP24, 2)):
         g.configure(temporal_k=k, precision=prec)
         g.set_storage_scale([2.0 ** 10 if prec in (so.FP16, so.FP16HL) else 1.0] * 6)
         if k == 0:

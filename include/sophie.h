@@ -76,6 +76,7 @@ extern "C" {
 #define SOPHIE_FP16 1
 #define SOPHIE_BF16 2
 #define SOPHIE_FP16HL 3  /* hi + lo pair of halves per value (4 B), see sophie_configure */
+#define SOPHIE_FP24 4    /* upper 24 bits of the float (3 B), see sophie_configure */
 
 /* Kernel ids for sophie_profile_read. */
 #define SOPHIE_KERNEL_PLAIN   0  /* one fused H+E step per launch           */
@@ -227,7 +228,14 @@ int sophie_sync(sophie_grid *g);
  * precision: SOPHIE_FP32, SOPHIE_FP16 or SOPHIE_BF16 storage of the fields,
  * or SOPHIE_FP16HL: each value v = field * scale kept as two halves
  * hi = half(v), lo = half(v - hi) (4 B, ~22 significant bits; the split
- * storage that wins back the accuracy half storage loses). A change converts
+ * storage that wins back the accuracy half storage loses), or SOPHIE_FP24:
+ * the upper 24 bits of each float (sign, the full 8-bit exponent, 15 mantissa
+ * bits; 3 B per value, no scale), the value first rounded to 16 significant
+ * bits by Veltkamp's splitting c = v * 257, hi = c + (v - c) in float
+ * arithmetic (a rounding to nearest; for subnormal values the dropped low
+ * byte is truncated). The device layout per z slab is then nine 2-byte
+ * planes: the high halves of ex, ey, ez, hx, hy, hz and the byte pairs of
+ * (ex, ey), (ez, hx), (hy, hz). A change converts
  * the current fields; synchronises. In the non-float modes one launch loads
  * the stored fields, computes its k steps in float and rounds once when
  * storing, so results depend on k (no longer bitwise equal across k).

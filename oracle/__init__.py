@@ -12,5 +12,6 @@ from .oracle import (  # noqa: F401
     build,
     cfl_dt,
     load,
+    round24,
     waveform,
 )

@@ -72,6 +72,8 @@ def load() -> ctypes.CDLL:
             lib.oracle_grad_f64.restype = D
             lib.oracle_waveform.argtypes = [I, D, D, D, D, D, L, L, P]
             lib.oracle_waveform.restype = None
+            lib.oracle_round24_f32.argtypes = [P, L]
+            lib.oracle_round24_f32.restype = None
             _lib = lib
     return _lib
 
@@ -91,6 +93,15 @@ def waveform(kind: int, amp: float, f0: float, bw: float, t0: float, dt: float,
     """amp * w((n0 + m + 1/2) dt) for m in [0, n), in float64."""
     out = np.empty(n, np.float64)
     load().oracle_waveform(int(kind), amp, f0, bw, t0, dt, int(n0), int(n), _ptr(out))
+    return out
+
+
+def round24(a: np.ndarray) -> np.ndarray:
+    """The 24-bit storage form of a float32 array (yee_oracle.c,
+    oracle_round24_f32): each value rounded to 16 significant bits by
+    Veltkamp's splitting, then the low 8 bits of its pattern dropped."""
+    out = np.ascontiguousarray(a, np.float32).copy()
+    load().oracle_round24_f32(_ptr(out), out.size)
     return out
 
 
@@ -191,6 +202,25 @@ class OracleGrid:
         for q in range(nprb):
             self.probe_trace[q].extend(pout[q].astype(np.float64).tolist())
         self.n += nsteps
+
+    def round_fields24(self) -> None:
+        """Store every field value in the 24-bit form (float32 grids)."""
+        assert self.precision == "f32"
+        for a in self.f:
+            load().oracle_round24_f32(_ptr(a), a.size)
+
+    def step_stored24(self, nsteps: int, k: int) -> None:
+        """nsteps steps with the fields held in the 24-bit form between
+        launches: launches of k steps while k steps remain, then single steps,
+        each launch computing in float and storing once at its end (the
+        library's launch sequence for sophie_step(nsteps) at temporal_k = k).
+        Probe samples are the unrounded values of every step."""
+        m = 0
+        while m < nsteps:
+            adv = k if (k >= 2 and nsteps - m >= k) else 1
+            self.step(adv)
+            self.round_fields24()
+            m += adv
 
     def _source_table(self, nsteps: int):
         nsrc = len(self.sources)

@@ -21,6 +21,8 @@
  */
 #include <math.h>
 #include <stddef.h>
+#include <stdint.h>
+#include <string.h>
 
 #define C0 299792458.0
 #define EPS0 8.8541878128e-12
@@ -59,6 +61,33 @@ void oracle_waveform(int kind, double amp, double f0, double bw, double t0, doub
         const double u = t - t0;
         const double env = exp(-(u * u) / (2.0 * st * st));
         out[m] = amp * (kind == 0 ? sin(2.0 * pi * f0 * u) * env : env);
+    }
+}
+
+/*
+ * The 24-bit storage form of the precision study (not in the paper; the
+ * north-star's reduced-storage form): every stored field value keeps the upper
+ * 24 bits of its float (sign, exponent, 15 mantissa bits). A value v is first
+ * rounded to 16 significant bits by Veltkamp's splitting (Dekker, "A
+ * floating-point technique for extending the available precision", 1971):
+ * with sigma = 2^8 + 1, c = sigma * v, hi = c + (v - c), three float
+ * operations each rounded to nearest (this file is compiled without
+ * contraction), which leaves hi with at most 24 - 8 = 16 significant bits;
+ * the low 8 bits of hi's pattern, zero for normal values, are then dropped
+ * (for subnormal values the split is not exact and the drop truncates).
+ * Rounds a[0..n) in place.
+ */
+void oracle_round24_f32(float *a, long n)
+{
+    for (long i = 0; i < n; ++i) {
+        const float v = a[i];
+        const float c = 257.0f * v;
+        const float d = v - c;
+        const float hi = c + d;
+        uint32_t u;
+        memcpy(&u, &hi, 4);
+        u &= 0xFFFFFF00u;
+        memcpy(&a[i], &u, 4);
     }
 }
 

@@ -42,7 +42,10 @@ def build(force: bool = False, verbose: bool = False, extra: list[str] | None = 
     if not force and not extra and os.path.exists(LIB) and os.path.getmtime(LIB) >= newest:
         return LIB
     os.makedirs(BUILD, exist_ok=True)
+    # host code: no contraction of a*b+c into fused multiply-adds, so that host
+    # float arithmetic (storage conversions) rounds the same on every machine
     flags = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
+                    "-Xcompiler", "-ffp-contract=off",
                     "-I", os.path.join(ROOT, "include"), "--expt-relaxed-constexpr"] + (extra or [])
     if verbose:
         flags += ["-Xptxas", "-v"]

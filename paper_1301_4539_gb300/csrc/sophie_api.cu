@@ -404,12 +404,15 @@ void free_grid(sophie_grid* g) {
   delete g;
 }
 
+// Copy plane `comp` of every z slab (elements of g->esz bytes; for the 24-bit
+// format planes 0..5 are the high halves, 6..8 the byte pairs).
 int copy_component(sophie_grid* g, int comp, void* host, bool to_device, int buf) {
   const Dims& d = g->d;
   cudaMemcpy3DParms p{};
   const size_t es = (size_t)g->esz;
+  const size_t planes = (size_t)(d.zstride / d.plane);
   cudaPitchedPtr dev = make_cudaPitchedPtr(static_cast<unsigned char*>(g->F[buf]) + (size_t)comp * d.plane * es,
-                                           (size_t)d.nxp * es, (size_t)d.nx + 1, (size_t)6 * d.ny1);
+                                           (size_t)d.nxp * es, (size_t)d.nx + 1, planes * d.ny1);
   cudaPitchedPtr hst = make_cudaPitchedPtr(host, (size_t)(d.nx + 1) * es, (size_t)d.nx + 1, (size_t)d.ny1);
   p.extent = make_cudaExtent((size_t)(d.nx + 1) * es, (size_t)d.ny1, (size_t)d.nz1);
   if (to_device) {
@@ -432,6 +435,25 @@ bool encode_all_maps(sophie_grid* g) {
          encode_maps(d, g->fmt, g->F[1], nullptr, bxp, plain_box_y(), &g->tmF[1], nullptr) &&
          encode_maps(d, g->fmt, g->F[0], g->mat, bxb, blocked_box_y(), &g->tmFB[0], &g->tmMB) &&
          encode_maps(d, g->fmt, g->F[1], nullptr, bxb, blocked_box_y(), &g->tmFB[1], nullptr);
+}
+
+// The 24-bit format's rounding (yee_store.cuh, Store<kF24>): Veltkamp's split
+// into 16 significant bits, three float operations in round-to-nearest (host
+// code is compiled without contraction), then the low byte dropped.
+uint32_t f24_bits(float v) {
+  const float c = v * 257.f;
+  const float dlt = v - c;
+  const float hi = c + dlt;
+  uint32_t u;
+  memcpy(&u, &hi, 4);
+  return u & 0xFFFFFF00u;
+}
+
+float f24_value(uint32_t hi16, uint32_t lo8) {
+  const uint32_t u = (hi16 << 16) | (lo8 << 8);
+  float v;
+  memcpy(&v, &u, 4);
+  return v;
 }
 
 // float <-> stored value (host side), stored = field * scale, round to nearest even.
@@ -471,9 +493,53 @@ void from_store(int fmt, float scale, const void* in, float* out, size_t n) {
   }
 }
 
+// 24-bit storage: the component's high halves (plane comp) and its byte of the
+// byte-pair plane 6 + comp/2, read-modify-written so that the other
+// component's bytes are kept.
+int set_component_f24(sophie_grid* g, int comp, const float* host) {
+  const Dims& d = g->d;
+  const size_t n = (size_t)(d.nx + 1) * d.ny1 * d.nz1;
+  std::vector<uint16_t> hi(n), lo(n);
+  const int sh = (comp & 1) * 8;
+  for (int b = 0; b < 2; ++b) {
+    int rc = copy_component(g, 6 + comp / 2, lo.data(), false, b);
+    if (rc) return rc;
+    CUDA_TRY(cudaStreamSynchronize(g->stream));
+    for (size_t i = 0; i < n; ++i) {
+      const uint32_t u = f24_bits(host[i]);
+      hi[i] = (uint16_t)(u >> 16);
+      lo[i] = (uint16_t)((lo[i] & ~(0xFFu << sh)) | (((u >> 8) & 0xFFu) << sh));
+    }
+    rc = copy_component(g, comp, hi.data(), true, b);
+    if (rc) return rc;
+    rc = copy_component(g, 6 + comp / 2, lo.data(), true, b);
+    if (rc) return rc;
+    cudaError_t e = launch_mask_component(g->F[b], g->esz, g->d, comp, g->stream, g->fmt);
+    if (e != cudaSuccess) return fail(SOPHIE_ECUDA, "mask launch failed: %s", cudaGetErrorString(e));
+    g->launches++;
+    CUDA_TRY(cudaStreamSynchronize(g->stream));  // the host arrays are reused
+  }
+  return SOPHIE_OK;
+}
+
+int get_component_f24(sophie_grid* g, int comp, float* host) {
+  const Dims& d = g->d;
+  const size_t n = (size_t)(d.nx + 1) * d.ny1 * d.nz1;
+  std::vector<uint16_t> hi(n), lo(n);
+  int rc = copy_component(g, comp, hi.data(), false, g->cur);
+  if (rc) return rc;
+  rc = copy_component(g, 6 + comp / 2, lo.data(), false, g->cur);
+  if (rc) return rc;
+  CUDA_TRY(cudaStreamSynchronize(g->stream));
+  const int sh = (comp & 1) * 8;
+  for (size_t i = 0; i < n; ++i) host[i] = f24_value(hi[i], (lo[i] >> sh) & 0xFFu);
+  return SOPHIE_OK;
+}
+
 int set_component(sophie_grid* g, int comp, const float* host) {
   g->gen++;
   g->box_all = true;  // caller's fields: nothing is known to be zero
+  if (g->fmt == kF24) return set_component_f24(g, comp, host);
   const Dims& d = g->d;
   const size_t n = (size_t)(d.nx + 1) * d.ny1 * d.nz1;
   std::vector<unsigned char> tmp;
@@ -486,7 +552,7 @@ int set_component(sophie_grid* g, int comp, const float* host) {
   for (int b = 0; b < 2; ++b) {
     int rc = copy_component(g, comp, const_cast<void*>(src), true, b);
     if (rc) return rc;
-    cudaError_t e = launch_mask_component(g->F[b], g->esz, g->d, comp, g->stream);
+    cudaError_t e = launch_mask_component(g->F[b], g->esz, g->d, comp, g->stream, g->fmt);
     if (e != cudaSuccess) return fail(SOPHIE_ECUDA, "mask launch failed: %s", cudaGetErrorString(e));
     g->launches++;
   }
@@ -498,6 +564,7 @@ int get_component(sophie_grid* g, int comp, float* host) {
   const Dims& d = g->d;
   const size_t n = (size_t)(d.nx + 1) * d.ny1 * d.nz1;
   if (g->fmt == kF32) return copy_component(g, comp, host, false, g->cur);
+  if (g->fmt == kF24) return get_component_f24(g, comp, host);
   std::vector<unsigned char> tmp(n * g->esz);
   int rc = copy_component(g, comp, tmp.data(), false, g->cur);
   if (rc) return rc;
@@ -517,9 +584,11 @@ int restore_fields(sophie_grid* g, int fmt, const float* sc) {
   }
   CUDA_TRY(cudaStreamSynchronize(g->stream));
   const int esz = store_bytes(fmt);
-  if (esz != g->esz) {
-    const size_t bytes = (size_t)d.zstride * d.nz1 * esz;
-    const size_t guard = field_guard(d, esz);
+  Dims nd = d;
+  nd.zstride = (long long)store_planes(fmt) * d.plane;
+  if (esz != g->esz || nd.zstride != d.zstride) {
+    const size_t bytes = (size_t)nd.zstride * nd.nz1 * esz;
+    const size_t guard = field_guard(nd, esz);
     void* nb[2] = {nullptr, nullptr};
     void* nbase[2] = {nullptr, nullptr};
     for (int b = 0; b < 2; ++b) {
@@ -538,6 +607,7 @@ int restore_fields(sophie_grid* g, int fmt, const float* sc) {
     }
     g->fguard = guard;
     g->esz = esz;
+    g->d.zstride = nd.zstride;
   }
   g->fmt = fmt;
   for (int c = 0; c < 6; ++c) g->sc[c] = sc[c];
@@ -632,7 +702,12 @@ int run_autotune(sophie_grid* g, double* best_ms_per_step) {
     // twice it, and the contiguous split
     std::vector<BlockedTiling> cands;
     const BlockedTiling model = blocked_tiling(d, K, g->num_sms, 1);
-    if (aenv) {
+    const char* zsenv = getenv("SOPHIE_BLOCKED_ZSPLIT");
+    if (zsenv && atoi(zsenv) > 0) {
+      // a fixed number of z ranges in both unit orders (tuning knob)
+      for (int order = 0; order < 2; ++order)
+        cands.push_back(blocked_tiling_split(d, K, g->num_sms, atoi(zsenv), order));
+    } else if (aenv) {
       const int mode = atoi(aenv);
       cands.push_back(blocked_tiling(d, K, g->num_sms, mode >= 0 && mode <= 3 ? mode : 1));
     } else {
@@ -642,6 +717,25 @@ int run_autotune(sophie_grid* g, double* best_ms_per_step) {
         if (zs >= 1 && zs <= d.nz)
           for (int order = 0; order < 2; ++order) cands.push_back(blocked_tiling_split(d, K, g->num_sms, zs, order));
       cands.push_back(blocked_tiling(d, K, g->num_sms, 0));
+    }
+    // K = 2 also runs with 16 warps of 2 rows per thread (Lay<2> in the
+    // blocked kernel): every split in both thread layouts
+    const char* renv = getenv("SOPHIE_BLOCKED_ROWS");
+    const int rows_fix = renv ? atoi(renv) : 0;
+    if (K == 2) {
+      const size_t nc = cands.size();
+      for (size_t q = 0; q < nc; ++q) {
+        cands[q].rows = 4;
+        BlockedTiling b2 = cands[q];
+        b2.rows = 2;
+        cands.push_back(b2);
+      }
+    }
+    if (rows_fix == 2 || rows_fix == 4) {
+      std::vector<BlockedTiling> keep;
+      for (const BlockedTiling& bt : cands)
+        if ((bt.rows == 2 ? 2 : 4) == rows_fix) keep.push_back(bt);
+      if (!keep.empty()) cands = keep;
     }
     for (const BlockedTiling& bt : cands) {
       const double ms = time_candidate(
@@ -1030,6 +1124,7 @@ int sophie_step(sophie_grid* g, int n) {
       box_grown(g, adv_steps, a.box);
       if (blocked) {
         bt_sub = blocked_tiling_box(g->d, K, g->num_sms, a.box);
+        bt_sub.rows = g->btile.K == K ? g->btile.rows : 0;  // the tuned thread layout
         none = bt_sub.grid == 0;
       } else {
         pt_sub = plain_tiling_box(g->d, g->num_sms, a.box);
@@ -1104,8 +1199,19 @@ int sophie_read_probe(sophie_grid* g, int probe_id, double* out, int cap, int* n
     unsigned char raw[4] = {0, 0, 0, 0};
     CUDA_TRY(cudaMemcpyAsync(raw, static_cast<unsigned char*>(g->F[g->cur]) + off * g->esz, g->esz,
                              cudaMemcpyDeviceToHost, g->stream));
+    if (g->fmt == kF24) {  // the component's byte of its byte-pair plane
+      const long long lo = off + (long long)(6 + pr.comp / 2 - pr.comp) * d.plane;
+      CUDA_TRY(cudaMemcpyAsync(raw + 2, static_cast<unsigned char*>(g->F[g->cur]) + lo * 2 + (pr.comp & 1), 1,
+                               cudaMemcpyDeviceToHost, g->stream));
+    }
     CUDA_TRY(cudaStreamSynchronize(g->stream));
-    from_store(g->fmt, g->sc[pr.comp], raw, &fixed_v, 1);
+    if (g->fmt == kF24) {
+      uint16_t h;
+      memcpy(&h, raw, 2);
+      fixed_v = f24_value(h, raw[2]);
+    } else {
+      from_store(g->fmt, g->sc[pr.comp], raw, &fixed_v, 1);
+    }
   } else if (m > 0) {
     CUDA_TRY(cudaMemcpyAsync(tmp.data(), g->pbuf + (size_t)probe_id * g->pcap, (size_t)m * 4,
                              cudaMemcpyDeviceToHost, g->stream));
@@ -1219,7 +1325,7 @@ int sophie_configure(sophie_grid* g, int temporal_k, int tile_x, int tile_y, int
     return fail(SOPHIE_ENOTSUP, "temporal_k = %d not built (supported: 1..4)", temporal_k);
   if (tile_x < 0 || tile_y < 0) return fail(SOPHIE_EINVAL, "tile sizes must be >= 0");
   if (tile_x != 0 && tile_x != 32 && tile_x != 64) return fail(SOPHIE_EINVAL, "tile_x must be 0, 32 or 64");
-  if (precision < SOPHIE_FP32 || precision > SOPHIE_FP16HL)
+  if (precision < SOPHIE_FP32 || precision > SOPHIE_FP24)
     return fail(SOPHIE_ENOTSUP, "precision %d not supported", precision);
   if (tile_x == 32 && precision != SOPHIE_FP32)
     return fail(SOPHIE_ENOTSUP, "the 32x8 reference kernel stores float only");

@@ -53,7 +53,7 @@ struct Dims {
   int nx, ny, nz;   // cells
   int nxp, ny1, nz1;  // storage extents (nxp padded)
   long long plane;  // ny1*nxp: elements of one component plane
-  long long zstride;  // 6*plane: elements of one z slab of all six components
+  long long zstride;  // elements of one z slab: 6*plane (9*plane for the 24-bit storage format)
 };
 
 // Source and probe tables passed by value to the step kernels.
@@ -142,6 +142,8 @@ struct BlockedTiling {
   int zsplit;
   int order;
   int tx0, ty0, zlo, zhi;  // the tiles start at tile (tx0, ty0); output planes [zlo, zhi)
+  // Rows of the 64 x 32 region per thread: 4 (8 warps; also 0) or 2 (16 warps).
+  int rows;
 };
 
 // Coefficient tables behind the material words (host copies). Class c:
@@ -214,7 +216,9 @@ cudaError_t launch_energy_scaled(const StepArgs& a, const double* eps_tab, doubl
 // Energy with partial sums in a fixed static device buffer (energy_noalloc.cu).
 int energy_noalloc(const StepArgs& a, const double* eps_tab, double scale, double* W_dev, cudaStream_t s,
                    const char** why);
-cudaError_t launch_mask_component(void* f, int esz, const Dims& d, int comp, cudaStream_t s);
+// fmt: the buffer's storage format (yee_store.cuh); kF24 also clears the
+// component's byte of its byte-pair plane.
+cudaError_t launch_mask_component(void* f, int esz, const Dims& d, int comp, cudaStream_t s, int fmt = 0);
 cudaError_t launch_or_flag(uint32_t* mat, long long pos, uint32_t bit, cudaStream_t s);
 
 // Batched cavities (yee_batch.cu, sophie_batch.cu). One descriptor per

@@ -42,48 +42,62 @@ namespace sophie {
 namespace {
 
 constexpr int kRX = 64;
-constexpr int kR = 4;         // rows per thread
-constexpr int kW = 8;         // consumer warps
-constexpr int kRY = kR * kW;  // 32
+constexpr int kRY = 32;  // region rows: R rows per thread, 32 / R warps
 constexpr int kNS = 3;
-constexpr int kConsumers = kW * 32;
-constexpr int kThreads = kConsumers;  // thread 0 also issues the TMA loads
 
-// TMA box of a storage format: the region rounded out to the 16-byte x granule.
+// Thread layout of a CTA with R rows per thread: W warps of 32 lanes (thread 0
+// also issues the TMA loads). R = 4: 8 warps; R = 2: 16 warps with half the
+// carried state per thread (more warps to hide latency, more warp seams).
+template <int R>
+struct Lay {
+  static constexpr int W = kRY / R;
+  static constexpr int kThreads = W * 32;
+  static_assert(W * R == kRY, "rows per thread must divide the region");
+};
+
+// TMA box of a storage format: the region rounded out to the 16-byte x granule,
+// all planes of the format (six components; nine 2-byte planes for kF24).
 template <int F>
 struct BoxCfg {
   using T = typename Store<F>::T;
   static constexpr int GX = Store<F>::kAlign;
   static constexpr int BX = kRX + GX;
-  static constexpr uint32_t kFieldBytes = BX * kRY * 6 * sizeof(T);
+  static constexpr int P = store_planes(F);
+  static constexpr uint32_t kFieldBytes = BX * kRY * P * sizeof(T);
+  static constexpr uint32_t kMatOff = (kFieldBytes + 127) / 128 * 128;  // material box, 128-byte aligned
   static constexpr uint32_t kMatBytes = BX * kRY * 4;
   static constexpr uint32_t kLoadBytes = kFieldBytes + kMatBytes;
-  static constexpr uint32_t kStageBytes = (kLoadBytes + 127) / 128 * 128;
-  static_assert(kFieldBytes % 128 == 0, "material box alignment");
+  static constexpr uint32_t kStageBytes = (kMatOff + kMatBytes + 127) / 128 * 128;
+  static constexpr long long CS = (long long)kRY * BX;  // elements between component planes
 };
 
-template <int K, int F>
+template <int K, int F, int R = 4>
 struct Cfg {
+  static constexpr int W = Lay<R>::W;
   static constexpr uint32_t kStageBytes = BoxCfg<F>::kStageBytes;
   static constexpr int TX = kRX - 2 * K;
   static constexpr int TY = kRY - 2 * K;
   static constexpr int PHI = K & 1;  // x tiles shifted so that region starts are even
-  // shared memory: stages | H seam rows [K][W][2][64] | E seam rows [K-1][2][W][2][64] | barriers
+  // shared memory: stages | H seam rows [K][W][2][64] | E seam rows [K-1][2][W][2][64] |
+  // class table | barriers | the loader's state (thread 0 only)
   static constexpr uint32_t kHpOff = kNS * kStageBytes;
-  static constexpr uint32_t kHpBytes = K * kW * 2 * kRX * 4;
+  static constexpr uint32_t kHpBytes = K * W * 2 * kRX * 4;
   static constexpr uint32_t kEpOff = kHpOff + kHpBytes;
-  static constexpr uint32_t kEpBytes = (K > 1 ? K - 1 : 1) * 2 * kW * 2 * kRX * 4;
+  static constexpr uint32_t kEpBytes = (K > 1 ? K - 1 : 1) * 2 * W * 2 * kRX * 4;
   static constexpr uint32_t kCoefOff = kEpOff + kEpBytes;
   static constexpr uint32_t kBarOff = kCoefOff + kMaxClasses * 8;
-  static constexpr uint32_t kSmem = kBarOff + kNS * 8;
+  static constexpr uint32_t kLdOff = kBarOff + kNS * 8;
+  static constexpr uint32_t kSmem = kLdOff + 64;
+  static_assert(kSmem <= 227 * 1024, "shared memory per CTA");
 };
 
 template <int F>
 __device__ __forceinline__ int FI(int f, int r, int c) { return (f * kRY + r) * BoxCfg<F>::BX + c; }
 
+template <int R>
 struct St {
-  float ex[kR][2], ey[kR][2], ez[kR][2], hx[kR][2], hy[kR][2], hz[kR][2];
-  uint32_t m[kR][2];
+  float ex[R][2], ey[R][2], ez[R][2], hx[R][2], hy[R][2], hz[R][2];
+  uint32_t m[R][2];
 };
 
 __device__ __forceinline__ void set_err(int* err, int code) { atomicOr(err, code); }
@@ -95,27 +109,32 @@ __device__ __forceinline__ void set_err(int* err, int code) { atomicOr(err, code
 // the same range, whose regions stream the same planes together (their
 // overlapping halos then come from L2). Otherwise the items are cut into
 // equal contiguous ranges, tile after tile.
+// Only the walking state is held (two counters); the tiling's constants are
+// read from the kernel parameter where they are used, keeping them out of
+// the registers of every thread.
 struct UnitIter {
-  long long i, hi;        // contiguous split: items [i, hi)
-  long long u, units, tiles;  // aligned split: next unit, unit count, tiles
-  int nz, zlo, zsplit, order;  // planes [zlo, zlo + nz) of every tile
-  __device__ UnitIter(const BlockedTiling& t) : nz(t.zhi - t.zlo), zlo(t.zlo), zsplit(t.zsplit), order(t.order) {
-    tiles = (long long)t.tiles_x * t.tiles_y;
-    u = blockIdx.x;
-    units = tiles * (zsplit > 0 ? zsplit : 0);
-    const long long n = tiles * nz;
-    i = n * blockIdx.x / gridDim.x;
-    hi = n * (blockIdx.x + 1) / gridDim.x;
+  long long i, hi;  // aligned split: next unit i; contiguous split: items [i, hi)
+  __device__ void init(const BlockedTiling& t) {
+    if (t.zsplit > 0) {
+      i = blockIdx.x;
+      hi = 0;
+    } else {
+      const long long n = (long long)t.tiles_x * t.tiles_y * (t.zhi - t.zlo);
+      i = n * blockIdx.x / gridDim.x;
+      hi = n * (blockIdx.x + 1) / gridDim.x;
+    }
   }
   // Next unit: tile index and planes [z0, z1). False when done.
-  __device__ bool next(long long& tile, int& z0, int& z1) {
-    if (zsplit > 0) {
-      if (u >= units) return false;
-      const long long r = order ? u / tiles : u % zsplit;
-      tile = order ? u % tiles : u / zsplit;
-      z0 = zlo + (int)((long long)nz * r / zsplit);
-      z1 = zlo + (int)((long long)nz * (r + 1) / zsplit);
-      u += gridDim.x;
+  __device__ bool next(const BlockedTiling& t, long long& tile, int& z0, int& z1) {
+    const long long tiles = (long long)t.tiles_x * t.tiles_y;
+    const int nz = t.zhi - t.zlo;
+    if (t.zsplit > 0) {
+      if (i >= tiles * t.zsplit) return false;
+      const long long r = t.order ? i / tiles : i % t.zsplit;
+      tile = t.order ? i % tiles : i / t.zsplit;
+      z0 = t.zlo + (int)((long long)nz * r / t.zsplit);
+      z1 = t.zlo + (int)((long long)nz * (r + 1) / t.zsplit);
+      i += gridDim.x;
       return true;
     }
     if (i >= hi) return false;
@@ -124,8 +143,8 @@ struct UnitIter {
     const long long room = hi - i;
     const int r1 = (int)((long long)r0 + room < nz ? r0 + room : nz);
     i += r1 - r0;
-    z0 = zlo + r0;
-    z1 = zlo + r1;
+    z0 = t.zlo + r0;
+    z1 = t.zlo + r1;
     return true;
   }
 };
@@ -157,13 +176,27 @@ __device__ __forceinline__ int first_iter(int z0) {
 
 
 // Issues the CTA's TMA loads in consumption order: for each unit, planes
-// first_iter-1 .. z1-1+K of its tile (thread 0 only).
+// first_iter-1 .. z1-1+K of its tile. Only thread 0 issues. The per-plane
+// counters stay in registers; the unit walk and the box origin, touched once
+// per unit, live in shared memory so that they take no registers of the other
+// threads.
+struct LoaderState {
+  UnitIter it;
+  int bx, ry;
+};
+
 template <int K, int F>
 struct Loader {
-  UnitIter it;
-  int p = 0, pend = -1, bx = 0, ry = 0;
-  long long issued = 0;
-  __device__ Loader(const BlockedTiling& t) : it(t) {}
+  LoaderState* st;
+  int p, pend;
+  long long issued;
+  __device__ void init(const BlockedTiling& t) {
+    st->it.init(t);
+    st->bx = st->ry = 0;
+    p = 0;
+    pend = -1;
+    issued = 0;
+  }
   // Issue the next plane into its stage; false when the sequence is exhausted.
   __device__ bool issue(const StepArgs& a, const BlockedTiling& t, const CUtensorMap* tmF, const CUtensorMap* tmM,
                         unsigned char* base, uint32_t bar0) {
@@ -171,22 +204,23 @@ struct Loader {
       long long tile;
       int z0, z1;
       do {
-        if (!it.next(tile, z0, z1)) return false;
+        if (!st->it.next(t, tile, z0, z1)) return false;
       } while (!unit_live<K>(a, t, tile, z0, z1));  // the consumers skip the same units
       int tx, ty;
       tile_xy(t, tile, tx, ty);
       const int rx = tx * Cfg<K, F>::TX - Cfg<K, F>::PHI - K;
-      ry = ty * Cfg<K, F>::TY - K;
-      bx = rx & ~(BoxCfg<F>::GX - 1);
+      st->ry = ty * Cfg<K, F>::TY - K;
+      st->bx = rx & ~(BoxCfg<F>::GX - 1);
       p = first_iter<K>(z0) - 1;
       pend = z1 - 1 + K;
     }
     const int s = (int)(issued % kNS);
     const uint32_t bar = bar0 + 8u * s;
     using B = BoxCfg<F>;
+    const int bx = st->bx, ry = st->ry;
     mbar_arrive_expect_tx(bar, B::kLoadBytes);
     tma_load_4d(smem_u32(base + s * B::kStageBytes), tmF, bx, ry, 0, p, bar);
-    tma_load_3d(smem_u32(base + s * B::kStageBytes + B::kFieldBytes), tmM, bx, ry, p, bar);
+    tma_load_3d(smem_u32(base + s * B::kStageBytes + B::kMatOff), tmM, bx, ry, p, bar);
     ++p;
     ++issued;
     return true;
@@ -196,13 +230,17 @@ struct Loader {
 // NU: non-uniform mesh; every bracket in the scaled form (yee_update.cuh),
 // the ratios of the lane's columns, its rows and the level's plane read per
 // level from the padded pair arrays (L1) rather than held in registers.
-template <int K, int FMT, bool NU>
-__global__ void __launch_bounds__(kThreads, 1)
+template <int K, int FMT, bool NU, int R>
+__global__ void __launch_bounds__(Lay<R>::kThreads, 1)
 yee_blocked_kernel(const __grid_constant__ CUtensorMap tmF, const __grid_constant__ CUtensorMap tmM,
-                   const __grid_constant__ StepArgs a, BlockedTiling t) {
-  using C = Cfg<K, FMT>;
+                   const __grid_constant__ StepArgs a, const __grid_constant__ BlockedTiling t) {
+  constexpr int kW = Lay<R>::W;
+  constexpr int kThreads = Lay<R>::kThreads;
+  constexpr int kConsumers = kThreads;
+  constexpr int kR = R;
+  using St = sophie::St<R>;
+  using C = Cfg<K, FMT, R>;
   using B = BoxCfg<FMT>;
-  using SF = Store<FMT>;
   using T = typename B::T;
   // Dynamic shared memory starts the CTA's shared window (no static shared
   // variables here), so it is 1024-byte aligned and its offsets are
@@ -216,7 +254,7 @@ yee_blocked_kernel(const __grid_constant__ CUtensorMap tmF, const __grid_constan
   const uint32_t bar0 = smem_u32(base + C::kBarOff);
   auto full = [&](int s) { return bar0 + 8u * s; };
   auto sF = [&](int s) { return reinterpret_cast<const T*>(base + s * B::kStageBytes); };
-  auto sM = [&](int s) { return reinterpret_cast<const uint32_t*>(base + s * B::kStageBytes + B::kFieldBytes); };
+  auto sM = [&](int s) { return reinterpret_cast<const uint32_t*>(base + s * B::kStageBytes + B::kMatOff); };
   // H seam rows: hp[level][warp][comp: 0 = hx, 1 = hz][64]
   float* hp = reinterpret_cast<float*>(base + C::kHpOff);
   // E seam rows: ep[level-1][parity][warp][comp: 0 = ex, 1 = ez][64]
@@ -233,8 +271,10 @@ yee_blocked_kernel(const __grid_constant__ CUtensorMap tmF, const __grid_constan
   }
   __syncthreads();
   const Dims d = a.d;
-  Loader<K, FMT> ld(t);
+  Loader<K, FMT> ld;
+  ld.st = reinterpret_cast<LoaderState*>(base + C::kLdOff);
   if (threadIdx.x == 0) {
+    ld.init(t);
     prefetch_tmap(&tmF);
     prefetch_tmap(&tmM);
     for (int s = 0; s < kNS; ++s)
@@ -244,12 +284,13 @@ yee_blocked_kernel(const __grid_constant__ CUtensorMap tmF, const __grid_constan
   const float S = a.S;
   const int wn = warp + 1 < kW ? warp + 1 : warp;  // seam partner below (clamped at the edge)
   const int wp = warp > 0 ? warp - 1 : warp;       // seam partner above
-  UnitIter it(t);
+  UnitIter it;
+  it.init(t);
   long long tile;
   int z0, z1;
   long long Cn = 0;  // consumed-plane counter (ring position)
   bool abort = false;
-  while (!abort && it.next(tile, z0, z1)) {
+  while (!abort && it.next(t, tile, z0, z1)) {
     if (!unit_live<K>(a, t, tile, z0, z1)) continue;  // known zeros: no planes loaded for it
     int tx, ty;
     tile_xy(t, tile, tx, ty);
@@ -293,6 +334,21 @@ yee_blocked_kernel(const __grid_constant__ CUtensorMap tmF, const __grid_constan
     for (int r = 0; r < kR; ++r)
 #pragma unroll
       for (int c = 0; c < 2; ++c) hxK[r][c] = hyK[r][c] = 0.f;
+    // This warp's E seam rows start at zero, like the carries: in a unit's first
+    // iteration level lv+1 reads the row "of the previous iteration", and for a
+    // unit that starts at plane 0 that state is the (zero) state below the grid,
+    // which reaches plane 0 through PEC coefficients -- a zero there, but a
+    // NaN left in shared memory by an earlier launch would survive the multiply.
+    // (Safe to write: every warp passed level lv+1's barrier of the previous
+    // unit's last iteration only after all reads of these rows.)
+#pragma unroll
+    for (int l = 0; l < (K > 1 ? K - 1 : 0); ++l)
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        float* epz = ep + (l * 2 + q) * (kW * 2 * kRX);
+        *reinterpret_cast<float2*>(&epz[(warp * 2 + 0) * kRX + 2 * lane]) = make_float2(0.f, 0.f);
+        *reinterpret_cast<float2*>(&epz[(warp * 2 + 1) * kRX + 2 * lane]) = make_float2(0.f, 0.f);
+      }
 
     for (int s = s0; s <= s1; ++s, ++Cn) {
       const int sc = (int)(Cn % kNS), sn = (int)((Cn + 1) % kNS);
@@ -312,15 +368,15 @@ yee_blocked_kernel(const __grid_constant__ CUtensorMap tmF, const __grid_constan
 #pragma unroll
       for (int r = 0; r < kR; ++r) {
         const int row = warp * kR + r;
-        const float2 v0 = SF::ld2(&F[FI<FMT>(0, row, col0)], a.isc[0]);
-        const float2 v1 = SF::ld2(&F[FI<FMT>(1, row, col0)], a.isc[1]);
-        const float2 v2 = SF::ld2(&F[FI<FMT>(2, row, col0)], a.isc[2]);
-        const float2 v3 = SF::ld2(&F[FI<FMT>(3, row, col0)], a.isc[3]);
-        const float2 v4 = SF::ld2(&F[FI<FMT>(4, row, col0)], a.isc[4]);
-        const float2 v5 = SF::ld2(&F[FI<FMT>(5, row, col0)], a.isc[5]);
+        const float2 v0 = ld2c<FMT>(&F[FI<FMT>(0, row, col0)], a.isc[0], 0, B::CS);
+        const float2 v1 = ld2c<FMT>(&F[FI<FMT>(1, row, col0)], a.isc[1], 1, B::CS);
+        const float2 v2 = ld2c<FMT>(&F[FI<FMT>(2, row, col0)], a.isc[2], 2, B::CS);
+        const float2 v3 = ld2c<FMT>(&F[FI<FMT>(3, row, col0)], a.isc[3], 3, B::CS);
+        const float2 v4 = ld2c<FMT>(&F[FI<FMT>(4, row, col0)], a.isc[4], 4, B::CS);
+        const float2 v5 = ld2c<FMT>(&F[FI<FMT>(5, row, col0)], a.isc[5], 5, B::CS);
         const uint2 mm = *reinterpret_cast<const uint2*>(&M[row * B::BX + col0]);
-        const float2 n0 = SF::ld2(&Fn[FI<FMT>(0, row, col0)], a.isc[0]);
-        const float2 n1 = SF::ld2(&Fn[FI<FMT>(1, row, col0)], a.isc[1]);
+        const float2 n0 = ld2c<FMT>(&Fn[FI<FMT>(0, row, col0)], a.isc[0], 0, B::CS);
+        const float2 n1 = ld2c<FMT>(&Fn[FI<FMT>(1, row, col0)], a.isc[1], 1, B::CS);
         in.ex[r][0] = v0.x; in.ex[r][1] = v0.y;
         in.ey[r][0] = v1.x; in.ey[r][1] = v1.y;
         in.ez[r][0] = v2.x; in.ez[r][1] = v2.y;
@@ -335,8 +391,8 @@ yee_blocked_kernel(const __grid_constant__ CUtensorMap tmF, const __grid_constan
       float bex[2], bez[2];
       {
         const int brow = warp * kR + kR < kRY ? warp * kR + kR : kRY - 1;
-        const float2 b0 = SF::ld2(&F[FI<FMT>(0, brow, col0)], a.isc[0]);
-        const float2 b2 = SF::ld2(&F[FI<FMT>(2, brow, col0)], a.isc[2]);
+        const float2 b0 = ld2c<FMT>(&F[FI<FMT>(0, brow, col0)], a.isc[0], 0, B::CS);
+        const float2 b2 = ld2c<FMT>(&F[FI<FMT>(2, brow, col0)], a.isc[2], 2, B::CS);
         bex[0] = b0.x; bex[1] = b0.y;
         bez[0] = b2.x; bez[1] = b2.y;
       }
@@ -569,17 +625,7 @@ yee_blocked_kernel(const __grid_constant__ CUtensorMap tmF, const __grid_constan
             const float vals[6][2] = {{out.ex[r][0], out.ex[r][1]}, {out.ey[r][0], out.ey[r][1]},
                                       {out.ez[r][0], out.ez[r][1]}, {out.hx[r][0], out.hx[r][1]},
                                       {out.hy[r][0], out.hy[r][1]}, {out.hz[r][0], out.hz[r][1]}};
-            if (v0 && v1) {
-#pragma unroll
-              for (int f = 0; f < 6; ++f)
-                SF::st2(o + f * d.plane, vals[f][0], vals[f][1], a.sc[f]);
-            } else if (v0) {
-#pragma unroll
-              for (int f = 0; f < 6; ++f) SF::st(o + f * d.plane, vals[f][0], a.sc[f]);
-            } else if (v1) {
-#pragma unroll
-              for (int f = 0; f < 6; ++f) SF::st(o + f * d.plane + 1, vals[f][1], a.sc[f]);
-            }
+            if (v0 || v1) st6<FMT>(o, d.plane, vals, a.sc, (v0 ? 1 : 0) | (v1 ? 2 : 0));
           }
         }
       }
@@ -595,18 +641,27 @@ yee_blocked_kernel(const __grid_constant__ CUtensorMap tmF, const __grid_constan
   }
 }
 
-template <int K, int F, bool NU>
-cudaError_t launch_kn(const StepArgs& a, const CUtensorMap& tmF, const CUtensorMap& tmM, const BlockedTiling& t,
-                      cudaStream_t s) {
+template <int K, int F, bool NU, int R>
+cudaError_t launch_knr(const StepArgs& a, const CUtensorMap& tmF, const CUtensorMap& tmM, const BlockedTiling& t,
+                       cudaStream_t s) {
   static bool attr = false;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(yee_blocked_kernel<K, F, NU>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)Cfg<K, F>::kSmem);
+    cudaError_t e = cudaFuncSetAttribute(yee_blocked_kernel<K, F, NU, R>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg<K, F, R>::kSmem);
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  yee_blocked_kernel<K, F, NU><<<t.grid, kThreads, Cfg<K, F>::kSmem, s>>>(tmF, tmM, a, t);
+  yee_blocked_kernel<K, F, NU, R><<<t.grid, Lay<R>::kThreads, Cfg<K, F, R>::kSmem, s>>>(tmF, tmM, a, t);
   return cudaGetLastError();
+}
+
+template <int K, int F, bool NU>
+cudaError_t launch_kn(const StepArgs& a, const CUtensorMap& tmF, const CUtensorMap& tmM, const BlockedTiling& t,
+                      cudaStream_t s) {
+  // the 16-warp layout's seam rows fit in shared memory beside the ring for K = 2 only
+  if constexpr (K == 2)
+    if (t.rows == 2) return launch_knr<K, F, NU, 2>(a, tmF, tmM, t, s);
+  return launch_knr<K, F, NU, 4>(a, tmF, tmM, t, s);
 }
 
 template <int K, int F>
@@ -711,6 +766,7 @@ cudaError_t launch_step_blocked(const StepArgs& a, const CUtensorMap& tmF, const
     case kF16: return launch_fmt<kF16>(a, tmF, tmM, t, s);
     case kBF16: return launch_fmt<kBF16>(a, tmF, tmM, t, s);
     case kF16HL: return launch_fmt<kF16HL>(a, tmF, tmM, t, s);
+    case kF24: return launch_fmt<kF24>(a, tmF, tmM, t, s);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -15,7 +15,7 @@ template <int F>
 __device__ __forceinline__ float ld_s(const typename Store<F>::T* f, const Dims& d, const float* isc, int c, int x,
                                       int y, int z) {
   if (x < 0 || x >= d.nxp || y < 0 || y >= d.ny1 || z < 0 || z >= d.nz1) return 0.f;
-  return Store<F>::ld(f + (long long)z * d.zstride + (long long)c * d.plane + (long long)y * d.nxp + x, isc[c]);
+  return ldc<F>(f + (long long)z * d.zstride + (long long)c * d.plane + (long long)y * d.nxp + x, isc[c], c, d.plane);
 }
 
 template <int F>

@@ -176,7 +176,8 @@ energy_final_kernel(const double* partials, int n, double scale, double* out) {
 }
 
 // Zero PEC edges and entries outside a component's valid range (see sophie.h).
-__global__ void mask_component_kernel(unsigned char* f, int esz, Dims d, int comp) {
+// kF24 storage: the component's high half and its byte of the byte-pair plane.
+__global__ void mask_component_kernel(unsigned char* f, int esz, Dims d, int comp, int fmt) {
   const long long npts = (long long)d.nz1 * d.ny1 * d.nxp;
   for (long long pt = (long long)blockIdx.x * blockDim.x + threadIdx.x; pt < npts;
        pt += (long long)gridDim.x * blockDim.x) {
@@ -194,8 +195,10 @@ __global__ void mask_component_kernel(unsigned char* f, int esz, Dims d, int com
       default: keep = x < d.nx && y < d.ny && z <= d.nz; break;
     }
     if (!keep) {
-      unsigned char* p = f + ((long long)z * d.zstride + (long long)comp * d.plane + (long long)y * d.nxp + x) * esz;
+      const long long e = (long long)z * d.zstride + (long long)y * d.nxp + x;
+      unsigned char* p = f + (e + (long long)comp * d.plane) * esz;
       for (int b = 0; b < esz; ++b) p[b] = 0;
+      if (fmt == kF24) f[(e + (long long)(6 + comp / 2) * d.plane) * esz + (comp & 1)] = 0;
     }
   }
 }
@@ -241,6 +244,7 @@ cudaError_t launch_energy_scaled(const StepArgs& a, const double* eps_tab, doubl
     case kF16: return launch_energy_f<kF16>(a, eps_tab, partials, nblocks, scale, out, s);
     case kBF16: return launch_energy_f<kBF16>(a, eps_tab, partials, nblocks, scale, out, s);
     case kF16HL: return launch_energy_f<kF16HL>(a, eps_tab, partials, nblocks, scale, out, s);
+    case kF24: return launch_energy_f<kF24>(a, eps_tab, partials, nblocks, scale, out, s);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -250,8 +254,8 @@ cudaError_t launch_energy(const StepArgs& a, const double* eps_tab, double* part
   return launch_energy_scaled(a, eps_tab, partials, nblocks, 1.0, out, s);
 }
 
-cudaError_t launch_mask_component(void* f, int esz, const Dims& d, int comp, cudaStream_t s) {
-  mask_component_kernel<<<152 * 4, 256, 0, s>>>(static_cast<unsigned char*>(f), esz, d, comp);
+cudaError_t launch_mask_component(void* f, int esz, const Dims& d, int comp, cudaStream_t s, int fmt) {
+  mask_component_kernel<<<152 * 4, 256, 0, s>>>(static_cast<unsigned char*>(f), esz, d, comp, fmt);
   return cudaGetLastError();
 }
 

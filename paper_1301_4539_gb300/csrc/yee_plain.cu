@@ -49,11 +49,14 @@ struct PCfg {
   using T = typename Store<F>::T;
   static constexpr int OX = Store<F>::kAlign;
   static constexpr int BX = kPX + 2 * OX;
+  static constexpr int P = store_planes(F);  // planes per slab (nine 2-byte planes for kF24)
   static constexpr bool kInPlace = sizeof(T) == 4;  // a float fits in the ring slot
-  static constexpr uint32_t kFieldBytes = BX * kBY * 6 * sizeof(T);
+  static constexpr uint32_t kFieldBytes = BX * kBY * P * sizeof(T);
+  static constexpr uint32_t kMatOff = (kFieldBytes + 127) / 128 * 128;  // material box, 128-byte aligned
   static constexpr uint32_t kMatBytes = BX * kBY * 4;
   static constexpr uint32_t kLoadBytes = kFieldBytes + kMatBytes;
-  static constexpr uint32_t kStageBytes = (kLoadBytes + 127) / 128 * 128;
+  static constexpr uint32_t kStageBytes = (kMatOff + kMatBytes + 127) / 128 * 128;
+  static constexpr long long CS = (long long)kBY * BX;  // elements between component planes
   static constexpr uint32_t kHbOff = kNS * kStageBytes;
   static constexpr uint32_t kHbBytes = kInPlace ? 0 : 2 * 3 * kBY * BX * 4;
   static constexpr uint32_t kBarOff = kHbOff + kHbBytes;
@@ -61,7 +64,6 @@ struct PCfg {
   // pre-scaled byte offsets (batches read their cavities' tables from L1)
   static constexpr uint32_t kCoefOff = (kBarOff + 2 * kNS * 8 + 15) / 16 * 16;
   static constexpr uint32_t kSmemBytes = kCoefOff + kMaxClasses * 8 + 128;
-  static_assert(kFieldBytes % 128 == 0, "material box must start 128-byte aligned");
 };
 
 struct Unit {
@@ -97,7 +99,6 @@ yee_plain_kernel(const __grid_constant__ CUtensorMap tmF, const __grid_constant_
   static_assert(!BATCH || FMT == kF32, "batches store float fields");
   static_assert(!(BATCH && NU), "batches are uniform meshes");
   using C = PCfg<FMT>;
-  using St = Store<FMT>;
   using T = typename C::T;
   constexpr int BX = C::BX;
   constexpr int OX = C::OX;
@@ -109,7 +110,7 @@ yee_plain_kernel(const __grid_constant__ CUtensorMap tmF, const __grid_constant_
   auto full = [&](int s) { return bar0 + 8u * s; };
   auto empty = [&](int s) { return bar0 + 8u * (kNS + s); };
   auto sF = [&](int s) { return reinterpret_cast<T*>(base + s * C::kStageBytes); };
-  auto sM = [&](int s) { return reinterpret_cast<const uint32_t*>(base + s * C::kStageBytes + C::kFieldBytes); };
+  auto sM = [&](int s) { return reinterpret_cast<const uint32_t*>(base + s * C::kStageBytes + C::kMatOff); };
   float* const hbuf = reinterpret_cast<float*>(base + C::kHbOff);
   const unsigned char* const scoefb = base + C::kCoefOff;
   if constexpr (!BATCH)
@@ -282,9 +283,9 @@ yee_plain_kernel(const __grid_constant__ CUtensorMap tmF, const __grid_constant_
 #pragma unroll
         for (int r = 0; r < 2; ++r) {
           const int row = r0 + r;
-          const float2 vex = St::ld2(&F[FI(0, row, c0)], a.isc[0]);
-          const float2 vey = St::ld2(&F[FI(1, row, c0)], a.isc[1]);
-          const float2 vez = St::ld2(&F[FI(2, row, c0)], a.isc[2]);
+          const float2 vex = ld2c<FMT>(&F[FI(0, row, c0)], a.isc[0], 0, C::CS);
+          const float2 vey = ld2c<FMT>(&F[FI(1, row, c0)], a.isc[1], 1, C::CS);
+          const float2 vez = ld2c<FMT>(&F[FI(2, row, c0)], a.isc[2], 2, C::CS);
           ex[r][0] = vex.x; ex[r][1] = vex.y;
           ey[r][0] = vey.x; ey[r][1] = vey.y;
           ez[r][0] = vez.x; ez[r][1] = vez.y;
@@ -292,23 +293,23 @@ yee_plain_kernel(const __grid_constant__ CUtensorMap tmF, const __grid_constant_
 #pragma unroll
         for (int r = 0; r < 2; ++r) {
           const int row = r0 + r;
-          const float2 vhx = St::ld2(&F[FI(3, row, c0)], a.isc[3]);
-          const float2 vhy = St::ld2(&F[FI(4, row, c0)], a.isc[4]);
-          const float2 vhz = St::ld2(&F[FI(5, row, c0)], a.isc[5]);
-          const float2 nex = St::ld2(&Fn[FI(0, row, c0)], a.isc[0]);
-          const float2 ney = St::ld2(&Fn[FI(1, row, c0)], a.isc[1]);
+          const float2 vhx = ld2c<FMT>(&F[FI(3, row, c0)], a.isc[3], 3, C::CS);
+          const float2 vhy = ld2c<FMT>(&F[FI(4, row, c0)], a.isc[4], 4, C::CS);
+          const float2 vhz = ld2c<FMT>(&F[FI(5, row, c0)], a.isc[5], 5, C::CS);
+          const float2 nex = ld2c<FMT>(&Fn[FI(0, row, c0)], a.isc[0], 0, C::CS);
+          const float2 ney = ld2c<FMT>(&Fn[FI(1, row, c0)], a.isc[1], 1, C::CS);
           float exj[2], ezj[2];
           if (r == 0) {
             exj[0] = ex[1][0]; exj[1] = ex[1][1];
             ezj[0] = ez[1][0]; ezj[1] = ez[1][1];
           } else {
-            const float2 a2 = St::ld2(&F[FI(0, row + 1, c0)], a.isc[0]);
-            const float2 b2 = St::ld2(&F[FI(2, row + 1, c0)], a.isc[2]);
+            const float2 a2 = ld2c<FMT>(&F[FI(0, row + 1, c0)], a.isc[0], 0, C::CS);
+            const float2 b2 = ld2c<FMT>(&F[FI(2, row + 1, c0)], a.isc[2], 2, C::CS);
             exj[0] = a2.x; exj[1] = a2.y;
             ezj[0] = b2.x; ezj[1] = b2.y;
           }
-          const float ez_ip1 = St::ld(&F[FI(2, row, c0 + 2)], a.isc[2]);
-          const float ey_ip1 = St::ld(&F[FI(1, row, c0 + 2)], a.isc[1]);
+          const float ez_ip1 = ldc<FMT>(&F[FI(2, row, c0 + 2)], a.isc[2], 2, C::CS);
+          const float ey_ip1 = ldc<FMT>(&F[FI(1, row, c0 + 2)], a.isc[1], 1, C::CS);
           // the lane's two x positions as packed pairs
           auto P = [](const float (&v)[2]) { return make_float2(v[0], v[1]); };
           if constexpr (NU) {
@@ -338,18 +339,18 @@ yee_plain_kernel(const __grid_constant__ CUtensorMap tmF, const __grid_constant_
           *reinterpret_cast<float2*>(hp(2, row, c0)) = make_float2(hz[r][0], hz[r][1]);
         }
         if (hr >= 0) {
-          const float e0 = St::ld(&F[FI(0, hr, hc)], a.isc[0]);
-          const float e1 = St::ld(&F[FI(1, hr, hc)], a.isc[1]);
-          const float e2 = St::ld(&F[FI(2, hr, hc)], a.isc[2]);
-          const float nx_ = h_upd_r<NU>(St::ld(&F[FI(3, hr, hc)], a.isc[3]), S, rz,
-                                        St::ld(&Fn[FI(1, hr, hc)], a.isc[1]), e1, ryh,
-                                        St::ld(&F[FI(2, hr + 1, hc)], a.isc[2]), e2);
-          const float ny_ = h_upd_r<NU>(St::ld(&F[FI(4, hr, hc)], a.isc[4]), S, rxh,
-                                        St::ld(&F[FI(2, hr, hc + 1)], a.isc[2]), e2, rz,
-                                        St::ld(&Fn[FI(0, hr, hc)], a.isc[0]), e0);
-          const float nz_ = h_upd_r<NU>(St::ld(&F[FI(5, hr, hc)], a.isc[5]), S, ryh,
-                                        St::ld(&F[FI(0, hr + 1, hc)], a.isc[0]), e0, rxh,
-                                        St::ld(&F[FI(1, hr, hc + 1)], a.isc[1]), e1);
+          const float e0 = ldc<FMT>(&F[FI(0, hr, hc)], a.isc[0], 0, C::CS);
+          const float e1 = ldc<FMT>(&F[FI(1, hr, hc)], a.isc[1], 1, C::CS);
+          const float e2 = ldc<FMT>(&F[FI(2, hr, hc)], a.isc[2], 2, C::CS);
+          const float nx_ = h_upd_r<NU>(ldc<FMT>(&F[FI(3, hr, hc)], a.isc[3], 3, C::CS), S, rz,
+                                        ldc<FMT>(&Fn[FI(1, hr, hc)], a.isc[1], 1, C::CS), e1, ryh,
+                                        ldc<FMT>(&F[FI(2, hr + 1, hc)], a.isc[2], 2, C::CS), e2);
+          const float ny_ = h_upd_r<NU>(ldc<FMT>(&F[FI(4, hr, hc)], a.isc[4], 4, C::CS), S, rxh,
+                                        ldc<FMT>(&F[FI(2, hr, hc + 1)], a.isc[2], 2, C::CS), e2, rz,
+                                        ldc<FMT>(&Fn[FI(0, hr, hc)], a.isc[0], 0, C::CS), e0);
+          const float nz_ = h_upd_r<NU>(ldc<FMT>(&F[FI(5, hr, hc)], a.isc[5], 5, C::CS), S, ryh,
+                                        ldc<FMT>(&F[FI(0, hr + 1, hc)], a.isc[0], 0, C::CS), e0, rxh,
+                                        ldc<FMT>(&F[FI(1, hr, hc + 1)], a.isc[1], 1, C::CS), e1);
           *hp(0, hr, hc) = nx_;
           *hp(1, hr, hc) = ny_;
           *hp(2, hr, hc) = nz_;
@@ -460,13 +461,7 @@ yee_plain_kernel(const __grid_constant__ CUtensorMap tmF, const __grid_constant_
           T* o = fout() + (long long)z * d.zstride() + (long long)y * d.nxp() + x;
           const float vals[6][2] = {{eo[0][0], eo[0][1]}, {eo[1][0], eo[1][1]}, {eo[2][0], eo[2][1]},
                                     {hx[r][0], hx[r][1]}, {hy[r][0], hy[r][1]}, {hz[r][0], hz[r][1]}};
-          if (x + 1 < d.nx()) {
-#pragma unroll
-            for (int f = 0; f < 6; ++f) St::st2(o + f * d.plane(), vals[f][0], vals[f][1], a.sc[f]);
-          } else {
-#pragma unroll
-            for (int f = 0; f < 6; ++f) St::st(o + f * d.plane(), vals[f][0], a.sc[f]);
-          }
+          st6<FMT>(o, d.plane(), vals, a.sc, x + 1 < d.nx() ? 3 : 1);
         }
 #pragma unroll
         for (int cc = 0; cc < 2; ++cc) {
@@ -510,13 +505,17 @@ bool encode_maps(const Dims& d, int fmt, void* fields, uint32_t* mat, int box_x,
   if (!fn) return false;
   const cuuint64_t esz = store_bytes(fmt);
   // hi+lo pairs move as 4-byte elements (zero fill = +0 + +0)
+  // (kF24: 2-byte elements of nine planes, zero fill = +0)
   const CUtensorMapDataType dt = fmt == kF32 || fmt == kF16HL ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
                                  : fmt == kF16                ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
+                                 : fmt == kF24                ? CU_TENSOR_MAP_DATA_TYPE_UINT16
                                                               : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+  const cuuint32_t planes = (cuuint32_t)store_planes(fmt);
+  if (d.zstride != (long long)planes * d.plane) return false;
   if (tmF) {
-    cuuint64_t gdF[4] = {(cuuint64_t)d.nxp, (cuuint64_t)d.ny1, 6, (cuuint64_t)d.nz1};
+    cuuint64_t gdF[4] = {(cuuint64_t)d.nxp, (cuuint64_t)d.ny1, planes, (cuuint64_t)d.nz1};
     cuuint64_t gsF[3] = {(cuuint64_t)d.nxp * esz, (cuuint64_t)d.plane * esz, (cuuint64_t)d.zstride * esz};
-    cuuint32_t boxF[4] = {(cuuint32_t)box_x, (cuuint32_t)box_y, 6, 1};
+    cuuint32_t boxF[4] = {(cuuint32_t)box_x, (cuuint32_t)box_y, planes, 1};
     cuuint32_t es[4] = {1, 1, 1, 1};
     if (fn(tmF, dt, 4, fields, gdF, gsF, boxF, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
@@ -629,6 +628,7 @@ cudaError_t launch_step_plain(const StepArgs& a, const CUtensorMap& tmF, const C
     case kF16: return launch_plain_f<kF16>(a, tmF, tmM, t, s);
     case kBF16: return launch_plain_f<kBF16>(a, tmF, tmM, t, s);
     case kF16HL: return launch_plain_f<kF16HL>(a, tmF, tmM, t, s);
+    case kF24: return launch_plain_f<kF24>(a, tmF, tmM, t, s);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -20,7 +20,7 @@ OK, EINVAL, EUNSTABLE, ENOMEM, ECUDA, ENONFINITE, ETIMEOUT, ETOOMANYMAT, ENOTSUP
     0, -1, -2, -3, -4, -5, -6, -7, -8)
 EX, EY, EZ, HX, HY, HZ = range(6)
 GAUSS_SINE, GAUSS = 0, 1
-FP32, FP16, BF16, FP16HL = 0, 1, 2, 3
+FP32, FP16, BF16, FP16HL, FP24 = 0, 1, 2, 3, 4
 KERNEL_PLAIN, KERNEL_BLOCKED, KERNEL_ENERGY, KERNEL_ADJOINT = 0, 1, 2, 3
 
 # Exported symbols with (restype, argtypes).

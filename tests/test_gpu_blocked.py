@@ -99,3 +99,28 @@ def test_unsupported_k(sophie):
     assert e.value.code == so.ENOTSUP
     with pytest.raises(so.SophieError):
         g.configure(temporal_k=9)
+
+
+@pytest.mark.parametrize("zsplit", ["13", "20"])
+@pytest.mark.parametrize("K", [2, 3, 4])
+def test_blocked_short_units(oracle_mod, sophie, monkeypatch, K, zsplit):
+    """Units of 2 to 3 planes (every tile's 40 planes cut into 13 or 20 z
+    ranges): most units start within the first planes or replay 3K - 2 planes,
+    and each starts its levels' state (carries and shared-memory seam rows)
+    from zero. Lossy materials with explicit entries, sources and probes."""
+    monkeypatch.setenv("SOPHIE_BLOCKED_ZSPLIT", zsplit)
+    nx, ny, nz = 130, 21, 40
+    eps, sig = wl.random_materials(nx, ny, nz, seed=11 * K, nmat=6, sigma=(0.0, 0.5))
+    eps = eps.copy()
+    eps[:, : ny // 3, : nx // 4] = np.random.default_rng(K).uniform(1, 9, size=(nz, ny // 3, nx // 4))
+    f = wl.random_fields(nx, ny, nz, seed=K + 3)
+    amp, f0, bw, t0, kind = wl.gaussian_sine_source()
+    srcs = [(2, nx // 2, ny // 2, nz // 2, 25.0, f0, bw, 4e-12, 0), (0, nx // 3, ny // 3, 1, 3.0, f0, bw, 5e-12, 1)]
+    prbs = wl.probe_edges(nx, ny, nz, 5, seed=nx) + [(3, nx // 2, ny // 2, 0), (5, 1, 1, nz)]
+    g, o = make_pair(oracle_mod, nx, ny, nz, eps, sig, f, srcs, prbs, temporal_k=K)
+    for n in (3 * K + 1, K + 2):
+        g.step(n)
+        o.step(n)
+        assert_fields_equal(g, o)
+    for q in range(len(prbs)):
+        np.testing.assert_array_equal(g.read_probe(q), o.probe(q))
