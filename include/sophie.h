@@ -426,6 +426,50 @@ int sophie_batch_launch_count(sophie_batch *b, long long *launches);
 int sophie_batch_sync(sophie_batch *b);
 
 /*
+ * Packed layout of a batch (the batching form with temporal blocking; no
+ * counterpart in the paper). sophie_batch_create_packed takes the arguments of
+ * sophie_batch_create and places every cavity in ONE grid, each separated from
+ * its neighbours (and the grid walls) by a layer of perfectly conducting
+ * cells: a conducting cell makes every edge it touches a PEC edge, exactly
+ * like a wall, so each cavity evolves bit for bit as it would alone (Sec. 3.3
+ * PEC walls; the cells outside the cavities stay zero). A step of the batch
+ * is then a step of that grid: the tuned single-grid kernels, temporally
+ * blocked with k and the tilings chosen by the grid's autotuner at the first
+ * step (or by sophie_batch_autotune), the launches of a run recorded into a
+ * CUDA graph and replayed like the work-list layout's. Every sophie_batch_*
+ * call applies to a packed batch, with these differences:
+ *   - materials: each cavity's words and tables are built as for a single
+ *     grid of its size; class materials are shared globally while all
+ *     cavities' classes fit the 511-entry table, otherwise those points
+ *     become explicit entries (same coefficients, same results);
+ *   - sophie_batch_configure accepts only tile_x = tile_y = zchunk = 0 (else
+ *     ENOTSUP) and the use_graph flag;
+ *   - sophie_batch_info / sophie_batch_autotune: work_items gets the packed
+ *     grid's cells, tile_x / tile_y the output tile of its step kernel
+ *     ((64 - 2k) x (32 - 2k) blocked, 64 x 16 plain), zchunk 0;
+ *   - energies are summed over each cavity's own index points (double), in a
+ *     fixed order; they equal the work-list layout's within rounding of the
+ *     sum (not bitwise).
+ * Field storage is float. Errors: those of sophie_batch_create and of
+ * sophie_create_grid for the packed grid (ENOMEM when it does not fit).
+ *
+ * sophie_batch_pack_plan: the placement alone, on the host (no GPU): origins
+ *   gets ncav x {x, y, z}, the first cell of each cavity in the packed grid,
+ *   extent the grid's {nx, ny, nz}. Cavities are sorted into rows along x by
+ *   z-thickness bands and height, rows stacked along y into layers, layers
+ *   along z; several footprints and band widths are tried, the smallest grid
+ *   kept. Errors: EINVAL.
+ * sophie_batch_layout: *packed = 1 for a packed batch (extent = its grid's
+ *   size, *temporal_k = the steps per launch in use), else 0.
+ * sophie_batch_cavity_origin: the first cell of cavity cav in the packed grid
+ *   (ENOTSUP for the work-list layout).
+ */
+int sophie_batch_create_packed(int ncav, const int *dims, double dx, double dt, sophie_batch **out);
+int sophie_batch_pack_plan(int ncav, const int *dims, int *origins, int *extent);
+int sophie_batch_layout(sophie_batch *b, int *packed, int *extent, int *temporal_k);
+int sophie_batch_cavity_origin(sophie_batch *b, int cav, int *xyz);
+
+/*
  * Diagnostics (no counterpart in the paper).
  * sophie_check_guards: each field buffer sits between two guard regions
  *   (one z slab of the six components, at least 1 MiB) filled with 0xA5 at

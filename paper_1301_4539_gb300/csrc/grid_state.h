@@ -124,6 +124,14 @@ struct sophie_grid {
   std::vector<sophie::grid::Probe> prb;
   float* sval = nullptr;  // device [kMaxSources][scap]
   int scap = 0;
+  // Many sources, installed by a packed batch of cavities (batch_packed.cu):
+  // when big_n > 0 the step kernels take their sources from these device
+  // arrays (SrcTable::nbig) instead of src / sval. Owned by the batch.
+  int big_n = 0, big_cap = 0;
+  const long long* big_pos = nullptr;
+  const int* big_comp = nullptr;
+  const int* big_row = nullptr;
+  const float* big_val = nullptr;
   float* pbuf = nullptr;  // device [kMaxProbes][pcap]
   int pcap = 0;
   long long n = 0;
@@ -174,6 +182,9 @@ int prof_drain(sophie_grid* g);
 StepArgs make_step_args(sophie_grid* g);
 // Synchronise; ETIMEOUT (and clear the word) if a kernel gave up a wait.
 int check_err_word(sophie_grid* g);
+// Enqueue the upload of g->mat_host and the host coefficient tables (the
+// explicit tables reallocated if they grew); records g->mat_upload_done.
+int upload_materials(sophie_grid* g);
 void free_tape(Tape& t);
 
 }  // namespace grid

@@ -135,6 +135,11 @@ int build_material_words(sophie_grid* g, const float* eps, const float* sig) {
   return SOPHIE_OK;
 }
 
+}  // namespace
+
+namespace sophie {
+namespace grid {
+
 int upload_materials(sophie_grid* g) {
   const Dims& d = g->d;
   const size_t npts = (size_t)d.nz1 * d.ny1 * d.nxp;
@@ -168,6 +173,11 @@ int upload_materials(sophie_grid* g) {
   // The tables are pageable host memory: the copies above complete before return.
   return SOPHIE_OK;
 }
+
+}  // namespace grid
+}  // namespace sophie
+
+namespace {
 
 double waveform(const Source& s, long long n, double dt) {
   return source_waveform(s.kind, s.amp, s.f0, s.bw, s.t0, dt, n);
@@ -286,6 +296,15 @@ StepArgs make_step_args(sophie_grid* g) {
   }
   a.src.val = g->sval;
   a.src.cap = g->scap;
+  if (g->big_n > 0) {
+    a.src.n = 0;
+    a.src.nbig = g->big_n;
+    a.src.bpos = g->big_pos;
+    a.src.bcomp = g->big_comp;
+    a.src.brow = g->big_row;
+    a.src.val = g->big_val;
+    a.src.cap = g->big_cap;
+  }
   a.prb.n = (int)g->prb.size();
   for (size_t p = 0; p < g->prb.size(); ++p) {
     a.prb.comp[p] = g->prb[p].comp;

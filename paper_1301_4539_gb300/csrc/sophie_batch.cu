@@ -106,6 +106,10 @@ struct sophie_batch {
   long long g_n0 = -1;
   int g_len = 0, g_cur = -1;
   long long launches = 0;
+  // Packed layout (sophie_batch_create_packed): the cavities in one grid;
+  // every call below goes to batch_packed.cu, only ncav, dims and cells above
+  // are used.
+  PackedBatch* pk = nullptr;
 };
 
 namespace {
@@ -118,6 +122,11 @@ void drop_graph(sophie_batch* b) {
 
 void free_batch(sophie_batch* b) {
   if (!b) return;
+  if (b->pk) {
+    packed_destroy(b->pk);
+    delete b;
+    return;
+  }
   if (b->stream) cudaStreamSynchronize(b->stream);
   drop_graph(b);
   void* bufs[] = {b->arena_base, b->words, b->coef, b->eps_tab, b->ecoef, b->eeps, b->sval, b->d_desc,
@@ -429,6 +438,78 @@ int sophie_batch_create(int ncav, const int* dims, double dx, double dt, sophie_
   return SOPHIE_OK;
 }
 
+int sophie_batch_pack_plan(int ncav, const int* dims, int* origins, int* extent) {
+  if (!dims || !origins || !extent) return bfail(SOPHIE_EINVAL, "NULL argument");
+  if (ncav < 1 || ncav > (1 << 22)) return bfail(SOPHIE_EINVAL, "cavity count must be in [1, 2^22]");
+  for (int c = 0; c < 3 * ncav; ++c)
+    if (dims[c] < 1 || dims[c] > 4096) return bfail(SOPHIE_EINVAL, "cavity %d: sizes must be in [1, 4096]", c / 3);
+  return packed_plan(ncav, dims, origins, extent);
+}
+
+int sophie_batch_create_packed(int ncav, const int* dims, double dx, double dt, sophie_batch** out) {
+  if (!out || !dims) return bfail(SOPHIE_EINVAL, "NULL argument");
+  *out = nullptr;
+  if (ncav < 1 || ncav > (1 << 22)) return bfail(SOPHIE_EINVAL, "cavity count must be in [1, 2^22]");
+  if (!(dx > 0) || !std::isfinite(dx) || !(dt > 0) || !std::isfinite(dt))
+    return bfail(SOPHIE_EINVAL, "dx and dt must be finite and > 0");
+  if (kC0b * dt * std::sqrt(3.0) > dx * (1.0 + 1e-12))
+    return bfail(SOPHIE_EUNSTABLE, "dt above the 3-D Courant limit dx/(c sqrt 3)");
+  sophie_batch* b = new (std::nothrow) sophie_batch();
+  if (!b) return bfail(SOPHIE_ENOMEM, "host allocation failed");
+  b->ncav = ncav;
+  b->dx = dx;
+  b->dt = dt;
+  for (int c = 0; c < ncav; ++c) {
+    const int nx = dims[3 * c], ny = dims[3 * c + 1], nz = dims[3 * c + 2];
+    if (nx < 1 || ny < 1 || nz < 1 || nx > 4096 || ny > 4096 || nz > 4096) {
+      delete b;
+      return bfail(SOPHIE_EINVAL, "cavity %d: sizes must be in [1, 4096]", c);
+    }
+    Dims d{};
+    d.nx = nx;
+    d.ny = ny;
+    d.nz = nz;
+    d.nxp = ((nx + 1) + 7) / 8 * 8;
+    d.ny1 = ny + 1;
+    d.nz1 = nz + 1;
+    d.plane = (long long)d.ny1 * d.nxp;
+    d.zstride = 6 * d.plane;
+    b->dims.push_back(d);
+    b->cells += (long long)nx * ny * nz;
+  }
+  b->src.resize(ncav);
+  const int rc = packed_create(ncav, dims, dx, dt, &b->pk);
+  if (rc) {
+    delete b;
+    return rc;
+  }
+  handle_register(b);
+  *out = b;
+  return SOPHIE_OK;
+}
+
+int sophie_batch_layout(sophie_batch* b, int* packed, int* extent, int* temporal_k) {
+  if (!b || !packed || !extent || !temporal_k) return bfail(SOPHIE_EINVAL, "NULL argument");
+  *packed = b->pk ? 1 : 0;
+  extent[0] = extent[1] = extent[2] = 0;
+  *temporal_k = 1;
+  if (b->pk) {
+    long long cells, gcells;
+    int tx, ty;
+    packed_info(b->pk, &cells, &gcells, &tx, &ty, temporal_k);
+    packed_extent(b->pk, extent);
+  }
+  return SOPHIE_OK;
+}
+
+int sophie_batch_cavity_origin(sophie_batch* b, int cav, int* xyz) {
+  const int rc = check_cav(b, cav);
+  if (rc) return rc;
+  if (!xyz) return bfail(SOPHIE_EINVAL, "NULL argument");
+  if (!b->pk) return bfail(SOPHIE_ENOTSUP, "not a packed batch");
+  return packed_origin(b->pk, cav, xyz);
+}
+
 int sophie_batch_destroy(sophie_batch* b) {
   if (!b) return SOPHIE_OK;
   if (!handle_release(b)) return bfail(SOPHIE_EINVAL, "not a live batch (already destroyed?)");
@@ -438,6 +519,7 @@ int sophie_batch_destroy(sophie_batch* b) {
 
 int sophie_batch_check_guards(sophie_batch* b, long long* bad_bytes) {
   if (!b || !bad_bytes) return bfail(SOPHIE_EINVAL, "NULL argument");
+  if (b->pk) return packed_check_guards(b->pk, bad_bytes);
   unsigned long long* d = nullptr;
   if (dev_malloc((void**)&d, sizeof(unsigned long long)) != cudaSuccess) {
     cudaGetLastError();
@@ -465,6 +547,7 @@ int sophie_batch_set_materials(sophie_batch* b, const float* eps, const float* s
       return bfail(SOPHIE_EINVAL, "eps_r[%lld] = %g must be >= 1 (+inf: conductor)", q, (double)eps[q]);
     return bfail(SOPHIE_EINVAL, "sigma[%lld] = %g must be finite and >= 0", q, (double)sig[q]);
   }
+  if (b->pk) return packed_set_materials(b->pk, eps, sig);
   BCUDA(cudaStreamSynchronize(b->stream));
   const int nc = b->ncav;
   std::vector<size_t> cofs(nc);
@@ -553,6 +636,12 @@ int sophie_batch_add_source(sophie_batch* b, int cav, int comp, int i, int j, in
     return bfail(SOPHIE_EINVAL, "bad waveform parameters");
   if ((int)b->src[cav].size() >= kBatchMaxSrc)
     return bfail(SOPHIE_EINVAL, "at most %d sources per cavity", kBatchMaxSrc);
+  if (b->pk) {
+    rc = packed_add_source(b->pk, cav, comp, i, j, k, amp, f0, bw, t0, kind);
+    if (rc) return rc;
+    b->src[cav].push_back({comp, kind, amp, f0, bw, t0, ((long long)k * d.ny1 + j) * d.nxp + i});
+    return SOPHIE_OK;
+  }
   const long long pos = ((long long)k * d.ny1 + j) * d.nxp + i;
   b->src[cav].push_back({comp, kind, amp, f0, bw, t0, pos});
   BCUDA(cudaStreamSynchronize(b->stream));
@@ -572,6 +661,7 @@ int sophie_batch_step(sophie_batch* b, int n) {
   if (!b) return bfail(SOPHIE_EINVAL, "NULL batch");
   if (n < 0) return bfail(SOPHIE_EINVAL, "n must be >= 0");
   if (n == 0) return SOPHIE_OK;
+  if (b->pk) return packed_step(b->pk, n);
   int rc = ensure_src_capacity(b, b->n + n);
   if (rc) return rc;
   if (!b->use_graph) {
@@ -609,13 +699,19 @@ int sophie_batch_step(sophie_batch* b, int n) {
 
 int sophie_batch_get_step(sophie_batch* b, long long* n) {
   if (!b || !n) return bfail(SOPHIE_EINVAL, "NULL argument");
-  *n = b->n;
+  *n = b->pk ? packed_step_count(b->pk) : b->n;
   return SOPHIE_OK;
 }
 
 int sophie_batch_info(sophie_batch* b, long long* cells, long long* work_items, int* tile_x, int* tile_y,
                       int* zchunk) {
   if (!b || !cells || !work_items || !tile_x || !tile_y || !zchunk) return bfail(SOPHIE_EINVAL, "NULL argument");
+  if (b->pk) {  // packed: the grid's cells, its step kernel's output tile, zchunk 0
+    int K = 1;
+    packed_info(b->pk, cells, work_items, tile_x, tile_y, &K);
+    *zchunk = 0;
+    return SOPHIE_OK;
+  }
   *cells = b->cells;
   *work_items = b->nitems;
   *tile_x = b->tile_x;
@@ -626,6 +722,7 @@ int sophie_batch_info(sophie_batch* b, long long* cells, long long* work_items, 
 
 int sophie_batch_energy(sophie_batch* b, double* W) {
   if (!b || !W) return bfail(SOPHIE_EINVAL, "NULL argument");
+  if (b->pk) return packed_energy(b->pk, W);
   const double dx = b->dx;
   const cudaError_t e = launch_batch_energy(b->d_desc, b->d_eitems, b->neitems, b->d_efirst, b->ncav, b->cur, b->S32,
                                             b->e_part, 0.5 * kEps0b * dx * dx * dx, b->e_out, b->stream);
@@ -644,6 +741,7 @@ int sophie_batch_set_fields(sophie_batch* b, int cav, int comp, const float* hos
   if (rc) return rc;
   if (!host) return bfail(SOPHIE_EINVAL, "NULL argument");
   if (comp < 0 || comp > 5) return bfail(SOPHIE_EINVAL, "comp must be in 0..5");
+  if (b->pk) return packed_set_fields(b->pk, cav, comp, host);
   for (int buf = 0; buf < 2; ++buf) {
     rc = copy_cavity_component(b, cav, comp, const_cast<float*>(host), true, buf);
     if (rc) return rc;
@@ -661,6 +759,7 @@ int sophie_batch_get_fields(sophie_batch* b, int cav, int comp, float* host) {
   if (rc) return rc;
   if (!host) return bfail(SOPHIE_EINVAL, "NULL argument");
   if (comp < 0 || comp > 5) return bfail(SOPHIE_EINVAL, "comp must be in 0..5");
+  if (b->pk) return packed_get_fields(b->pk, cav, comp, host);
   rc = copy_cavity_component(b, cav, comp, host, false, b->cur);
   if (rc) return rc;
   BCUDA(cudaStreamSynchronize(b->stream));
@@ -669,6 +768,7 @@ int sophie_batch_get_fields(sophie_batch* b, int cav, int comp, float* host) {
 
 int sophie_batch_reset(sophie_batch* b) {
   if (!b) return bfail(SOPHIE_EINVAL, "NULL batch");
+  if (b->pk) return packed_reset(b->pk);
   BCUDA(cudaMemsetAsync(b->arena, 0, b->abytes, b->stream));
   b->n = 0;
   b->cur = 0;
@@ -678,6 +778,7 @@ int sophie_batch_reset(sophie_batch* b) {
 int sophie_batch_set_stream(sophie_batch* b, void* cuda_stream) {
   if (!b) return bfail(SOPHIE_EINVAL, "NULL batch");
   if (!cuda_stream) return bfail(SOPHIE_EINVAL, "the batch needs a created stream (graphs cannot record the legacy stream)");
+  if (b->pk) return packed_set_stream(b->pk, cuda_stream);
   BCUDA(cudaStreamSynchronize(b->stream));
   if (b->own_stream) cudaStreamDestroy(b->stream);
   b->own_stream = false;
@@ -688,6 +789,11 @@ int sophie_batch_set_stream(sophie_batch* b, void* cuda_stream) {
 
 int sophie_batch_configure(sophie_batch* b, int tile_x, int tile_y, int zchunk, int use_graph) {
   if (!b) return bfail(SOPHIE_EINVAL, "NULL batch");
+  if (b->pk) {  // the packed grid's tilings come from its autotuner
+    if (tile_x || tile_y || zchunk) return bfail(SOPHIE_ENOTSUP, "a packed batch takes no tile or z chunk settings");
+    packed_set_graph(b->pk, use_graph != 0);
+    return SOPHIE_OK;
+  }
   const int tx = tile_x ? tile_x : b->tile_x;
   const int ty = tile_y ? tile_y : (tile_x == 64 ? 16 : b->tile_y);
   if (!tiles_supported(tx, ty)) return bfail(SOPHIE_ENOTSUP, "tiles %d x %d not built (64 x 16; 32 x 4, 8, 16)", tx, ty);
@@ -700,6 +806,15 @@ int sophie_batch_configure(sophie_batch* b, int tile_x, int tile_y, int zchunk, 
 
 int sophie_batch_autotune(sophie_batch* b, int* tile_x, int* tile_y, int* zchunk, double* ms_per_step) {
   if (!b || !tile_x || !tile_y || !zchunk || !ms_per_step) return bfail(SOPHIE_EINVAL, "NULL argument");
+  if (b->pk) {  // k and the tilings of the packed grid; zchunk gets 0
+    int K = 1;
+    const int rc = packed_autotune(b->pk, &K, ms_per_step);
+    if (rc) return rc;
+    long long c0, c1;
+    packed_info(b->pk, &c0, &c1, tile_x, tile_y, &K);
+    *zchunk = 0;
+    return SOPHIE_OK;
+  }
   int rc = ensure_src_capacity(b, b->n + 1);
   if (rc) return rc;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -757,12 +872,13 @@ int sophie_batch_autotune(sophie_batch* b, int* tile_x, int* tile_y, int* zchunk
 
 int sophie_batch_launch_count(sophie_batch* b, long long* launches) {
   if (!b || !launches) return bfail(SOPHIE_EINVAL, "NULL argument");
-  *launches = b->launches;
+  *launches = b->pk ? packed_launches(b->pk) : b->launches;
   return SOPHIE_OK;
 }
 
 int sophie_batch_sync(sophie_batch* b) {
   if (!b) return bfail(SOPHIE_EINVAL, "NULL batch");
+  if (b->pk) return packed_sync(b->pk);
   return check_err(b);
 }
 

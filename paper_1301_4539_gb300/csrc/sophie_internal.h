@@ -63,6 +63,14 @@ struct SrcTable {
   long long pos[kMaxSources];  // index-point offset (z*ny1 + y)*nxp + x
   const float* val;            // [kMaxSources][cap]; val[s*cap + step]
   int cap;
+  // Many sources (a packed batch of cavities): when nbig > 0 the arrays above
+  // are unused and source q (0 <= q < nbig) is at point bpos[q], component
+  // bcomp[q], waveform row brow[q] of val; bpos is sorted ascending, sources
+  // on one point in the order they were added.
+  int nbig;
+  const long long* bpos;
+  const int* bcomp;
+  const int* brow;
 };
 
 struct PrbTable {
@@ -265,6 +273,30 @@ cudaError_t launch_batch_step(const CavityDesc* descs, const BatchItem* items, i
 cudaError_t launch_batch_energy(const CavityDesc* descs, const EnergyItem* items, int nitems, const int* first,
                                 int ncav, int cur, float S, double* partials, double scale, double* out,
                                 cudaStream_t s);
+// Packed layout of a batch (batch_packed.cu): the cavities in one grid with
+// conducting layers between them, run by the single-grid step kernels.
+struct PackedBatch;
+int packed_plan(int ncav, const int* dims, int* origins, int* extent);
+int packed_create(int ncav, const int* dims, double dx, double dt, PackedBatch** out);
+void packed_destroy(PackedBatch* p);
+int packed_set_materials(PackedBatch* p, const float* eps, const float* sig);
+int packed_add_source(PackedBatch* p, int cav, int comp, int i, int j, int k, double amp, double f0, double bw,
+                      double t0, int kind);
+int packed_step(PackedBatch* p, int n);
+int packed_energy(PackedBatch* p, double* W);
+int packed_set_fields(PackedBatch* p, int cav, int comp, const float* host);
+int packed_get_fields(PackedBatch* p, int cav, int comp, float* host);
+int packed_reset(PackedBatch* p);
+int packed_set_stream(PackedBatch* p, void* stream);
+void packed_set_graph(PackedBatch* p, bool use_graph);
+int packed_autotune(PackedBatch* p, int* K, double* ms);
+void packed_info(PackedBatch* p, long long* cells, long long* grid_cells, int* tile_x, int* tile_y, int* K);
+int packed_origin(PackedBatch* p, int cav, int* xyz);
+long long packed_launches(PackedBatch* p);
+int packed_sync(PackedBatch* p);
+void packed_extent(PackedBatch* p, int* ext);
+int packed_check_guards(PackedBatch* p, long long* bad);
+long long packed_step_count(PackedBatch* p);
 // Set the thread's last-error message (sophie_last_error) and return code.
 int report_error(int code, const char* msg);
 

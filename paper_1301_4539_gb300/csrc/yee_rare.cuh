@@ -13,6 +13,23 @@ namespace sophie {
 // bracket, in the order the sources were added.
 static __device__ __noinline__ float3 apply_sources(float3 b, long long pt, long long nstep,
                                                     const SrcTable* src) {
+  if (src->nbig > 0) {
+    // the first source at or after pt (binary search), then those on pt
+    int lo = 0, hi = src->nbig;
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      if (src->bpos[mid] < pt) lo = mid + 1;
+      else hi = mid;
+    }
+    for (int q = lo; q < src->nbig && src->bpos[q] == pt; ++q) {
+      const float v = src->val[(long long)src->brow[q] * src->cap + nstep];
+      const int c = src->bcomp[q];
+      if (c == 0) b.x = __fadd_rn(b.x, v);
+      else if (c == 1) b.y = __fadd_rn(b.y, v);
+      else b.z = __fadd_rn(b.z, v);
+    }
+    return b;
+  }
   for (int q = 0; q < src->n; ++q) {
     if (src->pos[q] != pt) continue;
     const float v = src->val[(long long)q * src->cap + nstep];

@@ -74,6 +74,10 @@ SIGNATURES = {
                                ctypes.POINTER(_I), ctypes.POINTER(_I)]),
     "sophie_batch_launch_count": (_I, [_P, ctypes.POINTER(_LL)]),
     "sophie_batch_sync": (_I, [_P]),
+    "sophie_batch_create_packed": (_I, [_I, _P, _D, _D, ctypes.POINTER(_P)]),
+    "sophie_batch_pack_plan": (_I, [_I, _P, _P, _P]),
+    "sophie_batch_layout": (_I, [_P, ctypes.POINTER(_I), _P, ctypes.POINTER(_I)]),
+    "sophie_batch_cavity_origin": (_I, [_P, _I, _P]),
     "sophie_check_guards": (_I, [_P, ctypes.POINTER(_LL)]),
     "sophie_batch_check_guards": (_I, [_P, ctypes.POINTER(_LL)]),
     "sophie_selftest_wait_timeout": (_I, [_P, ctypes.POINTER(_D)]),
@@ -429,6 +433,35 @@ def sophie_batch_create(dims, dx: float, dt: float) -> int:
     return h.value
 
 
+def sophie_batch_create_packed(dims, dx: float, dt: float) -> int:
+    d = np.ascontiguousarray(dims, dtype=np.int32).reshape(-1, 3)
+    h = _P()
+    _chk(load().sophie_batch_create_packed(len(d), d.ctypes.data, dx, dt, ctypes.byref(h)))
+    return h.value
+
+
+def sophie_batch_pack_plan(dims):
+    """(origins ncav x 3, extent 3) of the packed placement (host only)."""
+    d = np.ascontiguousarray(dims, dtype=np.int32).reshape(-1, 3)
+    org = np.zeros((len(d), 3), np.int32)
+    ext = np.zeros(3, np.int32)
+    _chk(load().sophie_batch_pack_plan(len(d), d.ctypes.data, org.ctypes.data, ext.ctypes.data))
+    return org, ext
+
+
+def sophie_batch_layout(b: int):
+    packed, k = _I(), _I()
+    ext = np.zeros(3, np.int32)
+    _chk(load().sophie_batch_layout(b, ctypes.byref(packed), ext.ctypes.data, ctypes.byref(k)))
+    return {"packed": bool(packed.value), "extent": tuple(int(v) for v in ext), "temporal_k": k.value}
+
+
+def sophie_batch_cavity_origin(b: int, cav: int):
+    o = np.zeros(3, np.int32)
+    _chk(load().sophie_batch_cavity_origin(b, cav, o.ctypes.data))
+    return tuple(int(v) for v in o)
+
+
 def sophie_batch_destroy(b: int) -> None:
     _chk(load().sophie_batch_destroy(b))
 
@@ -513,9 +546,9 @@ def sophie_batch_sync(b: int) -> None:
 class Batch:
     """Owning handle of a batch of cavities (marshalling only)."""
 
-    def __init__(self, dims, dx: float, dt: float):
+    def __init__(self, dims, dx: float, dt: float, packed: bool = False):
         self.dims = [tuple(int(v) for v in d) for d in dims]
-        self.h = sophie_batch_create(self.dims, dx, dt)
+        self.h = (sophie_batch_create_packed if packed else sophie_batch_create)(self.dims, dx, dt)
 
     def close(self):
         if self.h:
@@ -580,3 +613,9 @@ class Batch:
 
     def sync(self):
         sophie_batch_sync(self.h)
+
+    def layout(self):
+        return sophie_batch_layout(self.h)
+
+    def origin(self, cav):
+        return sophie_batch_cavity_origin(self.h, cav)
