@@ -317,6 +317,17 @@ StepArgs make_step_args(sophie_grid* g) {
     a.prb.n += 1;
   }
   a.prb.buf = g->pbuf;
+  // 2-byte and hi+lo storage with six equal scales: the step kernels compute
+  // on the scaled values (no scale multiplications); currents are scaled and
+  // probe samples unscaled instead (both exact: powers of two).
+  if ((g->fmt == kF16 || g->fmt == kBF16 || g->fmt == kF16HL) && g->sc[0] == g->sc[1] && g->sc[0] == g->sc[2] &&
+      g->sc[0] == g->sc[3] && g->sc[0] == g->sc[4] && g->sc[0] == g->sc[5]) {
+    a.fold = 1;
+    a.src.vmul_on = 1;
+    a.src.vmul = a.sc[0];
+    a.prb.pmul_on = 1;
+    a.prb.pmul = a.isc[0];
+  }
   if (g->rat) {
     const Dims& d = g->d;
     const long long off[6] = {0, d.nx, d.nx + d.ny, d.nx + d.ny + d.nz, 2ll * d.nx + d.ny + d.nz + 1,

@@ -71,6 +71,10 @@ struct SrcTable {
   const long long* bpos;
   const int* bcomp;
   const int* brow;
+  // Unit-scale storage forms (yee_store.cuh kF16U...): the kernels compute on
+  // scaled fields, so the currents are multiplied by vmul when vmul_on.
+  int vmul_on;
+  float vmul;
 };
 
 struct PrbTable {
@@ -79,12 +83,18 @@ struct PrbTable {
   long long pos[kMaxProbes];
   float* buf;  // [kMaxProbes][cap]; buf[p*cap + step]
   int cap;
+  // Unit-scale storage forms: samples of scaled fields, multiplied by pmul
+  // (the inverse scale) when pmul_on.
+  int pmul_on;
+  float pmul;
 };
 
 struct StepArgs {
   const void* fin;  // field buffers in the storage format `fmt`
   void* fout;
   int fmt;          // StoreFmt (yee_store.cuh): 0 float, 1 half, 2 bfloat16
+  int fold;         // 2-byte and hi+lo forms with six equal scales: the step
+                    // kernels run the unit-scale form of fmt (kF16U, ...)
   float sc[6];      // stored value = field * sc[comp] (2-byte formats)
   float isc[6];     // 1 / sc
   const uint32_t* mat;

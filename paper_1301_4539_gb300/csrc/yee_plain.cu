@@ -625,9 +625,10 @@ cudaError_t launch_step_plain(const StepArgs& a, const CUtensorMap& tmF, const C
                               const PlainTiling& t, cudaStream_t s) {
   switch (a.fmt) {
     case kF32: return launch_plain_f<kF32>(a, tmF, tmM, t, s);
-    case kF16: return launch_plain_f<kF16>(a, tmF, tmM, t, s);
-    case kBF16: return launch_plain_f<kBF16>(a, tmF, tmM, t, s);
-    case kF16HL: return launch_plain_f<kF16HL>(a, tmF, tmM, t, s);
+    case kF16: return a.fold ? launch_plain_f<kF16U>(a, tmF, tmM, t, s) : launch_plain_f<kF16>(a, tmF, tmM, t, s);
+    case kBF16: return a.fold ? launch_plain_f<kBF16U>(a, tmF, tmM, t, s) : launch_plain_f<kBF16>(a, tmF, tmM, t, s);
+    case kF16HL:
+      return a.fold ? launch_plain_f<kF16HLU>(a, tmF, tmM, t, s) : launch_plain_f<kF16HL>(a, tmF, tmM, t, s);
     case kF24: return launch_plain_f<kF24>(a, tmF, tmM, t, s);
     default: return cudaErrorInvalidValue;
   }

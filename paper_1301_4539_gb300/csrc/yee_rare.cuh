@@ -22,7 +22,8 @@ static __device__ __noinline__ float3 apply_sources(float3 b, long long pt, long
       else hi = mid;
     }
     for (int q = lo; q < src->nbig && src->bpos[q] == pt; ++q) {
-      const float v = src->val[(long long)src->brow[q] * src->cap + nstep];
+      float v = src->val[(long long)src->brow[q] * src->cap + nstep];
+      if (src->vmul_on) v = __fmul_rn(v, src->vmul);
       const int c = src->bcomp[q];
       if (c == 0) b.x = __fadd_rn(b.x, v);
       else if (c == 1) b.y = __fadd_rn(b.y, v);
@@ -32,7 +33,8 @@ static __device__ __noinline__ float3 apply_sources(float3 b, long long pt, long
   }
   for (int q = 0; q < src->n; ++q) {
     if (src->pos[q] != pt) continue;
-    const float v = src->val[(long long)q * src->cap + nstep];
+    float v = src->val[(long long)q * src->cap + nstep];
+    if (src->vmul_on) v = __fmul_rn(v, src->vmul);
     if (src->comp[q] == 0) b.x = __fadd_rn(b.x, v);
     else if (src->comp[q] == 1) b.y = __fadd_rn(b.y, v);
     else b.z = __fadd_rn(b.z, v);
@@ -46,7 +48,8 @@ static __device__ __noinline__ void record_probes(long long pt, long long nstep,
   for (int q = 0; q < prb->n; ++q) {
     if (prb->pos[q] != pt) continue;
     const int c = prb->comp[q];
-    const float v = c == 0 ? ex : c == 1 ? ey : c == 2 ? ez : c == 3 ? hx : c == 4 ? hy : hz;
+    float v = c == 0 ? ex : c == 1 ? ey : c == 2 ? ez : c == 3 ? hx : c == 4 ? hy : hz;
+    if (prb->pmul_on) v = __fmul_rn(v, prb->pmul);
     prb->buf[(long long)q * prb->cap + nstep] = v;
   }
 }

@@ -29,7 +29,14 @@
 
 namespace sophie {
 
-enum StoreFmt : int { kF32 = 0, kF16 = 1, kBF16 = 2, kF16HL = 3, kF24 = 4 };
+enum StoreFmt : int { kF32 = 0, kF16 = 1, kBF16 = 2, kF16HL = 3, kF24 = 4,
+                      // the step kernels' forms of kF16 / kBF16 / kF16HL when all six
+                      // scales are equal: the kernel then computes on the scaled
+                      // values themselves (the scheme is linear and a power-of-two
+                      // scale commutes with round-to-nearest), with no scale
+                      // multiplications; sources are scaled and probe samples
+                      // unscaled instead (SrcTable::vmul, PrbTable::pmul)
+                      kF16U = 5, kBF16U = 6, kF16HLU = 7 };
 
 template <int F>
 struct Store;
@@ -139,8 +146,64 @@ struct Store<kF24> {
   }
 };
 
+// The unit-scale forms: the base format's storage with no scale factors.
+template <>
+struct Store<kF16U> {
+  using T = __half;
+  static constexpr int kAlign = 8;
+  static __device__ __forceinline__ float2 ld2(const T* p, float) {
+    return __half22float2(*reinterpret_cast<const __half2*>(p));
+  }
+  static __device__ __forceinline__ float ld(const T* p, float) { return __half2float(*p); }
+  static __device__ __forceinline__ void st2(T* p, float a, float b, float) {
+    *reinterpret_cast<__half2*>(p) = __floats2half2_rn(a, b);
+  }
+  static __device__ __forceinline__ void st(T* p, float a, float) { *p = __float2half_rn(a); }
+};
+
+template <>
+struct Store<kBF16U> {
+  using T = __nv_bfloat16;
+  static constexpr int kAlign = 8;
+  static __device__ __forceinline__ float2 ld2(const T* p, float) {
+    return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(p));
+  }
+  static __device__ __forceinline__ float ld(const T* p, float) { return __bfloat162float(*p); }
+  static __device__ __forceinline__ void st2(T* p, float a, float b, float) {
+    *reinterpret_cast<__nv_bfloat162*>(p) = __floats2bfloat162_rn(a, b);
+  }
+  static __device__ __forceinline__ void st(T* p, float a, float) { *p = __float2bfloat16_rn(a); }
+};
+
+template <>
+struct Store<kF16HLU> {
+  using T = __half2;  // .x = hi, .y = lo
+  static constexpr int kAlign = 4;
+  static __device__ __forceinline__ float dec(__half2 h) { return __fadd_rn(__low2float(h), __high2float(h)); }
+  static __device__ __forceinline__ __half2 enc(float v) {
+    const __half hi = __float2half_rn(v);
+    const __half lo = __float2half_rn(__fsub_rn(v, __half2float(hi)));
+    return __halves2half2(hi, lo);
+  }
+  static __device__ __forceinline__ float2 ld2(const T* p, float) {
+    const uint2 raw = *reinterpret_cast<const uint2*>(p);
+    return make_float2(dec(*reinterpret_cast<const __half2*>(&raw.x)), dec(*reinterpret_cast<const __half2*>(&raw.y)));
+  }
+  static __device__ __forceinline__ float ld(const T* p, float) { return dec(*p); }
+  static __device__ __forceinline__ void st2(T* p, float a, float b, float) {
+    const __half2 ha = enc(a), hb = enc(b);
+    uint2 raw;
+    raw.x = *reinterpret_cast<const unsigned int*>(&ha);
+    raw.y = *reinterpret_cast<const unsigned int*>(&hb);
+    *reinterpret_cast<uint2*>(p) = raw;
+  }
+  static __device__ __forceinline__ void st(T* p, float a, float) { *p = enc(a); }
+};
+
 // Bytes per stored element (a value, or for kF24 one of a value's 2-byte parts).
-__host__ __device__ constexpr int store_bytes(int fmt) { return fmt == kF16 || fmt == kBF16 || fmt == kF24 ? 2 : 4; }
+__host__ __device__ constexpr int store_bytes(int fmt) {
+  return fmt == kF16 || fmt == kBF16 || fmt == kF24 || fmt == kF16U || fmt == kBF16U ? 2 : 4;
+}
 // Planes per z slab: six components, or nine 2-byte planes for kF24.
 __host__ __device__ constexpr int store_planes(int fmt) { return fmt == kF24 ? 9 : 6; }
 
