@@ -359,6 +359,20 @@ int sophie_profile_read(sophie_grid *g, int kernel, long long *launches, double 
  */
 int sophie_objective_forward(sophie_grid *g, int nsteps, int comp, int i, int j, int k, int checkpoint_every,
                              double *J);
+/*
+ * sophie_objective_set_design registers the box of design cells (as for
+ * sophie_objective_grad_eps) for the following objective records; ni = nj =
+ * nk = 0 clears it. With a box registered, sophie_objective_forward runs one
+ * step per launch and gathers, after every step, e^n and the E bracket on the
+ * box's design edges ([nsteps][edges] floats twice, kept when they fit a
+ * quarter of the free device memory and 8 GB; otherwise the record is the
+ * checkpointed one); sophie_objective_grad_eps for that box then sweeps back
+ * without recomputing any step. Gradients are the same either way (the same
+ * float values are gathered). A traced record keeps no checkpoints: a
+ * gradient for another box is refused (EINVAL) until the objective is
+ * recorded again. Errors: EINVAL (NULL, box outside the cells).
+ */
+int sophie_objective_set_design(sophie_grid *g, int i0, int j0, int k0, int ni, int nj, int nk);
 int sophie_objective_grad_eps(sophie_grid *g, int i0, int j0, int k0, int ni, int nj, int nk, double *grad);
 int sophie_objective_release(sophie_grid *g);
 

@@ -28,6 +28,7 @@ class ProbeObjective(torch.autograd.Function):
         eps[k0:k0 + nk, j0:j0 + nj, i0:i0 + ni] = eps_design.detach().to("cpu", torch.float32).numpy()
         grid.set_materials(eps, sigma)
         grid.reset()
+        grid.objective_set_design(*box)  # the backward's box: traces instead of recomputation
         J = grid.objective_forward(nsteps, *probe, checkpoint_every)
         ctx.grid, ctx.box = grid, box
         ctx.dtype, ctx.device = eps_design.dtype, eps_design.device

@@ -82,6 +82,14 @@ struct Tape {
   double* gcb = nullptr;  // dJ/dCb, dJ/dCa per design edge
   double* gca = nullptr;
   int edge_cap = 0, tr_cap = 0;
+  // Traced record (a design box registered before the forward pass): e^n and
+  // the bracket on the box's design edges for every step, [N][nedge] each,
+  // gathered during the forward pass, so the reverse sweep needs no recompute.
+  bool traced = false;
+  int tbox[6] = {0, 0, 0, 0, 0, 0};
+  int tnedge = 0;
+  float* etr_all = nullptr;
+  float* ctr_all = nullptr;
 };
 
 }  // namespace grid
@@ -165,6 +173,9 @@ struct sophie_grid {
   long long rpair_off[3] = {0, 0, 0};  // float offset of each pair array's index 0
   long long gen = 0;       // bumped by every change of fields, materials, sources or mesh
   bool obj_rec = false;    // the step kernels also sample the objective point
+  // Design box registered for the next objective record (sophie_objective_set_design).
+  bool design_set = false;
+  int design[6] = {0, 0, 0, 0, 0, 0};
   sophie::grid::Tape tape;
 };
 

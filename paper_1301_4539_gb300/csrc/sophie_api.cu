@@ -396,7 +396,7 @@ namespace grid {
 void free_tape(Tape& t) {
   for (void* p : t.ck) cudaFree(p);
   t.ck.clear();
-  void* bufs[] = {t.samples, t.R[0], t.R[1], t.L[0], t.L[1], t.ecomp, t.ept, t.etr, t.ctr, t.gcb, t.gca};
+  void* bufs[] = {t.samples, t.R[0], t.R[1], t.L[0], t.L[1], t.ecomp, t.ept, t.etr, t.ctr, t.gcb, t.gca, t.etr_all, t.ctr_all};
   for (void* p : bufs)
     if (p) cudaFree(p);
   t = Tape{};

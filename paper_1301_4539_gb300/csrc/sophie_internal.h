@@ -339,6 +339,12 @@ cudaError_t launch_gather(const StepArgs& a, const int* edge_comp, const long lo
 // gcb[t] += l_e(edge t) * c_in[t], gca[t] += l_e(edge t) * e_in[t] (double).
 cudaError_t launch_grad_accum(const float* l, const Dims& d, const int* edge_comp, const long long* edge_pt, int nedge,
                               const float* e_in, const float* c_in, double* gcb, double* gca, cudaStream_t s);
+// The two above in one launch: l(comp at pt) += two_dt * sample[0], then the
+// accumulation; t_obj = the design edge on (comp, pt), or -1.
+cudaError_t launch_objective_grad_accum(float* l, const Dims& d, int comp, long long pt, const float* sample,
+                                        double two_dt, int t_obj, const int* edge_comp, const long long* edge_pt,
+                                        int nedge, const float* e_in, const float* c_in, double* gcb, double* gca,
+                                        cudaStream_t s);
 // l(comp at point pt) += two_dt * sample[0].
 cudaError_t launch_add_objective(float* l, const Dims& d, int comp, long long pt, const float* sample, double two_dt,
                                  cudaStream_t s);

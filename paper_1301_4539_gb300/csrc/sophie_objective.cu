@@ -16,7 +16,90 @@
 using namespace sophie;
 using namespace sophie::grid;
 
+namespace {
+
+// The design edges of a box of cells: the interior, non-conducting edges of
+// its cells, with the float Cb the kernels use and the derivatives of the
+// edge's (Cb, Ca) with respect to its mean eps (box index -> edge index map).
+struct DesignEdges {
+  int ext[3][3];
+  std::vector<int> map[3];
+  std::vector<int> comp;
+  std::vector<long long> pt;
+  std::vector<double> dcb, dca;
+  std::vector<float> cbf;
+};
+
+void design_edges(const sophie_grid* g, int i0, int j0, int k0, int ni, int nj, int nk, DesignEdges& de) {
+  const Dims& d = g->d;
+  const int ext[3][3] = {{ni, nj + 1, nk + 1}, {ni + 1, nj, nk + 1}, {ni + 1, nj + 1, nk}};
+  memcpy(de.ext, ext, sizeof ext);
+  for (int c = 0; c < 3; ++c) {
+    de.map[c].assign((size_t)ext[c][0] * ext[c][1] * ext[c][2], -1);
+    for (int kk = 0; kk < ext[c][2]; ++kk)
+      for (int jj = 0; jj < ext[c][1]; ++jj)
+        for (int ii = 0; ii < ext[c][0]; ++ii) {
+          const int i = i0 + ii, j = j0 + jj, k = k0 + kk;
+          if (!e_edge_interior(d, c, i, j, k)) continue;
+          const long long pt = point_index(d, i, j, k);
+          const uint32_t w = g->mat_host[pt];
+          const float cb_edge = (w & kExpFlag) ? g->ecoef_h[3 * (size_t)(w >> 3) + c].y : g->coef_h[cls_of(w, c)].y;
+          if (cb_edge == 0.f) continue;  // edge of a conducting cell: no eps dependence
+          double e, sg;
+          if (w & kExpFlag) {
+            const size_t q = w >> 3;
+            e = g->eeps_h[3 * q + c];
+            sg = g->esig_h[3 * q + c];
+          } else {
+            e = g->eps_h[cls_of(w, c)];
+            sg = g->sig_h[cls_of(w, c)];
+          }
+          // Cb = (S/e)/(1+beta), Ca = (1-beta)/(1+beta), beta = sigma dt/(2 eps0 e)
+          const double beta = (sg * g->dt) / (2.0 * kEps0 * e);
+          const double cb = (g->S64 / e) / (1.0 + beta);
+          de.map[c][((size_t)kk * ext[c][1] + jj) * ext[c][0] + ii] = (int)de.pt.size();
+          de.cbf.push_back(cb_edge);
+          de.comp.push_back(c);
+          de.pt.push_back(pt);
+          de.dcb.push_back(-cb / (e * (1.0 + beta)));
+          de.dca.push_back(2.0 * beta / (e * (1.0 + beta) * (1.0 + beta)));
+        }
+  }
+}
+
+bool box_ok(const Dims& d, int i0, int j0, int k0, int ni, int nj, int nk) {
+  return ni >= 1 && nj >= 1 && nk >= 1 && i0 >= 0 && j0 >= 0 && k0 >= 0 && i0 + ni <= d.nx && j0 + nj <= d.ny &&
+         k0 + nk <= d.nz;
+}
+
+// Grow device array *p to hold `bytes` (contents not kept).
+bool grow_dev(void** p, size_t bytes) {
+  if (*p) cudaFree(*p);
+  *p = nullptr;
+  if (dev_malloc(p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    return false;
+  }
+  return true;
+}
+
+}  // namespace
+
 extern "C" {
+
+int sophie_objective_set_design(sophie_grid* g, int i0, int j0, int k0, int ni, int nj, int nk) {
+  if (!g) return fail(SOPHIE_EINVAL, "NULL grid");
+  if (ni == 0 && nj == 0 && nk == 0) {
+    g->design_set = false;
+    return SOPHIE_OK;
+  }
+  if (!box_ok(g->d, i0, j0, k0, ni, nj, nk)) return fail(SOPHIE_EINVAL, "design box outside the grid's cells");
+  const int b[6] = {i0, j0, k0, ni, nj, nk};
+  memcpy(g->design, b, sizeof b);
+  g->design_set = true;
+  return SOPHIE_OK;
+}
 
 int sophie_objective_release(sophie_grid* g) {
   if (!g) return fail(SOPHIE_EINVAL, "NULL grid");
@@ -46,7 +129,39 @@ int sophie_objective_forward(sophie_grid* g, int nsteps, int comp, int i, int j,
   int rc = ensure_capacity(g, g->n + nsteps);
   if (rc) return rc;
   CUDA_TRY(cudaStreamSynchronize(g->stream));
-  while ((int)t.ck.size() < nseg) {
+  // Traced record: with a registered design box whose traces fit (both
+  // [nsteps][nedge] float arrays within a quarter of the free device memory
+  // and 8 GB), the forward pass runs one step per launch and gathers e^n and
+  // the bracket on the design edges after every step; the reverse sweep then
+  // needs neither checkpoints nor recomputation.
+  t.traced = false;
+  bool trace = false;
+  int nedge = 0;
+  if (g->design_set) {
+    DesignEdges de;
+    design_edges(g, g->design[0], g->design[1], g->design[2], g->design[3], g->design[4], g->design[5], de);
+    nedge = (int)de.pt.size();
+    const size_t bytes = (size_t)nedge * nsteps * 4;
+    size_t fr = 0, tot = 0;
+    if (nedge > 0 && cudaMemGetInfo(&fr, &tot) == cudaSuccess && 2 * bytes <= std::min<size_t>(fr / 4, 8ull << 30)) {
+      trace = grow_dev((void**)&t.etr_all, bytes) && grow_dev((void**)&t.ctr_all, bytes);
+      if (trace && nedge > t.edge_cap) {
+        trace = grow_dev((void**)&t.ecomp, (size_t)nedge * 4) && grow_dev((void**)&t.ept, (size_t)nedge * 8) &&
+                grow_dev((void**)&t.gcb, (size_t)nedge * 8) && grow_dev((void**)&t.gca, (size_t)nedge * 8);
+        t.edge_cap = trace ? nedge : 0;
+        t.tr_cap = 0;
+      }
+      if (trace) {
+        CUDA_TRY(cudaMemcpyAsync(t.ecomp, de.comp.data(), (size_t)nedge * 4, cudaMemcpyHostToDevice, g->stream));
+        CUDA_TRY(cudaMemcpyAsync(t.ept, de.pt.data(), (size_t)nedge * 8, cudaMemcpyHostToDevice, g->stream));
+      } else {
+        if (t.etr_all) cudaFree(t.etr_all);
+        if (t.ctr_all) cudaFree(t.ctr_all);
+        t.etr_all = t.ctr_all = nullptr;
+      }
+    }
+  }
+  while (!trace && (int)t.ck.size() < nseg) {
     void* p = nullptr;
     if (dev_malloc((void**)&p, fbytes) != cudaSuccess) {
       cudaGetLastError();
@@ -75,7 +190,25 @@ int sophie_objective_forward(sophie_grid* g, int nsteps, int comp, int i, int j,
   g->launches++;
   const int slot = (int)g->prb.size();
   g->obj_rec = true;
-  for (int sg = 0; sg < nseg; ++sg) {
+  for (int n = 0; trace && n < nsteps; ++n) {
+    rc = sophie_step(g, 1);
+    if (rc) {
+      g->obj_rec = false;
+      return rc;
+    }
+    StepArgs a = make_step_args(g);
+    a.fin = g->F[1 - g->cur];  // the state before the step
+    a.fout = g->F[g->cur];     // after it
+    a.n0 = g->n - 1;
+    const cudaError_t e = launch_gather(a, t.ecomp, t.ept, nedge, t.etr_all + (size_t)n * nedge,
+                                        t.ctr_all + (size_t)n * nedge, g->stream);
+    if (e != cudaSuccess) {
+      g->obj_rec = false;
+      return fail(SOPHIE_ECUDA, "gather launch failed: %s", cudaGetErrorString(e));
+    }
+    g->launches++;
+  }
+  for (int sg = 0; !trace && sg < nseg; ++sg) {
     const cudaError_t e = cudaMemcpyAsync(t.ck[sg], g->F[g->cur], fbytes, cudaMemcpyDeviceToDevice, g->stream);
     if (e != cudaSuccess) {
       g->obj_rec = false;
@@ -101,6 +234,9 @@ int sophie_objective_forward(sophie_grid* g, int nsteps, int comp, int i, int j,
   if (!std::isfinite(*J)) return fail(SOPHIE_ENONFINITE, "objective is not finite");
   t.valid = true;
   t.gen = g->gen;
+  t.traced = trace;
+  t.tnedge = nedge;
+  if (trace) memcpy(t.tbox, g->design, sizeof t.tbox);
   return SOPHIE_OK;
 }
 
@@ -114,43 +250,15 @@ int sophie_objective_grad_eps(sophie_grid* g, int i0, int j0, int k0, int ni, in
       k0 + nk > d.nz)
     return fail(SOPHIE_EINVAL, "design box outside the grid's cells");
   // Design edges: interior edges of the box's cells; box index -> edge index.
-  const int ext[3][3] = {{ni, nj + 1, nk + 1}, {ni + 1, nj, nk + 1}, {ni + 1, nj + 1, nk}};
-  std::vector<int> map[3];
-  std::vector<int> hcomp;
-  std::vector<long long> hpt;
-  std::vector<double> dcb, dca;
-  std::vector<float> cbf;  // the float Cb the step kernels use on each design edge
-  for (int c = 0; c < 3; ++c) {
-    map[c].assign((size_t)ext[c][0] * ext[c][1] * ext[c][2], -1);
-    for (int kk = 0; kk < ext[c][2]; ++kk)
-      for (int jj = 0; jj < ext[c][1]; ++jj)
-        for (int ii = 0; ii < ext[c][0]; ++ii) {
-          const int i = i0 + ii, j = j0 + jj, k = k0 + kk;
-          if (!e_edge_interior(d, c, i, j, k)) continue;
-          const long long pt = point_index(d, i, j, k);
-          const uint32_t w = g->mat_host[pt];
-          const float cb_edge = (w & kExpFlag) ? g->ecoef_h[3 * (size_t)(w >> 3) + c].y : g->coef_h[cls_of(w, c)].y;
-          if (cb_edge == 0.f) continue;  // edge of a conducting cell: no eps dependence
-          double e, sg;
-          if (w & kExpFlag) {
-            const size_t q = w >> 3;
-            e = g->eeps_h[3 * q + c];
-            sg = g->esig_h[3 * q + c];
-          } else {
-            e = g->eps_h[cls_of(w, c)];
-            sg = g->sig_h[cls_of(w, c)];
-          }
-          // Cb = (S/e)/(1+beta), Ca = (1-beta)/(1+beta), beta = sigma dt/(2 eps0 e)
-          const double beta = (sg * g->dt) / (2.0 * kEps0 * e);
-          const double cb = (g->S64 / e) / (1.0 + beta);
-          map[c][((size_t)kk * ext[c][1] + jj) * ext[c][0] + ii] = (int)hpt.size();
-          cbf.push_back(cb_edge);
-          hcomp.push_back(c);
-          hpt.push_back(pt);
-          dcb.push_back(-cb / (e * (1.0 + beta)));
-          dca.push_back(2.0 * beta / (e * (1.0 + beta) * (1.0 + beta)));
-        }
-  }
+  DesignEdges de;
+  design_edges(g, i0, j0, k0, ni, nj, nk, de);
+  const int(&ext)[3][3] = de.ext;
+  const std::vector<int>* map = de.map;
+  const std::vector<int>& hcomp = de.comp;
+  const std::vector<long long>& hpt = de.pt;
+  const std::vector<double>& dcb = de.dcb;
+  const std::vector<double>& dca = de.dca;
+  const std::vector<float>& cbf = de.cbf;  // the float Cb the step kernels use on each design edge
   const int nedge = (int)hpt.size();
   const size_t fbytes = (size_t)d.zstride * d.nz1 * 4;
   CUDA_TRY(cudaStreamSynchronize(g->stream));
@@ -223,11 +331,25 @@ int sophie_objective_grad_eps(sophie_grid* g, int i0, int j0, int k0, int ni, in
     }
   }
   const double two_dt = 2.0 * g->dt * obj_scale;
+  // the design edge on the objective's component and point, if any
+  int t_obj = -1;
+  for (int q = 0; q < nedge && t.comp < 3; ++q)
+    if (hpt[q] == t.pt && hcomp[q] == t.comp) t_obj = q;
   int lc = 0;
   const int nseg = (t.N + t.K - 1) / t.K;
-  for (int sg = nseg - 1; sg >= 0; --sg) {
-    const long long ns = t.n0 + (long long)sg * t.K;
-    const int len = std::min(t.K, t.N - sg * t.K);
+  // A traced record of this box: the traces of every step are on the device
+  // already (gathered by the forward pass), so the reverse sweep runs as one
+  // segment of all N steps with no recomputation.
+  const int b6[6] = {i0, j0, k0, ni, nj, nk};
+  const bool traced = t.traced && nedge == t.tnedge && memcmp(b6, t.tbox, sizeof b6) == 0;
+  if (t.traced && !traced)  // a traced record keeps no checkpoints
+    return fail(SOPHIE_EINVAL, "the objective record traced another design box; record again for this box");
+  for (int sg = traced ? 0 : nseg - 1; sg >= 0; --sg) {
+    const long long ns = traced ? t.n0 : t.n0 + (long long)sg * t.K;
+    const int len = traced ? t.N : std::min(t.K, t.N - sg * t.K);
+    float* const etr = traced ? t.etr_all : t.etr;
+    float* const ctr = traced ? t.ctr_all : t.ctr;
+    if (!traced) {
     // Recompute the segment from its checkpoint, keeping the design-edge values.
     CUDA_TRY(cudaMemcpyAsync(t.R[0], t.ck[sg], fbytes, cudaMemcpyDeviceToDevice, g->stream));
     for (int m = 0; m < len; ++m) {
@@ -252,14 +374,14 @@ int sophie_objective_grad_eps(sophie_grid* g, int i0, int j0, int k0, int ni, in
       int rc = prof_drain(g);
       if (rc) return rc;
     }
+    }  // recompute
     // Reverse sweep over the segment.
     for (int m = len - 1; m >= 0; --m) {
       const long long n = ns + m;
       float* l = static_cast<float*>(t.L[lc]);
-      cudaError_t e = launch_add_objective(l, d, t.comp, t.pt, t.samples + (n - t.n0), two_dt, g->stream);
-      if (e == cudaSuccess)
-        e = launch_grad_accum(l, d, t.ecomp, t.ept, nedge, t.etr + (size_t)m * nedge, t.ctr + (size_t)m * nedge,
-                              t.gcb, t.gca, g->stream);
+      cudaError_t e = launch_objective_grad_accum(l, d, t.comp, t.pt, t.samples + (n - t.n0), two_dt, t_obj, t.ecomp,
+                                                  t.ept, nedge, etr + (size_t)m * nedge, ctr + (size_t)m * nedge,
+                                                  t.gcb, t.gca, g->stream);
       if (e == cudaSuccess) {
         StepArgs a = make_step_args(g);
         a.fin = t.L[lc];
@@ -276,7 +398,7 @@ int sophie_objective_grad_eps(sophie_grid* g, int i0, int j0, int k0, int ni, in
         }
       }
       if (e != cudaSuccess) return fail(SOPHIE_ECUDA, "adjoint launch failed: %s", cudaGetErrorString(e));
-      g->launches += nedge ? 3 : 2;
+      g->launches += 2;
       lc = 1 - lc;
     }
   }

@@ -143,6 +143,28 @@ __global__ void grad_accum_kernel(const float* l, Dims d, const int* edge_comp, 
   gca[t] += le * (double)e_in[t];
 }
 
+// The objective's direct term l[comp at pt] += 2 dt f (f = sample[0]) and
+// then the accumulation of grad_accum_kernel, in one launch: the objective's
+// entry is read and written by one thread only (the design edge on it, t_obj,
+// or the extra thread nedge when it is not a design edge), so no thread reads
+// it while it changes.
+__global__ void objective_grad_accum_kernel(float* l, Dims d, int comp, long long opt, const float* sample,
+                                            double two_dt, int t_obj, const int* edge_comp, const long long* edge_pt,
+                                            int nedge, const float* e_in, const float* c_in, double* gcb, double* gca) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t > nedge) return;
+  const long long sz = (long long)d.ny1 * d.nxp;
+  if (t == (t_obj >= 0 ? t_obj : nedge)) {
+    float* p = l + (opt / sz) * d.zstride + (long long)comp * d.plane + opt % sz;
+    *p = __fadd_rn(*p, (float)(two_dt * (double)sample[0]));
+  }
+  if (t == nedge) return;
+  const long long pt = edge_pt[t];
+  const double le = l[(pt / sz) * d.zstride + (long long)edge_comp[t] * d.plane + pt % sz];
+  gcb[t] += le * (double)c_in[t];
+  gca[t] += le * (double)e_in[t];
+}
+
 // The objective's direct term: l[comp at pt] += 2 dt f, f = sample[0].
 __global__ void add_objective_kernel(float* l, Dims d, int comp, long long pt, const float* sample, double two_dt) {
   const long long sz = (long long)d.ny1 * d.nxp;
@@ -169,6 +191,15 @@ cudaError_t launch_grad_accum(const float* l, const Dims& d, const int* edge_com
                               const float* e_in, const float* c_in, double* gcb, double* gca, cudaStream_t s) {
   if (nedge <= 0) return cudaSuccess;
   grad_accum_kernel<<<(nedge + 255) / 256, 256, 0, s>>>(l, d, edge_comp, edge_pt, nedge, e_in, c_in, gcb, gca);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_objective_grad_accum(float* l, const Dims& d, int comp, long long pt, const float* sample,
+                                        double two_dt, int t_obj, const int* edge_comp, const long long* edge_pt,
+                                        int nedge, const float* e_in, const float* c_in, double* gcb, double* gca,
+                                        cudaStream_t s) {
+  objective_grad_accum_kernel<<<(nedge + 1 + 255) / 256, 256, 0, s>>>(l, d, comp, pt, sample, two_dt, t_obj, edge_comp,
+                                                                      edge_pt, nedge, e_in, c_in, gcb, gca);
   return cudaGetLastError();
 }
 

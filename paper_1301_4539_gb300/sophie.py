@@ -56,6 +56,7 @@ SIGNATURES = {
     "sophie_objective_forward": (_I, [_P, _I, _I, _I, _I, _I, _I, ctypes.POINTER(_D)]),
     "sophie_objective_grad_eps": (_I, [_P, _I, _I, _I, _I, _I, _I, _P]),
     "sophie_objective_release": (_I, [_P]),
+    "sophie_objective_set_design": (_I, [_P, _I, _I, _I, _I, _I, _I]),
     "sophie_batch_create": (_I, [_I, _P, _D, _D, ctypes.POINTER(_P)]),
     "sophie_batch_destroy": (_I, [_P]),
     "sophie_batch_set_materials": (_I, [_P, _P, _P]),
@@ -268,6 +269,11 @@ def sophie_objective_grad_eps(g: int, i0: int, j0: int, k0: int, ni: int, nj: in
     return out
 
 
+def sophie_objective_set_design(g: int, i0: int = 0, j0: int = 0, k0: int = 0, ni: int = 0, nj: int = 0,
+                                nk: int = 0) -> None:
+    _chk(load().sophie_objective_set_design(g, i0, j0, k0, ni, nj, nk))
+
+
 def sophie_objective_release(g: int) -> None:
     _chk(load().sophie_objective_release(g))
 
@@ -377,6 +383,9 @@ class Grid:
 
     def objective_grad_eps(self, i0, j0, k0, ni, nj, nk):
         return sophie_objective_grad_eps(self.h, i0, j0, k0, ni, nj, nk)
+
+    def objective_set_design(self, i0=0, j0=0, k0=0, ni=0, nj=0, nk=0):
+        sophie_objective_set_design(self.h, i0, j0, k0, ni, nj, nk)
 
     def objective_release(self):
         sophie_objective_release(self.h)

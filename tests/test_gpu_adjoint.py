@@ -31,7 +31,7 @@ def _small_case(seed=41):
     return (nx, ny, nz), eps, sig, src, probe, box
 
 
-def _gpu_grad(n3, eps, sig, src, probe, box, nsteps, K=0, temporal_k=2, fields=None):
+def _gpu_grad(n3, eps, sig, src, probe, box, nsteps, K=0, temporal_k=2, fields=None, traced=False):
     g = so.Grid(*n3, DX, wl.cfl_dt(DX))
     g.configure(temporal_k=temporal_k)
     g.set_materials(eps, sig)
@@ -39,6 +39,8 @@ def _gpu_grad(n3, eps, sig, src, probe, box, nsteps, K=0, temporal_k=2, fields=N
         for c in range(6):
             g.set_field(c, fields[c])
     g.add_source(*src)
+    if traced:
+        g.objective_set_design(*box)
     J = g.objective_forward(nsteps, *probe, K)
     grad = g.objective_grad_eps(*box)
     return g, J, grad
@@ -94,6 +96,40 @@ def test_grad_independent_of_checkpoint_interval_and_step_kernel(sophie):
         else:
             assert J == ref[0]
             np.testing.assert_array_equal(grad, ref[1])
+
+
+def test_traced_record_equals_checkpointed(sophie):
+    """A design box registered before the forward pass: the traces of every
+    step are gathered during it and the reverse sweep recomputes nothing; the
+    gradient is bitwise the checkpointed record's (the same float values are
+    gathered), for an E and an H objective. A traced record keeps no
+    checkpoints, so another box is refused; after clearing the box the next
+    record is checkpointed again and serves any box."""
+    n3, eps, sig, src, probe, box = _small_case(seed=11)
+    N = 90
+    for pc in (2, 3):
+        pr = (pc,) + probe[1:]
+        _, J0, g0 = _gpu_grad(n3, eps, sig, src, pr, box, N, K=30)
+        g1, J1, gr1 = _gpu_grad(n3, eps, sig, src, pr, box, N, K=30, traced=True)
+        assert J0 == J1
+        np.testing.assert_array_equal(gr1, g0)
+        # the forward state is that of plain steps either way
+        g2 = so.Grid(*n3, DX, wl.cfl_dt(DX))
+        g2.set_materials(eps, sig)
+        g2.add_source(*src)
+        g2.step(N)
+        for c in range(6):
+            np.testing.assert_array_equal(g1.get_field(c), g2.get_field(c))
+        other = (box[0] + 1, box[1], box[2], box[3] - 2, box[4], box[5])
+        with pytest.raises(so.SophieError):
+            g1.objective_grad_eps(*other)
+        g1.objective_set_design()  # cleared: the next record is checkpointed again
+        g1.reset()
+        J3 = g1.objective_forward(N, *pr, 30)
+        np.testing.assert_array_equal(g1.objective_grad_eps(*box), g0)
+        assert J3 == J0 and g1.objective_grad_eps(*other).shape == (other[5], other[4], other[3])
+    with pytest.raises(so.SophieError):
+        g1.objective_set_design(0, 0, 0, n3[0] + 1, 1, 1)
 
 
 def test_forward_state_equals_plain_steps_and_probes_unaffected(sophie):
@@ -189,7 +225,7 @@ def test_design_cavity_vs_central_differences(oracle_mod, sophie):
     n3 = (w["nx"], w["ny"], w["nz"])
     eps, sig, src, probe = w["eps"], w["sigma"], w["sources"][0], w["probe"]
     N = 800
-    g, J, grad = _gpu_grad(n3, eps, sig, src, probe, w["design"], N, K=50)
+    g, J, grad = _gpu_grad(n3, eps, sig, src, probe, w["design"], N, K=50, traced=True)
     lo = w["design"][0]
     gc = np.array([grad[k - lo, j - lo, i - lo] for (i, j, k) in w["cells"]])
     Jo, go = _oracle_grad(oracle_mod, n3, eps, sig, src, probe, w["cells"], N)
