@@ -51,8 +51,8 @@ STORAGE_FIELD_BYTES = {"fp32": 48, "fp16": 24, "bf16": 24, "fp16hl": 48, "fp24":
 LAYOUT_BYTES = FIELD_BYTES + LAYOUT_MAT_BYTES
 # DRAM bytes (read + write) per launch from one ncu capture of each kernel on
 # this workload (the kept ncu summaries); None where the kernel changed since.
-NCU_TRAFFIC = {("yee_blocked", 2): 521.599744e6 + 358.377472e6,
-               ("yee_plain", 1): 505.030912e6 + 361.748480e6,
+NCU_TRAFFIC = {("yee_blocked", 2): 522.219520e6 + 358.833664e6,  # 8 warps x 4 rows; 16 x 2: 876.9 MB
+               ("yee_plain", 1): 504.180736e6 + 361.739008e6,
                ("yee_plain_nu", 1): 510.027264e6 + 364.156416e6,  # graded 256^3 cavity
                ("yee_blocked_nu", 2): 512.795648e6 + 356.909824e6}
 # Batching workload: DRAM bytes per cell per launch of the batch-mode plain
