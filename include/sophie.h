@@ -248,7 +248,10 @@ int sophie_configure(sophie_grid *g, int temporal_k, int tile_x, int tile_y, int
  * in [2^-61, 2^60], default 1): component c is stored as field * scale[c], so
  * a scale that brings the fields' working range near 1 keeps them clear of the
  * half format's subnormals and overflow. The current fields are converted.
- * No effect on float storage. Errors: EINVAL.
+ * No effect on float or 24-bit storage. With six equal scales the step kernels
+ * run in unit-scale form (on the scaled values, with no scale multiplications;
+ * the results are those of the scaled arithmetic, which a power-of-two scale
+ * leaves exact outside the float subnormal range). Errors: EINVAL.
  */
 int sophie_set_storage_scale(sophie_grid *g, const float *scale);
 
