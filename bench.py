@@ -398,7 +398,7 @@ def run_ours(args):
     # the other step kernels on the same workload (fewer runs), for comparison
     variants = {"autotuned" if not args.k else f"k{K}": value}
     nv = max(2, min(args.steps, 3))
-    for kk in (1, 2, 3, 4):
+    for kk in (1, 2, 3, 4, 6, 8):
         if kk == K and args.k:
             continue
         vms, _, _, _ = timed(kk, nv, 1, False)

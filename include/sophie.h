@@ -219,7 +219,9 @@ int sophie_sync(sophie_grid *g);
 
 /*
  * temporal_k: steps fused per launch (1 = plain kernel, 2..4 = temporally
- * blocked; 5..8 reserved, ENOTSUP), 0 = autotuned (the default: the first
+ * blocked; 6 and 8 = deeper blocking with float storage only, each 64x32
+ * region then yielding (64-2k)x(32-2k) points; 5, 7 and 6 or 8 with another
+ * precision: ENOTSUP), 0 = autotuned over 1..4 (the default: the first
  * sophie_step measures the candidates, see sophie_autotune). With a fixed k
  * the first sophie_step still measures that k's work splits (and the plain
  * kernel's z chunks) and keeps the fastest; results are the same. tile_x: 0 or 64 = TMA-staged 64x16 tiles

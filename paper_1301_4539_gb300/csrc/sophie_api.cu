@@ -1141,7 +1141,7 @@ int sophie_step(sophie_grid* g, int n) {
   }
   for (int m = 0; m < n;) {
     const int K = g->temporal_k == 0 ? g->tuned_k : g->temporal_k;
-    const bool blocked = !g->use_simple && K >= 2 && n - m >= K && blocked_supported(K);
+    const bool blocked = !g->use_simple && K >= 2 && n - m >= K && blocked_supported(K, g->fmt);
     StepArgs a = make_step_args(g);
     const int adv_steps = blocked ? K : 1;
     // Zero-field skipping: this launch covers only the tiles and planes of the
@@ -1351,8 +1351,10 @@ int sophie_sync(sophie_grid* g) {
 int sophie_configure(sophie_grid* g, int temporal_k, int tile_x, int tile_y, int precision) {
   if (!g) return fail(SOPHIE_EINVAL, "NULL grid");
   if (temporal_k < 0 || temporal_k > 8) return fail(SOPHIE_EINVAL, "temporal_k must be in 0..8");
-  if (temporal_k >= 2 && !blocked_supported(temporal_k))
-    return fail(SOPHIE_ENOTSUP, "temporal_k = %d not built (supported: 1..4)", temporal_k);
+  if (temporal_k >= 2 && precision >= SOPHIE_FP32 && precision <= SOPHIE_FP24 &&
+      !blocked_supported(temporal_k, precision))
+    return fail(SOPHIE_ENOTSUP, "temporal_k = %d not built for precision %d (1..4; 6 and 8 with float storage)",
+                temporal_k, precision);
   if (tile_x < 0 || tile_y < 0) return fail(SOPHIE_EINVAL, "tile sizes must be >= 0");
   if (tile_x != 0 && tile_x != 32 && tile_x != 64) return fail(SOPHIE_EINVAL, "tile_x must be 0, 32 or 64");
   if (precision < SOPHIE_FP32 || precision > SOPHIE_FP24)

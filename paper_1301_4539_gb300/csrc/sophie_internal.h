@@ -216,7 +216,9 @@ BlockedTiling blocked_tiling(const Dims& d, int K, int num_sms, int aligned);
 // The aligned split with exactly zsplit z ranges (clamped to [1, nz]) taken
 // in unit order `order` (BlockedTiling::order).
 BlockedTiling blocked_tiling_split(const Dims& d, int K, int num_sms, int zsplit, int order);
-bool blocked_supported(int K);
+// K = 2..4 for every storage format; K = 6 and 8 (two-stage ring) for float
+// storage only.
+bool blocked_supported(int K, int fmt);
 int blocked_box_x(int fmt);
 int blocked_box_y();
 cudaError_t launch_step_blocked(const StepArgs& a, const CUtensorMap& tmF, const CUtensorMap& tmM,

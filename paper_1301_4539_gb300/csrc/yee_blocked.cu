@@ -100,7 +100,7 @@ BlockedTiling blocked_tiling_box(const Dims& d, int K, int num_sms, const int* b
   return t;
 }
 
-bool blocked_supported(int K) { return K >= 2 && K <= 4; }
+bool blocked_supported(int K, int fmt) { return (K >= 2 && K <= 4) || ((K == 6 || K == 8) && fmt == kF32); }
 
 cudaError_t launch_step_blocked(const StepArgs& a, const CUtensorMap& tmF, const CUtensorMap& tmM,
                                 const BlockedTiling& t, cudaStream_t s) {

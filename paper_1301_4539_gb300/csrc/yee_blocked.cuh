@@ -48,7 +48,10 @@ namespace {
 
 constexpr int kRX = 64;
 constexpr int kRY = 32;  // region rows: R rows per thread, 32 / R warps
-constexpr int kNS = 3;
+// Stages of the TMA ring: 3; 2 for K >= 5, whose per-level seam rows leave no
+// room for a third (the load of plane s+1 then overlaps the K-1 deeper levels
+// of iteration s).
+__host__ __device__ constexpr int ring_stages(int K) { return K >= 5 ? 2 : 3; }
 
 // Thread layout of a CTA with R rows per thread: W warps of 32 lanes (thread 0
 // also issues the TMA loads). R = 4: 8 warps; R = 2: 16 warps with half the
@@ -78,6 +81,7 @@ struct BoxCfg {
 
 template <int K, int F, int R = 4>
 struct Cfg {
+  static constexpr int kNS = ring_stages(K);
   static constexpr int W = Lay<R>::W;
   static constexpr uint32_t kStageBytes = BoxCfg<F>::kStageBytes;
   static constexpr int TX = kRX - 2 * K;
@@ -219,6 +223,7 @@ struct Loader {
       p = first_iter<K>(z0) - 1;
       pend = z1 - 1 + K;
     }
+    constexpr int kNS = ring_stages(K);
     const int s = (int)(issued % kNS);
     const uint32_t bar = bar0 + 8u * s;
     using B = BoxCfg<F>;
@@ -245,6 +250,7 @@ yee_blocked_kernel(const __grid_constant__ CUtensorMap tmF, const __grid_constan
   constexpr int kR = R;
   using St = sophie::St<R>;
   using C = Cfg<K, FMT, R>;
+  constexpr int kNS = C::kNS;
   using B = BoxCfg<FMT>;
   using T = typename B::T;
   // Dynamic shared memory starts the CTA's shared window (no static shared
@@ -682,6 +688,9 @@ cudaError_t launch_fmt(const StepArgs& a, const CUtensorMap& tmF, const CUtensor
     case 2: return launch_k<2, F>(a, tmF, tmM, t, s);
     case 3: return launch_k<3, F>(a, tmF, tmM, t, s);
     case 4: return launch_k<4, F>(a, tmF, tmM, t, s);
+    // the deep forms (a two-stage ring) are built for float storage only
+    case 6: if constexpr (F == kF32) return launch_k<6, F>(a, tmF, tmM, t, s); else return cudaErrorInvalidValue;
+    case 8: if constexpr (F == kF32) return launch_k<8, F>(a, tmF, tmM, t, s); else return cudaErrorInvalidValue;
     default: return cudaErrorInvalidValue;
   }
 }

@@ -22,7 +22,7 @@ SIZES = [(5, 6, 7), (17, 33, 9), (40, 21, 35), (70, 9, 20), (130, 70, 50), (61, 
          (50, 200, 13)]
 
 
-@pytest.mark.parametrize("K", [2, 3, 4])
+@pytest.mark.parametrize("K", [2, 3, 4, 6, 8])
 @pytest.mark.parametrize("n3", SIZES)
 def test_blocked_equals_oracle(oracle_mod, sophie, K, n3):
     nx, ny, nz = n3
@@ -69,7 +69,7 @@ def test_blocked_many_tiles_several_units_per_cta(oracle_mod, sophie, monkeypatc
         np.testing.assert_array_equal(g.read_probe(q), o.probe(q))
 
 
-@pytest.mark.parametrize("K", [2, 3, 4])
+@pytest.mark.parametrize("K", [2, 3, 4, 6, 8])
 def test_blocked_equals_plain_long(sophie, K):
     nx, ny, nz = 100, 90, 80
     eps, sig = wl.sphere_materials(nx, ny, nz, nspheres=12, seed=9, radius=(3, 15))
@@ -94,15 +94,25 @@ def test_blocked_equals_plain_long(sophie, K):
 
 def test_unsupported_k(sophie):
     g = so.Grid(8, 8, 8, DX, wl.cfl_dt(DX))
+    for k in (5, 7):
+        with pytest.raises(so.SophieError) as e:
+            g.configure(temporal_k=k)
+        assert e.value.code == so.ENOTSUP
+    # the deep forms are built for float storage only
+    for prec in (so.FP16, so.BF16, so.FP16HL, so.FP24):
+        with pytest.raises(so.SophieError) as e:
+            g.configure(temporal_k=6, precision=prec)
+        assert e.value.code == so.ENOTSUP
+    g.configure(temporal_k=8)
     with pytest.raises(so.SophieError) as e:
-        g.configure(temporal_k=7)
+        g.configure(temporal_k=8, precision=so.FP24)
     assert e.value.code == so.ENOTSUP
     with pytest.raises(so.SophieError):
         g.configure(temporal_k=9)
 
 
 @pytest.mark.parametrize("zsplit", ["13", "20"])
-@pytest.mark.parametrize("K", [2, 3, 4])
+@pytest.mark.parametrize("K", [2, 3, 4, 6, 8])
 def test_blocked_short_units(oracle_mod, sophie, monkeypatch, K, zsplit):
     """Units of 2 to 3 planes (every tile's 40 planes cut into 13 or 20 z
     ranges): most units start within the first planes or replay 3K - 2 planes,

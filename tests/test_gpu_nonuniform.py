@@ -62,7 +62,7 @@ def _graded_pair(oracle_mod, nx, ny, nz, seed, tile_x=64, lossy=True, fields=Tru
     return g, o, prbs, (wx, wy, wz)
 
 
-@pytest.mark.parametrize("kernel", ["plain", "direct", "k2", "k3", "k4"])
+@pytest.mark.parametrize("kernel", ["plain", "direct", "k2", "k3", "k4", "k6", "k8"])
 @pytest.mark.parametrize("n3,steps", [((70, 37, 19), 23), ((130, 21, 40), 11), ((64, 16, 8), 7), ((3, 90, 5), 9)])
 def test_graded_mesh_equals_oracle(oracle_mod, sophie, kernel, n3, steps):
     tile_x = 32 if kernel == "direct" else 64

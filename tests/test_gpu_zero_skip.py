@@ -14,7 +14,7 @@ from paper_1301_4539_gb300 import workloads as wl
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("K", [0, 1, 2, 3])
+@pytest.mark.parametrize("K", [0, 1, 2, 3, 8])
 def test_skip_matches_oracle_while_the_box_grows(oracle_mod, sophie, K):
     """K = 0: autotuned, so the first step runs the tuner's trial launches
     (which write the spare buffer everywhere) with skipping already on."""
