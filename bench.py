@@ -49,15 +49,36 @@ ALG_BYTES = FIELD_BYTES + MAT_BYTES
 # Field bytes per cell-update (six values read and written) of each storage form.
 STORAGE_FIELD_BYTES = {"fp32": 48, "fp16": 24, "bf16": 24, "fp16hl": 48, "fp24": 36}
 LAYOUT_BYTES = FIELD_BYTES + LAYOUT_MAT_BYTES
-# DRAM bytes (read + write) per launch from one ncu capture of each kernel on
-# this workload (the kept ncu summaries); None where the kernel changed since.
-NCU_TRAFFIC = {("yee_blocked", 2): 522.219520e6 + 358.833664e6,  # 8 warps x 4 rows; 16 x 2: 876.9 MB
-               ("yee_plain", 1): 504.180736e6 + 361.739008e6,
-               ("yee_plain_nu", 1): 510.027264e6 + 364.156416e6,  # graded 256^3 cavity
-               ("yee_blocked_nu", 2): 512.795648e6 + 356.909824e6}
+# DRAM bytes (read + write) per launch from ncu captures of each kernel on
+# this workload (the kept ncu summaries), each with the launch configuration
+# it was captured in (Grid.launch_config keys). A blocked launch's traffic
+# depends on its work split (how many halo planes are re-read, and whether
+# neighbouring tiles stream the same planes from L2 at the same time), so a
+# figure is reported only for a run in the captured configuration.
+NCU_TRAFFIC = {
+    ("yee_blocked", 2): [({"blocked_ctas": 150, "blocked_rows": 4}, 522.219520e6 + 358.833664e6),
+                         ({"blocked_ctas": 150, "blocked_rows": 2}, 876.9e6)],
+    ("yee_plain", 1): [({"plain_ctas": 256}, 504.180736e6 + 361.739008e6)],
+    # graded 256^3 cavity
+    ("yee_plain_nu", 1): [({"plain_ctas": 256}, 509.154304e6 + 363.904512e6)],
+    ("yee_blocked_nu", 2): [({"blocked_ctas": 150, "blocked_rows": 4}, 512.795648e6 + 356.909824e6),
+                            ({"blocked_ctas": 152, "blocked_rows": 4}, 723.845376e6 + 370.375680e6)],
+}
+
+
+def ncu_traffic(kernel: str, k: int, cfg: dict):
+    """(DRAM bytes per launch, the captured configurations): the bytes of the
+    capture whose configuration the run shares, else None."""
+    entries = NCU_TRAFFIC.get((kernel, k), [])
+    for want, v in entries:
+        if all(cfg.get(key) == val for key, val in want.items()):
+            return v, [c for c, _ in entries]
+    return None, [c for c, _ in entries]
+
+
 # Batching workload: DRAM bytes per cell per launch of the batch-mode plain
-# kernel (3.712641 GB for the 54436430 cells of a 300-cavity instance).
-BATCH_TRAFFIC_PER_CELL = (2.365019e9 + 1.347622e9) / 54436430
+# kernel (3.697188 GB for the 54436430 cells of a 300-cavity instance).
+BATCH_TRAFFIC_PER_CELL = (2.349405e9 + 1.347783e9) / 54436430
 
 
 def parse():
@@ -384,9 +405,11 @@ def run_ours(args):
     layout_bytes = STORAGE_FIELD_BYTES[args.precision] + LAYOUT_MAT_BYTES
     achieved_layout = cells * layout_bytes / (avg_ms / 1e3) / 1e9
     kname = {0: "yee_plain", 1: "yee_blocked", 2: "energy"}[kid]
+    launch_cfg = g.launch_config()
+    traffic, traffic_cfgs = ncu_traffic(kname, K if kid == so.KERNEL_BLOCKED else 1, launch_cfg)
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": NCU_TRAFFIC.get((kname, K if kid == so.KERNEL_BLOCKED else 1)) if args.precision == "fp32"
-            else None, "kernel": kname,
+            "traffic": traffic if args.precision == "fp32" else None, "launch_config": launch_cfg,
+            "traffic_captured_configs": traffic_cfgs, "kernel": kname,
             "steps_per_launch": K if kid == so.KERNEL_BLOCKED else 1, "avg_launch_ms": avg_ms,
             "peak_source": peak_kind, "algorithmic_bytes_per_launch": bytes_per_launch,
             "algorithmic_bytes_per_cell": alg_bytes,
@@ -398,11 +421,14 @@ def run_ours(args):
     # the other step kernels on the same workload (fewer runs), for comparison
     variants = {"autotuned" if not args.k else f"k{K}": value}
     nv = max(2, min(args.steps, 3))
+    cfg_k1 = launch_cfg if args.k == 1 else {}
     for kk in (1, 2, 3, 4, 6, 8):
         if kk == K and args.k:
             continue
         vms, _, _, _ = timed(kk, nv, 1, False)
         variants[f"k{kk}"] = cells * args.tsteps * nv * world / (vms / 1e3) / 1e9
+        if kk == 1:
+            cfg_k1 = g.launch_config()
     # storage-precision forms (float arithmetic; 2-, 3- or 4-byte values in HBM)
     for pname, prec in (("fp16", so.FP16), ("bf16", so.BF16), ("fp16hl", so.FP16HL), ("fp24", so.FP24)):
         g.configure(temporal_k=1, precision=prec)
@@ -441,7 +467,8 @@ def run_ours(args):
                   "frac_49B": variants["k1"] * ALG_BYTES / peaks()[0],
                   "frac_52B_layout": variants["k1"] * LAYOUT_BYTES / peaks()[0],
                   "frac_48B_fields_only": variants["k1"] * FIELD_BYTES / peaks()[0],
-                  "traffic": NCU_TRAFFIC.get(("yee_plain", 1)), "peak": peaks()[0], "unit": "GB/s"}
+                  "traffic": ncu_traffic("yee_plain", 1, cfg_k1)[0], "launch_config": cfg_k1,
+                  "peak": peaks()[0], "unit": "GB/s"}
     g_prec[0] = so.FP32
     g.configure(temporal_k=0 if not args.k else K, precision=so.FP32)
     if not args.k:
@@ -578,7 +605,7 @@ def run_adjoint(stream, reps: int = 3):
             "unit_cell_steps": "G (forward + adjoint step) cell-updates/s",
             "adjoint_kernel": {"bound": "hbm", "avg_launch_ms": avg, "achieved": achieved, "peak": peak,
                                "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_kind,
-                               "launches": la // reps},
+                               "launches": la},  # of the last repetition (profile() clears the totals)
             "forward_kernel_avg_launch_ms": pms / max(lp, 1), "reps": reps,
             "forward_temporal_k": k_tuned}
 
@@ -671,12 +698,14 @@ def run_graded(stream, uniform_k1: float, n: int = 256, tsteps: int = 1000, reps
         kl, kms = prof[kid]
         name = "yee_blocked (non-uniform)" if kid == so.KERNEL_BLOCKED else "yee_plain (non-uniform)"
         achieved = n ** 3 * ALG_BYTES / (kms / max(kl, 1) / 1e3) / 1e9
-        traffic = (NCU_TRAFFIC.get(("yee_plain_nu", 1)) if kid == so.KERNEL_PLAIN
-                   else NCU_TRAFFIC.get(("yee_blocked_nu", kk)))
+        cfg = g.launch_config()
+        traffic, cfgs = ncu_traffic("yee_plain_nu" if kid == so.KERNEL_PLAIN else "yee_blocked_nu",
+                                    1 if kid == so.KERNEL_PLAIN else kk, cfg)
         return kk, n ** 3 * tsteps * reps / (ms / 1e3) / 1e9, energy, {
             "kernel": name, "steps_per_launch": kk if kid == so.KERNEL_BLOCKED else 1, "bound": "hbm",
             "achieved": achieved, "peak": peaks()[0], "unit": "GB/s", "frac": achieved / peaks()[0],
-            "traffic": traffic, "avg_launch_ms": kms / max(kl, 1), "launches": kl}
+            "traffic": traffic, "launch_config": cfg, "traffic_captured_configs": cfgs,
+            "avg_launch_ms": kms / max(kl, 1), "launches": kl}
 
     kk, rate, energy, roof = one(k)
     k1, rate1, _, roof1 = one(1) if kk != 1 else (kk, rate, energy, roof)

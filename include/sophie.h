@@ -273,6 +273,18 @@ int sophie_set_storage_scale(sophie_grid *g, const float *scale);
 int sophie_autotune(sophie_grid *g, int *temporal_k, double *ms_per_step);
 
 /*
+ * The launch configuration the next sophie_step uses, in out[0..6]: steps per
+ * launch (the fixed or tuned k; 1 = plain kernel), the plain kernel's z planes
+ * per work unit and its CTAs, then the blocked kernel's CTAs, z ranges per tile
+ * (0 = equal contiguous work ranges), unit order (0 tile-major, 1 range-major)
+ * and rows of the region per thread (4: 8 warps, 2: 16 warps); the four
+ * blocked entries are 0 when k = 1. Before the first step of a grid that is not
+ * tuned yet these are the cost model's choices, which the first step's
+ * measurements may replace. No synchronisation. Errors: EINVAL.
+ */
+int sophie_launch_config(sophie_grid *g, int *out);
+
+/*
  * Zero-field skipping (early-time sparsity; the paper skips sub-domains whose
  * fields are all zero on their boundary, Sec. 4). With enable != 0 the step
  * kernels skip the work units whose outputs lie outside a box known to hold

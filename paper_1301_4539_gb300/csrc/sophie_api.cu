@@ -1471,6 +1471,21 @@ int sophie_autotune(sophie_grid* g, int* temporal_k, double* ms_per_step) {
   return SOPHIE_OK;
 }
 
+int sophie_launch_config(sophie_grid* g, int* out) {
+  if (!g || !out) return fail(SOPHIE_EINVAL, "NULL argument");
+  const int k = g->use_simple ? 1 : g->temporal_k ? g->temporal_k : g->tuned ? g->tuned_k : 1;
+  out[0] = k;
+  out[1] = g->ptile.zchunk;
+  out[2] = g->ptile.grid;
+  BlockedTiling bt{};
+  if (k >= 2) bt = g->btile.K == k ? g->btile : blocked_tiling(g->d, k, g->num_sms, 1);
+  out[3] = k >= 2 ? bt.grid : 0;
+  out[4] = k >= 2 ? bt.zsplit : 0;
+  out[5] = k >= 2 ? bt.order : 0;
+  out[6] = k >= 2 ? (bt.rows == 2 ? 2 : 4) : 0;
+  return SOPHIE_OK;
+}
+
 int sophie_launch_count(sophie_grid* g, long long* launches) {
   if (!g || !launches) return fail(SOPHIE_EINVAL, "NULL argument");
   *launches = g->launches;

@@ -51,6 +51,7 @@ SIGNATURES = {
     "sophie_set_zero_skip": (_I, [_P, _I]),
     "sophie_set_spacing": (_I, [_P, _P, _P, _P]),
     "sophie_launch_count": (_I, [_P, ctypes.POINTER(_LL)]),
+    "sophie_launch_config": (_I, [_P, ctypes.POINTER(_I)]),
     "sophie_profile": (_I, [_P, _I]),
     "sophie_profile_read": (_I, [_P, _I, ctypes.POINTER(_LL), ctypes.POINTER(_D)]),
     "sophie_objective_forward": (_I, [_P, _I, _I, _I, _I, _I, _I, ctypes.POINTER(_D)]),
@@ -238,6 +239,15 @@ def sophie_set_spacing(g: int, wx, wy, wz) -> None:
     _chk(load().sophie_set_spacing(g, *ptrs))
 
 
+def sophie_launch_config(g: int) -> dict:
+    """The launch configuration of the next step (see include/sophie.h)."""
+    out = (_I * 7)()
+    _chk(load().sophie_launch_config(g, out))
+    v = list(out)
+    return {"k": v[0], "plain_zchunk": v[1], "plain_ctas": v[2], "blocked_ctas": v[3],
+            "blocked_zsplit": v[4], "blocked_order": v[5], "blocked_rows": v[6]}
+
+
 def sophie_launch_count(g: int) -> int:
     n = _LL()
     _chk(load().sophie_launch_count(g, ctypes.byref(n)))
@@ -365,6 +375,9 @@ class Grid:
 
     def launch_count(self):
         return sophie_launch_count(self.h)
+
+    def launch_config(self):
+        return sophie_launch_config(self.h)
 
     def profile(self, enable):
         sophie_profile(self.h, enable)

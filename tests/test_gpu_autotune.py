@@ -48,3 +48,26 @@ def test_autotune_half_storage_keeps_k2(sophie):
     g.configure(temporal_k=0, precision=so.FP16)
     k, ms = g.autotune()
     assert k == 2 and ms > 0
+
+
+@pytest.mark.parametrize("tk", [0, 1, 2, 3])
+def test_launch_config_reports_the_tuned_choice(sophie, tk):
+    """sophie_launch_config: the k in use and a valid split for it, before the
+    first step (the cost model's) and after it (the measured choice)."""
+    g = so.Grid(96, 80, 72, DX, wl.cfl_dt(DX))
+    g.configure(temporal_k=tk)
+    for when in ("model", "tuned"):
+        cfg = g.launch_config()
+        assert cfg["plain_zchunk"] >= 1 and cfg["plain_ctas"] >= 1
+        if tk:
+            assert cfg["k"] == tk
+        if cfg["k"] >= 2:
+            assert cfg["blocked_ctas"] >= 1 and cfg["blocked_rows"] in (2, 4)
+            assert cfg["blocked_zsplit"] >= 0 and cfg["blocked_order"] in (0, 1)
+        else:
+            assert cfg["blocked_ctas"] == cfg["blocked_zsplit"] == cfg["blocked_rows"] == 0
+        if when == "model":
+            g.step(max(tk, 1))
+    if tk == 0:
+        k, _ = g.autotune()
+        assert g.launch_config()["k"] == k
