@@ -389,6 +389,7 @@ int sophie_objective_grad_eps(sophie_grid* g, int i0, int j0, int k0, int ni, in
         a.n0 = n;
         a.prb.n = 0;
         a.src.n = 0;
+        a.src.nbig = 0;  // (the many-source table too: the reverse steps take no source)
         cudaEvent_t ea = g->prof ? prof_event(g) : nullptr, eb = g->prof ? prof_event(g) : nullptr;
         if (ea) cudaEventRecord(ea, g->stream);
         e = direct ? launch_adj_step(a, g->stream) : launch_step_plain(a, t.tmL[lc], t.tmRM, g->ptile, g->stream);
