@@ -6,6 +6,9 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <stdlib.h>
+
+#include <utility>
 #include <vector>
 
 namespace sophie {
@@ -124,6 +127,36 @@ struct StepArgs {
   // load); entries outside an array's range are 0.
   const float2* rpair[3];
 };
+
+// Launch a step kernel with programmatic dependent launch allowed, so that its
+// CTAs can start as the previous kernel's retire (the kernels wait with
+// griddepcontrol.wait before touching global memory). Launches recorded into
+// a CUDA graph (batches) keep plain edges, which replayed ~1 % faster there;
+// SOPHIE_PDL=0 launches every step kernel plainly.
+inline bool pdl_enabled() {
+  static const bool on = [] {
+    const char* v = getenv("SOPHIE_PDL");
+    return !(v && atoi(v) == 0);
+  }();
+  return on;
+}
+template <typename... P, typename... A>
+cudaError_t launch_step_kernel(void (*kernel)(P...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                               A&&... args) {
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cs) != cudaSuccess) return cudaGetLastError();
+  cfg.numAttrs = pdl_enabled() && cs == cudaStreamCaptureStatusNone ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, kernel, std::forward<A>(args)...);
+}
 
 constexpr int kRatioPad = 8;    // pairs before index 0
 constexpr int kRatioTail = 72;  // pairs from index n on (a 64-wide tile plus halo beyond the last cell)

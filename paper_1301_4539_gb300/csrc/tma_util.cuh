@@ -113,4 +113,15 @@ __device__ __forceinline__ void named_bar(int id, int nthreads) {
   asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
 }
 
+// Programmatic dependent launch (launch_step_kernel): wait until the previous
+// kernel of the stream has completed and its writes are visible (no wait for
+// a launch without the attribute); then let the stream's next such launch
+// place its CTAs on the SMs as this grid's CTAs retire, so that its launch
+// and shared-memory set-up overlap this grid's tail. A step kernel reads no
+// global memory a kernel writes before pdl_wait().
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_launch_dependents() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 }  // namespace sophie

@@ -281,6 +281,8 @@ yee_blocked_kernel(const __grid_constant__ CUtensorMap tmF, const __grid_constan
     fence_mbar_init();
   }
   __syncthreads();
+  pdl_wait();  // (the class table above comes from a host copy, not a kernel)
+  pdl_launch_dependents();
   const Dims d = a.d;
   Loader<K, FMT> ld;
   ld.st = reinterpret_cast<LoaderState*>(base + C::kLdOff);
@@ -662,8 +664,8 @@ cudaError_t launch_knr(const StepArgs& a, const CUtensorMap& tmF, const CUtensor
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  yee_blocked_kernel<K, F, NU, R><<<t.grid, Lay<R>::kThreads, Cfg<K, F, R>::kSmem, s>>>(tmF, tmM, a, t);
-  return cudaGetLastError();
+  return launch_step_kernel(yee_blocked_kernel<K, F, NU, R>, dim3(t.grid), dim3(Lay<R>::kThreads), Cfg<K, F, R>::kSmem,
+                            s, tmF, tmM, a, t);
 }
 
 template <int K, int F, bool NU>

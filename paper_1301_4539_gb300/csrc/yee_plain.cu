@@ -126,6 +126,8 @@ yee_plain_kernel(const __grid_constant__ CUtensorMap tmF, const __grid_constant_
     fence_mbar_init();
   }
   __syncthreads();
+  pdl_wait();  // (the class table above comes from a host copy, not a kernel)
+  pdl_launch_dependents();
   const long long nunits = BATCH ? (long long)pb.nitems : t.units;
   // Unit u: its tile and z range, and (batches) its cavity's descriptor.
   auto unit_at = [&](long long u, const CavityDesc*& cd) -> Unit {
@@ -574,8 +576,8 @@ cudaError_t launch_plain_fn(const StepArgs& a, const CUtensorMap& tmF, const CUt
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  yee_plain_kernel<F, false, NU><<<t.grid, kThreads, PCfg<F>::kSmemBytes, s>>>(tmF, tmM, a, t, PlainBatch{});
-  return cudaGetLastError();
+  return launch_step_kernel(yee_plain_kernel<F, false, NU>, dim3(t.grid), dim3(kThreads), PCfg<F>::kSmemBytes, s, tmF,
+                            tmM, a, t, PlainBatch{});
 }
 
 template <int F>
@@ -617,8 +619,8 @@ cudaError_t launch_step_plain_batch(const StepArgs& a, const PlainBatch& pb, int
   }
   CUtensorMap none{};
   PlainTiling t{};
-  yee_plain_kernel<kF32, true, false><<<grid, kThreads, PCfg<kF32>::kSmemBytes, s>>>(none, none, a, t, pb);
-  return cudaGetLastError();
+  return launch_step_kernel(yee_plain_kernel<kF32, true, false>, dim3(grid), dim3(kThreads), PCfg<kF32>::kSmemBytes, s,
+                            none, none, a, t, pb);
 }
 
 cudaError_t launch_step_plain(const StepArgs& a, const CUtensorMap& tmF, const CUtensorMap& tmM,
