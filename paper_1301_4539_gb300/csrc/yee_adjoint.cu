@@ -15,6 +15,7 @@
 // Cb*le in the H half and coefficients (Ca, -S) in the E half; PEC edges
 // (Ca = Cb = 0) keep le = 0.
 #include "sophie_internal.h"
+#include "tma_util.cuh"
 #include "yee_update.cuh"
 
 namespace sophie {
@@ -105,6 +106,8 @@ __global__ void __launch_bounds__((kTX + 1) * (kTY + 1)) adj_step_kernel(const _
 // edge, e^n (before) and the step's E bracket B(h^{n+1/2}) + s (after).
 __global__ void gather_kernel(const __grid_constant__ StepArgs a, const int* edge_comp, const long long* edge_pt,
                               int nedge, float* e_out, float* c_out) {
+  pdl_wait();  // launched like the step kernels, between them
+  pdl_launch_dependents();
   const Dims d = a.d;
   const float* fo = static_cast<const float*>(a.fin);
   const float* fn = static_cast<const float*>(a.fout);
@@ -151,6 +154,8 @@ __global__ void grad_accum_kernel(const float* l, Dims d, const int* edge_comp, 
 __global__ void objective_grad_accum_kernel(float* l, Dims d, int comp, long long opt, const float* sample,
                                             double two_dt, int t_obj, const int* edge_comp, const long long* edge_pt,
                                             int nedge, const float* e_in, const float* c_in, double* gcb, double* gca) {
+  pdl_wait();  // launched like the step kernels, between them
+  pdl_launch_dependents();
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t > nedge) return;
   const long long sz = (long long)d.ny1 * d.nxp;
@@ -183,8 +188,8 @@ cudaError_t launch_adj_step(const StepArgs& a, cudaStream_t s) {
 cudaError_t launch_gather(const StepArgs& a, const int* edge_comp, const long long* edge_pt, int nedge, float* e_out,
                           float* c_out, cudaStream_t s) {
   if (nedge <= 0) return cudaSuccess;
-  gather_kernel<<<(nedge + 255) / 256, 256, 0, s>>>(a, edge_comp, edge_pt, nedge, e_out, c_out);
-  return cudaGetLastError();
+  return launch_step_kernel(gather_kernel, dim3((nedge + 255) / 256), dim3(256), 0, s, a, edge_comp, edge_pt, nedge,
+                            e_out, c_out);
 }
 
 cudaError_t launch_grad_accum(const float* l, const Dims& d, const int* edge_comp, const long long* edge_pt, int nedge,
@@ -198,9 +203,8 @@ cudaError_t launch_objective_grad_accum(float* l, const Dims& d, int comp, long 
                                         double two_dt, int t_obj, const int* edge_comp, const long long* edge_pt,
                                         int nedge, const float* e_in, const float* c_in, double* gcb, double* gca,
                                         cudaStream_t s) {
-  objective_grad_accum_kernel<<<(nedge + 1 + 255) / 256, 256, 0, s>>>(l, d, comp, pt, sample, two_dt, t_obj, edge_comp,
-                                                                      edge_pt, nedge, e_in, c_in, gcb, gca);
-  return cudaGetLastError();
+  return launch_step_kernel(objective_grad_accum_kernel, dim3((nedge + 1 + 255) / 256), dim3(256), 0, s, l, d, comp,
+                            pt, sample, two_dt, t_obj, edge_comp, edge_pt, nedge, e_in, c_in, gcb, gca);
 }
 
 cudaError_t launch_add_objective(float* l, const Dims& d, int comp, long long pt, const float* sample, double two_dt,
