@@ -317,7 +317,8 @@ int sophie_set_zero_skip(sophie_grid *g, int enable);
  * sophie_energy weights each term by its edge or face volume in units of
  * dx^3, so the lossless energy stays conserved.
  * Every step kernel (plain with either tile choice, temporally blocked k =
- * 2..4; every storage format) and zero-field skipping apply as on the
+ * 2..4 with every storage format, 6 and 8 with float storage) and
+ * zero-field skipping apply as on the
  * uniform mesh, with the same results across k for float storage.
  * Stability needs c dt sqrt(1/min(wx)^2 + 1/min(wy)^2 + 1/min(wz)^2) <= 1.
  * A probe objective record (sophie_objective_forward) is invalidated; probe
