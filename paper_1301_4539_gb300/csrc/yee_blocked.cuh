@@ -96,7 +96,8 @@ struct Cfg {
   static constexpr uint32_t kCoefOff = kEpOff + kEpBytes;
   static constexpr uint32_t kBarOff = kCoefOff + kMaxClasses * 8;
   static constexpr uint32_t kLdOff = kBarOff + kNS * 8;
-  static constexpr uint32_t kSmem = kLdOff + 64;
+  static constexpr uint32_t kPrbOff = kLdOff + 64;  // the probe table (PrbShared)
+  static constexpr uint32_t kSmem = kPrbOff + sizeof(PrbShared);
   static_assert(kSmem <= 227 * 1024, "shared memory per CTA");
 };
 
@@ -275,6 +276,7 @@ yee_blocked_kernel(const __grid_constant__ CUtensorMap tmF, const __grid_constan
   float2* scoef = reinterpret_cast<float2*>(base + C::kCoefOff);
   const unsigned char* scoefb = base + C::kCoefOff;
   for (int c = threadIdx.x; c < kMaxClasses; c += kThreads) scoef[c] = a.coef[c];
+  load_probes(reinterpret_cast<PrbShared*>(base + C::kPrbOff), a.prb, threadIdx.x, kThreads);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
     for (int s = 0; s < kNS; ++s) mbar_init(full(s), 1);
@@ -596,7 +598,8 @@ yee_blocked_kernel(const __grid_constant__ CUtensorMap tmF, const __grid_constan
               if ((m & kPrbFlag) && p >= z0 && p < z1 && y >= yo0 && y < yo1 && y < d.ny &&
                   x + cc >= xo0 && x + cc < xo1 && x + cc < d.nx)
                 record_probes(((long long)p * d.ny1 + y) * d.nxp + x + cc, nstep, out.ex[r][cc], out.ey[r][cc],
-                              out.ez[r][cc], hx[r][cc], hy[r][cc], hz[r][cc], &a.prb);
+                              out.ez[r][cc], hx[r][cc], hy[r][cc], hz[r][cc],
+                              reinterpret_cast<const PrbShared*>(base + C::kPrbOff));
             }
           }
         }

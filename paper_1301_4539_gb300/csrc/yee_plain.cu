@@ -63,7 +63,8 @@ struct PCfg {
   // class table (Ca, Cb) of a single grid, indexed by the material word's
   // pre-scaled byte offsets (batches read their cavities' tables from L1)
   static constexpr uint32_t kCoefOff = (kBarOff + 2 * kNS * 8 + 15) / 16 * 16;
-  static constexpr uint32_t kSmemBytes = kCoefOff + kMaxClasses * 8 + 128;
+  static constexpr uint32_t kPrbOff = kCoefOff + kMaxClasses * 8;  // the probe table (PrbShared)
+  static constexpr uint32_t kSmemBytes = kPrbOff + sizeof(PrbShared) + 128;
 };
 
 struct Unit {
@@ -116,6 +117,7 @@ yee_plain_kernel(const __grid_constant__ CUtensorMap tmF, const __grid_constant_
   if constexpr (!BATCH)
     for (int c = threadIdx.x; c < kMaxClasses; c += kThreads)
       reinterpret_cast<float2*>(base + C::kCoefOff)[c] = a.coef[c];
+  load_probes(reinterpret_cast<PrbShared*>(base + C::kPrbOff), a.prb, threadIdx.x, kThreads);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
@@ -457,7 +459,7 @@ yee_plain_kernel(const __grid_constant__ CUtensorMap tmF, const __grid_constant_
           eo[2][cc] = e_upd(ez[r][cc], k2, bz);
           if ((m & kPrbFlag) && out_plane && y < d.ny() && x + cc < d.nx())
             record_probes(((long long)z * d.ny1() + y) * d.nxp() + x + cc, a.n0, eo[0][cc], eo[1][cc], eo[2][cc],
-                          hx[r][cc], hy[r][cc], hz[r][cc], &a.prb);
+                          hx[r][cc], hy[r][cc], hz[r][cc], reinterpret_cast<const PrbShared*>(base + C::kPrbOff));
         }
         if (out_plane && y < d.ny() && x < d.nx()) {
           T* o = fout() + (long long)z * d.zstride() + (long long)y * d.nxp() + x;
