@@ -78,3 +78,43 @@ def test_full_size_sphere_cavity_1000_steps(oracle_mod, sophie):
         assert abs(W - Wo) <= 1e-12 * abs(Wo)
         assert W > 0
         g.close()
+
+
+def test_launches_with_and_without_programmatic_dependent_launch(tmp_path):
+    """The step kernels wait for the previous kernel before any global access
+    (programmatic dependent launch); SOPHIE_PDL=0 launches them plainly. A
+    mixed sequence (plain and blocked steps, a precision change, probes, the
+    energy) gives bitwise the same fields either way; each run is a fresh
+    process, since the switch is read once."""
+    import subprocess
+    import sys
+
+    code = r"""
+import sys, numpy as np
+from paper_1301_4539_gb300 import sophie as so, workloads as wl
+nx, ny, nz = 150, 70, 60
+eps, sig = wl.random_materials(nx, ny, nz, seed=5, nmat=6, sigma=(0.0, 0.3))
+g = so.Grid(nx, ny, nz, 1e-3, wl.cfl_dt(1e-3))
+g.set_materials(eps, sig)
+amp, f0, bw, t0, kind = wl.gaussian_sine_source()
+g.add_source(2, 75, 35, 30, 20.0, f0, bw, 3e-12, 0)
+pid = g.add_probe(2, 80, 30, 31)
+for k, n in ((1, 7), (2, 12), (3, 7), (0, 9)):
+    g.configure(temporal_k=k)
+    g.step(n)
+g.configure(temporal_k=2, precision=so.FP24)
+g.step(10)
+W = g.energy()
+np.savez(sys.argv[1], *[g.get_field(c) for c in range(6)], probe=g.read_probe(pid), W=np.array([W]))
+"""
+    outs = []
+    for v in ("1", "0"):
+        path = tmp_path / f"pdl{v}.npz"
+        env = dict(__import__("os").environ, SOPHIE_PDL=v)
+        root = __import__("os").path.dirname(__import__("os").path.dirname(__import__("os").path.abspath(__file__)))
+        r = subprocess.run([sys.executable, "-c", code, str(path)], env=env, capture_output=True, text=True,
+                           timeout=600, cwd=root)
+        assert r.returncode == 0, r.stderr[-2000:]
+        outs.append(np.load(path))
+    for key in outs[0].files:
+        np.testing.assert_array_equal(outs[0][key], outs[1][key])
