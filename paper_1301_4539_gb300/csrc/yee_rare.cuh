@@ -70,8 +70,8 @@ __device__ __forceinline__ void load_probes(PrbShared* s, const PrbTable& prb, i
 }
 
 // Sec. 3.4 pin-point outputs: sample nstep of every probe on index point pt.
-static __device__ __noinline__ void record_probes(long long pt, long long nstep, float ex, float ey, float ez,
-                                                  float hx, float hy, float hz, const PrbShared* s) {
+__device__ __forceinline__ void record_probes_inline(long long pt, long long nstep, float ex, float ey, float ez,
+                                                     float hx, float hy, float hz, const PrbShared* s) {
   for (int q = 0; q < s->n; ++q) {
     if (s->pos[q] != pt) continue;
     const int c = s->comp[q];
@@ -79,6 +79,12 @@ static __device__ __noinline__ void record_probes(long long pt, long long nstep,
     if (s->pmul_on) v = __fmul_rn(v, s->pmul);
     s->buf[(long long)q * s->cap + nstep] = v;
   }
+}
+// The same out of line (a call the kernels make only at flagged points),
+// which keeps most kernels' register allocation of the hot loop unchanged.
+static __device__ __noinline__ void record_probes(long long pt, long long nstep, float ex, float ey, float ez,
+                                                  float hx, float hy, float hz, const PrbShared* s) {
+  record_probes_inline(pt, nstep, ex, ey, ez, hx, hy, hz, s);
 }
 
 }  // namespace sophie
