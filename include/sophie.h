@@ -274,7 +274,8 @@ int sophie_autotune(sophie_grid *g, int *temporal_k, double *ms_per_step);
 
 /*
  * The launch configuration the next sophie_step uses, in out[0..6]: steps per
- * launch (the fixed or tuned k; 1 = plain kernel), the plain kernel's z planes
+ * launch (the fixed or tuned k; 1 = plain kernel, also for an autotuned grid
+ * that has not measured yet), the plain kernel's z planes
  * per work unit and its CTAs, then the blocked kernel's CTAs, z ranges per tile
  * (0 = equal contiguous work ranges), unit order (0 tile-major, 1 range-major)
  * and rows of the region per thread (4: 8 warps, 2: 16 warps); the four
